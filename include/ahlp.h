@@ -1,0 +1,266 @@
+/*
+ * ahlp.h -- C ABI of a GB300 (sm_103a) library that solves arrowhead linear
+ * programs with local linking structure by a primal-dual interior-point
+ * method whose per-iteration KKT systems are factored and solved through a
+ * block Schur-complement decomposition on one GPU.
+ *
+ * Problem (Sec. 3.2, eq. fig:blockstructure, equality rows and x >= 0; local
+ * and global linking rows as in Sec. 3.3):
+ *
+ *     min  c_0'x_0 + sum_i c_i'x_i
+ *     s.t. W_i x_0 + A_i x_i                     = b_i       i = 1..N
+ *          F0_j x_0 + FL_j x_j + FR_j x_{j+1}    = blink_j   j = 1..N-1
+ *          Fg0 x_0 + sum_i Fg_i x_i              = bg
+ *          x >= 0
+ *
+ * (The paper calls the block matrices B_i and the linking-variable blocks
+ * A_i; here they are A_i and W_i.)
+ *
+ * Global vector orderings used by every entry point:
+ *     x, z, dx, dz, r_d, r_c : [x_1 .. x_N, x_0]                    length n_total
+ *     y, dy, r_p             : [y_1 .. y_N, y_link(pair 1..N-1), y_g] length m_total
+ *
+ * Pointers.  Every vector argument may be a host pointer or a device
+ * pointer of the current CUDA device; the library tells them apart with
+ * cudaPointerGetAttributes.  Host vectors are staged through the library's
+ * own device buffers (the call then synchronises its stream before
+ * returning); device vectors are used in place on the problem's stream.
+ * Matrix data in ahlp_desc are host pointers and are copied at create: the
+ * caller keeps ownership of everything it passes in.
+ *
+ * Errors.  Every call returns an int status (AHLP_OK = 0 or a negative
+ * code below).  Nothing aborts, prints or traps; the text of the last error
+ * is available from ahlp_last_error().  A handle is not thread-safe.
+ */
+#ifndef AHLP_H
+#define AHLP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define AHLP_OK                   0
+#define AHLP_ERR_INVALID_ARG     -1  /* NaN/Inf, negative size, bad index, NULL where required */
+#define AHLP_ERR_DIM_MISMATCH    -2  /* block sizes disagree with each other                 */
+#define AHLP_ERR_UNSUPPORTED     -3  /* finite upper bounds, lower bounds != 0, batch > 1 ... */
+#define AHLP_ERR_NOT_SPD         -4  /* a pivot became NaN / negative beyond repair            */
+#define AHLP_ERR_REFINE_FAIL     -5  /* refinement did not reach refine_tol                    */
+#define AHLP_ERR_MAX_ITER        -6  /* ipm_solve hit max_iter                                 */
+#define AHLP_ERR_INFEASIBLE      -7  /* iterates diverge (primal or dual infeasible LP)        */
+#define AHLP_ERR_CUDA            -8  /* a CUDA runtime call failed                             */
+#define AHLP_ERR_OOM             -9  /* device allocation failed                               */
+#define AHLP_ERR_TIMEOUT        -10  /* a bounded device wait ran out                          */
+
+#define AHLP_PREC_FP64   0   /* every stage in FP64                                    */
+#define AHLP_PREC_MIXED  1   /* FP32 block factors, FP64 Schur factor and refinement   */
+
+/* ---- problem description (host memory, copied at create) --------------- */
+
+/* Compressed sparse column matrix, 0-based.  colptr has n+1 entries,
+ * rowidx/val have colptr[n] entries; rows within a column may be in any
+ * order, duplicates are summed.  m or n may be 0 (then all pointers may be
+ * NULL). */
+typedef struct {
+  int32_t m, n;
+  const int32_t *colptr;
+  const int32_t *rowidx;
+  const double *val;
+} ahlp_csc;
+
+/* The arrowhead LP (Sec. 3.2/3.3).  Arrays of per-block items have N
+ * entries, per-pair items N-1.  lb/ub: NULL means x >= 0, no upper bound;
+ * otherwise every lb must be 0 and every ub +inf (other bounds return
+ * AHLP_ERR_UNSUPPORTED). */
+typedef struct {
+  int32_t N;                       /* number of blocks (>= 1)                  */
+  int32_t n0;                      /* linking variables x_0 (>= 0)             */
+  int32_t mg;                      /* global linking rows (>= 0)               */
+  const double *c0;                /* [n0]                                     */
+  const ahlp_csc *A;               /* [N]  m_i x n_i block matrices            */
+  const ahlp_csc *W;               /* [N]  m_i x n0 linking-variable blocks    */
+  const double *const *b;          /* [N]  -> [m_i]                            */
+  const double *const *c;          /* [N]  -> [n_i]                            */
+  const int32_t *l;                /* [N-1] local link rows of pair (j, j+1)   */
+  const ahlp_csc *FL;              /* [N-1] l_j x n_j                          */
+  const ahlp_csc *FR;              /* [N-1] l_j x n_{j+1}                      */
+  const ahlp_csc *F0;              /* [N-1] l_j x n0                           */
+  const double *const *blink;      /* [N-1] -> [l_j]                           */
+  const ahlp_csc *Fg;              /* [N]  mg x n_i                            */
+  const ahlp_csc *Fg0;             /* mg x n0 (may be NULL when mg*n0 == 0)    */
+  const double *bg;                /* [mg]                                     */
+  const double *const *lb;         /* [N] -> [n_i] or NULL                     */
+  const double *const *ub;         /* [N] -> [n_i] or NULL                     */
+  const double *lb0, *ub0;         /* [n0] or NULL                             */
+} ahlp_desc;
+
+typedef struct {
+  int32_t precision;    /* AHLP_PREC_FP64 (default) or AHLP_PREC_MIXED            */
+  int32_t max_iter;     /* IPM iteration cap (200)                                */
+  double  tol;          /* relative infeasibility and gap tolerance (1e-8)        */
+  double  eta;          /* step-to-boundary factor (0.9995)                       */
+  double  delta;        /* dual regularisation of the factor: +delta on the diagonal
+                           of M_i, of the link rows and of the global rows (1e-8).
+                           Only the preconditioner is regularised: kkt_solve
+                           solves the unregularised Newton system.              */
+  double  rho;          /* primal regularisation of the factor on x_0 (0)        */
+  int32_t refine_max;   /* GMRES iterations per KKT solve, at most 64 (20)        */
+  double  refine_tol;   /* target relative Newton residual (1e-10)                */
+  double  pivot_tol;    /* a pivot not above pivot_tol * (its diagonal before
+                           elimination) has lost its digits to cancellation and
+                           is clamped to that value (1e-12); ipm_solve coarsens
+                           it x100 (up to 1e-8) when a direction's residual
+                           stays above 1e-6                                      */
+  int32_t verbose;      /* 0: silent                                              */
+} ahlp_options;
+
+typedef struct {
+  int32_t status;         /* same code the call returned                          */
+  int32_t iterations;
+  double  pobj, dobj;     /* c'x and b'y                                          */
+  double  rel_gap;        /* |c'x - b'y| / (1 + |c'x|)                            */
+  double  pinf, dinf;     /* ||b-Ax||_inf/(1+||b||_inf), ||c-A'y-z||_inf/(1+||c||_inf) */
+  double  mu;             /* x'z / n                                              */
+  double  ms_total;       /* wall time of the solve                               */
+  double  ms_factor;      /* summed kkt_factor time                               */
+  double  ms_solve;       /* summed kkt_solve time (incl. refinement)             */
+  int32_t refine_steps;   /* summed refinement steps                              */
+  int32_t tiny_pivots;    /* pivots clamped in the last factor                    */
+  double  kkt_residual;   /* largest relative Newton residual seen                */
+  int32_t escalations;    /* times the pivot threshold was coarsened (x100)       */
+} ahlp_result;
+
+typedef struct {
+  int32_t refine_steps;   /* refinement steps taken                               */
+  double  rel_residual;   /* ||J d - r||_2 / ||r||_2 of the returned direction    */
+} ahlp_solve_info;
+
+typedef struct ahlp_problem ahlp_problem;   /* opaque; owns its device memory */
+
+/* Fill *opt with the defaults listed above. */
+void ahlp_default_options(ahlp_options *opt);
+
+/* Human-readable name of a status code (static storage). */
+const char *ahlp_status_string(int status);
+
+/*
+ * arrowhead_lp_create -- validate the LP, copy it to the current CUDA device
+ * and run the symbolic analysis (storage layout of the per-block augmented
+ * matrices, formation patterns, Schur-complement index maps).
+ *   descs : [batch] problem descriptions (host memory)
+ *   batch : must be 1 in this version (else AHLP_ERR_UNSUPPORTED)
+ *   opt   : options, or NULL for defaults
+ *   out   : receives the handle; *out is NULL on error
+ * The structure follows Sec. 3.2 (blocks, linking variables and rows) and
+ * Sec. 3.3 (local two-links vs global rows); the Schur layout is App. A.
+ */
+int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_options *opt,
+                        ahlp_problem **out);
+
+/* Free every device and host resource of the handle (NULL is a no-op). */
+void arrowhead_lp_destroy(ahlp_problem *p);
+
+/* Text of the last error on this handle (or of the last failed create when
+ * p is NULL).  Valid until the next call on the handle. */
+const char *ahlp_last_error(const ahlp_problem *p);
+
+/* Sizes of the global vectors. */
+int arrowhead_lp_sizes(const ahlp_problem *p, int64_t *n_total, int64_t *m_total);
+
+/* Stream used by all later calls on this handle (a cudaStream_t; NULL =
+ * the legacy default stream). */
+int arrowhead_lp_set_stream(ahlp_problem *p, void *stream);
+
+/* Replace the options of an existing handle (same fields as at create). */
+int arrowhead_lp_set_options(ahlp_problem *p, const ahlp_options *opt);
+
+/*
+ * kkt_factor -- factor the Newton system at the interior point (x, z)
+ * (Alg. 2 of Sec. 3.2 with the block systems in normal-equation form):
+ *   (a) per block, M_i = A_i D_i A_i' + delta I with D_i = X_i Z_i^-1, stacked
+ *       with G_i = [W_i | A_i D_i U_i' | A_i D_i Fg_i'] into the augmented
+ *       matrix [M_i G_i; G_i' C_i] (C_i = [U_i;Fg_i] D_i [U_i;Fg_i]');
+ *   (b) one batched partial Cholesky of all augmented matrices over their
+ *       first m_i pivots, which leaves Y_i' = (L_i^-1 G_i)' below the factor
+ *       and the Schur contribution C_i - G_i' M_i^-1 G_i in the corner
+ *       (Alg. 1 / Alg. 2 lines 1-2; the partial-factorisation idea of
+ *       Sec. 3.2);
+ *   (c) fixed-order summation of the contributions into the block-
+ *       tridiagonal-plus-border Schur complement of App. A, its block
+ *       Cholesky along the link chain and the quasi-definite border factor
+ *       (Alg. 2 lines 3-4).
+ *   x, z : [n_total], strictly positive (host or device)
+ *   delta, rho : regularisation for this factor (negative = use options)
+ * Returns AHLP_ERR_INVALID_ARG if some x or z is not > 0, AHLP_ERR_NOT_SPD if
+ * a pivot is NaN.  Tiny pivots are replaced (their count is kept).
+ */
+int kkt_factor(ahlp_problem *p, const double *x, const double *z, double delta, double rho);
+
+/*
+ * kkt_solve -- solve the Newton system of Sec. 2.3 at the last factored
+ * point,
+ *     [0 A' I; A 0 0; Z 0 X] [dx; dy; dz] = [r_d; r_p; r_c],
+ * by Alg. 3 (block forward solves, Schur right-hand side, Schur solve,
+ * block back-substitution) followed by dx = D(A'dy - r_d + X^-1 r_c) and
+ * dz = X^-1 (r_c - Z dx) (the elimination of Sec. 2.3).  When the relative
+ * residual of the unregularised Newton system is still above refine_tol,
+ * right-preconditioned FGMRES on that system (the block solve above as the
+ * preconditioner) runs for at most refine_max iterations.
+ *   r_d [n_total], r_p [m_total], r_c [n_total] : right-hand side
+ *   dx [n_total], dy [m_total], dz [n_total]    : output (caller-allocated)
+ *   info : optional (NULL allowed)
+ * Returns AHLP_ERR_INVALID_ARG if no factor exists.  Missing the refinement
+ * target is reported in info, not as an error.
+ */
+int kkt_solve(ahlp_problem *p, const double *r_d, const double *r_p, const double *r_c,
+              double *dx, double *dy, double *dz, ahlp_solve_info *info);
+
+/*
+ * kkt_adjoint_solve -- solve the transposed Newton system J' lam = g at the
+ * last factored point, reusing the factors: J' reduces to the same
+ * symmetric matrix [-D^-1 A'; A 0] with right-hand side
+ * [g_x - Z X^-1 g_z; g_y], and lam_z = X^-1 (g_z - lam_x).  Used for
+ * implicit differentiation of the optimum: with g = (c, 0, 0) at the
+ * optimum, dObj/dc = x + lam_x and dObj/db = lam_y.
+ *   g_x [n_total], g_y [m_total], g_z [n_total]; outputs likewise.
+ */
+int kkt_adjoint_solve(ahlp_problem *p, const double *g_x, const double *g_y, const double *g_z,
+                      double *lam_x, double *lam_y, double *lam_z, ahlp_solve_info *info);
+
+/*
+ * ipm_solve -- infeasible primal-dual Mehrotra predictor-corrector IPM
+ * (Sec. 2 and 2.3) with every linear-algebra step in this library's
+ * kernels.  Starting point: Mehrotra's heuristic computed with two solves
+ * at D = I, unless a warm start (x0, y0, z0 all non-NULL) is given.
+ *   x0, y0, z0 : optional warm start (host or device, NULL = cold start)
+ *   x, y, z    : final iterate (host or device, may be NULL)
+ *   res        : optional result record
+ * Returns AHLP_OK at convergence, AHLP_ERR_MAX_ITER, AHLP_ERR_INFEASIBLE or
+ * an error from the KKT calls.
+ */
+int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, const double *z0,
+              double *x, double *y, double *z, ahlp_result *res);
+
+/*
+ * kkt_schur_dense -- diagnostic: copy the Schur complement assembled by the
+ * last kkt_factor (before it was factored) into host memory as a dense
+ * column-major matrix with leading dimension ld, ordered
+ * [link rows (pair 1..N-1) | x_0 | global rows] (App. A, permuted).
+ *   S  : host buffer of ld * dim doubles, dim = sum(l) + n0 + mg
+ */
+int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld);
+
+/*
+ * kkt_stage_times -- diagnostic: device times (ms) of the stages of the last
+ * kkt_factor and kkt_solve: out[0] formation, out[1] block partial
+ * Cholesky, out[2] Schur assembly + factor, out[3] last kkt_solve.
+ */
+int kkt_stage_times(ahlp_problem *p, double *out4);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AHLP_H */

@@ -121,6 +121,8 @@ def _distinct_rows(rng: np.random.Generator, m: int, n: int, k: int) -> np.ndarr
 def _random_csc(rng, m, n, k_per_col, values="normal") -> sp.csc_matrix:
     rows = _distinct_rows(rng, m, n, k_per_col)
     k = rows.shape[1]
+    if k == 0:
+        return sp.csc_matrix((m, n))
     if values == "normal":
         vals = rng.standard_normal(n * k)
     else:

@@ -75,7 +75,7 @@ def solve(A, b, c, tol: float = 1e-8, max_iter: int = 200, eta: float = 0.9995,
         r_p, r_d = lpm.residuals(A, b, c, x, y, z)
         meas = lpm.measures(A, b, c, x, y, z)
         if record is not None:
-            record.append(dict(meas, iter=it))
+            record.append(dict(meas, iter=it, x=x.copy(), y=y.copy(), z=z.copy()))
         if verbose:
             print(it, meas)
         if meas["pinf"] <= tol and meas["dinf"] <= tol and meas["gap"] <= tol:

@@ -1,0 +1,361 @@
+"""ctypes binding of the C ABI in include/ahlp.h (argument marshalling only).
+
+Every computation happens inside ``libahlp.so``; this module only converts a
+block LP description into the C structs, passes pointers through and turns
+status codes into exceptions.  It refuses to run without the compiled library:
+there is no Python or CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libahlp.so")
+
+AHLP_OK = 0
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "DIM_MISMATCH", -3: "UNSUPPORTED", -4: "NOT_SPD",
+          -5: "REFINE_FAIL", -6: "MAX_ITER", -7: "INFEASIBLE_OR_UNBOUNDED", -8: "CUDA",
+          -9: "OOM", -10: "TIMEOUT"}
+PREC_FP64, PREC_MIXED = 0, 1
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class CSC(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("colptr", _ip), ("rowidx", _ip),
+                ("val", _dp)]
+
+
+class Desc(C.Structure):
+    _fields_ = [("N", C.c_int32), ("n0", C.c_int32), ("mg", C.c_int32), ("c0", _dp),
+                ("A", C.POINTER(CSC)), ("W", C.POINTER(CSC)), ("b", C.POINTER(_dp)),
+                ("c", C.POINTER(_dp)), ("l", _ip), ("FL", C.POINTER(CSC)),
+                ("FR", C.POINTER(CSC)), ("F0", C.POINTER(CSC)), ("blink", C.POINTER(_dp)),
+                ("Fg", C.POINTER(CSC)), ("Fg0", C.POINTER(CSC)), ("bg", _dp),
+                ("lb", C.POINTER(_dp)), ("ub", C.POINTER(_dp)), ("lb0", _dp), ("ub0", _dp)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
+                ("eta", C.c_double), ("delta", C.c_double), ("rho", C.c_double),
+                ("refine_max", C.c_int32), ("refine_tol", C.c_double),
+                ("pivot_tol", C.c_double), ("verbose", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("pobj", C.c_double),
+                ("dobj", C.c_double), ("rel_gap", C.c_double), ("pinf", C.c_double),
+                ("dinf", C.c_double), ("mu", C.c_double), ("ms_total", C.c_double),
+                ("ms_factor", C.c_double), ("ms_solve", C.c_double),
+                ("refine_steps", C.c_int32), ("tiny_pivots", C.c_int32),
+                ("kkt_residual", C.c_double), ("escalations", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("refine_steps", C.c_int32), ("rel_residual", C.c_double)]
+
+
+EXPORTS = ["ahlp_default_options", "ahlp_status_string", "arrowhead_lp_create",
+           "arrowhead_lp_destroy", "ahlp_last_error", "arrowhead_lp_sizes",
+           "arrowhead_lp_set_stream", "arrowhead_lp_set_options", "kkt_factor", "kkt_solve",
+           "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense", "kkt_stage_times"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load libahlp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"{p} not found: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(p)
+    vp = C.c_void_p
+    L.ahlp_default_options.argtypes = [C.POINTER(Options)]
+    L.ahlp_default_options.restype = None
+    L.ahlp_status_string.argtypes = [C.c_int]
+    L.ahlp_status_string.restype = C.c_char_p
+    L.arrowhead_lp_create.argtypes = [C.POINTER(Desc), C.c_int32, C.POINTER(Options),
+                                      C.POINTER(vp)]
+    L.arrowhead_lp_create.restype = C.c_int
+    L.arrowhead_lp_destroy.argtypes = [vp]
+    L.arrowhead_lp_destroy.restype = None
+    L.ahlp_last_error.argtypes = [vp]
+    L.ahlp_last_error.restype = C.c_char_p
+    L.arrowhead_lp_sizes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.arrowhead_lp_set_stream.argtypes = [vp, vp]
+    L.arrowhead_lp_set_options.argtypes = [vp, C.POINTER(Options)]
+    L.kkt_factor.argtypes = [vp, vp, vp, C.c_double, C.c_double]
+    L.kkt_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(SolveInfo)]
+    L.kkt_adjoint_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(SolveInfo)]
+    L.ipm_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(Result)]
+    L.kkt_schur_dense.argtypes = [vp, vp, C.c_int64]
+    L.kkt_stage_times.argtypes = [vp, _dp]
+    for name in ("arrowhead_lp_sizes", "arrowhead_lp_set_stream", "arrowhead_lp_set_options",
+                 "kkt_factor", "kkt_solve", "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense",
+                 "kkt_stage_times"):
+        getattr(L, name).restype = C.c_int
+    if path is None:
+        _lib = L
+    return L
+
+
+class AHLPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().ahlp_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+class _Keep:
+    """Holds every buffer handed to C for the lifetime of one call."""
+
+    def __init__(self):
+        self.refs = []
+
+    def f64(self, a):
+        a = _f64(a)
+        self.refs.append(a)
+        return a.ctypes.data_as(_dp)
+
+    def i32(self, a):
+        a = _i32(a)
+        self.refs.append(a)
+        return a.ctypes.data_as(_ip)
+
+    def csc(self, M, shape):
+        s = CSC()
+        if M is None:
+            s.m, s.n = shape
+            return s
+        M = M.tocsc()
+        s.m, s.n = M.shape
+        s.colptr = self.i32(M.indptr)
+        s.rowidx = self.i32(M.indices)
+        s.val = self.f64(M.data)
+        return s
+
+    def csc_array(self, mats, shapes):
+        arr = (CSC * max(len(mats), 1))()
+        for k, (M, sh) in enumerate(zip(mats, shapes)):
+            arr[k] = self.csc(M, sh)
+        self.refs.append(arr)
+        return arr
+
+    def ptr_array(self, vecs):
+        arr = (_dp * max(len(vecs), 1))()
+        for k, v in enumerate(vecs):
+            arr[k] = self.f64(v)
+        self.refs.append(arr)
+        return arr
+
+
+def make_desc(lp, keep: _Keep) -> Desc:
+    """Block LP (instances.BlockLP or anything with the same fields) -> Desc."""
+    d = Desc()
+    N, n0, mg = lp.N, lp.n0, lp.mg
+    d.N, d.n0, d.mg = N, n0, mg
+    ms = [a.shape[0] for a in lp.A]
+    ns = [a.shape[1] for a in lp.A]
+    l = [int(v) for v in lp.l]
+    d.c0 = keep.f64(lp.c0 if n0 else np.zeros(1))
+    d.A = keep.csc_array(lp.A, [a.shape for a in lp.A])
+    d.W = keep.csc_array(lp.W, [(m, n0) for m in ms])
+    d.b = keep.ptr_array(lp.b)
+    d.c = keep.ptr_array(lp.c)
+    d.l = keep.i32(l if l else [0])
+    d.FL = keep.csc_array(lp.FL, [(l[j], ns[j]) for j in range(N - 1)])
+    d.FR = keep.csc_array(lp.FR, [(l[j], ns[j + 1]) for j in range(N - 1)])
+    d.F0 = keep.csc_array(lp.F0, [(l[j], n0) for j in range(N - 1)])
+    d.blink = keep.ptr_array([v if len(v) else np.zeros(1) for v in lp.blink])
+    d.Fg = keep.csc_array(lp.Fg, [(mg, n) for n in ns])
+    fg0 = (CSC * 1)()
+    fg0[0] = keep.csc(lp.Fg0, (mg, n0))
+    keep.refs.append(fg0)
+    d.Fg0 = fg0
+    d.bg = keep.f64(lp.bg if mg else np.zeros(1))
+    return d
+
+
+def _vec_ptr(v, keep: _Keep, n: int, name: str):
+    """Pointer of a host (numpy) or device (torch) vector of length n."""
+    if v is None:
+        return None
+    if hasattr(v, "data_ptr"):          # torch tensor, host or device
+        if v.dtype.__str__() != "torch.float64" or v.numel() != n or not v.is_contiguous():
+            raise ValueError(f"{name}: need a contiguous float64 tensor of length {n}")
+        keep.refs.append(v)
+        return C.c_void_p(v.data_ptr())
+    a = _f64(v)
+    if a.shape != (n,):
+        raise ValueError(f"{name}: expected length {n}, got {a.shape}")
+    keep.refs.append(a)
+    return C.c_void_p(a.ctypes.data)
+
+
+def _out_like(template, n):
+    if template is not None and hasattr(template, "data_ptr"):
+        import torch
+        return torch.empty(n, dtype=torch.float64, device=template.device)
+    return np.empty(n)
+
+
+class Problem:
+    """Owner of one ``ahlp_problem`` handle."""
+
+    def __init__(self, handle, lib, n, m):
+        self._h = handle
+        self._lib = lib
+        self.n, self.m = n, m
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            self._lib.arrowhead_lp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != AHLP_OK:
+            raise AHLPError(st, self._lib.ahlp_last_error(self._h).decode())
+
+    def _stream_for(self, *vs):
+        for v in vs:
+            if v is not None and hasattr(v, "is_cuda") and v.is_cuda:
+                import torch
+                self._lib.arrowhead_lp_set_stream(
+                    self._h, C.c_void_p(torch.cuda.current_stream(v.device).cuda_stream))
+                return
+
+
+def arrowhead_lp_create(lp, options: Options | None = None, batch: int = 1) -> Problem:
+    L = load()
+    keep = _Keep()
+    descs = (Desc * batch)()
+    lps = lp if isinstance(lp, (list, tuple)) else [lp]
+    for k in range(batch):
+        descs[k] = make_desc(lps[min(k, len(lps) - 1)], keep)
+    h = C.c_void_p()
+    st = L.arrowhead_lp_create(descs, batch, C.byref(options) if options is not None else None,
+                               C.byref(h))
+    if st != AHLP_OK:
+        raise AHLPError(st, L.ahlp_last_error(None).decode())
+    n, m = C.c_int64(), C.c_int64()
+    L.arrowhead_lp_sizes(h, C.byref(n), C.byref(m))
+    prob = Problem(h, L, n.value, m.value)
+    prob.schur_dim = int(sum(int(v) for v in lps[0].l)) + lps[0].n0 + lps[0].mg
+    return prob
+
+
+def set_options(prob: Problem, options: Options):
+    prob._check(prob._lib.arrowhead_lp_set_options(prob._h, C.byref(options)))
+
+
+def kkt_factor(prob: Problem, x, z, delta: float = -1.0, rho: float = -1.0):
+    keep = _Keep()
+    prob._stream_for(x, z)
+    prob._check(prob._lib.kkt_factor(prob._h, _vec_ptr(x, keep, prob.n, "x"),
+                                     _vec_ptr(z, keep, prob.n, "z"), delta, rho))
+
+
+def _solve(fn, prob, a, b, c, out):
+    keep = _Keep()
+    prob._stream_for(a, b, c)
+    if out is None:
+        out = (_out_like(a, prob.n), _out_like(a, prob.m), _out_like(a, prob.n))
+    info = SolveInfo()
+    st = fn(prob._h, _vec_ptr(a, keep, prob.n, "arg1"), _vec_ptr(b, keep, prob.m, "arg2"),
+            _vec_ptr(c, keep, prob.n, "arg3"), _vec_ptr(out[0], keep, prob.n, "out1"),
+            _vec_ptr(out[1], keep, prob.m, "out2"), _vec_ptr(out[2], keep, prob.n, "out3"),
+            C.byref(info))
+    prob._check(st)
+    return out, {"refine_steps": info.refine_steps, "rel_residual": info.rel_residual}
+
+
+def kkt_solve(prob: Problem, r_d, r_p, r_c, out=None):
+    """(dx, dy, dz), info for J d = (r_d, r_p, r_c) at the factored point."""
+    return _solve(prob._lib.kkt_solve, prob, r_d, r_p, r_c, out)
+
+
+def kkt_adjoint_solve(prob: Problem, g_x, g_y, g_z, out=None):
+    """(lam_x, lam_y, lam_z), info for J' lam = (g_x, g_y, g_z)."""
+    return _solve(prob._lib.kkt_adjoint_solve, prob, g_x, g_y, g_z, out)
+
+
+def ipm_solve(prob: Problem, x0=None, y0=None, z0=None, out=None, check: bool = True):
+    """Run the IPM; returns (x, y, z), result dict."""
+    keep = _Keep()
+    prob._stream_for(x0, y0, z0, *(out or ()))
+    if out is None:
+        out = (np.empty(prob.n), np.empty(prob.m), np.empty(prob.n))
+    res = Result()
+    st = prob._lib.ipm_solve(prob._h, _vec_ptr(x0, keep, prob.n, "x0"),
+                             _vec_ptr(y0, keep, prob.m, "y0"), _vec_ptr(z0, keep, prob.n, "z0"),
+                             _vec_ptr(out[0], keep, prob.n, "x"),
+                             _vec_ptr(out[1], keep, prob.m, "y"),
+                             _vec_ptr(out[2], keep, prob.n, "z"), C.byref(res))
+    r = res.as_dict()
+    r["status_name"] = STATUS.get(st, st)
+    if check and st not in (AHLP_OK,):
+        raise AHLPError(st, prob._lib.ahlp_last_error(prob._h).decode())
+    return out, r
+
+
+def kkt_schur_dense(prob: Problem) -> np.ndarray:
+    nS = _schur_dim(prob)
+    S = np.zeros((nS, nS), order="F")
+    prob._check(prob._lib.kkt_schur_dense(prob._h, C.c_void_p(S.ctypes.data), max(nS, 1)))
+    return S
+
+
+def _schur_dim(prob):
+    return prob.schur_dim
+
+
+def kkt_stage_times(prob: Problem):
+    out = (C.c_double * 4)()
+    prob._check(prob._lib.kkt_stage_times(prob._h, out))
+    return {"form_ms": out[0], "block_factor_ms": out[1], "schur_ms": out[2],
+            "last_solve_ms": out[3]}

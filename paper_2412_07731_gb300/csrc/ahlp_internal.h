@@ -1,0 +1,232 @@
+// Internal declarations shared by the host runtime and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ahlp.h"
+
+namespace ahlp {
+
+constexpr int NB = 64;            // tile edge of the FP64 dense kernels
+constexpr int kThreads = 256;     // threads per CTA of the dense kernels
+
+// One dense lower-triangular "partial Cholesky" problem: an a x a matrix
+// (column-major, leading dimension lda, element offset base) whose first p
+// pivots are eliminated.  After the factorisation the (p..a) x (p..a) corner
+// holds the Schur complement of the leading p x p block.
+struct BlkInfo {
+  long long base;    // offset of element (0,0) in its buffer
+  long long voff;    // offset of this problem's vector segment in solve vectors
+  long long d0off;   // offset of its original diagonal in the diag0 array
+  int lda, a, p;
+  int T, Tp;         // tiles of a, tiles holding pivots
+  long long cdoff;   // offset of the corner (non-pivot) diagonal in cdiag0
+};
+
+#ifdef __CUDACC__
+// Pivot safeguard shared by every Cholesky in the library.  A pivot that is
+// not above tol * (the diagonal entry it started from) has lost all its
+// significant digits to cancellation; it is clamped to that threshold, which
+// keeps the factor nonsingular (the Krylov refinement of kkt_solve then
+// corrects the solve against the exact Newton matrix).  NaN pivots are
+// counted in status[0] with the first location, clamped pivots in status[1].
+__device__ __forceinline__ void pivot_fix(double &piv, double orig, double tol, int *status,
+                                          int where, int row) {
+  const double floor_v = tol * orig > 0.0 ? tol * orig : 1.0;
+  if (!(piv == piv)) {
+    if (atomicAdd(&status[0], 1) == 0) {
+      status[2] = where;
+      status[3] = row;
+    }
+    piv = floor_v;
+  } else if (!(piv > tol * orig) || !(piv > 0.0)) {
+    atomicAdd(&status[1], 1);
+    piv = floor_v;
+  }
+}
+#endif
+
+// One formation tile: block, tile row, tile column.
+struct FormTile {
+  int blk, I, J, pad;
+};
+
+// Per-block layout of the local Schur columns k_i = n0 + lprev + lnext + mg.
+struct SchurBlk {
+  int m;       // pivots (rows of A_i)
+  int k;       // local Schur columns
+  int lprev, lnext;
+  int link_prev_off, link_next_off;   // offsets of pairs i-1 and i in the link block
+};
+
+struct DeviceBuf {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace ahlp
+
+struct ahlp_problem {
+  // ---- sizes -------------------------------------------------------------
+  int N = 0, n0 = 0, mg = 0, B = 0, nl = 0, nS = 0;
+  long long n = 0, m = 0, msum = 0;   // n_total, m_total, sum of m_i
+  std::vector<int> mi, ni, ki, lprev, lnext;
+  std::vector<long long> xoff, yoff, link_off;   // link_off has N entries (pairs + 1)
+  int amax = 0;          // largest augmented order
+  ahlp_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double bnorm_inf = 0, cnorm_inf = 0;
+  int device = 0;
+
+  // ---- LP data on the device ----------------------------------------------
+  double *b = nullptr, *c = nullptr;               // global rhs, cost
+  int *A_rp = nullptr, *A_ci = nullptr;            // CSR of A (m x n)
+  double *A_v = nullptr;
+  int *AT_rp = nullptr, *AT_ci = nullptr;          // CSR of A' (n x m)
+  double *AT_v = nullptr;
+  unsigned char *is_x0 = nullptr;                  // [n] 1 for x_0 columns
+
+  // ---- factor storage -----------------------------------------------------
+  double *aug = nullptr;            // all augmented matrices
+  long long aug_elems = 0;
+  ahlp::BlkInfo *blk = nullptr;     // [N]
+  std::vector<ahlp::BlkInfo> h_blk;
+  ahlp::SchurBlk *sblk = nullptr;   // [N]
+  std::vector<ahlp::SchurBlk> h_sblk;
+  double *diag0 = nullptr;          // original diagonals (blocks)
+  double *cdiag0 = nullptr;         // corner diagonals before elimination ([U;Fg] D [U;Fg]')
+  double *sb_ref = nullptr;         // reference diagonal of the border pivots
+  long long cdiag_elems = 0;
+  long long vec_elems = 0;          // sum of a_i
+  int maxT = 0, maxTp = 0;
+
+  // ---- formation pattern --------------------------------------------------
+  ahlp::FormTile *ftiles = nullptr;
+  long long *tile_ent = nullptr;    // [ntiles+1]
+  int *ent_pos = nullptr;           // [nent]
+  long long *ent_cb = nullptr;      // [nent+1]
+  int *con_idx = nullptr;           // [ncon]
+  double *con_coef = nullptr;       // [ncon]
+  long long ntiles = 0, nent = 0, ncon = 0;
+
+  // ---- Schur complement ---------------------------------------------------
+  std::vector<long long> td_off, h_off;   // offsets of T_j (l_j^2) and H_j (l_{j+1} l_j)
+  long long td_elems = 0, h_elems = 0;
+  double *Td = nullptr, *Hd = nullptr, *Et = nullptr, *SB = nullptr;
+  double *Td_asm = nullptr, *Hd_asm = nullptr, *Et_asm = nullptr, *SB_asm = nullptr;
+  double *Td_diag0 = nullptr;        // assembled diagonal of T (pivot test)
+  long long *td_off_d = nullptr, *h_off_d = nullptr;
+  int *l_d = nullptr;                // [N-1]
+  long long *link_off_d = nullptr;   // [N]
+  int *kmap = nullptr;               // local Schur index -> global S index
+  int *link_pair_d = nullptr;        // [nl] pair of each link row
+  long long *yoff_d = nullptr;       // [N] start of y_i
+  long long *kmap_off_d = nullptr;   // [N]
+  std::vector<long long> kmap_off;
+  long long *f0_idx = nullptr; double *f0_val = nullptr; long long nf0 = 0;   // Et constants
+  long long *fg0_idx = nullptr; double *fg0_val = nullptr; long long nfg0 = 0; // SB constants
+  // border (quasi-definite) factor
+  double *border = nullptr; int Bld = 0;
+  ahlp::BlkInfo *bx_info = nullptr, *bp_info = nullptr;
+  ahlp::BlkInfo h_bx{}, h_bp{};
+  double *border_diag0 = nullptr;
+
+  // ---- vectors ------------------------------------------------------------
+  double *x = nullptr, *z = nullptr, *dscale = nullptr;   // current point, d = x/z
+  double *vec = nullptr;      // block solve segments [sum a_i]
+  double *svec = nullptr;     // Schur vector [nS]
+  double *f = nullptr, *g = nullptr, *rhat = nullptr;      // solve scratch
+  double *stg[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // staging for host I/O
+  double *res[3] = {nullptr, nullptr, nullptr};            // refinement residual
+  double *cor[3] = {nullptr, nullptr, nullptr};            // refinement correction
+  double *ipmv[12] = {};      // IPM work vectors
+  double *red_part = nullptr; // reduction partials
+  double *mdot_part = nullptr;  // multi-dot partials [kMaxKrylov+1][304]
+  double *gm_V = nullptr, *gm_Z = nullptr;   // Krylov bases, allocated on first use
+  double *gm_coef = nullptr;    // device coefficients for multi-axpy
+  int gm_cap = 0;               // vectors allocated in gm_Z (gm_V has one more)
+  double *scal = nullptr;     // device scalars
+  double *h_scal = nullptr;   // pinned host scalars
+  int *status = nullptr;      // device status words [4]
+  int tiny_pivots = 0;
+  bool factored = false;
+  double fac_delta = 0, fac_rho = 0, fac_pivot_tol = 0;
+
+  // ---- timing -------------------------------------------------------------
+  cudaEvent_t ev[8] = {};
+  float stage_ms[4] = {0, 0, 0, 0};
+
+  std::vector<ahlp::DeviceBuf> allocs;
+};
+
+namespace ahlp {
+
+// ---- kernels (launch wrappers) --------------------------------------------
+// All wrappers enqueue on p->stream and return the cudaError_t of the launch.
+cudaError_t launch_dscale(ahlp_problem *p);   // dscale = x / z
+cudaError_t launch_form(ahlp_problem *p, double delta);
+cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
+                         const double *diag0, double tol, int *status, cudaStream_t s);
+cudaError_t launch_schur_assemble(ahlp_problem *p, double delta, double rho);
+cudaError_t launch_schur_factor(ahlp_problem *p);
+cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
+                         const double *r_c, double *dx, double *dy, double *dz, bool adjoint);
+cudaError_t launch_residual(ahlp_problem *p, const double *r_d, const double *r_p,
+                            const double *r_c, const double *dx, const double *dy,
+                            const double *dz, double *e_d, double *e_p, double *e_c,
+                            bool adjoint);
+
+// ---- vector utilities ------------------------------------------------------
+enum RedOp { RED_DOT = 0, RED_MAXABS = 1, RED_MINSTEP = 2, RED_MIN = 3, RED_SUM = 4 };
+// out <- reduce(op, a, b) over len entries, deterministic order; out is a
+// device scalar.
+cudaError_t launch_reduce(ahlp_problem *p, int op, const double *a, const double *b,
+                          long long len, double *out);
+cudaError_t launch_spmv(const int *rp, const int *ci, const double *v, long long rows,
+                        const double *x, double *y, double alpha, const double *yadd,
+                        cudaStream_t s);   // y = yadd + alpha * A x   (yadd may be null)
+cudaError_t launch_axpby(double *y, const double *x, double a, double b, long long n,
+                         cudaStream_t s);  // y = a x + b y
+// generic elementwise kernels for the IPM
+cudaError_t launch_ipm_rc(double *rc, const double *x, const double *z, const double *dxa,
+                          const double *dza, double sigma_mu, long long n, cudaStream_t s);
+cudaError_t launch_fill(double *y, double v, long long n, cudaStream_t s);
+cudaError_t launch_add_scalar(double *y, const double *x, double s, long long n,
+                              cudaStream_t st);   // y = x + s
+constexpr int kMaxKrylov = 64;   // cap on GMRES iterations per solve
+// out[i] = <V_i, w>, i < k (V_i = V + i*ld), deterministic
+cudaError_t launch_mdot(ahlp_problem *p, const double *V, long long ld, int k, const double *w,
+                        long long len, double *out);
+// w += sum_i coef[i] V_i   (coef in device memory)
+cudaError_t launch_maxpy(const double *V, long long ld, int k, const double *coef, double *w,
+                         long long len, cudaStream_t s);
+// o = J v (Newton matrix of Sec. 2.3) or J' v
+cudaError_t launch_jmul(ahlp_problem *p, const double *vx, const double *vy, const double *vz,
+                        double *ox, double *oy, double *oz, bool adjoint);
+cudaError_t launch_mul(double *y, const double *a, const double *b, double scale, long long n,
+                       cudaStream_t s);   // y = scale * a .* b
+cudaError_t launch_step_dot(const double *x, const double *dx, double ap, const double *z,
+                            const double *dz, double ad, long long n, double *part,
+                            double *out, cudaStream_t s);  // (x+ap dx)'(z+ad dz)
+
+// ---- host runtime helpers (api.cpp) -------------------------------------------
+bool is_device_ptr(const void *ptr);
+const double *stage_in(ahlp_problem *p, const double *v, long long n, double *staging);
+int set_err(ahlp_problem *p, int code, const std::string &msg);
+void read_scalars(ahlp_problem *p, int k);
+int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol);
+int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double *rc, double *dx,
+               double *dy, double *dz, bool adjoint, ahlp_solve_info *info);
+void ck(cudaError_t e, const char *what);   // throws on error
+
+struct Fail {
+  int code;
+  std::string msg;
+};
+
+}  // namespace ahlp

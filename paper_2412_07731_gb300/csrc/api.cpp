@@ -1,0 +1,965 @@
+// Host runtime of the C ABI: validation, symbolic analysis, device memory,
+// and the kkt_factor / kkt_solve / kkt_adjoint_solve entry points.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+#include "ahlp_internal.h"
+
+using namespace ahlp;
+
+namespace ahlp {
+cudaError_t set_dense_smem_limits(int bytes);
+cudaError_t set_schur_smem_limits(int bytes);
+}
+
+static std::string g_create_err;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// canonical sparse matrices on the host
+// ---------------------------------------------------------------------------
+struct Csc {
+  int m = 0, n = 0;
+  std::vector<int> cp, ri;
+  std::vector<double> v;
+  long long nnz() const { return (long long)ri.size(); }
+};
+
+[[noreturn]] void fail(int code, const std::string &msg) { throw Fail{code, msg}; }
+
+bool finite(double v) { return std::isfinite(v); }
+
+// Validate and canonicalise (sort rows, sum duplicates).  in == NULL means the
+// zero matrix of the expected shape.
+Csc canon(const ahlp_csc *in, int m, int n, const std::string &what) {
+  Csc out;
+  out.m = m;
+  out.n = n;
+  out.cp.assign(n + 1, 0);
+  if (in == nullptr) return out;
+  if (in->m != m || in->n != n)
+    fail(AHLP_ERR_DIM_MISMATCH, what + ": shape " + std::to_string(in->m) + "x" +
+                                    std::to_string(in->n) + ", expected " + std::to_string(m) +
+                                    "x" + std::to_string(n));
+  if (n == 0) return out;
+  if (!in->colptr) fail(AHLP_ERR_INVALID_ARG, what + ": colptr is NULL");
+  if (in->colptr[0] != 0) fail(AHLP_ERR_INVALID_ARG, what + ": colptr[0] != 0");
+  for (int j = 0; j < n; ++j)
+    if (in->colptr[j + 1] < in->colptr[j])
+      fail(AHLP_ERR_INVALID_ARG, what + ": colptr not monotone");
+  const int nnz = in->colptr[n];
+  if (nnz > 0 && (!in->rowidx || !in->val))
+    fail(AHLP_ERR_INVALID_ARG, what + ": rowidx/val NULL");
+  std::vector<std::pair<int, double>> col;
+  for (int j = 0; j < n; ++j) {
+    col.clear();
+    for (int k = in->colptr[j]; k < in->colptr[j + 1]; ++k) {
+      const int r = in->rowidx[k];
+      const double v = in->val[k];
+      if (r < 0 || r >= m) fail(AHLP_ERR_INVALID_ARG, what + ": row index out of range");
+      if (!finite(v)) fail(AHLP_ERR_INVALID_ARG, what + ": non-finite value");
+      col.push_back({r, v});
+    }
+    std::sort(col.begin(), col.end(),
+              [](const std::pair<int, double> &a, const std::pair<int, double> &b) {
+                return a.first < b.first;
+              });
+    for (size_t k = 0; k < col.size(); ++k) {
+      if (!out.ri.empty() && (int)out.ri.size() > out.cp[j] && out.ri.back() == col[k].first)
+        out.v.back() += col[k].second;
+      else {
+        out.ri.push_back(col[k].first);
+        out.v.push_back(col[k].second);
+      }
+    }
+    out.cp[j + 1] = (int)out.ri.size();
+  }
+  return out;
+}
+
+std::vector<double> vec_in(const double *p, long long n, const std::string &what) {
+  std::vector<double> v((size_t)n);
+  if (n == 0) return v;
+  if (!p) fail(AHLP_ERR_INVALID_ARG, what + " is NULL");
+  for (long long i = 0; i < n; ++i) {
+    if (!finite(p[i])) fail(AHLP_ERR_INVALID_ARG, what + ": non-finite entry");
+    v[(size_t)i] = p[i];
+  }
+  return v;
+}
+
+void check_bounds(const double *lb, const double *ub, int n, const std::string &what) {
+  for (int j = 0; j < n; ++j) {
+    if (lb && lb[j] != 0.0)
+      fail(AHLP_ERR_UNSUPPORTED, what + ": only lower bounds of 0 are supported");
+    if (ub && !(std::isinf(ub[j]) && ub[j] > 0))
+      fail(AHLP_ERR_UNSUPPORTED, what + ": finite upper bounds are not supported");
+  }
+}
+
+long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+template <class T>
+T *dalloc(ahlp_problem *p, long long count) {
+  if (count <= 0) count = 1;
+  void *ptr = nullptr;
+  size_t bytes = (size_t)count * sizeof(T);
+  cudaError_t e = cudaMalloc(&ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? AHLP_ERR_OOM : AHLP_ERR_CUDA,
+         std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  p->allocs.push_back({ptr, bytes});
+  return reinterpret_cast<T *>(ptr);
+}
+
+template <class T>
+T *dupload(ahlp_problem *p, const std::vector<T> &h) {
+  T *d = dalloc<T>(p, (long long)h.size());
+  if (!h.empty()) {
+    cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) fail(AHLP_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+  }
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// formation pattern of one block (Alg. 2 line 1 in normal-equation form):
+// entries of M_i, G_i' and C_i as sums coef * d[j] (j = -1: constant 1)
+// ---------------------------------------------------------------------------
+struct Con {
+  long long key;   // tile id * NB*NB + ct*NB + rt
+  int didx;
+  double coef;
+};
+
+struct Pattern {
+  std::vector<FormTile> tiles;
+  std::vector<long long> tile_ent;   // entry begin per tile (absolute)
+  std::vector<int> ent_pos;
+  std::vector<long long> ent_cb;     // contribution begin per entry (absolute)
+  std::vector<int> con_idx;
+  std::vector<double> con_coef;
+};
+
+struct URow {   // one link / global row restricted to the block's columns
+  std::vector<int> j;
+  std::vector<double> u;
+};
+
+void build_block_pattern(int blk, const Csc &A, const Csc &W, const std::vector<URow> &urows,
+                         int n0, int m, int k, long long xoff, Pattern &P) {
+  const int a = m + k;
+  const int T = (a + NB - 1) / NB;
+  auto tile_id = [T](long long It, long long Jt) { return Jt * T - Jt * (Jt - 1) / 2 + (It - Jt); };
+  std::vector<Con> cons;
+  auto add = [&](int R, int C, int didx, double coef) {
+    if (R < C) std::swap(R, C);
+    const long long key = tile_id(R / NB, C / NB) * (long long)(NB * NB) + (long long)(C % NB) * NB +
+                          (R % NB);
+    cons.push_back({key, didx, coef});
+  };
+  // M_i = A_i D_i A_i'
+  for (int j = 0; j < A.n; ++j)
+    for (int p = A.cp[j]; p < A.cp[j + 1]; ++p)
+      for (int q = A.cp[j]; q <= p; ++q)
+        add(A.ri[p], A.ri[q], (int)(xoff + j), A.v[p] * A.v[q]);
+  for (int r = 0; r < m; ++r) add(r, r, -1, 0.0);   // every diagonal entry exists
+  // G_i' rows: W_i part (constant) ...
+  for (int t = 0; t < n0; ++t)
+    for (int q = W.cp[t]; q < W.cp[t + 1]; ++q) add(m + t, W.ri[q], -1, W.v[q]);
+  // ... and A_i D_i u' for every link / global row u touching the block
+  std::vector<std::vector<std::pair<int, double>>> ucol(A.n);
+  for (size_t tt = 0; tt < urows.size(); ++tt) {
+    const int t = n0 + (int)tt;
+    const URow &u = urows[tt];
+    for (size_t e = 0; e < u.j.size(); ++e) {
+      const int j = u.j[e];
+      ucol[j].push_back({t, u.u[e]});
+      for (int q = A.cp[j]; q < A.cp[j + 1]; ++q)
+        add(m + t, A.ri[q], (int)(xoff + j), A.v[q] * u.u[e]);
+    }
+  }
+  // C_i = [U_i; Fg_i] D_i [U_i; Fg_i]'
+  for (int j = 0; j < A.n; ++j)
+    for (size_t x = 0; x < ucol[j].size(); ++x)
+      for (size_t y = 0; y <= x; ++y)
+        add(m + ucol[j][x].first, m + ucol[j][y].first, (int)(xoff + j),
+            ucol[j][x].second * ucol[j][y].second);
+  std::stable_sort(cons.begin(), cons.end(), [](const Con &x, const Con &y) { return x.key < y.key; });
+  // tiles in id order (J-major lower), entries grouped by key
+  size_t c = 0;
+  for (int Jt = 0; Jt < T; ++Jt)
+    for (int It = Jt; It < T; ++It) {
+      const long long id = tile_id(It, Jt);
+      P.tiles.push_back({blk, It, Jt, 0});
+      P.tile_ent.push_back((long long)P.ent_pos.size());
+      while (c < cons.size() && cons[c].key / (NB * NB) == id) {
+        const long long key = cons[c].key;
+        const int within = (int)(key % (NB * NB));
+        const int ct = within / NB, rt = within % NB;
+        const int R = It * NB + rt, C = Jt * NB + ct;
+        int pos = (rt << 8) | ct;
+        if (R == C && R < m) pos |= (1 << 16);
+        else if (R == C) pos |= (1 << 17);
+        P.ent_pos.push_back(pos);
+        P.ent_cb.push_back((long long)P.con_idx.size());
+        while (c < cons.size() && cons[c].key == key) {
+          P.con_idx.push_back(cons[c].didx);
+          P.con_coef.push_back(cons[c].coef);
+          ++c;
+        }
+      }
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void ahlp_default_options(ahlp_options *o) {
+  if (!o) return;
+  o->precision = AHLP_PREC_FP64;
+  o->max_iter = 200;
+  o->tol = 1e-8;
+  o->eta = 0.9995;
+  o->delta = 1e-8;
+  o->rho = 0.0;
+  o->refine_max = 20;
+  o->refine_tol = 1e-10;
+  o->pivot_tol = 1e-12;
+  o->verbose = 0;
+}
+
+const char *ahlp_status_string(int s) {
+  switch (s) {
+    case AHLP_OK: return "OK";
+    case AHLP_ERR_INVALID_ARG: return "INVALID_ARG";
+    case AHLP_ERR_DIM_MISMATCH: return "DIM_MISMATCH";
+    case AHLP_ERR_UNSUPPORTED: return "UNSUPPORTED";
+    case AHLP_ERR_NOT_SPD: return "NOT_SPD";
+    case AHLP_ERR_REFINE_FAIL: return "REFINE_FAIL";
+    case AHLP_ERR_MAX_ITER: return "MAX_ITER";
+    case AHLP_ERR_INFEASIBLE: return "INFEASIBLE_OR_UNBOUNDED";
+    case AHLP_ERR_CUDA: return "CUDA";
+    case AHLP_ERR_OOM: return "OOM";
+    case AHLP_ERR_TIMEOUT: return "TIMEOUT";
+    default: return "UNKNOWN";
+  }
+}
+
+const char *ahlp_last_error(const ahlp_problem *p) {
+  return p ? p->err.c_str() : g_create_err.c_str();
+}
+
+void arrowhead_lp_destroy(ahlp_problem *p) {
+  if (!p) return;
+  for (auto &b : p->allocs) cudaFree(b.ptr);
+  if (p->gm_V) cudaFree(p->gm_V);
+  if (p->gm_Z) cudaFree(p->gm_Z);
+  if (p->h_scal) cudaFreeHost(p->h_scal);
+  for (auto &e : p->ev)
+    if (e) cudaEventDestroy(e);
+  delete p;
+}
+
+int arrowhead_lp_sizes(const ahlp_problem *p, int64_t *n_total, int64_t *m_total) {
+  if (!p) return AHLP_ERR_INVALID_ARG;
+  if (n_total) *n_total = p->n;
+  if (m_total) *m_total = p->m;
+  return AHLP_OK;
+}
+
+int arrowhead_lp_set_stream(ahlp_problem *p, void *stream) {
+  if (!p) return AHLP_ERR_INVALID_ARG;
+  p->stream = reinterpret_cast<cudaStream_t>(stream);
+  return AHLP_OK;
+}
+
+static int check_options(const ahlp_options &o, std::string &err) {
+  if (o.precision != AHLP_PREC_FP64) {
+    err = "only AHLP_PREC_FP64 is available in this build";
+    return AHLP_ERR_UNSUPPORTED;
+  }
+  if (o.max_iter < 0 || !(o.tol > 0) || !(o.eta > 0 && o.eta < 1) || o.delta < 0 || o.rho < 0 ||
+      o.refine_max < 0 || !(o.refine_tol > 0) || !(o.pivot_tol >= 0)) {
+    err = "invalid option value";
+    return AHLP_ERR_INVALID_ARG;
+  }
+  return AHLP_OK;
+}
+
+int arrowhead_lp_set_options(ahlp_problem *p, const ahlp_options *opt) {
+  if (!p || !opt) return AHLP_ERR_INVALID_ARG;
+  int s = check_options(*opt, p->err);
+  if (s != AHLP_OK) return s;
+  p->opt = *opt;
+  return AHLP_OK;
+}
+
+int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_options *opt,
+                        ahlp_problem **out) {
+  if (!out) return AHLP_ERR_INVALID_ARG;
+  *out = nullptr;
+  g_create_err.clear();
+  if (!descs) {
+    g_create_err = "descs is NULL";
+    return AHLP_ERR_INVALID_ARG;
+  }
+  if (batch != 1) {
+    g_create_err = "batch != 1 is not supported in this build";
+    return AHLP_ERR_UNSUPPORTED;
+  }
+  ahlp_problem *p = new ahlp_problem();
+  ahlp_default_options(&p->opt);
+  if (opt) {
+    int s = check_options(*opt, g_create_err);
+    if (s != AHLP_OK) {
+      delete p;
+      return s;
+    }
+    p->opt = *opt;
+  }
+  try {
+    const ahlp_desc &D = descs[0];
+    if (D.N < 1 || D.n0 < 0 || D.mg < 0) fail(AHLP_ERR_INVALID_ARG, "N >= 1, n0 >= 0, mg >= 0 required");
+    if (!D.A || !D.W || !D.b || !D.c) fail(AHLP_ERR_INVALID_ARG, "A, W, b, c must be given");
+    if (D.N > 1 && !D.l) fail(AHLP_ERR_INVALID_ARG, "l must be given when N > 1");
+    const int N = D.N, n0 = D.n0, mg = D.mg;
+    p->N = N;
+    p->n0 = n0;
+    p->mg = mg;
+    p->B = n0 + mg;
+    // ---- blocks -----------------------------------------------------------
+    std::vector<Csc> A(N), W(N), Fg(N), FL(N > 1 ? N - 1 : 0), FR(FL.size()), F0(FL.size());
+    std::vector<std::vector<double>> b(N), c(N), blink(FL.size());
+    for (int i = 0; i < N; ++i) {
+      const std::string tag = "block " + std::to_string(i);
+      if (D.A[i].m < 0 || D.A[i].n < 0) fail(AHLP_ERR_INVALID_ARG, tag + ": negative size");
+      A[i] = canon(&D.A[i], D.A[i].m, D.A[i].n, tag + " A");
+      W[i] = canon(&D.W[i], A[i].m, n0, tag + " W");
+      Fg[i] = canon(D.Fg ? &D.Fg[i] : nullptr, mg, A[i].n, tag + " Fg");
+      b[i] = vec_in(D.b[i], A[i].m, tag + " b");
+      c[i] = vec_in(D.c[i], A[i].n, tag + " c");
+      check_bounds(D.lb ? D.lb[i] : nullptr, D.ub ? D.ub[i] : nullptr, A[i].n, tag);
+      p->mi.push_back(A[i].m);
+      p->ni.push_back(A[i].n);
+    }
+    check_bounds(D.lb0, D.ub0, n0, "x0");
+    std::vector<int> l(FL.size());
+    for (size_t j = 0; j < FL.size(); ++j) {
+      const std::string tag = "pair " + std::to_string(j);
+      if (D.l[j] < 0) fail(AHLP_ERR_INVALID_ARG, tag + ": negative link count");
+      l[j] = D.l[j];
+      if (l[j] > 0 && (!D.FL || !D.FR)) fail(AHLP_ERR_INVALID_ARG, tag + ": FL/FR missing");
+      FL[j] = canon(D.FL ? &D.FL[j] : nullptr, l[j], A[j].n, tag + " FL");
+      FR[j] = canon(D.FR ? &D.FR[j] : nullptr, l[j], A[j + 1].n, tag + " FR");
+      F0[j] = canon(D.F0 ? &D.F0[j] : nullptr, l[j], n0, tag + " F0");
+      blink[j] = vec_in(D.blink ? D.blink[j] : nullptr, l[j], tag + " blink");
+    }
+    Csc Fg0 = canon(D.Fg0, mg, n0, "Fg0");
+    std::vector<double> c0 = vec_in(D.c0, n0, "c0");
+    std::vector<double> bg = vec_in(D.bg, mg, "bg");
+    // ---- global sizes and offsets --------------------------------------------
+    p->xoff.resize(N + 1);
+    p->yoff.resize(N);
+    long long xo = 0, yo = 0;
+    for (int i = 0; i < N; ++i) {
+      p->xoff[i] = xo;
+      p->yoff[i] = yo;
+      xo += A[i].n;
+      yo += A[i].m;
+    }
+    p->xoff[N] = xo;
+    p->msum = yo;
+    p->n = xo + n0;
+    p->link_off.assign(N, 0);
+    for (int j = 0; j + 1 < N; ++j) p->link_off[j + 1] = p->link_off[j] + l[j];
+    p->nl = (int)p->link_off[N - 1];
+    p->m = p->msum + p->nl + mg;
+    p->nS = p->nl + p->B;
+    // ---- monolithic A (CSR) and A' (CSR) for residuals ------------------------
+    std::vector<long long> R, C;
+    std::vector<double> V;
+    auto put = [&](const Csc &M, long long r0, long long c0_) {
+      for (int j = 0; j < M.n; ++j)
+        for (int q = M.cp[j]; q < M.cp[j + 1]; ++q) {
+          R.push_back(r0 + M.ri[q]);
+          C.push_back(c0_ + j);
+          V.push_back(M.v[q]);
+        }
+    };
+    const long long grow0 = p->msum + p->nl;
+    for (int i = 0; i < N; ++i) {
+      put(A[i], p->yoff[i], p->xoff[i]);
+      put(W[i], p->yoff[i], p->xoff[N]);
+      put(Fg[i], grow0, p->xoff[i]);
+    }
+    for (size_t j = 0; j < FL.size(); ++j) {
+      put(FL[j], p->msum + p->link_off[j], p->xoff[j]);
+      put(FR[j], p->msum + p->link_off[j], p->xoff[j + 1]);
+      put(F0[j], p->msum + p->link_off[j], p->xoff[N]);
+    }
+    put(Fg0, grow0, p->xoff[N]);
+    const long long nnz = (long long)V.size();
+    if (nnz >= (1LL << 31)) fail(AHLP_ERR_UNSUPPORTED, "more than 2^31 nonzeros");
+    auto to_csr = [&](const std::vector<long long> &rr, const std::vector<long long> &cc,
+                      long long rows, std::vector<int> &rp, std::vector<int> &ci,
+                      std::vector<double> &vv) {
+      rp.assign(rows + 1, 0);
+      for (long long k = 0; k < nnz; ++k) rp[rr[k] + 1]++;
+      for (long long r = 0; r < rows; ++r) rp[r + 1] += rp[r];
+      std::vector<int> fill(rp.begin(), rp.end() - 1);
+      ci.resize(nnz);
+      vv.resize(nnz);
+      for (long long k = 0; k < nnz; ++k) {   // stable: keeps input order within a row
+        const int pos = fill[rr[k]]++;
+        ci[pos] = (int)cc[k];
+        vv[pos] = V[k];
+      }
+      // sort columns within rows (sum order of the mat-vec is then fixed)
+      for (long long r = 0; r < rows; ++r) {
+        std::vector<std::pair<int, double>> row;
+        for (int q = rp[r]; q < rp[r + 1]; ++q) row.push_back({ci[q], vv[q]});
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int, double> &x, const std::pair<int, double> &y) {
+                    return x.first < y.first;
+                  });
+        for (int q = rp[r]; q < rp[r + 1]; ++q) {
+          ci[q] = row[q - rp[r]].first;
+          vv[q] = row[q - rp[r]].second;
+        }
+      }
+    };
+    std::vector<int> Arp, Aci, ATrp, ATci;
+    std::vector<double> Av, ATv;
+    to_csr(R, C, p->m, Arp, Aci, Av);
+    to_csr(C, R, p->n, ATrp, ATci, ATv);
+    std::vector<double> bgl, cgl;
+    for (int i = 0; i < N; ++i) bgl.insert(bgl.end(), b[i].begin(), b[i].end());
+    for (auto &v : blink) bgl.insert(bgl.end(), v.begin(), v.end());
+    bgl.insert(bgl.end(), bg.begin(), bg.end());
+    for (int i = 0; i < N; ++i) cgl.insert(cgl.end(), c[i].begin(), c[i].end());
+    cgl.insert(cgl.end(), c0.begin(), c0.end());
+    for (double v : bgl) p->bnorm_inf = std::max(p->bnorm_inf, std::fabs(v));
+    for (double v : cgl) p->cnorm_inf = std::max(p->cnorm_inf, std::fabs(v));
+    std::vector<unsigned char> isx0(p->n, 0);
+    for (long long k = p->xoff[N]; k < p->n; ++k) isx0[k] = 1;
+    // ---- per-block layout ------------------------------------------------------
+    p->h_blk.resize(N);
+    p->h_sblk.resize(N);
+    long long base = 0, voff = 0, d0 = 0, cd = 0;
+    for (int i = 0; i < N; ++i) {
+      const int lp = i > 0 ? l[i - 1] : 0, ln = i + 1 < N ? l[i] : 0;
+      const int k = n0 + lp + ln + mg;
+      const int m = A[i].m, a = m + k;
+      p->ki.push_back(k);
+      p->lprev.push_back(lp);
+      p->lnext.push_back(ln);
+      BlkInfo bi{};
+      bi.base = base;
+      bi.voff = voff;
+      bi.d0off = d0;
+      bi.cdoff = cd;
+      bi.lda = (int)round_up(std::max(a, 1), 8);
+      bi.a = a;
+      bi.p = m;
+      bi.T = (a + NB - 1) / NB;
+      bi.Tp = (m + NB - 1) / NB;
+      p->h_blk[i] = bi;
+      base += round_up((long long)bi.lda * a, 32);
+      voff += a;
+      d0 += m;
+      cd += k;
+      p->amax = std::max(p->amax, a);
+      p->maxT = std::max(p->maxT, bi.T);
+      p->maxTp = std::max(p->maxTp, bi.Tp);
+      SchurBlk sb{};
+      sb.m = m;
+      sb.k = k;
+      sb.lprev = lp;
+      sb.lnext = ln;
+      sb.link_prev_off = i > 0 ? (int)p->link_off[i - 1] : 0;
+      sb.link_next_off = i + 1 < N ? (int)p->link_off[i] : 0;
+      p->h_sblk[i] = sb;
+    }
+    p->aug_elems = base;
+    p->vec_elems = voff;
+    if ((long long)p->amax * 8 > 200 * 1024 || (long long)p->B * 8 > 200 * 1024)
+      fail(AHLP_ERR_UNSUPPORTED, "a block's augmented order exceeds 25600");
+    // ---- formation patterns --------------------------------------------------
+    Pattern P;
+    for (int i = 0; i < N; ++i) {
+      std::vector<URow> urows(p->ki[i] - n0);
+      auto rows_of = [&](const Csc &F, int off) {
+        for (int j = 0; j < F.n; ++j)
+          for (int q = F.cp[j]; q < F.cp[j + 1]; ++q) {
+            urows[off + F.ri[q]].j.push_back(j);
+            urows[off + F.ri[q]].u.push_back(F.v[q]);
+          }
+      };
+      if (i > 0) rows_of(FR[i - 1], 0);
+      if (i + 1 < N) rows_of(FL[i], p->lprev[i]);
+      rows_of(Fg[i], p->lprev[i] + p->lnext[i]);
+      const long long t0 = (long long)P.tiles.size();
+      build_block_pattern(i, A[i], W[i], urows, n0, A[i].m, p->ki[i], p->xoff[i], P);
+      (void)t0;
+    }
+    P.tile_ent.push_back((long long)P.ent_pos.size());
+    P.ent_cb.push_back((long long)P.con_idx.size());
+    p->ntiles = (long long)P.tiles.size();
+    p->nent = (long long)P.ent_pos.size();
+    p->ncon = (long long)P.con_idx.size();
+    // ---- Schur maps ---------------------------------------------------------------
+    std::vector<int> kmap;
+    for (int i = 0; i < N; ++i) {
+      p->kmap_off.push_back((long long)kmap.size());
+      for (int t = 0; t < p->ki[i]; ++t) {
+        int s;
+        if (t < n0) s = p->nl + t;
+        else if (t < n0 + p->lprev[i]) s = (int)p->link_off[i - 1] + (t - n0);
+        else if (t < n0 + p->lprev[i] + p->lnext[i]) s = (int)p->link_off[i] + (t - n0 - p->lprev[i]);
+        else s = p->nl + n0 + (t - n0 - p->lprev[i] - p->lnext[i]);
+        kmap.push_back(s);
+      }
+    }
+    std::vector<int> link_pair(p->nl);
+    for (size_t j = 0; j < FL.size(); ++j)
+      for (int r = 0; r < l[j]; ++r) link_pair[p->link_off[j] + r] = (int)j;
+    long long te = 0, he = 0;
+    for (size_t j = 0; j < FL.size(); ++j) {
+      p->td_off.push_back(te);
+      te += (long long)l[j] * l[j];
+      if (j + 1 < FL.size()) {
+        p->h_off.push_back(he);
+        he += (long long)l[j + 1] * l[j];
+      }
+    }
+    p->td_elems = te;
+    p->h_elems = he;
+    std::vector<long long> f0i, fg0i;
+    std::vector<double> f0v, fg0v;
+    for (size_t j = 0; j < FL.size(); ++j)
+      for (int cc = 0; cc < n0; ++cc)
+        for (int q = F0[j].cp[cc]; q < F0[j].cp[cc + 1]; ++q) {
+          f0i.push_back((long long)cc * p->nl + p->link_off[j] + F0[j].ri[q]);
+          f0v.push_back(F0[j].v[q]);
+        }
+    for (int cc = 0; cc < n0; ++cc)
+      for (int q = Fg0.cp[cc]; q < Fg0.cp[cc + 1]; ++q) {
+        const long long g = n0 + Fg0.ri[q];
+        fg0i.push_back((long long)cc * p->B + g);
+        fg0v.push_back(Fg0.v[q]);
+        fg0i.push_back(g * p->B + cc);
+        fg0v.push_back(Fg0.v[q]);
+      }
+    p->nf0 = (long long)f0i.size();
+    p->nfg0 = (long long)fg0i.size();
+    p->Bld = (int)round_up(std::max(p->B, 1), 8);
+    p->h_bx = BlkInfo{0, 0, 0, p->Bld, p->B, n0, (p->B + NB - 1) / NB, (n0 + NB - 1) / NB, 0};
+    p->h_bp = BlkInfo{(long long)n0 * p->Bld + n0, n0, n0, p->Bld, mg, mg, (mg + NB - 1) / NB,
+                      (mg + NB - 1) / NB, 0};
+    // ---- device memory ----------------------------------------------------------
+    ck(cudaGetDevice(&p->device), "cudaGetDevice");
+    p->b = dupload(p, bgl);
+    p->c = dupload(p, cgl);
+    p->A_rp = dupload(p, Arp);
+    p->A_ci = dupload(p, Aci);
+    p->A_v = dupload(p, Av);
+    p->AT_rp = dupload(p, ATrp);
+    p->AT_ci = dupload(p, ATci);
+    p->AT_v = dupload(p, ATv);
+    p->is_x0 = dupload(p, isx0);
+    p->aug = dalloc<double>(p, p->aug_elems);
+    p->blk = dupload(p, p->h_blk);
+    p->sblk = dupload(p, p->h_sblk);
+    p->diag0 = dalloc<double>(p, std::max(d0, 1LL));
+    p->cdiag0 = dalloc<double>(p, std::max(cd, 1LL));
+    p->cdiag_elems = cd;
+    p->sb_ref = dalloc<double>(p, p->B);
+    p->ftiles = dupload(p, P.tiles);
+    p->tile_ent = dupload(p, P.tile_ent);
+    p->ent_pos = dupload(p, P.ent_pos);
+    p->ent_cb = dupload(p, P.ent_cb);
+    p->con_idx = dupload(p, P.con_idx);
+    p->con_coef = dupload(p, P.con_coef);
+    p->Td = dalloc<double>(p, te);
+    p->Hd = dalloc<double>(p, he);
+    p->Et = dalloc<double>(p, (long long)p->nl * p->B);
+    p->SB = dalloc<double>(p, (long long)p->B * p->B);
+    p->Td_asm = dalloc<double>(p, te);
+    p->Hd_asm = dalloc<double>(p, he);
+    p->Et_asm = dalloc<double>(p, (long long)p->nl * p->B);
+    p->SB_asm = dalloc<double>(p, (long long)p->B * p->B);
+    p->Td_diag0 = dalloc<double>(p, p->nl);
+    p->td_off_d = dupload(p, p->td_off);
+    p->h_off_d = dupload(p, p->h_off);
+    p->l_d = dupload(p, l);
+    p->link_off_d = dupload(p, p->link_off);
+    p->kmap = dupload(p, kmap);
+    p->kmap_off_d = dupload(p, p->kmap_off);
+    p->link_pair_d = dupload(p, link_pair);
+    p->yoff_d = dupload(p, p->yoff);
+    p->f0_idx = dupload(p, f0i);
+    p->f0_val = dupload(p, f0v);
+    p->fg0_idx = dupload(p, fg0i);
+    p->fg0_val = dupload(p, fg0v);
+    p->border = dalloc<double>(p, (long long)p->Bld * std::max(p->B, 1));
+    p->bx_info = dupload(p, std::vector<BlkInfo>(1, p->h_bx));
+    p->bp_info = dupload(p, std::vector<BlkInfo>(1, p->h_bp));
+    p->border_diag0 = dalloc<double>(p, p->B);
+    p->x = dalloc<double>(p, p->n);
+    p->z = dalloc<double>(p, p->n);
+    p->dscale = dalloc<double>(p, p->n);
+    p->vec = dalloc<double>(p, p->vec_elems);
+    p->svec = dalloc<double>(p, p->nS);
+    p->f = dalloc<double>(p, p->n);
+    p->g = dalloc<double>(p, std::max(p->n, p->m));
+    p->rhat = dalloc<double>(p, p->m);
+    const long long mx = std::max(p->n, p->m);
+    for (auto &s : p->stg) s = dalloc<double>(p, mx);
+    for (auto &s : p->res) s = dalloc<double>(p, mx);
+    for (auto &s : p->cor) s = dalloc<double>(p, mx);
+    for (auto &s : p->ipmv) s = dalloc<double>(p, mx);
+    p->red_part = dalloc<double>(p, 1024);
+    p->mdot_part = dalloc<double>(p, (long long)(kMaxKrylov + 1) * 304);
+    p->gm_coef = dalloc<double>(p, kMaxKrylov + 1);
+    p->scal = dalloc<double>(p, 64);
+    p->status = dalloc<int>(p, 8);
+    ck(cudaMallocHost(&p->h_scal, 256 * sizeof(double)), "cudaMallocHost");
+    for (auto &e : p->ev) ck(cudaEventCreate(&e), "cudaEventCreate");
+    ck(set_dense_smem_limits(200 * 1024), "smem limit");
+    ck(set_schur_smem_limits(200 * 1024), "smem limit");
+    ck(cudaDeviceSynchronize(), "create sync");
+  } catch (const Fail &f) {
+    g_create_err = f.msg;
+    arrowhead_lp_destroy(p);
+    return f.code;
+  } catch (const std::bad_alloc &) {
+    g_create_err = "host allocation failed";
+    arrowhead_lp_destroy(p);
+    return AHLP_ERR_OOM;
+  }
+  *out = p;
+  return AHLP_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// helpers for the compute entry points
+// ===========================================================================
+namespace ahlp {
+
+void ck(cudaError_t e, const char *what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Fail{AHLP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+  }
+}
+
+bool is_device_ptr(const void *ptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// device view of an input vector (copied into staging when it is on the host)
+const double *stage_in(ahlp_problem *p, const double *v, long long n, double *staging) {
+  if (is_device_ptr(v)) return v;
+  if (n > 0) ck(cudaMemcpyAsync(staging, v, n * 8, cudaMemcpyHostToDevice, p->stream), "H2D");
+  return staging;
+}
+
+int set_err(ahlp_problem *p, int code, const std::string &msg) {
+  p->err = msg;
+  return code;
+}
+
+// read k device scalars into p->h_scal (synchronises the stream)
+void read_scalars(ahlp_problem *p, int k) {
+  ck(cudaMemcpyAsync(p->h_scal, p->scal, k * sizeof(double), cudaMemcpyDeviceToHost, p->stream),
+     "D2H scalars");
+  ck(cudaStreamSynchronize(p->stream), "stream sync");
+}
+
+int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
+  p->fac_pivot_tol = pivot_tol;
+  cudaStream_t s = p->stream;
+  // strictly positive point required (Sec. 2.3: x, z > 0)
+  ck(launch_reduce(p, RED_MIN, p->x, nullptr, p->n, p->scal + 0), "reduce");
+  ck(launch_reduce(p, RED_MIN, p->z, nullptr, p->n, p->scal + 1), "reduce");
+  read_scalars(p, 2);
+  if (p->n > 0 && (!(p->h_scal[0] > 0) || !(p->h_scal[1] > 0)))
+    return set_err(p, AHLP_ERR_INVALID_ARG, "kkt_factor: x and z must be strictly positive");
+  p->factored = false;
+  p->fac_delta = delta;
+  p->fac_rho = rho;
+  ck(cudaMemsetAsync(p->status, 0, 8 * sizeof(int), s), "memset");
+  ck(cudaEventRecord(p->ev[0], s), "event");
+  ck(cudaMemsetAsync(p->cdiag0, 0, std::max(p->cdiag_elems, 1LL) * sizeof(double), s), "memset");
+  ck(launch_dscale(p), "dscale");
+  ck(launch_form(p, delta), "form");
+  ck(cudaEventRecord(p->ev[1], s), "event");
+  ck(launch_pchol(p->aug, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s), "pchol");
+  ck(cudaEventRecord(p->ev[2], s), "event");
+  ck(launch_schur_assemble(p, delta, rho), "schur assemble");
+  ck(launch_schur_factor(p), "schur factor");
+  ck(cudaEventRecord(p->ev[3], s), "event");
+  int st[8];
+  ck(cudaMemcpyAsync(st, p->status, sizeof(st), cudaMemcpyDeviceToHost, s), "D2H status");
+  ck(cudaStreamSynchronize(s), "factor sync");
+  cudaEventElapsedTime(&p->stage_ms[0], p->ev[0], p->ev[1]);
+  cudaEventElapsedTime(&p->stage_ms[1], p->ev[1], p->ev[2]);
+  cudaEventElapsedTime(&p->stage_ms[2], p->ev[2], p->ev[3]);
+  p->tiny_pivots = st[1];
+  if (st[0] > 0) {
+    char buf[160];
+    if (st[2] >= 0)
+      snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in block %d row %d", st[2], st[3]);
+    else
+      snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in link pair %d row %d", -1 - st[2], st[3]);
+    return set_err(p, AHLP_ERR_NOT_SPD, buf);
+  }
+  p->factored = true;
+  return AHLP_OK;
+}
+
+// one solve + refinement, all arguments device pointers
+int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double *rc, double *dx,
+               double *dy, double *dz, bool adjoint, ahlp_solve_info *info) {
+  cudaStream_t s = p->stream;
+  ck(cudaEventRecord(p->ev[4], s), "event");
+  ck(launch_solve(p, rd, rp, rc, dx, dy, dz, adjoint), "solve");
+  ck(launch_reduce(p, RED_DOT, rd, rd, p->n, p->scal + 10), "reduce");
+  ck(launch_reduce(p, RED_DOT, rp, rp, p->m, p->scal + 11), "reduce");
+  ck(launch_reduce(p, RED_DOT, rc, rc, p->n, p->scal + 12), "reduce");
+  const long long n = p->n, m = p->m, L = 2 * n + m;
+  // e = r - J d; returns (||e||, ||r||)
+  auto residual_norms = [&]() {
+    ck(launch_residual(p, rd, rp, rc, dx, dy, dz, p->res[0], p->res[1], p->res[2], adjoint),
+       "residual");
+    ck(launch_reduce(p, RED_DOT, p->res[0], p->res[0], n, p->scal + 13), "reduce");
+    ck(launch_reduce(p, RED_DOT, p->res[1], p->res[1], m, p->scal + 14), "reduce");
+    ck(launch_reduce(p, RED_DOT, p->res[2], p->res[2], n, p->scal + 15), "reduce");
+    ck(cudaMemcpyAsync(p->h_scal + 10, p->scal + 10, 6 * sizeof(double), cudaMemcpyDeviceToHost, s),
+       "D2H");
+    ck(cudaStreamSynchronize(s), "sync");
+    return std::make_pair(std::sqrt(p->h_scal[13] + p->h_scal[14] + p->h_scal[15]),
+                          std::sqrt(p->h_scal[10] + p->h_scal[11] + p->h_scal[12]));
+  };
+  auto [en, rn] = residual_norms();
+  double rel = rn > 0 ? en / rn : en;
+  int steps = 0;
+  const double tol = p->opt.refine_tol;
+  const int kmax = std::min(p->opt.refine_max, kMaxKrylov);
+  if (rel > tol && kmax > 0 && en > 0 && std::isfinite(en)) {
+    // Right-preconditioned FGMRES on the unregularised Newton system: the
+    // (regularised) block factorisation is the preconditioner, so the result
+    // solves J d = r itself, not the regularised system.
+    if (p->gm_cap < kmax) {
+      if (p->gm_V) cudaFree(p->gm_V);
+      if (p->gm_Z) cudaFree(p->gm_Z);
+      p->gm_V = p->gm_Z = nullptr;
+      p->gm_cap = 0;
+      ck(cudaMalloc(&p->gm_V, (size_t)(kmax + 1) * L * sizeof(double)), "Krylov alloc");
+      ck(cudaMalloc(&p->gm_Z, (size_t)kmax * L * sizeof(double)), "Krylov alloc");
+      p->gm_cap = kmax;
+    }
+    double *V = p->gm_V, *Z = p->gm_Z;
+    double *hbuf = p->h_scal + 64, *cbuf = p->h_scal + 64 + kMaxKrylov + 1;
+    ck(cudaMemcpyAsync(V, p->res[0], n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+    ck(cudaMemcpyAsync(V + n, p->res[1], m * 8, cudaMemcpyDeviceToDevice, s), "copy");
+    ck(cudaMemcpyAsync(V + n + m, p->res[2], n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+    ck(launch_axpby(V, V, 1.0 / en, 0.0, L, s), "scale");
+    std::vector<double> H((size_t)(kmax + 1) * kmax, 0.0), cs(kmax), sn(kmax), g(kmax + 1, 0.0);
+    g[0] = en;
+    int j = 0;
+    for (; j < kmax;) {
+      double *Vj = V + (long long)j * L, *Zj = Z + (long long)j * L, *W = V + (long long)(j + 1) * L;
+      ck(launch_solve(p, Vj, Vj + n, Vj + n + m, Zj, Zj + n, Zj + n + m, adjoint), "precond");
+      ck(launch_jmul(p, Zj, Zj + n, Zj + n + m, W, W + n, W + n + m, adjoint), "jmul");
+      double *h = &H[(size_t)j * (kmax + 1)];
+      for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+        ck(launch_mdot(p, V, L, j + 1, W, L, p->gm_coef), "mdot");
+        ck(cudaMemcpyAsync(hbuf, p->gm_coef, (j + 1) * 8, cudaMemcpyDeviceToHost, s), "D2H");
+        ck(cudaStreamSynchronize(s), "sync");
+        for (int i = 0; i <= j; ++i) {
+          h[i] += hbuf[i];
+          cbuf[i] = -hbuf[i];
+        }
+        ck(cudaMemcpyAsync(p->gm_coef, cbuf, (j + 1) * 8, cudaMemcpyHostToDevice, s), "H2D");
+        ck(launch_maxpy(V, L, j + 1, p->gm_coef, W, L, s), "maxpy");
+      }
+      ck(launch_reduce(p, RED_DOT, W, W, L, p->scal + 16), "reduce");
+      read_scalars(p, 17);
+      const double hn = std::sqrt(p->h_scal[16]);
+      h[j + 1] = hn;
+      if (hn > 0) ck(launch_axpby(W, W, 1.0 / hn, 0.0, L, s), "scale");
+      for (int i = 0; i < j; ++i) {   // previous Givens rotations
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+      }
+      const double rr = std::hypot(h[j], h[j + 1]);
+      cs[j] = rr > 0 ? h[j] / rr : 1.0;
+      sn[j] = rr > 0 ? h[j + 1] / rr : 0.0;
+      h[j] = rr;
+      h[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++j;
+      if (!(std::fabs(g[j]) > tol * rn) || !(hn > 1e-300 * en)) break;
+    }
+    // y = R^-1 g, d += Z y
+    std::vector<double> y(j, 0.0);
+    for (int i = j - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int k = i + 1; k < j; ++k) t -= H[(size_t)k * (kmax + 1) + i] * y[k];
+      const double d = H[(size_t)i * (kmax + 1) + i];
+      y[i] = d != 0.0 ? t / d : 0.0;
+    }
+    for (int i = 0; i < j; ++i) cbuf[i] = y[i];
+    ck(cudaMemcpyAsync(p->gm_coef, cbuf, j * 8, cudaMemcpyHostToDevice, s), "H2D");
+    ck(launch_maxpy(Z, L, j, p->gm_coef, dx, n, s), "maxpy");
+    ck(launch_maxpy(Z + n, L, j, p->gm_coef, dy, m, s), "maxpy");
+    ck(launch_maxpy(Z + n + m, L, j, p->gm_coef, dz, n, s), "maxpy");
+    steps = j;
+    std::tie(en, rn) = residual_norms();
+    rel = rn > 0 ? en / rn : en;
+  }
+  ck(cudaEventRecord(p->ev[5], s), "event");
+  ck(cudaEventSynchronize(p->ev[5]), "sync");
+  cudaEventElapsedTime(&p->stage_ms[3], p->ev[4], p->ev[5]);
+  if (info) {
+    info->refine_steps = steps;
+    info->rel_residual = rel;
+  }
+  if (!(rel == rel)) return set_err(p, AHLP_ERR_NOT_SPD, "kkt_solve: NaN in the direction");
+  return AHLP_OK;
+}
+
+}  // namespace ahlp
+
+extern "C" {
+
+int kkt_factor(ahlp_problem *p, const double *x, const double *z, double delta, double rho) {
+  if (!p) return AHLP_ERR_INVALID_ARG;
+  if (!x || !z) return set_err(p, AHLP_ERR_INVALID_ARG, "kkt_factor: x and z are required");
+  try {
+    const double *dx = stage_in(p, x, p->n, p->stg[0]);
+    const double *dz = stage_in(p, z, p->n, p->stg[1]);
+    if (p->n > 0) {
+      ck(cudaMemcpyAsync(p->x, dx, p->n * 8, cudaMemcpyDeviceToDevice, p->stream), "copy x");
+      ck(cudaMemcpyAsync(p->z, dz, p->n * 8, cudaMemcpyDeviceToDevice, p->stream), "copy z");
+    }
+    return factor_impl(p, delta < 0 ? p->opt.delta : delta, rho < 0 ? p->opt.rho : rho,
+                       p->opt.pivot_tol);
+  } catch (const Fail &f) {
+    return set_err(p, f.code, f.msg);
+  }
+}
+
+static int solve_entry(ahlp_problem *p, const double *a, const double *b, const double *c,
+                       double *o1, double *o2, double *o3, ahlp_solve_info *info, bool adjoint) {
+  if (!p) return AHLP_ERR_INVALID_ARG;
+  if (!p->factored) return set_err(p, AHLP_ERR_INVALID_ARG, "no factor: call kkt_factor first");
+  if (!a || !b || !c || !o1 || !o2 || !o3)
+    return set_err(p, AHLP_ERR_INVALID_ARG, "NULL vector argument");
+  try {
+    const double *da = stage_in(p, a, p->n, p->stg[0]);
+    const double *db = stage_in(p, b, p->m, p->stg[1]);
+    const double *dc = stage_in(p, c, p->n, p->stg[2]);
+    const bool d1 = is_device_ptr(o1), d2 = is_device_ptr(o2), d3 = is_device_ptr(o3);
+    double *w1 = d1 ? o1 : p->stg[3], *w2 = d2 ? o2 : p->stg[4], *w3 = d3 ? o3 : p->stg[5];
+    int st = solve_impl(p, da, db, dc, w1, w2, w3, adjoint, info);
+    if (!d1) ck(cudaMemcpyAsync(o1, w1, p->n * 8, cudaMemcpyDeviceToHost, p->stream), "D2H");
+    if (!d2) ck(cudaMemcpyAsync(o2, w2, p->m * 8, cudaMemcpyDeviceToHost, p->stream), "D2H");
+    if (!d3) ck(cudaMemcpyAsync(o3, w3, p->n * 8, cudaMemcpyDeviceToHost, p->stream), "D2H");
+    if (!(d1 && d2 && d3)) ck(cudaStreamSynchronize(p->stream), "sync");
+    return st;
+  } catch (const Fail &f) {
+    return set_err(p, f.code, f.msg);
+  }
+}
+
+int kkt_solve(ahlp_problem *p, const double *r_d, const double *r_p, const double *r_c,
+              double *dx, double *dy, double *dz, ahlp_solve_info *info) {
+  return solve_entry(p, r_d, r_p, r_c, dx, dy, dz, info, false);
+}
+
+int kkt_adjoint_solve(ahlp_problem *p, const double *g_x, const double *g_y, const double *g_z,
+                      double *lam_x, double *lam_y, double *lam_z, ahlp_solve_info *info) {
+  return solve_entry(p, g_x, g_y, g_z, lam_x, lam_y, lam_z, info, true);
+}
+
+int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld) {
+  if (!p || !S) return AHLP_ERR_INVALID_ARG;
+  if (!p->factored) return set_err(p, AHLP_ERR_INVALID_ARG, "no factor: call kkt_factor first");
+  const int dim = p->nS;
+  if (ld < dim) return set_err(p, AHLP_ERR_INVALID_ARG, "ld < dimension");
+  try {
+    std::vector<double> Td(p->td_elems), Hd(p->h_elems), Et((size_t)p->nl * p->B),
+        SB((size_t)p->B * p->B);
+    ck(cudaStreamSynchronize(p->stream), "sync");
+    if (!Td.empty()) ck(cudaMemcpy(Td.data(), p->Td_asm, Td.size() * 8, cudaMemcpyDeviceToHost), "D2H");
+    if (!Hd.empty()) ck(cudaMemcpy(Hd.data(), p->Hd_asm, Hd.size() * 8, cudaMemcpyDeviceToHost), "D2H");
+    if (!Et.empty()) ck(cudaMemcpy(Et.data(), p->Et_asm, Et.size() * 8, cudaMemcpyDeviceToHost), "D2H");
+    if (!SB.empty()) ck(cudaMemcpy(SB.data(), p->SB_asm, SB.size() * 8, cudaMemcpyDeviceToHost), "D2H");
+    for (long long cidx = 0; cidx < dim; ++cidx)
+      for (long long r = 0; r < dim; ++r) S[cidx * ld + r] = 0.0;
+    for (int j = 0; j + 1 < p->N; ++j) {
+      const int lj = (int)(p->link_off[j + 1] - p->link_off[j]);
+      const long long o = p->link_off[j];
+      for (int s = 0; s < lj; ++s)
+        for (int r = 0; r < lj; ++r) S[(o + s) * ld + o + r] = Td[p->td_off[j] + (long long)s * lj + r];
+      if (j + 2 < p->N) {
+        const int ln = (int)(p->link_off[j + 2] - p->link_off[j + 1]);
+        const long long on = p->link_off[j + 1];
+        for (int s = 0; s < lj; ++s)
+          for (int r = 0; r < ln; ++r) {
+            const double v = Hd[p->h_off[j] + (long long)s * ln + r];
+            S[(o + s) * ld + on + r] = v;
+            S[(on + r) * ld + o + s] = v;
+          }
+      }
+    }
+    for (int rb = 0; rb < p->B; ++rb) {
+      for (int q = 0; q < p->nl; ++q) {
+        const double v = Et[(size_t)rb * p->nl + q];
+        S[(long long)q * ld + p->nl + rb] = v;
+        S[(long long)(p->nl + rb) * ld + q] = v;
+      }
+      for (int sb = 0; sb < p->B; ++sb) S[(long long)(p->nl + sb) * ld + p->nl + rb] = SB[(size_t)sb * p->B + rb];
+    }
+    return AHLP_OK;
+  } catch (const Fail &f) {
+    return set_err(p, f.code, f.msg);
+  }
+}
+
+int kkt_stage_times(ahlp_problem *p, double *out4) {
+  if (!p || !out4) return AHLP_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i) out4[i] = p->stage_ms[i];
+  return AHLP_OK;
+}
+
+}  // extern "C"

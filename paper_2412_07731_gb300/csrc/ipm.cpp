@@ -1,0 +1,210 @@
+// ipm_solve: infeasible primal-dual Mehrotra predictor-corrector method
+// (Sec. 2 and 2.3).  The host only steers (a handful of scalars per
+// iteration); residuals, KKT factor/solve, ratio tests and updates all run
+// in this library's kernels on the problem's stream.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+
+#include "ahlp_internal.h"
+
+using namespace ahlp;
+
+namespace {
+
+enum {
+  V_X = 0, V_Y, V_Z, V_RP, V_RD, V_RC, V_DXA, V_DYA, V_DZA, V_DX, V_DY, V_DZ
+};
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, const double *z0,
+                         double *x, double *y, double *z, ahlp_result *res) {
+  if (!p) return AHLP_ERR_INVALID_ARG;
+  const double t_start = now_ms();
+  ahlp_result R{};
+  int status = AHLP_OK;
+  try {
+    cudaStream_t s = p->stream;
+    const long long n = p->n, m = p->m;
+    double **v = p->ipmv;
+    double *X = v[V_X], *Y = v[V_Y], *Z = v[V_Z];
+    const double eta = p->opt.eta;
+    const double delta = p->opt.delta, rho = p->opt.rho;
+    // Pivot clamping threshold.  It starts at pivot_tol; when a direction's
+    // Newton residual stays above kEscalate after the Krylov refinement (the
+    // degenerate end game, where the clamped block factors stop being a good
+    // preconditioner) the factor is redone with a 100x coarser threshold, up
+    // to kMaxPivotTol, and the coarser value is kept for later iterations.
+    constexpr double kEscalate = 1e-6, kMaxPivotTol = 1e-8;
+    double ptol = p->opt.pivot_tol;
+    double last_rel = 0.0;
+    auto factor_at = [&](const double *xx, const double *zz) {
+      ck(cudaMemcpyAsync(p->x, xx, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+      ck(cudaMemcpyAsync(p->z, zz, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+      int st = factor_impl(p, delta, rho, ptol);
+      R.ms_factor += p->stage_ms[0] + p->stage_ms[1] + p->stage_ms[2];
+      R.tiny_pivots = p->tiny_pivots;
+      return st;
+    };
+    auto solve = [&](const double *rd, const double *rp, const double *rc, double *dx, double *dy,
+                     double *dz) {
+      ahlp_solve_info info{};
+      int st = solve_impl(p, rd, rp, rc, dx, dy, dz, false, &info);
+      R.ms_solve += p->stage_ms[3];
+      R.refine_steps += info.refine_steps;
+      R.kkt_residual = std::max(R.kkt_residual, info.rel_residual);
+      last_rel = info.rel_residual;
+      return st;
+    };
+    auto can_escalate = [&]() { return !(last_rel <= kEscalate) && ptol * 100.0 <= kMaxPivotTol * 1.0001; };
+    const bool warm = x0 && y0 && z0;
+    if (warm) {
+      const double *a = stage_in(p, x0, n, p->stg[0]);
+      ck(cudaMemcpyAsync(X, a, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+      const double *b = stage_in(p, y0, m, p->stg[1]);
+      ck(cudaMemcpyAsync(Y, b, m * 8, cudaMemcpyDeviceToDevice, s), "copy");
+      const double *c = stage_in(p, z0, n, p->stg[2]);
+      ck(cudaMemcpyAsync(Z, c, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+    } else {
+      // Mehrotra's starting point from two solves at D = I
+      double *ones = v[V_RC], *zero_n = v[V_RD], *zero_m = v[V_RP];
+      ck(launch_fill(ones, 1.0, n, s), "fill");
+      ck(launch_fill(zero_n, 0.0, n, s), "fill");
+      ck(launch_fill(zero_m, 0.0, m, s), "fill");
+      int st = factor_at(ones, ones);
+      if (st != AHLP_OK) throw Fail{st, p->err};
+      ck(launch_fill(ones, 0.0, n, s), "fill");   // r_c = 0 from here on
+      // x~ = A'(AA')^-1 b
+      st = solve(zero_n, p->b, ones, v[V_DX], v[V_DY], v[V_DZ]);
+      if (st != AHLP_OK) throw Fail{st, p->err};
+      // y~ = (AA')^-1 A c, z~ = c - A'y~ (= the dz of this solve)
+      st = solve(p->c, zero_m, ones, v[V_DXA], Y, Z);
+      if (st != AHLP_OK) throw Fail{st, p->err};
+      ck(cudaMemcpyAsync(X, v[V_DX], n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+      ck(launch_reduce(p, RED_MIN, X, nullptr, n, p->scal + 0), "reduce");
+      ck(launch_reduce(p, RED_MIN, Z, nullptr, n, p->scal + 1), "reduce");
+      read_scalars(p, 2);
+      ck(launch_add_scalar(X, X, std::max(-1.5 * p->h_scal[0], 0.0), n, s), "shift");
+      ck(launch_add_scalar(Z, Z, std::max(-1.5 * p->h_scal[1], 0.0), n, s), "shift");
+      ck(launch_reduce(p, RED_DOT, X, Z, n, p->scal + 0), "reduce");
+      ck(launch_reduce(p, RED_SUM, X, nullptr, n, p->scal + 1), "reduce");
+      ck(launch_reduce(p, RED_SUM, Z, nullptr, n, p->scal + 2), "reduce");
+      read_scalars(p, 3);
+      const double xz = p->h_scal[0], sx = p->h_scal[1], sz = p->h_scal[2];
+      const double ax = sz > 0 ? 0.5 * xz / sz : 1.0, az = sx > 0 ? 0.5 * xz / sx : 1.0;
+      ck(launch_add_scalar(X, X, ax > 0 ? ax : 1.0, n, s), "shift");
+      ck(launch_add_scalar(Z, Z, az > 0 ? az : 1.0, n, s), "shift");
+    }
+    int it = 0;
+    status = AHLP_ERR_MAX_ITER;
+    for (it = 0;; ++it) {
+      // residuals r_p = b - Ax, r_d = c - A'y - z
+      ck(launch_spmv(p->A_rp, p->A_ci, p->A_v, m, X, v[V_RP], -1.0, p->b, s), "spmv");
+      ck(launch_spmv(p->AT_rp, p->AT_ci, p->AT_v, n, Y, v[V_RD], -1.0, p->c, s), "spmv");
+      ck(launch_axpby(v[V_RD], Z, -1.0, 1.0, n, s), "axpby");
+      ck(launch_reduce(p, RED_MAXABS, v[V_RP], nullptr, m, p->scal + 0), "reduce");
+      ck(launch_reduce(p, RED_MAXABS, v[V_RD], nullptr, n, p->scal + 1), "reduce");
+      ck(launch_reduce(p, RED_DOT, p->c, X, n, p->scal + 2), "reduce");
+      ck(launch_reduce(p, RED_DOT, p->b, Y, m, p->scal + 3), "reduce");
+      ck(launch_reduce(p, RED_DOT, X, Z, n, p->scal + 4), "reduce");
+      ck(launch_reduce(p, RED_MAXABS, X, nullptr, n, p->scal + 5), "reduce");
+      ck(launch_reduce(p, RED_MAXABS, Y, nullptr, m, p->scal + 6), "reduce");
+      read_scalars(p, 7);
+      const double *hs = p->h_scal;
+      R.pinf = hs[0] / (1.0 + p->bnorm_inf);
+      R.dinf = hs[1] / (1.0 + p->cnorm_inf);
+      R.pobj = hs[2];
+      R.dobj = hs[3];
+      R.rel_gap = std::fabs(hs[2] - hs[3]) / (1.0 + std::fabs(hs[2]));
+      R.mu = n > 0 ? hs[4] / n : 0.0;
+      R.iterations = it;
+      if (p->opt.verbose)
+        printf("ipm %3d  pobj %+.10e  dobj %+.10e  pinf %.2e  dinf %.2e  gap %.2e  mu %.2e\n", it,
+               R.pobj, R.dobj, R.pinf, R.dinf, R.rel_gap, R.mu);
+      if (!(R.pinf == R.pinf) || !(R.dinf == R.dinf)) {
+        status = AHLP_ERR_NOT_SPD;
+        p->err = "ipm_solve: NaN in the iterate";
+        break;
+      }
+      if (R.pinf <= p->opt.tol && R.dinf <= p->opt.tol && R.rel_gap <= p->opt.tol) {
+        status = AHLP_OK;
+        break;
+      }
+      if (hs[5] > 1e30 || hs[6] > 1e30) {
+        status = AHLP_ERR_INFEASIBLE;
+        p->err = "ipm_solve: iterates diverge (LP infeasible or unbounded)";
+        break;
+      }
+      if (it >= p->opt.max_iter) {
+        status = AHLP_ERR_MAX_ITER;
+        p->err = "ipm_solve: iteration limit reached";
+        break;
+      }
+      const double mu = R.mu;
+      for (;;) {
+        int st = factor_at(X, Z);
+        if (st != AHLP_OK) throw Fail{st, p->err};
+        // predictor: r_c = -XZe
+        ck(launch_mul(v[V_RC], X, Z, -1.0, n, s), "mul");
+        st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DXA], v[V_DYA], v[V_DZA]);
+        if (st != AHLP_OK) throw Fail{st, p->err};
+        if (can_escalate()) {
+          ptol *= 100.0;
+          ++R.escalations;
+          continue;
+        }
+        ck(launch_reduce(p, RED_MINSTEP, X, v[V_DXA], n, p->scal + 0), "reduce");
+        ck(launch_reduce(p, RED_MINSTEP, Z, v[V_DZA], n, p->scal + 1), "reduce");
+        read_scalars(p, 2);
+        const double apa = std::min(1.0, p->h_scal[0]), ada = std::min(1.0, p->h_scal[1]);
+        ck(launch_step_dot(X, v[V_DXA], apa, Z, v[V_DZA], ada, n, p->red_part, p->scal + 0, s),
+           "reduce");
+        read_scalars(p, 1);
+        const double mu_aff = p->h_scal[0] / n;
+        const double sigma = std::pow(mu_aff / mu, 3.0);
+        // corrector: r_c = sigma mu e - XZe - dXa dZa e
+        ck(launch_ipm_rc(v[V_RC], X, Z, v[V_DXA], v[V_DZA], sigma * mu, n, s), "rc");
+        st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DX], v[V_DY], v[V_DZ]);
+        if (st != AHLP_OK) throw Fail{st, p->err};
+        if (can_escalate()) {
+          ptol *= 100.0;
+          ++R.escalations;
+          continue;
+        }
+        break;
+      }
+      ck(launch_reduce(p, RED_MINSTEP, X, v[V_DX], n, p->scal + 0), "reduce");
+      ck(launch_reduce(p, RED_MINSTEP, Z, v[V_DZ], n, p->scal + 1), "reduce");
+      read_scalars(p, 2);
+      const double ap = std::min(1.0, eta * p->h_scal[0]), ad = std::min(1.0, eta * p->h_scal[1]);
+      ck(launch_axpby(X, v[V_DX], ap, 1.0, n, s), "update");
+      ck(launch_axpby(Y, v[V_DY], ad, 1.0, m, s), "update");
+      ck(launch_axpby(Z, v[V_DZ], ad, 1.0, n, s), "update");
+    }
+    // outputs
+    auto put = [&](double *dst, const double *src, long long len) {
+      if (!dst || len == 0) return;
+      ck(cudaMemcpyAsync(dst, src, len * 8,
+                         is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
+         "copy out");
+    };
+    put(x, X, n);
+    put(y, Y, m);
+    put(z, Z, n);
+    ck(cudaStreamSynchronize(s), "sync");
+  } catch (const Fail &f) {
+    status = f.code;
+    p->err = f.msg;
+  }
+  R.status = status;
+  R.ms_total = now_ms() - t_start;
+  if (res) *res = R;
+  return status;
+}

@@ -1,0 +1,587 @@
+// Schur complement of the block system (App. A) and the solve pipeline.
+//
+// Ordering of the Schur unknowns: [local link rows (pair 1..N-1) | x_0 | y_g].
+// With local links the matrix is
+//     S = [ T   E' ]     T block tridiagonal: T_j (l_j x l_j) on the diagonal,
+//         [ E   SB ]     H_j (l_{j+1} x l_j) below it; E, SB the dense border.
+// T is positive definite and SB quasi-definite (x_0 part negative, y_g part
+// positive), so S = [L_T 0; Z' I] diag(I, SB - Z'Z) [L_T' Z; 0 I] with
+// Z = L_T^-1 E' is factored by a block Cholesky along the link chain
+// followed by a partial Cholesky of -(SB - Z'Z) over the x_0 pivots and a
+// Cholesky of the remaining y_g Schur complement.
+#include <algorithm>
+
+#include "ahlp_internal.h"
+
+namespace ahlp {
+
+cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,
+                        bool forward, cudaStream_t s);
+
+namespace {
+
+struct SArgs {
+  const double *aug;
+  const BlkInfo *blk;
+  const SchurBlk *sb;
+  int N, n0, mg, B, nl;
+  const long long *td_off, *h_off, *link_off;
+  const int *l;
+  double *Td, *Hd, *Et, *SB, *Td_diag0;
+  const double *dscale;
+  long long x0off;
+  double delta, rho;
+  const double *cdiag0;   // per-block corner diagonal before elimination
+  double *sb_ref;         // reference diagonal of the border pivots
+};
+
+// entry (r, c) of block i's Schur contribution, local indices, symmetric
+__device__ __forceinline__ double cget(const double *aug, const BlkInfo &bi, int m, int r, int c) {
+  const int R = m + max(r, c), C = m + min(r, c);
+  return aug[bi.base + (long long)C * bi.lda + R];
+}
+
+__device__ __forceinline__ int border_local(const SchurBlk &s, int n0, int rb) {
+  return rb < n0 ? rb : n0 + s.lprev + s.lnext + (rb - n0);
+}
+
+__global__ void assemble_T_kernel(SArgs A) {
+  const int j = blockIdx.y;
+  const int lj = A.l[j];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= lj * lj) return;
+  const int r = idx % lj, s = idx / lj;
+  const BlkInfo b0 = A.blk[j], b1 = A.blk[j + 1];
+  const SchurBlk s0 = A.sb[j], s1 = A.sb[j + 1];
+  double v = cget(A.aug, b0, s0.m, A.n0 + s0.lprev + r, A.n0 + s0.lprev + s)   // block j, next
+           + cget(A.aug, b1, s1.m, A.n0 + r, A.n0 + s);                        // block j+1, prev
+  if (r == s) {
+    v += A.delta;
+    // pivot reference: the link row's diagonal of the full normal matrix,
+    // sum_i (U_i D_i U_i')_qq + delta, i.e. before the block eliminations
+    // cancel most of it
+    A.Td_diag0[A.link_off[j] + r] = A.cdiag0[b0.cdoff + A.n0 + s0.lprev + r] +
+                                    A.cdiag0[b1.cdoff + A.n0 + r] + A.delta;
+  }
+  A.Td[A.td_off[j] + (long long)s * lj + r] = v;
+}
+
+__global__ void assemble_H_kernel(SArgs A) {
+  const int j = blockIdx.y;   // H_j couples pair j+1 (rows) and pair j (cols) through block j+1
+  const int lr = A.l[j + 1], lc = A.l[j];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= lr * lc) return;
+  const int r = idx % lr, s = idx / lr;
+  const BlkInfo b1 = A.blk[j + 1];
+  const SchurBlk s1 = A.sb[j + 1];
+  A.Hd[A.h_off[j] + (long long)s * lr + r] =
+      cget(A.aug, b1, s1.m, A.n0 + s1.lprev + r, A.n0 + s);
+}
+
+__global__ void assemble_E_kernel(SArgs A) {
+  const int j = blockIdx.y;
+  const int lj = A.l[j];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= lj * A.B) return;
+  const int r = idx % lj, rb = idx / lj;
+  const BlkInfo b0 = A.blk[j], b1 = A.blk[j + 1];
+  const SchurBlk s0 = A.sb[j], s1 = A.sb[j + 1];
+  const double v = cget(A.aug, b0, s0.m, border_local(s0, A.n0, rb), A.n0 + s0.lprev + r) +
+                   cget(A.aug, b1, s1.m, border_local(s1, A.n0, rb), A.n0 + r);
+  A.Et[(long long)rb * A.nl + A.link_off[j] + r] = v;
+}
+
+__global__ void assemble_SB_kernel(SArgs A) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= A.B * A.B) return;
+  const int rb = idx % A.B, sb = idx / A.B;
+  double v = 0.0;
+  for (int i = 0; i < A.N; ++i) {   // fixed order over blocks
+    const SchurBlk s = A.sb[i];
+    v += cget(A.aug, A.blk[i], s.m, border_local(s, A.n0, rb), border_local(s, A.n0, sb));
+  }
+  if (rb == sb) v += (rb < A.n0) ? (-1.0 / A.dscale[A.x0off + rb] - A.rho) : A.delta;
+  A.SB[(long long)sb * A.B + rb] = v;
+  if (rb == sb && rb >= A.n0) {   // y_g pivot reference, as for the link rows
+    double ref = A.delta;
+    for (int i = 0; i < A.N; ++i) {
+      const SchurBlk s = A.sb[i];
+      ref += A.cdiag0[A.blk[i].cdoff + border_local(s, A.n0, rb)];
+    }
+    A.sb_ref[rb] = ref;
+  }
+}
+
+__global__ void scatter_add_kernel(double *dst, const long long *idx, const double *val,
+                                   long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[idx[i]] += val[i];
+}
+
+// --------------------------------------------------------------------------
+// link chain: block Cholesky of T, X_j = H_j L_j^-T, Z = L_T^-1 E'
+// one CTA, sequential over the chain
+// --------------------------------------------------------------------------
+struct CArgs {
+  int N, B, nl;
+  const int *l;
+  const long long *td_off, *h_off, *link_off;
+  double *Td, *Hd, *Et;
+  const double *Td_diag0;
+  double tol;
+  int *status;
+};
+
+__global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
+  extern __shared__ double T[];   // lmax * lmax
+  __shared__ double s_inv;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int j = 0; j < A.N - 1; ++j) {
+    const int lj = A.l[j];
+    if (lj == 0) continue;
+    const int lp = (j > 0) ? A.l[j - 1] : 0;
+    double *Tg = A.Td + A.td_off[j];
+    for (int i = tid; i < lj * lj; i += bd) T[i] = Tg[i];
+    __syncthreads();
+    if (lp > 0) {
+      const double *X = A.Hd + A.h_off[j - 1];   // l_j x l_{j-1}, ld l_j
+      for (int i = tid; i < lj * lj; i += bd) {
+        const int r = i % lj, s = i / lj;
+        if (r < s) continue;
+        double acc = 0.0;
+        for (int c = 0; c < lp; ++c) acc = fma(X[r + (long long)c * lj], X[s + (long long)c * lj], acc);
+        T[i] -= acc;
+      }
+    }
+    __syncthreads();
+    for (int c = 0; c < lj; ++c) {
+      if (tid == 0) {
+        double piv = T[c + c * lj];
+        pivot_fix(piv, A.Td_diag0[A.link_off[j] + c], A.tol, A.status, -1 - j, c);
+        const double lcc = sqrt(piv);
+        T[c + c * lj] = lcc;
+        s_inv = 1.0 / lcc;
+      }
+      __syncthreads();
+      for (int r = c + 1 + tid; r < lj; r += bd) T[r + c * lj] *= s_inv;
+      __syncthreads();
+      const int m = lj - c - 1;
+      for (int i = tid; i < m * m; i += bd) {
+        const int rr = i % m, ss = i / m;
+        if (rr >= ss) T[(c + 1 + rr) + (c + 1 + ss) * lj] -= T[(c + 1 + rr) + c * lj] * T[(c + 1 + ss) + c * lj];
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < lj * lj; i += bd) {
+      const int r = i % lj, s = i / lj;
+      Tg[i] = (r >= s) ? T[i] : 0.0;
+    }
+    // Z_j = L_j^-1 (E_j' - X_{j-1} Z_{j-1}), one column of Z per thread
+    for (int rb = tid; rb < A.B; rb += bd) {
+      double *zc = A.Et + (long long)rb * A.nl + A.link_off[j];
+      if (lp > 0) {
+        const double *X = A.Hd + A.h_off[j - 1];
+        const double *zp = A.Et + (long long)rb * A.nl + A.link_off[j - 1];
+        for (int r = 0; r < lj; ++r) {
+          double acc = 0.0;
+          for (int c = 0; c < lp; ++c) acc = fma(X[r + (long long)c * lj], zp[c], acc);
+          zc[r] -= acc;
+        }
+      }
+      for (int r = 0; r < lj; ++r) {
+        double acc = zc[r];
+        for (int c = 0; c < r; ++c) acc -= T[r + c * lj] * zc[c];
+        zc[r] = acc / T[r + r * lj];
+      }
+    }
+    // X_j = H_j L_j^-T, one row per thread
+    if (j < A.N - 2) {
+      const int ln = A.l[j + 1];
+      double *H = A.Hd + A.h_off[j];   // l_{j+1} x l_j, ld l_{j+1}
+      for (int r = tid; r < ln; r += bd) {
+        for (int c = 0; c < lj; ++c) {
+          double acc = H[r + (long long)c * ln];
+          for (int q = 0; q < c; ++q) acc -= H[r + (long long)q * ln] * T[c + q * lj];
+          H[r + (long long)c * ln] = acc / T[c + c * lj];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// SB' = SB - Z'Z, written negated into the lower part of the border buffer
+__global__ void border_prep_kernel(const double *SB, const double *Z, int B, int nl, double *bd,
+                                   int ld, double *bdiag0) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= B * B) return;
+  const int rb = idx % B, sb = idx / B;
+  if (rb < sb) return;
+  double acc = SB[(long long)sb * B + rb];
+  const double *zr = Z + (long long)rb * nl, *zs = Z + (long long)sb * nl;
+  for (int q = 0; q < nl; ++q) acc -= zr[q] * zs[q];
+  bd[(long long)sb * ld + rb] = -acc;
+  if (rb == sb) bdiag0[rb] = -acc;
+}
+
+// after eliminating the x_0 pivots the y_g corner holds -P; flip its sign
+__global__ void negate_corner_kernel(double *bd, int ld, int n0, int mg, double *bdiag0,
+                                     const double *sb_ref) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= mg * mg) return;
+  const int r = idx % mg, s = idx / mg;
+  if (r < s) return;
+  double *e = bd + (long long)(n0 + s) * ld + n0 + r;
+  *e = -*e;
+  if (r == s) {
+    const double ref = sb_ref[n0 + r];
+    bdiag0[n0 + r] = ref > 0.0 ? ref : *e;
+  }
+}
+
+// --------------------------------------------------------------------------
+// solve pipeline kernels
+// --------------------------------------------------------------------------
+// f = r_d - X^-1 r_c (forward) or g_x - Z X^-1 g_z (adjoint); g = D f on block columns
+__global__ void prep_f_kernel(double *f, double *g, const double *rd, const double *rc,
+                              const double *x, const double *z, const double *d,
+                              const unsigned char *is_x0, long long n, int adjoint) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double fi = adjoint ? rd[i] - z[i] * rc[i] / x[i] : rd[i] - rc[i] / x[i];
+  f[i] = fi;
+  g[i] = is_x0[i] ? 0.0 : d[i] * fi;
+}
+
+__global__ void pack_rhs_kernel(const BlkInfo *blk, const SchurBlk *sb, const long long *yoff,
+                                const double *rhat, double *vec) {
+  const int i = blockIdx.y;
+  const BlkInfo bi = blk[i];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= bi.a) return;
+  vec[bi.voff + r] = (r < sb[i].m) ? rhat[yoff[i] + r] : 0.0;
+}
+
+struct RArgs {
+  int N, n0, mg, B, nl;
+  const BlkInfo *blk;
+  const SchurBlk *sb;
+  const int *link_pair;
+  const double *vec, *rhat, *f;
+  long long msum, x0off;
+  double *svec;
+};
+
+// Schur right-hand side: base rows plus every block's -L21 w_i, fixed order
+__global__ void schur_rhs_kernel(RArgs A) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= A.nl + A.B) return;
+  double v;
+  if (q < A.nl) {
+    const int j = A.link_pair[q];
+    const SchurBlk s0 = A.sb[j], s1 = A.sb[j + 1];
+    const int r = q - s0.link_next_off;
+    v = A.rhat[A.msum + q];
+    v += A.vec[A.blk[j].voff + s0.m + A.n0 + s0.lprev + r];
+    v += A.vec[A.blk[j + 1].voff + s1.m + A.n0 + r];
+  } else {
+    const int rb = q - A.nl;
+    v = (rb < A.n0) ? A.f[A.x0off + rb] : A.rhat[A.msum + A.nl + (rb - A.n0)];
+    for (int i = 0; i < A.N; ++i) {
+      const SchurBlk s = A.sb[i];
+      v += A.vec[A.blk[i].voff + s.m + border_local(s, A.n0, rb)];
+    }
+  }
+  A.svec[q] = v;
+}
+
+// forward (dir = 0) or backward (dir = 1) solve with the block-bidiagonal L_T
+__global__ void __launch_bounds__(256) chain_solve_kernel(CArgs A, double *u, int dir) {
+  const int tid = threadIdx.x;
+  if (dir == 0) {
+    for (int j = 0; j < A.N - 1; ++j) {
+      const int lj = A.l[j];
+      if (lj == 0) continue;
+      const int lp = j > 0 ? A.l[j - 1] : 0;
+      double *uj = u + A.link_off[j];
+      if (lp > 0) {
+        const double *X = A.Hd + A.h_off[j - 1];
+        const double *up = u + A.link_off[j - 1];
+        for (int r = tid; r < lj; r += blockDim.x) {
+          double acc = 0.0;
+          for (int c = 0; c < lp; ++c) acc = fma(X[r + (long long)c * lj], up[c], acc);
+          uj[r] -= acc;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const double *L = A.Td + A.td_off[j];
+        for (int r = 0; r < lj; ++r) {
+          double acc = uj[r];
+          for (int c = 0; c < r; ++c) acc -= L[r + (long long)c * lj] * uj[c];
+          uj[r] = acc / L[r + (long long)r * lj];
+        }
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int j = A.N - 2; j >= 0; --j) {
+      const int lj = A.l[j];
+      if (lj == 0) continue;
+      double *uj = u + A.link_off[j];
+      if (j < A.N - 2 && A.l[j + 1] > 0) {
+        const int ln = A.l[j + 1];
+        const double *X = A.Hd + A.h_off[j];   // l_{j+1} x l_j
+        const double *un = u + A.link_off[j + 1];
+        for (int c = tid; c < lj; c += blockDim.x) {
+          double acc = 0.0;
+          for (int r = 0; r < ln; ++r) acc = fma(X[r + (long long)c * ln], un[r], acc);
+          uj[c] -= acc;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const double *L = A.Td + A.td_off[j];
+        for (int r = lj - 1; r >= 0; --r) {
+          double acc = uj[r];
+          for (int c = r + 1; c < lj; ++c) acc -= L[c + (long long)r * lj] * uj[c];
+          uj[r] = acc / L[r + (long long)r * lj];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// border rhs: sB -= Z' uT      (one thread per border row)
+__global__ void border_rhs_kernel(const double *Z, int B, int nl, double *svec) {
+  const int rb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rb >= B) return;
+  const double *zc = Z + (long long)rb * nl;
+  double acc = 0.0;
+  for (int q = 0; q < nl; ++q) acc = fma(zc[q], svec[q], acc);
+  svec[nl + rb] -= acc;
+}
+
+// uT -= Z sB      (one thread per link row)
+__global__ void link_back_kernel(const double *Z, int B, int nl, double *svec) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nl) return;
+  double acc = 0.0;
+  for (int rb = 0; rb < B; ++rb) acc = fma(Z[(long long)rb * nl + q], svec[nl + rb], acc);
+  svec[q] -= acc;
+}
+
+__global__ void scale_kernel(double *v, double a, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] *= a;
+}
+
+__global__ void gather_schur_kernel(const BlkInfo *blk, const SchurBlk *sb, const int *kmap,
+                                    const long long *kmap_off, const double *svec, double *vec) {
+  const int i = blockIdx.y;
+  const SchurBlk s = sb[i];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s.k) return;
+  vec[blk[i].voff + s.m + t] = svec[kmap[kmap_off[i] + t]];
+}
+
+__global__ void scatter_dy_kernel(const BlkInfo *blk, const SchurBlk *sb, const long long *yoff,
+                                  const double *vec, double *dy) {
+  const int i = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= sb[i].m) return;
+  dy[yoff[i] + r] = vec[blk[i].voff + r];
+}
+
+__global__ void schur_dy_kernel(const double *svec, int nl, int n0, int mg, long long msum,
+                                double *dy) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nl) dy[msum + q] = svec[q];
+  else if (q < nl + mg) dy[msum + q] = svec[n0 + q];
+}
+
+// dx = (A'dy - f) / (1/d + rho[x0]);  dz = X^-1 (r_c - Z dx)  or  X^-1 (g_z - dx)
+__global__ void finish_kernel(double *dx, double *dz, const double *aty, const double *f,
+                              const double *d, const double *x, const double *z, const double *rc,
+                              const unsigned char *is_x0, double rho, long long n, int adjoint) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double dxi = (aty[i] - f[i]) / (1.0 / d[i] + (is_x0[i] ? rho : 0.0));
+  dx[i] = dxi;
+  dz[i] = adjoint ? (rc[i] - dxi) / x[i] : (rc[i] - z[i] * dxi) / x[i];
+}
+
+// residual blocks of J d = r (forward) or J' d = r (adjoint)
+__global__ void residual_tail_kernel(double *e_d, double *e_c, const double *dx,
+                                     const double *dz, const double *rc, const double *x,
+                                     const double *z, long long n, int adjoint) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (adjoint) {
+    e_d[i] -= z[i] * dz[i];
+    e_c[i] = rc[i] - dx[i] - x[i] * dz[i];
+  } else {
+    e_d[i] -= dz[i];
+    e_c[i] = rc[i] - z[i] * dx[i] - x[i] * dz[i];
+  }
+}
+
+inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+SArgs sargs(ahlp_problem *p, double delta, double rho) {
+  return SArgs{p->aug, p->blk, p->sblk, p->N, p->n0, p->mg, p->B, p->nl,
+               p->td_off_d, p->h_off_d, p->link_off_d, p->l_d,
+               p->Td, p->Hd, p->Et, p->SB, p->Td_diag0, p->dscale,
+               p->xoff[p->N], delta, rho, p->cdiag0, p->sb_ref};
+}
+
+CArgs cargs(ahlp_problem *p) {
+  return CArgs{p->N, p->B, p->nl, p->l_d, p->td_off_d, p->h_off_d, p->link_off_d,
+               p->Td, p->Hd, p->Et, p->Td_diag0, p->fac_pivot_tol, p->status};
+}
+
+}  // namespace
+
+cudaError_t launch_schur_assemble(ahlp_problem *p, double delta, double rho) {
+  cudaStream_t s = p->stream;
+  SArgs A = sargs(p, delta, rho);
+  int lmax = 0;
+  for (int j = 0; j + 1 < p->N; ++j) lmax = std::max(lmax, (int)(p->link_off[j + 1] - p->link_off[j]));
+  if (p->N > 1 && lmax > 0) {
+    assemble_T_kernel<<<dim3(nb((long long)lmax * lmax, 256), p->N - 1), 256, 0, s>>>(A);
+    if (p->N > 2)
+      assemble_H_kernel<<<dim3(nb((long long)lmax * lmax, 256), p->N - 2), 256, 0, s>>>(A);
+    if (p->B > 0)
+      assemble_E_kernel<<<dim3(nb((long long)lmax * p->B, 256), p->N - 1), 256, 0, s>>>(A);
+  }
+  if (p->B > 0) assemble_SB_kernel<<<nb((long long)p->B * p->B, 256), 256, 0, s>>>(A);
+  if (p->nf0 > 0) scatter_add_kernel<<<nb(p->nf0, 256), 256, 0, s>>>(p->Et, p->f0_idx, p->f0_val, p->nf0);
+  if (p->nfg0 > 0)
+    scatter_add_kernel<<<nb(p->nfg0, 256), 256, 0, s>>>(p->SB, p->fg0_idx, p->fg0_val, p->nfg0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // keep the assembled matrix for diagnostics
+  if (p->td_elems) cudaMemcpyAsync(p->Td_asm, p->Td, p->td_elems * 8, cudaMemcpyDeviceToDevice, s);
+  if (p->h_elems) cudaMemcpyAsync(p->Hd_asm, p->Hd, p->h_elems * 8, cudaMemcpyDeviceToDevice, s);
+  if ((long long)p->nl * p->B)
+    cudaMemcpyAsync(p->Et_asm, p->Et, (size_t)p->nl * p->B * 8, cudaMemcpyDeviceToDevice, s);
+  if (p->B) cudaMemcpyAsync(p->SB_asm, p->SB, (size_t)p->B * p->B * 8, cudaMemcpyDeviceToDevice, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schur_factor(ahlp_problem *p) {
+  cudaStream_t s = p->stream;
+  int lmax = 0;
+  for (int j = 0; j + 1 < p->N; ++j) lmax = std::max(lmax, (int)(p->link_off[j + 1] - p->link_off[j]));
+  if (p->N > 1 && lmax > 0) {
+    chain_factor_kernel<<<1, 512, (size_t)lmax * lmax * 8, s>>>(cargs(p));
+  }
+  if (p->B > 0) {
+    border_prep_kernel<<<nb((long long)p->B * p->B, 256), 256, 0, s>>>(
+        p->SB, p->Et, p->B, p->nl, p->border, p->Bld, p->border_diag0);
+    std::vector<BlkInfo> hx(1, p->h_bx);
+    if (p->n0 > 0) {
+      cudaError_t e = launch_pchol(p->border, p->bx_info, hx, p->border_diag0, p->fac_pivot_tol,
+                                   p->status, s);
+      if (e != cudaSuccess) return e;
+    }
+    if (p->mg > 0) {
+      negate_corner_kernel<<<nb((long long)p->mg * p->mg, 256), 256, 0, s>>>(
+          p->border, p->Bld, p->n0, p->mg, p->border_diag0, p->sb_ref);
+      std::vector<BlkInfo> hp(1, p->h_bp);
+      cudaError_t e = launch_pchol(p->border, p->bp_info, hp, p->border_diag0, p->fac_pivot_tol,
+                                   p->status, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
+                         const double *r_c, double *dx, double *dy, double *dz, bool adjoint) {
+  cudaStream_t s = p->stream;
+  const long long n = p->n;
+  cudaError_t e;
+  prep_f_kernel<<<nb(n, 256), 256, 0, s>>>(p->f, p->g, r_d, r_c, p->x, p->z, p->dscale, p->is_x0,
+                                          n, adjoint ? 1 : 0);
+  e = launch_spmv(p->A_rp, p->A_ci, p->A_v, p->m, p->g, p->rhat, 1.0, r_p, s);
+  if (e != cudaSuccess) return e;
+  pack_rhs_kernel<<<dim3(nb(p->amax, 256), p->N), 256, 0, s>>>(p->blk, p->sblk, p->yoff_d,
+                                                                p->rhat, p->vec);
+  e = launch_ptri(p->aug, p->blk, p->N, p->amax, p->vec, true, s);
+  if (e != cudaSuccess) return e;
+  if (p->nS > 0) {
+    int lmax = 0;
+    for (int j = 0; j + 1 < p->N; ++j)
+      lmax = std::max(lmax, (int)(p->link_off[j + 1] - p->link_off[j]));
+    RArgs R{p->N, p->n0, p->mg, p->B, p->nl, p->blk, p->sblk,
+            p->link_pair_d, p->vec, p->rhat, p->f, p->msum,
+            p->xoff[p->N], p->svec};
+    schur_rhs_kernel<<<nb(p->nS, 256), 256, 0, s>>>(R);
+    CArgs C = cargs(p);
+    if (p->nl > 0 && lmax > 0) chain_solve_kernel<<<1, 256, 0, s>>>(C, p->svec, 0);
+    if (p->B > 0) {
+      if (p->nl > 0) border_rhs_kernel<<<nb(p->B, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
+      double *sb = p->svec + p->nl;
+      if (p->n0 > 0) {
+        e = launch_ptri(p->border, p->bx_info, 1, p->B, sb, true, s);
+        if (e != cudaSuccess) return e;
+        scale_kernel<<<nb(p->n0, 256), 256, 0, s>>>(sb, -1.0, p->n0);
+      }
+      if (p->mg > 0) {
+        e = launch_ptri(p->border, p->bp_info, 1, p->B, sb, true, s);
+        if (e != cudaSuccess) return e;
+        e = launch_ptri(p->border, p->bp_info, 1, p->B, sb, false, s);
+        if (e != cudaSuccess) return e;
+      }
+      if (p->n0 > 0) {
+        e = launch_ptri(p->border, p->bx_info, 1, p->B, sb, false, s);
+        if (e != cudaSuccess) return e;
+      }
+      if (p->nl > 0) link_back_kernel<<<nb(p->nl, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
+    }
+    if (p->nl > 0 && lmax > 0) chain_solve_kernel<<<1, 256, 0, s>>>(C, p->svec, 1);
+    int kmax = 0;
+    for (int k : p->ki) kmax = std::max(kmax, k);
+    if (kmax > 0)
+      gather_schur_kernel<<<dim3(nb(kmax, 256), p->N), 256, 0, s>>>(p->blk, p->sblk, p->kmap,
+                                                                  p->kmap_off_d, p->svec, p->vec);
+  }
+  e = launch_ptri(p->aug, p->blk, p->N, p->amax, p->vec, false, s);
+  if (e != cudaSuccess) return e;
+  int mmax = 0;
+  for (int v : p->mi) mmax = std::max(mmax, v);
+  scatter_dy_kernel<<<dim3(nb(mmax, 256), p->N), 256, 0, s>>>(
+      p->blk, p->sblk, p->yoff_d, p->vec, dy);
+  if (p->nl + p->mg > 0)
+    schur_dy_kernel<<<nb(p->nl + p->mg, 256), 256, 0, s>>>(p->svec, p->nl, p->n0, p->mg, p->msum,
+                                                          dy);
+  // dx, dz
+  e = launch_spmv(p->AT_rp, p->AT_ci, p->AT_v, n, dy, p->g, 1.0, nullptr, s);
+  if (e != cudaSuccess) return e;
+  finish_kernel<<<nb(n, 256), 256, 0, s>>>(dx, dz, p->g, p->f, p->dscale, p->x, p->z, r_c,
+                                          p->is_x0, p->fac_rho, n, adjoint ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(ahlp_problem *p, const double *r_d, const double *r_p,
+                            const double *r_c, const double *dx, const double *dy,
+                            const double *dz, double *e_d, double *e_p, double *e_c,
+                            bool adjoint) {
+  cudaStream_t s = p->stream;
+  cudaError_t e = launch_spmv(p->AT_rp, p->AT_ci, p->AT_v, p->n, dy, e_d, -1.0, r_d, s);
+  if (e != cudaSuccess) return e;
+  e = launch_spmv(p->A_rp, p->A_ci, p->A_v, p->m, dx, e_p, -1.0, r_p, s);
+  if (e != cudaSuccess) return e;
+  residual_tail_kernel<<<nb(p->n, 256), 256, 0, s>>>(e_d, e_c, dx, dz, r_c, p->x, p->z, p->n,
+                                                    adjoint ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t set_schur_smem_limits(int bytes) {
+  return cudaFuncSetAttribute(chain_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
+}
+
+}  // namespace ahlp

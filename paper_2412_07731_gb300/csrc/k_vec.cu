@@ -1,0 +1,265 @@
+// Vector kernels of the IPM: sparse mat-vecs, deterministic reductions and
+// elementwise updates.  All bandwidth-bound FP64.
+#include "ahlp_internal.h"
+
+namespace ahlp {
+
+namespace {
+
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs, fixed so sums are reproducible
+constexpr int kRedThreads = 256;
+
+struct RedArgs {
+  int op;
+  const double *a, *b, *c, *d;
+  double s1, s2;
+  long long len;
+};
+
+__device__ __forceinline__ double red_identity(int op) {
+  return (op == RED_MAXABS) ? 0.0 : ((op == RED_MINSTEP || op == RED_MIN) ? 1e300 : 0.0);
+}
+
+__device__ __forceinline__ double red_combine(int op, double u, double v) {
+  switch (op) {
+    case RED_MAXABS: return fmax(u, v);
+    case RED_MINSTEP:
+    case RED_MIN: return fmin(u, v);
+    default: return u + v;
+  }
+}
+
+__device__ __forceinline__ double red_elem(const RedArgs &r, long long i) {
+  switch (r.op) {
+    case RED_DOT: return r.a[i] * r.b[i];
+    case RED_MAXABS: return fabs(r.a[i]);
+    case RED_MINSTEP: {
+      // largest step keeping a + t b >= 0
+      double bi = r.b[i];
+      return bi < 0.0 ? -r.a[i] / bi : 1e300;
+    }
+    case RED_MIN: return r.a[i];
+    case RED_SUM: return r.a[i];
+    case 5:  // (a + s1 b)(c + s2 d)
+      return (r.a[i] + r.s1 * r.b[i]) * (r.c[i] + r.s2 * r.d[i]);
+    default: return 0.0;
+  }
+}
+
+__device__ double block_reduce(int op, double v, double *sh) {
+  int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) sh[t] = red_combine(op, sh[t], sh[t + s]);
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+__global__ void __launch_bounds__(kRedThreads) reduce_stage1(RedArgs r, double *part) {
+  __shared__ double sh[kRedThreads];
+  double acc = red_identity(r.op);
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < r.len; i += stride)
+    acc = red_combine(r.op, acc, red_elem(r, i));
+  double v = block_reduce(r.op, acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(kRedThreads) reduce_stage2(int op, const double *part, int np,
+                                                             double *out) {
+  __shared__ double sh[kRedThreads];
+  double acc = red_identity(op);
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc = red_combine(op, acc, part[i]);
+  double v = block_reduce(op, acc, sh);
+  if (threadIdx.x == 0) *out = v;
+}
+
+cudaError_t run_reduce(const RedArgs &r, double *part, double *out, cudaStream_t s) {
+  reduce_stage1<<<kRedBlocks, kRedThreads, 0, s>>>(r, part);
+  reduce_stage2<<<1, kRedThreads, 0, s>>>(r.op, part, kRedBlocks, out);
+  return cudaGetLastError();
+}
+
+// y[r] = yadd[r] + alpha * sum_k v[k] x[ci[k]], one warp per row
+__global__ void spmv_warp(const int *rp, const int *ci, const double *v, long long rows,
+                          const double *x, double *y, double alpha, const double *yadd) {
+  long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  int k0 = rp[w], k1 = rp[w + 1];
+  double s = 0.0;
+  for (int k = k0 + lane; k < k1; k += 32) s += v[k] * x[ci[k]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[w] = (yadd ? yadd[w] : 0.0) + alpha * s;
+}
+
+__global__ void axpby_k(double *y, const double *x, double a, double b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void fill_k(double *y, double v, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = v;
+}
+
+__global__ void mul_k(double *y, const double *a, const double *b, double sc, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = sc * a[i] * b[i];
+}
+
+// r_c = sigma_mu - x z - dxa dza
+__global__ void ipm_rc_k(double *rc, const double *x, const double *z, const double *dxa,
+                         const double *dza, double smu, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rc[i] = smu - x[i] * z[i] - (dxa ? dxa[i] * dza[i] : 0.0);
+}
+
+__global__ void add_scalar_k(double *y, const double *x, double s, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x[i] + s;
+}
+
+// part[i * gridDim.x + block] = partial of <V_i, w> for i < k (vectors of
+// length len, stride ld); fixed assignment of entries to threads
+__global__ void __launch_bounds__(kRedThreads) mdot_stage1(const double *V, long long ld, int k,
+                                                           const double *w, long long len,
+                                                           double *part) {
+  __shared__ double sh[kRedThreads];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int i = 0; i < k; ++i) {
+    const double *v = V + (long long)i * ld;
+    double acc = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride)
+      acc = fma(v[e], w[e], acc);
+    const double s = block_reduce(RED_DOT, acc, sh);
+    if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = s;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) mdot_stage2(const double *part, int np,
+                                                           double *out) {
+  __shared__ double sh[kRedThreads];
+  const double *pp = part + (long long)blockIdx.x * np;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += pp[i];
+  const double v = block_reduce(RED_DOT, acc, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
+// w[e] += sum_i coef[i] V_i[e], fixed order over i
+__global__ void maxpy_k(const double *V, long long ld, int k, const double *coef, double *w,
+                        long long len) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  double acc = w[e];
+  for (int i = 0; i < k; ++i) acc = fma(coef[i], V[(long long)i * ld + e], acc);
+  w[e] = acc;
+}
+
+// J v tail: oz = z vx + x vz (Newton), oz = vx + x vz (transposed); ox += z vz (transposed)
+__global__ void jmul_tail_k(double *ox, double *oz, const double *vx, const double *vz,
+                            const double *x, const double *z, long long n, int adjoint) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (adjoint) {
+    ox[i] += z[i] * vz[i];
+    oz[i] = vx[i] + x[i] * vz[i];
+  } else {
+    oz[i] = z[i] * vx[i] + x[i] * vz[i];
+  }
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_mdot(ahlp_problem *p, const double *V, long long ld, int k, const double *w,
+                        long long len, double *out) {
+  if (k <= 0) return cudaSuccess;
+  mdot_stage1<<<kRedBlocks, kRedThreads, 0, p->stream>>>(V, ld, k, w, len, p->mdot_part);
+  mdot_stage2<<<k, kRedThreads, 0, p->stream>>>(p->mdot_part, kRedBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxpy(const double *V, long long ld, int k, const double *coef, double *w,
+                         long long len, cudaStream_t s) {
+  if (k <= 0 || len <= 0) return cudaSuccess;
+  maxpy_k<<<blocks_for(len, 256), 256, 0, s>>>(V, ld, k, coef, w, len);
+  return cudaGetLastError();
+}
+
+// o = J v (adjoint: J' v) for v = [vx; vy; vz], o = [ox; oy; oz]
+cudaError_t launch_jmul(ahlp_problem *p, const double *vx, const double *vy, const double *vz,
+                        double *ox, double *oy, double *oz, bool adjoint) {
+  cudaStream_t s = p->stream;
+  cudaError_t e = launch_spmv(p->AT_rp, p->AT_ci, p->AT_v, p->n, vy, ox, 1.0,
+                              adjoint ? nullptr : vz, s);
+  if (e != cudaSuccess) return e;
+  e = launch_spmv(p->A_rp, p->A_ci, p->A_v, p->m, vx, oy, 1.0, nullptr, s);
+  if (e != cudaSuccess) return e;
+  if (p->n > 0)
+    jmul_tail_k<<<blocks_for(p->n, 256), 256, 0, s>>>(ox, oz, vx, vz, p->x, p->z, p->n,
+                                                       adjoint ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_scalar(double *y, const double *x, double s, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  add_scalar_k<<<blocks_for(n, 256), 256, 0, st>>>(y, x, s, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(ahlp_problem *p, int op, const double *a, const double *b,
+                          long long len, double *out) {
+  RedArgs r{op, a, b, nullptr, nullptr, 0.0, 0.0, len};
+  return run_reduce(r, p->red_part, out, p->stream);
+}
+
+cudaError_t launch_step_dot(const double *x, const double *dx, double ap, const double *z,
+                            const double *dz, double ad, long long n, double *part, double *out,
+                            cudaStream_t s) {
+  RedArgs r{5, x, dx, z, dz, ap, ad, n};
+  return run_reduce(r, part, out, s);
+}
+
+cudaError_t launch_spmv(const int *rp, const int *ci, const double *v, long long rows,
+                        const double *x, double *y, double alpha, const double *yadd,
+                        cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  spmv_warp<<<blocks_for(rows * 32, 256), 256, 0, s>>>(rp, ci, v, rows, x, y, alpha, yadd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(double *y, const double *x, double a, double b, long long n,
+                         cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  axpby_k<<<blocks_for(n, 256), 256, 0, s>>>(y, x, a, b, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double *y, double v, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  fill_k<<<blocks_for(n, 256), 256, 0, s>>>(y, v, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mul(double *y, const double *a, const double *b, double scale, long long n,
+                       cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  mul_k<<<blocks_for(n, 256), 256, 0, s>>>(y, a, b, scale, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ipm_rc(double *rc, const double *x, const double *z, const double *dxa,
+                          const double *dza, double sigma_mu, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ipm_rc_k<<<blocks_for(n, 256), 256, 0, s>>>(rc, x, z, dxa, dza, sigma_mu, n);
+  return cudaGetLastError();
+}
+
+}  // namespace ahlp

@@ -1,0 +1,113 @@
+"""Host-side checks of the C ABI (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ahlp.h")
+
+
+def _lib():
+    from paper_2412_07731_gb300 import _lib as L
+    if not os.path.exists(L.lib_path()):
+        import __graft_entry__
+        __graft_entry__.build()
+    return L
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src,
+                                 flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for fn in ("arrowhead_lp_create", "ipm_solve", "kkt_factor", "kkt_solve",
+               "kkt_adjoint_solve"):
+        assert fn in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib()
+    lib = ctypes.CDLL(L.lib_path())
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(declared_functions()) <= set(L.EXPORTS)
+
+
+def test_default_options_and_status_strings():
+    L = _lib()
+    o = L.default_options()
+    assert o.precision == 0 and o.max_iter == 200
+    assert o.tol == 1e-8 and o.refine_tol == 1e-10 and o.eta == 0.9995
+    lib = L.load()
+    assert lib.ahlp_status_string(-4) == b"NOT_SPD"
+    assert lib.ahlp_status_string(0) == b"OK"
+
+
+def _small_lp():
+    from instances import config0
+    return config0()
+
+
+def _create_status(lp, batch=1, options=None):
+    L = _lib()
+    lib = L.load()
+    keep = L._Keep()
+    descs = (L.Desc * batch)()
+    for k in range(batch):
+        descs[k] = L.make_desc(lp, keep)
+    h = ctypes.c_void_p()
+    st = lib.arrowhead_lp_create(descs, batch, ctypes.byref(options) if options else None,
+                                 ctypes.byref(h))
+    if st == 0:
+        lib.arrowhead_lp_destroy(h)
+    return st, lib.ahlp_last_error(None).decode()
+
+
+def test_validation_nan_rhs():
+    lp = _small_lp()
+    lp.b[1] = lp.b[1].copy()
+    lp.b[1][3] = np.nan
+    st, msg = _create_status(lp)
+    assert st == -1 and "non-finite" in msg
+
+
+def test_validation_bad_shape():
+    lp = _small_lp()
+    lp.W[2] = sp.csc_matrix(np.ones((lp.A[2].shape[0], lp.n0 + 1)))
+    st, msg = _create_status(lp)
+    assert st == -2 and "W" in msg
+
+
+def test_validation_row_index_out_of_range():
+    lp = _small_lp()
+    A = lp.A[0].copy()
+    A.indices = A.indices.copy()
+    A.indices[0] = A.shape[0] + 5
+    lp.A[0] = A
+    st, msg = _create_status(lp)
+    assert st == -1 and "out of range" in msg
+
+
+def test_unsupported_batch_and_precision():
+    lp = _small_lp()
+    st, _ = _create_status(lp, batch=2)
+    assert st == -3
+    L = _lib()
+    st, msg = _create_status(lp, options=L.default_options(precision=1))
+    assert st == -3 and "FP64" in msg
+
+
+def test_valid_problem_without_gpu_reports_cuda_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, msg = _create_status(_small_lp())
+    assert st == -8

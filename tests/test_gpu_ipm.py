@@ -1,0 +1,87 @@
+"""End-to-end GPU IPM against the oracle (objective to 1e-8 relative)."""
+import numpy as np
+import pytest
+
+from instances import config0, random_block_lp, tiny_lp
+from oracle import ipm as oipm
+from oracle import lp as olp
+from helpers import GOLDEN_FILES, load_golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2412_07731_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return abs(a - b) / (1.0 + abs(b))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_c0_planted(P, seed):
+    lp = config0(seed)
+    A, b, c = olp.assemble(lp)
+    prob = P.arrowhead_lp_create(lp)
+    (x, y, z), r = P.ipm_solve(prob)
+    obj = float(c @ lp.xstar)
+    assert r["status"] == 0
+    assert _rel(r["pobj"], obj) <= 1e-8
+    m = olp.measures(A, b, c, x, y, z)
+    assert m["pinf"] <= 1e-8 and m["dinf"] <= 1e-8 and m["gap"] <= 1e-8
+    ref = oipm.solve(A, b, c)
+    assert _rel(r["pobj"], ref["pobj"]) <= 1e-8
+
+
+@pytest.mark.parametrize("name", GOLDEN_FILES)
+def test_golden(P, name):
+    lp, d = load_golden(name)
+    prob = P.arrowhead_lp_create(lp)
+    (x, y, z), r = P.ipm_solve(prob)
+    assert r["status"] == 0
+    assert _rel(r["pobj"], d["objective"]) <= 1e-7
+    np.testing.assert_allclose(x, d["x"], atol=1e-6)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tiny_matches_oracle(P, seed):
+    lp = tiny_lp(seed, N=3, m=2, n=4, n0=1, l=1, mg=1)
+    A, b, c = olp.assemble(lp)
+    ref = oipm.solve(A, b, c)
+    prob = P.arrowhead_lp_create(lp)
+    (x, y, z), r = P.ipm_solve(prob)
+    assert r["status"] == 0
+    assert _rel(r["pobj"], ref["pobj"]) <= 1e-8
+
+
+def test_structured_shape_planted(P):
+    lp = random_block_lp(21, N=6, m_sizes=[90, 130, 70, 64, 100, 150],
+                         n_sizes=[135, 195, 105, 96, 150, 225], nnz_per_col=6, n0=8,
+                         w_density=0.1, l=[4, 5, 3, 6, 2], mg=2, global_nnz=6,
+                         x0_link_nnz=2, x0_global_nnz=2)
+    A, b, c = olp.assemble(lp)
+    prob = P.arrowhead_lp_create(lp)
+    (x, y, z), r = P.ipm_solve(prob)
+    assert r["status"] == 0
+    assert _rel(r["pobj"], float(c @ lp.xstar)) <= 1e-8
+
+
+def test_warm_start_from_optimum(P):
+    lp = config0(4)
+    A, b, c = olp.assemble(lp)
+    prob = P.arrowhead_lp_create(lp)
+    (x, y, z), r = P.ipm_solve(prob)
+    (x2, y2, z2), r2 = P.ipm_solve(prob, x0=x, y0=y, z0=z)
+    assert r2["status"] == 0 and r2["iterations"] <= 1
+
+
+def test_iteration_cap(P):
+    lp = config0(5)
+    prob = P.arrowhead_lp_create(lp, P.default_options(max_iter=2))
+    _, r = P.ipm_solve(prob, check=False)
+    assert r["status"] == -6 and r["iterations"] == 2
