@@ -259,6 +259,11 @@ int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld);
  */
 int kkt_stage_times(ahlp_problem *p, double *out4);
 
+/* Diagnostic: number of CUDA kernels this library has launched in this
+ * process so far (all handles).  The difference of two readings is the
+ * launch count of the calls made in between. */
+int64_t ahlp_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

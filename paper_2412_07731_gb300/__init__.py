@@ -19,6 +19,7 @@ from ._lib import (  # noqa: F401
     kkt_schur_dense,
     kkt_solve,
     kkt_stage_times,
+    launch_count,
     lib_path,
     load,
     set_options,

@@ -65,7 +65,13 @@ class SolveInfo(C.Structure):
 EXPORTS = ["ahlp_default_options", "ahlp_status_string", "arrowhead_lp_create",
            "arrowhead_lp_destroy", "ahlp_last_error", "arrowhead_lp_sizes",
            "arrowhead_lp_set_stream", "arrowhead_lp_set_options", "kkt_factor", "kkt_solve",
-           "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense", "kkt_stage_times"]
+           "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense", "kkt_stage_times",
+           "ahlp_launch_count"]
+
+
+def launch_count() -> int:
+    """Kernels launched by libahlp.so in this process so far."""
+    return int(load().ahlp_launch_count())
 
 _lib = None
 
@@ -105,6 +111,8 @@ def load(path: str | None = None):
     L.ipm_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(Result)]
     L.kkt_schur_dense.argtypes = [vp, vp, C.c_int64]
     L.kkt_stage_times.argtypes = [vp, _dp]
+    L.ahlp_launch_count.argtypes = []
+    L.ahlp_launch_count.restype = C.c_int64
     for name in ("arrowhead_lp_sizes", "arrowhead_lp_set_stream", "arrowhead_lp_set_options",
                  "kkt_factor", "kkt_solve", "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense",
                  "kkt_stage_times"):

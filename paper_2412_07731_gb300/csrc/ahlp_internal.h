@@ -166,6 +166,11 @@ struct ahlp_problem {
 
 namespace ahlp {
 
+// Every kernel launch of the library is written `count_launch(), k<<<...>>>(...)`
+// so the number of launches can be reported (arrowhead_lp_launch_count).
+void count_launch();
+long long launch_count();
+
 // ---- kernels (launch wrappers) --------------------------------------------
 // All wrappers enqueue on p->stream and return the cudaError_t of the launch.
 cudaError_t launch_dscale(ahlp_problem *p);   // dscale = x / z

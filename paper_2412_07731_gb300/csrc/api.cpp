@@ -1,6 +1,7 @@
 // Host runtime of the C ABI: validation, symbolic analysis, device memory,
 // and the kkt_factor / kkt_solve / kkt_adjoint_solve entry points.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -664,6 +665,10 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
 // ===========================================================================
 namespace ahlp {
 
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 void ck(cudaError_t e, const char *what) {
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -955,6 +960,8 @@ int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld) {
     return set_err(p, f.code, f.msg);
   }
 }
+
+int64_t ahlp_launch_count(void) { return ahlp::launch_count(); }
 
 int kkt_stage_times(ahlp_problem *p, double *out4) {
   if (!p || !out4) return AHLP_ERR_INVALID_ARG;

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) ptri_bwd_kernel(const double *__rest
 // ---------------------------------------------------------------------------
 cudaError_t launch_dscale(ahlp_problem *p) {
   if (p->n <= 0) return cudaSuccess;
-  dscale_kernel<<<(unsigned)((p->n + 255) / 256), 256, 0, p->stream>>>(p->x, p->z, p->dscale,
+  count_launch(), dscale_kernel<<<(unsigned)((p->n + 255) / 256), 256, 0, p->stream>>>(p->x, p->z, p->dscale,
                                                                        p->n);
   return cudaGetLastError();
 }
@@ -316,7 +316,7 @@ cudaError_t launch_form(ahlp_problem *p, double delta) {
   if (p->ntiles <= 0) return cudaSuccess;
   FormArgs A{p->ftiles, p->tile_ent, p->ent_pos, p->ent_cb, p->con_idx, p->con_coef,
              p->dscale, p->blk, p->aug, p->diag0, p->cdiag0, delta};
-  form_aug_kernel<<<(unsigned)p->ntiles, kThreads, 0, p->stream>>>(A);
+  count_launch(), form_aug_kernel<<<(unsigned)p->ntiles, kThreads, 0, p->stream>>>(A);
   return cudaGetLastError();
 }
 
@@ -336,11 +336,11 @@ cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<Blk
       if (t > maxPanel) maxPanel = t;
       if (t * (t + 1) / 2 > maxTrail) maxTrail = t * (t + 1) / 2;
     }
-    pchol_potrf_kernel<<<nblk, kThreads, 0, s>>>(buf, info, k, diag0, tol, status);
+    count_launch(), pchol_potrf_kernel<<<nblk, kThreads, 0, s>>>(buf, info, k, diag0, tol, status);
     if (maxPanel > 0)
-      pchol_trsm_kernel<<<dim3((unsigned)maxPanel, nblk), kThreads, kTrsmSmem, s>>>(buf, info, k);
+      count_launch(), pchol_trsm_kernel<<<dim3((unsigned)maxPanel, nblk), kThreads, kTrsmSmem, s>>>(buf, info, k);
     if (maxTrail > 0)
-      pchol_update_kernel<<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(buf, info, k);
+      count_launch(), pchol_update_kernel<<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(buf, info, k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -352,9 +352,9 @@ cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int am
   if (nblk == 0 || amax == 0) return cudaSuccess;
   size_t sm = (size_t)amax * sizeof(double);
   if (forward)
-    ptri_fwd_kernel<<<nblk, kThreads, sm, s>>>(buf, info, vec);
+    count_launch(), ptri_fwd_kernel<<<nblk, kThreads, sm, s>>>(buf, info, vec);
   else
-    ptri_bwd_kernel<<<nblk, kThreads, sm, s>>>(buf, info, vec);
+    count_launch(), ptri_bwd_kernel<<<nblk, kThreads, sm, s>>>(buf, info, vec);
   return cudaGetLastError();
 }
 

@@ -449,16 +449,16 @@ cudaError_t launch_schur_assemble(ahlp_problem *p, double delta, double rho) {
   int lmax = 0;
   for (int j = 0; j + 1 < p->N; ++j) lmax = std::max(lmax, (int)(p->link_off[j + 1] - p->link_off[j]));
   if (p->N > 1 && lmax > 0) {
-    assemble_T_kernel<<<dim3(nb((long long)lmax * lmax, 256), p->N - 1), 256, 0, s>>>(A);
+    count_launch(), assemble_T_kernel<<<dim3(nb((long long)lmax * lmax, 256), p->N - 1), 256, 0, s>>>(A);
     if (p->N > 2)
-      assemble_H_kernel<<<dim3(nb((long long)lmax * lmax, 256), p->N - 2), 256, 0, s>>>(A);
+      count_launch(), assemble_H_kernel<<<dim3(nb((long long)lmax * lmax, 256), p->N - 2), 256, 0, s>>>(A);
     if (p->B > 0)
-      assemble_E_kernel<<<dim3(nb((long long)lmax * p->B, 256), p->N - 1), 256, 0, s>>>(A);
+      count_launch(), assemble_E_kernel<<<dim3(nb((long long)lmax * p->B, 256), p->N - 1), 256, 0, s>>>(A);
   }
-  if (p->B > 0) assemble_SB_kernel<<<nb((long long)p->B * p->B, 256), 256, 0, s>>>(A);
-  if (p->nf0 > 0) scatter_add_kernel<<<nb(p->nf0, 256), 256, 0, s>>>(p->Et, p->f0_idx, p->f0_val, p->nf0);
+  if (p->B > 0) count_launch(), assemble_SB_kernel<<<nb((long long)p->B * p->B, 256), 256, 0, s>>>(A);
+  if (p->nf0 > 0) count_launch(), scatter_add_kernel<<<nb(p->nf0, 256), 256, 0, s>>>(p->Et, p->f0_idx, p->f0_val, p->nf0);
   if (p->nfg0 > 0)
-    scatter_add_kernel<<<nb(p->nfg0, 256), 256, 0, s>>>(p->SB, p->fg0_idx, p->fg0_val, p->nfg0);
+    count_launch(), scatter_add_kernel<<<nb(p->nfg0, 256), 256, 0, s>>>(p->SB, p->fg0_idx, p->fg0_val, p->nfg0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // keep the assembled matrix for diagnostics
@@ -475,10 +475,10 @@ cudaError_t launch_schur_factor(ahlp_problem *p) {
   int lmax = 0;
   for (int j = 0; j + 1 < p->N; ++j) lmax = std::max(lmax, (int)(p->link_off[j + 1] - p->link_off[j]));
   if (p->N > 1 && lmax > 0) {
-    chain_factor_kernel<<<1, 512, (size_t)lmax * lmax * 8, s>>>(cargs(p));
+    count_launch(), chain_factor_kernel<<<1, 512, (size_t)lmax * lmax * 8, s>>>(cargs(p));
   }
   if (p->B > 0) {
-    border_prep_kernel<<<nb((long long)p->B * p->B, 256), 256, 0, s>>>(
+    count_launch(), border_prep_kernel<<<nb((long long)p->B * p->B, 256), 256, 0, s>>>(
         p->SB, p->Et, p->B, p->nl, p->border, p->Bld, p->border_diag0);
     std::vector<BlkInfo> hx(1, p->h_bx);
     if (p->n0 > 0) {
@@ -487,7 +487,7 @@ cudaError_t launch_schur_factor(ahlp_problem *p) {
       if (e != cudaSuccess) return e;
     }
     if (p->mg > 0) {
-      negate_corner_kernel<<<nb((long long)p->mg * p->mg, 256), 256, 0, s>>>(
+      count_launch(), negate_corner_kernel<<<nb((long long)p->mg * p->mg, 256), 256, 0, s>>>(
           p->border, p->Bld, p->n0, p->mg, p->border_diag0, p->sb_ref);
       std::vector<BlkInfo> hp(1, p->h_bp);
       cudaError_t e = launch_pchol(p->border, p->bp_info, hp, p->border_diag0, p->fac_pivot_tol,
@@ -503,11 +503,11 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
   cudaStream_t s = p->stream;
   const long long n = p->n;
   cudaError_t e;
-  prep_f_kernel<<<nb(n, 256), 256, 0, s>>>(p->f, p->g, r_d, r_c, p->x, p->z, p->dscale, p->is_x0,
+  count_launch(), prep_f_kernel<<<nb(n, 256), 256, 0, s>>>(p->f, p->g, r_d, r_c, p->x, p->z, p->dscale, p->is_x0,
                                           n, adjoint ? 1 : 0);
   e = launch_spmv(p->A_rp, p->A_ci, p->A_v, p->m, p->g, p->rhat, 1.0, r_p, s);
   if (e != cudaSuccess) return e;
-  pack_rhs_kernel<<<dim3(nb(p->amax, 256), p->N), 256, 0, s>>>(p->blk, p->sblk, p->yoff_d,
+  count_launch(), pack_rhs_kernel<<<dim3(nb(p->amax, 256), p->N), 256, 0, s>>>(p->blk, p->sblk, p->yoff_d,
                                                                 p->rhat, p->vec);
   e = launch_ptri(p->aug, p->blk, p->N, p->amax, p->vec, true, s);
   if (e != cudaSuccess) return e;
@@ -518,16 +518,16 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
     RArgs R{p->N, p->n0, p->mg, p->B, p->nl, p->blk, p->sblk,
             p->link_pair_d, p->vec, p->rhat, p->f, p->msum,
             p->xoff[p->N], p->svec};
-    schur_rhs_kernel<<<nb(p->nS, 256), 256, 0, s>>>(R);
+    count_launch(), schur_rhs_kernel<<<nb(p->nS, 256), 256, 0, s>>>(R);
     CArgs C = cargs(p);
-    if (p->nl > 0 && lmax > 0) chain_solve_kernel<<<1, 256, 0, s>>>(C, p->svec, 0);
+    if (p->nl > 0 && lmax > 0) count_launch(), chain_solve_kernel<<<1, 256, 0, s>>>(C, p->svec, 0);
     if (p->B > 0) {
-      if (p->nl > 0) border_rhs_kernel<<<nb(p->B, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
+      if (p->nl > 0) count_launch(), border_rhs_kernel<<<nb(p->B, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
       double *sb = p->svec + p->nl;
       if (p->n0 > 0) {
         e = launch_ptri(p->border, p->bx_info, 1, p->B, sb, true, s);
         if (e != cudaSuccess) return e;
-        scale_kernel<<<nb(p->n0, 256), 256, 0, s>>>(sb, -1.0, p->n0);
+        count_launch(), scale_kernel<<<nb(p->n0, 256), 256, 0, s>>>(sb, -1.0, p->n0);
       }
       if (p->mg > 0) {
         e = launch_ptri(p->border, p->bp_info, 1, p->B, sb, true, s);
@@ -539,28 +539,28 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
         e = launch_ptri(p->border, p->bx_info, 1, p->B, sb, false, s);
         if (e != cudaSuccess) return e;
       }
-      if (p->nl > 0) link_back_kernel<<<nb(p->nl, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
+      if (p->nl > 0) count_launch(), link_back_kernel<<<nb(p->nl, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
     }
-    if (p->nl > 0 && lmax > 0) chain_solve_kernel<<<1, 256, 0, s>>>(C, p->svec, 1);
+    if (p->nl > 0 && lmax > 0) count_launch(), chain_solve_kernel<<<1, 256, 0, s>>>(C, p->svec, 1);
     int kmax = 0;
     for (int k : p->ki) kmax = std::max(kmax, k);
     if (kmax > 0)
-      gather_schur_kernel<<<dim3(nb(kmax, 256), p->N), 256, 0, s>>>(p->blk, p->sblk, p->kmap,
+      count_launch(), gather_schur_kernel<<<dim3(nb(kmax, 256), p->N), 256, 0, s>>>(p->blk, p->sblk, p->kmap,
                                                                   p->kmap_off_d, p->svec, p->vec);
   }
   e = launch_ptri(p->aug, p->blk, p->N, p->amax, p->vec, false, s);
   if (e != cudaSuccess) return e;
   int mmax = 0;
   for (int v : p->mi) mmax = std::max(mmax, v);
-  scatter_dy_kernel<<<dim3(nb(mmax, 256), p->N), 256, 0, s>>>(
+  count_launch(), scatter_dy_kernel<<<dim3(nb(mmax, 256), p->N), 256, 0, s>>>(
       p->blk, p->sblk, p->yoff_d, p->vec, dy);
   if (p->nl + p->mg > 0)
-    schur_dy_kernel<<<nb(p->nl + p->mg, 256), 256, 0, s>>>(p->svec, p->nl, p->n0, p->mg, p->msum,
+    count_launch(), schur_dy_kernel<<<nb(p->nl + p->mg, 256), 256, 0, s>>>(p->svec, p->nl, p->n0, p->mg, p->msum,
                                                           dy);
   // dx, dz
   e = launch_spmv(p->AT_rp, p->AT_ci, p->AT_v, n, dy, p->g, 1.0, nullptr, s);
   if (e != cudaSuccess) return e;
-  finish_kernel<<<nb(n, 256), 256, 0, s>>>(dx, dz, p->g, p->f, p->dscale, p->x, p->z, r_c,
+  count_launch(), finish_kernel<<<nb(n, 256), 256, 0, s>>>(dx, dz, p->g, p->f, p->dscale, p->x, p->z, r_c,
                                           p->is_x0, p->fac_rho, n, adjoint ? 1 : 0);
   return cudaGetLastError();
 }
@@ -574,7 +574,7 @@ cudaError_t launch_residual(ahlp_problem *p, const double *r_d, const double *r_
   if (e != cudaSuccess) return e;
   e = launch_spmv(p->A_rp, p->A_ci, p->A_v, p->m, dx, e_p, -1.0, r_p, s);
   if (e != cudaSuccess) return e;
-  residual_tail_kernel<<<nb(p->n, 256), 256, 0, s>>>(e_d, e_c, dx, dz, r_c, p->x, p->z, p->n,
+  count_launch(), residual_tail_kernel<<<nb(p->n, 256), 256, 0, s>>>(e_d, e_c, dx, dz, r_c, p->x, p->z, p->n,
                                                     adjoint ? 1 : 0);
   return cudaGetLastError();
 }

@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(kRedThreads) reduce_stage2(int op, const doubl
 }
 
 cudaError_t run_reduce(const RedArgs &r, double *part, double *out, cudaStream_t s) {
-  reduce_stage1<<<kRedBlocks, kRedThreads, 0, s>>>(r, part);
-  reduce_stage2<<<1, kRedThreads, 0, s>>>(r.op, part, kRedBlocks, out);
+  count_launch(), reduce_stage1<<<kRedBlocks, kRedThreads, 0, s>>>(r, part);
+  count_launch(), reduce_stage2<<<1, kRedThreads, 0, s>>>(r.op, part, kRedBlocks, out);
   return cudaGetLastError();
 }
 
@@ -181,15 +181,15 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 cudaError_t launch_mdot(ahlp_problem *p, const double *V, long long ld, int k, const double *w,
                         long long len, double *out) {
   if (k <= 0) return cudaSuccess;
-  mdot_stage1<<<kRedBlocks, kRedThreads, 0, p->stream>>>(V, ld, k, w, len, p->mdot_part);
-  mdot_stage2<<<k, kRedThreads, 0, p->stream>>>(p->mdot_part, kRedBlocks, out);
+  count_launch(), mdot_stage1<<<kRedBlocks, kRedThreads, 0, p->stream>>>(V, ld, k, w, len, p->mdot_part);
+  count_launch(), mdot_stage2<<<k, kRedThreads, 0, p->stream>>>(p->mdot_part, kRedBlocks, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_maxpy(const double *V, long long ld, int k, const double *coef, double *w,
                          long long len, cudaStream_t s) {
   if (k <= 0 || len <= 0) return cudaSuccess;
-  maxpy_k<<<blocks_for(len, 256), 256, 0, s>>>(V, ld, k, coef, w, len);
+  count_launch(), maxpy_k<<<blocks_for(len, 256), 256, 0, s>>>(V, ld, k, coef, w, len);
   return cudaGetLastError();
 }
 
@@ -203,14 +203,14 @@ cudaError_t launch_jmul(ahlp_problem *p, const double *vx, const double *vy, con
   e = launch_spmv(p->A_rp, p->A_ci, p->A_v, p->m, vx, oy, 1.0, nullptr, s);
   if (e != cudaSuccess) return e;
   if (p->n > 0)
-    jmul_tail_k<<<blocks_for(p->n, 256), 256, 0, s>>>(ox, oz, vx, vz, p->x, p->z, p->n,
+    count_launch(), jmul_tail_k<<<blocks_for(p->n, 256), 256, 0, s>>>(ox, oz, vx, vz, p->x, p->z, p->n,
                                                        adjoint ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_scalar(double *y, const double *x, double s, long long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  add_scalar_k<<<blocks_for(n, 256), 256, 0, st>>>(y, x, s, n);
+  count_launch(), add_scalar_k<<<blocks_for(n, 256), 256, 0, st>>>(y, x, s, n);
   return cudaGetLastError();
 }
 
@@ -231,34 +231,34 @@ cudaError_t launch_spmv(const int *rp, const int *ci, const double *v, long long
                         const double *x, double *y, double alpha, const double *yadd,
                         cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
-  spmv_warp<<<blocks_for(rows * 32, 256), 256, 0, s>>>(rp, ci, v, rows, x, y, alpha, yadd);
+  count_launch(), spmv_warp<<<blocks_for(rows * 32, 256), 256, 0, s>>>(rp, ci, v, rows, x, y, alpha, yadd);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpby(double *y, const double *x, double a, double b, long long n,
                          cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  axpby_k<<<blocks_for(n, 256), 256, 0, s>>>(y, x, a, b, n);
+  count_launch(), axpby_k<<<blocks_for(n, 256), 256, 0, s>>>(y, x, a, b, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill(double *y, double v, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  fill_k<<<blocks_for(n, 256), 256, 0, s>>>(y, v, n);
+  count_launch(), fill_k<<<blocks_for(n, 256), 256, 0, s>>>(y, v, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mul(double *y, const double *a, const double *b, double scale, long long n,
                        cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  mul_k<<<blocks_for(n, 256), 256, 0, s>>>(y, a, b, scale, n);
+  count_launch(), mul_k<<<blocks_for(n, 256), 256, 0, s>>>(y, a, b, scale, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ipm_rc(double *rc, const double *x, const double *z, const double *dxa,
                           const double *dza, double sigma_mu, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  ipm_rc_k<<<blocks_for(n, 256), 256, 0, s>>>(rc, x, z, dxa, dza, sigma_mu, n);
+  count_launch(), ipm_rc_k<<<blocks_for(n, 256), 256, 0, s>>>(rc, x, z, dxa, dza, sigma_mu, n);
   return cudaGetLastError();
 }
 
