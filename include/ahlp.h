@@ -264,6 +264,33 @@ int kkt_stage_times(ahlp_problem *p, double *out4);
  * launch count of the calls made in between. */
 int64_t ahlp_launch_count(void);
 
+/*
+ * kkt_residual_noalloc -- ||J d - r||_2 / ||r||_2 for a direction
+ * d = (dx, dy, dz) and right-hand side r = (r_d, r_p, r_c) at the point of
+ * the last kkt_factor, J the Newton matrix of kkt_solve.  The paper has no
+ * counterpart: this is a utility for callers that cannot allocate device
+ * memory when they need the check (a memory budget that forbids new
+ * allocations, an allocator owned by another component, or code that must
+ * avoid the synchronisation an allocation can cause).  It allocates
+ * nothing: besides the caller's vectors and the existing handle it uses one
+ * fixed 192 KB device array compiled into the library (per GPU, held until
+ * the process exits).
+ *   all seven pointers : device memory of the current device (else
+ *                        AHLP_ERR_INVALID_ARG); rel_out receives one double,
+ *                        written asynchronously on the handle's stream
+ *   limits             : n_total and m_total at most 67,108,864, else
+ *                        AHLP_ERR_UNSUPPORTED
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call reuses the same array, and each call overwrites every slot it
+ * reads, so nothing carries over between calls -- but calls that run at the
+ * same time on the GPU (other streams, other handles, other threads) race on
+ * it and must be serialised by the caller.
+ */
+int kkt_residual_noalloc(ahlp_problem *p, const double *r_d, const double *r_p,
+                         const double *r_c, const double *dx, const double *dy,
+                         const double *dz, double *rel_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,7 +66,7 @@ EXPORTS = ["ahlp_default_options", "ahlp_status_string", "arrowhead_lp_create",
            "arrowhead_lp_destroy", "ahlp_last_error", "arrowhead_lp_sizes",
            "arrowhead_lp_set_stream", "arrowhead_lp_set_options", "kkt_factor", "kkt_solve",
            "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense", "kkt_stage_times",
-           "ahlp_launch_count"]
+           "ahlp_launch_count", "kkt_residual_noalloc"]
 
 
 def launch_count() -> int:
@@ -113,6 +113,8 @@ def load(path: str | None = None):
     L.kkt_stage_times.argtypes = [vp, _dp]
     L.ahlp_launch_count.argtypes = []
     L.ahlp_launch_count.restype = C.c_int64
+    L.kkt_residual_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.kkt_residual_noalloc.restype = C.c_int
     for name in ("arrowhead_lp_sizes", "arrowhead_lp_set_stream", "arrowhead_lp_set_options",
                  "kkt_factor", "kkt_solve", "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense",
                  "kkt_stage_times"):
@@ -367,3 +369,19 @@ def kkt_stage_times(prob: Problem):
     prob._check(prob._lib.kkt_stage_times(prob._h, out))
     return {"form_ms": out[0], "block_factor_ms": out[1], "schur_ms": out[2],
             "last_solve_ms": out[3]}
+
+
+def kkt_residual_noalloc(prob: Problem, r_d, r_p, r_c, dx, dy, dz, out):
+    """Relative Newton residual of (dx, dy, dz) for (r_d, r_p, r_c), written
+    into the one-element float64 CUDA tensor ``out`` without any device
+    allocation (for callers that cannot allocate at that point).  Every
+    argument must be a CUDA tensor."""
+    keep = _Keep()
+    prob._stream_for(r_d, out)
+    st = prob._lib.kkt_residual_noalloc(
+        prob._h, _vec_ptr(r_d, keep, prob.n, "r_d"), _vec_ptr(r_p, keep, prob.m, "r_p"),
+        _vec_ptr(r_c, keep, prob.n, "r_c"), _vec_ptr(dx, keep, prob.n, "dx"),
+        _vec_ptr(dy, keep, prob.m, "dy"), _vec_ptr(dz, keep, prob.n, "dz"),
+        _vec_ptr(out, keep, 1, "out"))
+    prob._check(st)
+    return out
