@@ -129,7 +129,9 @@ typedef struct {
   int32_t refine_steps;   /* summed refinement steps                              */
   int32_t tiny_pivots;    /* pivots clamped in the last factor                    */
   double  kkt_residual;   /* largest relative Newton residual seen                */
-  int32_t escalations;    /* times the pivot threshold was coarsened (x100)       */
+  int32_t escalations;    /* FP32->FP64 switches plus pivot-threshold coarsenings  */
+  int32_t fp64_switch_iter; /* mixed mode: iteration from which the block factors
+                             are FP64 (-1: never); FP64 mode: 0                   */
 } ahlp_result;
 
 typedef struct {
@@ -251,6 +253,19 @@ int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, const double 
  *   S  : host buffer of ld * dim doubles, dim = sum(l) + n0 + mg
  */
 int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld);
+
+/*
+ * kkt_block_factor_dense -- diagnostic: copy block i's augmented matrix after
+ * the last kkt_factor (its partial Cholesky over the first m_i pivots:
+ * L_i on top, Y_i' below it, the Schur contribution C_i - G_i' M_i^-1 G_i in
+ * the corner; Alg. 2 lines 1-2) into host memory as a dense column-major
+ * a x a lower triangle, a = m_i + k_i (the upper triangle is zeroed).
+ *   block : 0 <= block < N;  A : host buffer of ld * a doubles;  ld >= a
+ *   order : receives a (may be NULL)
+ * Values are widened to double in mixed precision.
+ */
+int kkt_block_factor_dense(ahlp_problem *p, int32_t block, double *A, int64_t ld,
+                           int32_t *order);
 
 /*
  * kkt_stage_times -- diagnostic: device times (ms) of the stages of the last

@@ -52,7 +52,8 @@ class Result(C.Structure):
                 ("dinf", C.c_double), ("mu", C.c_double), ("ms_total", C.c_double),
                 ("ms_factor", C.c_double), ("ms_solve", C.c_double),
                 ("refine_steps", C.c_int32), ("tiny_pivots", C.c_int32),
-                ("kkt_residual", C.c_double), ("escalations", C.c_int32)]
+                ("kkt_residual", C.c_double), ("escalations", C.c_int32),
+                ("fp64_switch_iter", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -66,7 +67,21 @@ EXPORTS = ["ahlp_default_options", "ahlp_status_string", "arrowhead_lp_create",
            "arrowhead_lp_destroy", "ahlp_last_error", "arrowhead_lp_sizes",
            "arrowhead_lp_set_stream", "arrowhead_lp_set_options", "kkt_factor", "kkt_solve",
            "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense", "kkt_stage_times",
-           "ahlp_launch_count", "kkt_residual_noalloc"]
+           "ahlp_launch_count", "kkt_residual_noalloc", "kkt_block_factor_dense"]
+
+
+def kkt_block_factor_dense(prob, block: int):
+    """Block ``block``'s partially factored augmented matrix (lower, dense)."""
+    a = C.c_int32(0)
+    probe = np.zeros(1)
+    prob._lib.kkt_block_factor_dense(prob._h, block, C.c_void_p(probe.ctypes.data), 0, C.byref(a))
+    if a.value <= 0:
+        prob._check(prob._lib.kkt_block_factor_dense(prob._h, block,
+                                                     C.c_void_p(probe.ctypes.data), 0, None))
+    out = np.zeros((a.value, a.value), order="F")
+    prob._check(prob._lib.kkt_block_factor_dense(prob._h, block, C.c_void_p(out.ctypes.data),
+                                                 max(a.value, 1), C.byref(a)))
+    return out
 
 
 def launch_count() -> int:
@@ -115,6 +130,8 @@ def load(path: str | None = None):
     L.ahlp_launch_count.restype = C.c_int64
     L.kkt_residual_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.kkt_residual_noalloc.restype = C.c_int
+    L.kkt_block_factor_dense.argtypes = [vp, C.c_int32, vp, C.c_int64, C.POINTER(C.c_int32)]
+    L.kkt_block_factor_dense.restype = C.c_int
     for name in ("arrowhead_lp_sizes", "arrowhead_lp_set_stream", "arrowhead_lp_set_options",
                  "kkt_factor", "kkt_solve", "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense",
                  "kkt_stage_times"):

@@ -11,7 +11,12 @@
 
 namespace ahlp {
 
-constexpr int NB = 64;            // tile edge of the FP64 dense kernels
+constexpr int NB = 64;            // tile edge of the dense kernels
+constexpr int kPrecFP64 = 0;      // factor storage of the block matrices
+constexpr int kPrecFP32 = 1;
+constexpr double kFp32PivotTol = 1e-6;   // smallest clamp threshold for FP32 pivots
+constexpr long long kSmemVecBytes = 160 * 1024;   // dynamic smem of the block solves
+constexpr double kCondSwitch = 1e10;     // max(d)/min(d) above which FP32 factors give way to FP64
 constexpr int kThreads = 256;     // threads per CTA of the dense kernels
 
 // One dense lower-triangular "partial Cholesky" problem: an a x a matrix
@@ -24,8 +29,11 @@ struct BlkInfo {
   long long d0off;   // offset of its original diagonal in the diag0 array
   int lda, a, p;
   int T, Tp;         // tiles of a, tiles holding pivots
+  int tag;           // added to the problem index in pivot reports (kTag*)
   long long cdoff;   // offset of the corner (non-pivot) diagonal in cdiag0
 };
+constexpr int kTagBorderX = 1 << 20;   // pivot reports of the border x_0 factor
+constexpr int kTagBorderG = 2 << 20;   // pivot reports of the border y_g factor
 
 #ifdef __CUDACC__
 // Pivot safeguard shared by every Cholesky in the library.  A pivot that is
@@ -92,8 +100,10 @@ struct ahlp_problem {
   unsigned char *is_x0 = nullptr;                  // [n] 1 for x_0 columns
 
   // ---- factor storage -----------------------------------------------------
-  double *aug = nullptr;            // all augmented matrices
+  double *aug = nullptr;            // all augmented matrices, FP64 (allocated when first used)
+  float *aug32 = nullptr;           // the same layout in FP32 (mixed mode)
   long long aug_elems = 0;
+  int fac_prec = 0;                 // precision of the current factor (kPrecFP64/kPrecFP32)
   ahlp::BlkInfo *blk = nullptr;     // [N]
   std::vector<ahlp::BlkInfo> h_blk;
   ahlp::SchurBlk *sblk = nullptr;   // [N]
@@ -120,6 +130,9 @@ struct ahlp_problem {
   double *Td = nullptr, *Hd = nullptr, *Et = nullptr, *SB = nullptr;
   double *Td_asm = nullptr, *Hd_asm = nullptr, *Et_asm = nullptr, *SB_asm = nullptr;
   double *Td_diag0 = nullptr;        // assembled diagonal of T (pivot test)
+  double *Linv = nullptr;            // L_j^-1 per pair (layout of Td)
+  double *Yf = nullptr, *Yb = nullptr;   // chain coupling operators (layout of Hd)
+  double *chain_tmp = nullptr;       // [nl] chain-solve scratch
   long long *td_off_d = nullptr, *h_off_d = nullptr;
   int *l_d = nullptr;                // [N-1]
   long long *link_off_d = nullptr;   // [N]
@@ -155,6 +168,7 @@ struct ahlp_problem {
   int *status = nullptr;      // device status words [4]
   int tiny_pivots = 0;
   bool factored = false;
+  bool assembled = false;     // the Schur complement of the last kkt_factor exists
   double fac_delta = 0, fac_rho = 0, fac_pivot_tol = 0;
 
   // ---- timing -------------------------------------------------------------
@@ -177,6 +191,13 @@ cudaError_t launch_dscale(ahlp_problem *p);   // dscale = x / z
 cudaError_t launch_form(ahlp_problem *p, double delta);
 cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
                          const double *diag0, double tol, int *status, cudaStream_t s);
+cudaError_t launch_pchol_f32(float *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
+                             const double *diag0, double tol, int *status, cudaStream_t s);
+// forward / backward solves with the partial factors (vectors FP64)
+cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,
+                        bool forward, cudaStream_t s);
+cudaError_t launch_ptri_f32(const float *buf, const BlkInfo *info, int nblk, int amax,
+                            double *vec, bool forward, cudaStream_t s);
 cudaError_t launch_schur_assemble(ahlp_problem *p, double delta, double rho);
 cudaError_t launch_schur_factor(ahlp_problem *p);
 cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,

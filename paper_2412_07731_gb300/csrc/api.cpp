@@ -291,9 +291,9 @@ int arrowhead_lp_set_stream(ahlp_problem *p, void *stream) {
 }
 
 static int check_options(const ahlp_options &o, std::string &err) {
-  if (o.precision != AHLP_PREC_FP64) {
-    err = "only AHLP_PREC_FP64 is available in this build";
-    return AHLP_ERR_UNSUPPORTED;
+  if (o.precision != AHLP_PREC_FP64 && o.precision != AHLP_PREC_MIXED) {
+    err = "precision must be AHLP_PREC_FP64 or AHLP_PREC_MIXED";
+    return AHLP_ERR_INVALID_ARG;
   }
   if (o.max_iter < 0 || !(o.tol > 0) || !(o.eta > 0 && o.eta < 1) || o.delta < 0 || o.rho < 0 ||
       o.refine_max < 0 || !(o.refine_tol > 0) || !(o.pivot_tol >= 0)) {
@@ -499,8 +499,12 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     }
     p->aug_elems = base;
     p->vec_elems = voff;
-    if ((long long)p->amax * 8 > 200 * 1024 || (long long)p->B * 8 > 200 * 1024)
-      fail(AHLP_ERR_UNSUPPORTED, "a block's augmented order exceeds 25600");
+    // the block solves keep a block's vector in shared memory next to a
+    // staged 64x64 tile; the link-chain kernels keep one l x l block there
+    if ((long long)p->amax * 8 > kSmemVecBytes || (long long)p->B * 8 > kSmemVecBytes)
+      fail(AHLP_ERR_UNSUPPORTED, "a block's augmented order exceeds 20480");
+    for (int v : l)
+      if (v > 96) fail(AHLP_ERR_UNSUPPORTED, "more than 96 local link rows per block pair");
     // ---- formation patterns --------------------------------------------------
     Pattern P;
     for (int i = 0; i < N; ++i) {
@@ -570,9 +574,10 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->nf0 = (long long)f0i.size();
     p->nfg0 = (long long)fg0i.size();
     p->Bld = (int)round_up(std::max(p->B, 1), 8);
-    p->h_bx = BlkInfo{0, 0, 0, p->Bld, p->B, n0, (p->B + NB - 1) / NB, (n0 + NB - 1) / NB, 0};
+    p->h_bx = BlkInfo{0, 0, 0, p->Bld, p->B, n0, (p->B + NB - 1) / NB, (n0 + NB - 1) / NB,
+                      kTagBorderX, 0};
     p->h_bp = BlkInfo{(long long)n0 * p->Bld + n0, n0, n0, p->Bld, mg, mg, (mg + NB - 1) / NB,
-                      (mg + NB - 1) / NB, 0};
+                      (mg + NB - 1) / NB, kTagBorderG, 0};
     // ---- device memory ----------------------------------------------------------
     ck(cudaGetDevice(&p->device), "cudaGetDevice");
     p->b = dupload(p, bgl);
@@ -584,7 +589,11 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->AT_ci = dupload(p, ATci);
     p->AT_v = dupload(p, ATv);
     p->is_x0 = dupload(p, isx0);
-    p->aug = dalloc<double>(p, p->aug_elems);
+    if (p->opt.precision == AHLP_PREC_MIXED)
+      p->aug32 = dalloc<float>(p, p->aug_elems);
+    else
+      p->aug = dalloc<double>(p, p->aug_elems);
+    p->fac_prec = p->opt.precision == AHLP_PREC_MIXED ? kPrecFP32 : kPrecFP64;
     p->blk = dupload(p, p->h_blk);
     p->sblk = dupload(p, p->h_sblk);
     p->diag0 = dalloc<double>(p, std::max(d0, 1LL));
@@ -606,6 +615,10 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->Et_asm = dalloc<double>(p, (long long)p->nl * p->B);
     p->SB_asm = dalloc<double>(p, (long long)p->B * p->B);
     p->Td_diag0 = dalloc<double>(p, p->nl);
+    p->Linv = dalloc<double>(p, te);
+    p->Yf = dalloc<double>(p, he);
+    p->Yb = dalloc<double>(p, he);
+    p->chain_tmp = dalloc<double>(p, p->nl);
     p->td_off_d = dupload(p, p->td_off);
     p->h_off_d = dupload(p, p->h_off);
     p->l_d = dupload(p, l);
@@ -642,8 +655,8 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->status = dalloc<int>(p, 8);
     ck(cudaMallocHost(&p->h_scal, 256 * sizeof(double)), "cudaMallocHost");
     for (auto &e : p->ev) ck(cudaEventCreate(&e), "cudaEventCreate");
-    ck(set_dense_smem_limits(200 * 1024), "smem limit");
-    ck(set_schur_smem_limits(200 * 1024), "smem limit");
+    ck(set_dense_smem_limits((int)kSmemVecBytes), "smem limit");
+    ck(set_schur_smem_limits(128 * 128 * 8), "smem limit");
     ck(cudaDeviceSynchronize(), "create sync");
   } catch (const Fail &f) {
     g_create_err = f.msg;
@@ -707,7 +720,10 @@ void read_scalars(ahlp_problem *p, int k) {
 }
 
 int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
-  p->fac_pivot_tol = pivot_tol;
+  // an FP32 pivot that lost six digits is rounding noise
+  p->fac_pivot_tol = p->fac_prec == kPrecFP32 ? std::max(pivot_tol, kFp32PivotTol) : pivot_tol;
+  if (p->fac_prec == kPrecFP32 && !p->aug32) p->aug32 = dalloc<float>(p, p->aug_elems);
+  if (p->fac_prec == kPrecFP64 && !p->aug) p->aug = dalloc<double>(p, p->aug_elems);
   cudaStream_t s = p->stream;
   // strictly positive point required (Sec. 2.3: x, z > 0)
   ck(launch_reduce(p, RED_MIN, p->x, nullptr, p->n, p->scal + 0), "reduce");
@@ -722,11 +738,29 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
   ck(cudaEventRecord(p->ev[0], s), "event");
   ck(cudaMemsetAsync(p->cdiag0, 0, std::max(p->cdiag_elems, 1LL) * sizeof(double), s), "memset");
   ck(launch_dscale(p), "dscale");
+  if (p->fac_prec == kPrecFP32 && p->n > 0) {
+    // adaptive precision: once D = X Z^-1 spans more than kCondSwitch the
+    // block normal matrices are too ill-conditioned for FP32 factors
+    ck(launch_reduce(p, RED_MAXABS, p->dscale, nullptr, p->n, p->scal + 2), "reduce");
+    ck(launch_reduce(p, RED_MIN, p->dscale, nullptr, p->n, p->scal + 3), "reduce");
+    ck(cudaMemcpyAsync(p->h_scal + 2, p->scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
+       "D2H");
+    ck(cudaStreamSynchronize(s), "sync");
+    if (!(p->h_scal[2] <= kCondSwitch * p->h_scal[3])) {
+      p->fac_prec = kPrecFP64;
+      return factor_impl(p, delta, rho, pivot_tol);
+    }
+  }
   ck(launch_form(p, delta), "form");
   ck(cudaEventRecord(p->ev[1], s), "event");
-  ck(launch_pchol(p->aug, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s), "pchol");
+  if (p->fac_prec == kPrecFP32)
+    ck(launch_pchol_f32(p->aug32, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s),
+       "pchol");
+  else
+    ck(launch_pchol(p->aug, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s), "pchol");
   ck(cudaEventRecord(p->ev[2], s), "event");
   ck(launch_schur_assemble(p, delta, rho), "schur assemble");
+  p->assembled = true;
   ck(launch_schur_factor(p), "schur factor");
   ck(cudaEventRecord(p->ev[3], s), "event");
   int st[8];
@@ -736,9 +770,18 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
   cudaEventElapsedTime(&p->stage_ms[1], p->ev[1], p->ev[2]);
   cudaEventElapsedTime(&p->stage_ms[2], p->ev[2], p->ev[3]);
   p->tiny_pivots = st[1];
+  if (st[0] > 0 && p->fac_prec == kPrecFP32) {   // FP32 range exceeded: redo in FP64
+    p->fac_prec = kPrecFP64;
+    return factor_impl(p, delta, rho, pivot_tol);
+  }
   if (st[0] > 0) {
     char buf[160];
-    if (st[2] >= 0)
+    if (st[2] >= kTagBorderG)
+      snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in the border (global row %d)", st[3]);
+    else if (st[2] >= kTagBorderX)
+      snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in the border (linking variable %d)",
+               st[3]);
+    else if (st[2] >= 0)
       snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in block %d row %d", st[2], st[3]);
     else
       snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in link pair %d row %d", -1 - st[2], st[3]);
@@ -876,6 +919,7 @@ int kkt_factor(ahlp_problem *p, const double *x, const double *z, double delta, 
       ck(cudaMemcpyAsync(p->x, dx, p->n * 8, cudaMemcpyDeviceToDevice, p->stream), "copy x");
       ck(cudaMemcpyAsync(p->z, dz, p->n * 8, cudaMemcpyDeviceToDevice, p->stream), "copy z");
     }
+    p->fac_prec = p->opt.precision == AHLP_PREC_MIXED ? kPrecFP32 : kPrecFP64;
     return factor_impl(p, delta < 0 ? p->opt.delta : delta, rho < 0 ? p->opt.rho : rho,
                        p->opt.pivot_tol);
   } catch (const Fail &f) {
@@ -918,7 +962,8 @@ int kkt_adjoint_solve(ahlp_problem *p, const double *g_x, const double *g_y, con
 
 int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld) {
   if (!p || !S) return AHLP_ERR_INVALID_ARG;
-  if (!p->factored) return set_err(p, AHLP_ERR_INVALID_ARG, "no factor: call kkt_factor first");
+  if (!p->assembled)
+    return set_err(p, AHLP_ERR_INVALID_ARG, "no Schur complement: call kkt_factor first");
   const int dim = p->nS;
   if (ld < dim) return set_err(p, AHLP_ERR_INVALID_ARG, "ld < dimension");
   try {
@@ -962,6 +1007,35 @@ int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld) {
 }
 
 int64_t ahlp_launch_count(void) { return ahlp::launch_count(); }
+
+int kkt_block_factor_dense(ahlp_problem *p, int32_t block, double *A, int64_t ld,
+                           int32_t *order) {
+  if (!p || !A) return AHLP_ERR_INVALID_ARG;
+  if (!p->assembled)
+    return set_err(p, AHLP_ERR_INVALID_ARG, "no factor: call kkt_factor first");
+  if (block < 0 || block >= p->N) return set_err(p, AHLP_ERR_INVALID_ARG, "block out of range");
+  const BlkInfo &bi = p->h_blk[block];
+  if (order) *order = bi.a;
+  if (ld < bi.a) return set_err(p, AHLP_ERR_INVALID_ARG, "ld < order");
+  try {
+    ck(cudaStreamSynchronize(p->stream), "sync");
+    const size_t cnt = (size_t)bi.lda * bi.a;
+    std::vector<double> h(cnt);
+    if (p->fac_prec == kPrecFP32) {
+      std::vector<float> hf(cnt);
+      if (cnt) ck(cudaMemcpy(hf.data(), p->aug32 + bi.base, cnt * 4, cudaMemcpyDeviceToHost), "D2H");
+      for (size_t i = 0; i < cnt; ++i) h[i] = hf[i];
+    } else if (cnt) {
+      ck(cudaMemcpy(h.data(), p->aug + bi.base, cnt * 8, cudaMemcpyDeviceToHost), "D2H");
+    }
+    for (long long c = 0; c < bi.a; ++c)
+      for (long long r = 0; r < bi.a; ++r) A[c * ld + r] = r >= c ? h[c * bi.lda + r] : 0.0;
+    if (order) *order = bi.a;
+    return AHLP_OK;
+  } catch (const Fail &f) {
+    return set_err(p, f.code, f.msg);
+  }
+}
 
 int kkt_stage_times(ahlp_problem *p, double *out4) {
   if (!p || !out4) return AHLP_ERR_INVALID_ARG;

@@ -45,10 +45,19 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     constexpr double kEscalate = 1e-6, kMaxPivotTol = 1e-8;
     double ptol = p->opt.pivot_tol;
     double last_rel = 0.0;
+    int cur_iter = 0;
+    // Mixed precision starts with FP32 block factors.  The factor itself
+    // switches to FP64 once D spans more than kCondSwitch (or an FP32 pivot
+    // overflows); a direction whose residual stalls switches too.
+    p->fac_prec = p->opt.precision == AHLP_PREC_MIXED ? kPrecFP32 : kPrecFP64;
+    R.fp64_switch_iter = p->fac_prec == kPrecFP32 ? -1 : 0;
     auto factor_at = [&](const double *xx, const double *zz) {
       ck(cudaMemcpyAsync(p->x, xx, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
       ck(cudaMemcpyAsync(p->z, zz, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+      const int before = p->fac_prec;
       int st = factor_impl(p, delta, rho, ptol);
+      if (before == kPrecFP32 && p->fac_prec == kPrecFP64 && R.fp64_switch_iter < 0)
+        R.fp64_switch_iter = cur_iter;
       R.ms_factor += p->stage_ms[0] + p->stage_ms[1] + p->stage_ms[2];
       R.tiny_pivots = p->tiny_pivots;
       return st;
@@ -63,7 +72,22 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       last_rel = info.rel_residual;
       return st;
     };
-    auto can_escalate = [&]() { return !(last_rel <= kEscalate) && ptol * 100.0 <= kMaxPivotTol * 1.0001; };
+    // Escalation after a stalled direction: first FP32 -> FP64 factors, then
+    // coarser pivot thresholds.
+    auto can_escalate = [&]() {
+      if (last_rel <= kEscalate) return false;
+      if (p->fac_prec == kPrecFP32) return true;
+      return ptol * 100.0 <= kMaxPivotTol * 1.0001;
+    };
+    auto escalate = [&]() {
+      if (p->fac_prec == kPrecFP32) {
+        p->fac_prec = kPrecFP64;
+        R.fp64_switch_iter = cur_iter;
+      } else {
+        ptol *= 100.0;
+      }
+      ++R.escalations;
+    };
     const bool warm = x0 && y0 && z0;
     if (warm) {
       const double *a = stage_in(p, x0, n, p->stg[0]);
@@ -148,16 +172,26 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         break;
       }
       const double mu = R.mu;
+      cur_iter = it;
       for (;;) {
         int st = factor_at(X, Z);
+        // A NaN pivot in an FP64 factor comes from a pivot that lost nearly all
+        // its digits to cancellation yet passed the threshold: the rounding
+        // noise it carries is amplified through the later clamped columns.  A
+        // coarser threshold clamps it instead, so refactor with one.
+        while (st == AHLP_ERR_NOT_SPD && p->fac_prec == kPrecFP64 &&
+               ptol * 100.0 <= kMaxPivotTol * 1.0001) {
+          ptol *= 100.0;
+          ++R.escalations;
+          st = factor_at(X, Z);
+        }
         if (st != AHLP_OK) throw Fail{st, p->err};
         // predictor: r_c = -XZe
         ck(launch_mul(v[V_RC], X, Z, -1.0, n, s), "mul");
         st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DXA], v[V_DYA], v[V_DZA]);
         if (st != AHLP_OK) throw Fail{st, p->err};
         if (can_escalate()) {
-          ptol *= 100.0;
-          ++R.escalations;
+          escalate();
           continue;
         }
         ck(launch_reduce(p, RED_MINSTEP, X, v[V_DXA], n, p->scal + 0), "reduce");
@@ -174,8 +208,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DX], v[V_DY], v[V_DZ]);
         if (st != AHLP_OK) throw Fail{st, p->err};
         if (can_escalate()) {
-          ptol *= 100.0;
-          ++R.escalations;
+          escalate();
           continue;
         }
         break;

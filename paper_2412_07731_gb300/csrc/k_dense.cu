@@ -7,6 +7,10 @@
 // stored column-major.  Eliminating its first m_i pivots (Alg. 2 lines 1-2
 // in normal-equation form) leaves L_i on top, Y_i' = (L_i^-1 G_i)' below it
 // and C_i - G_i' M_i^-1 G_i in the corner -- the block's Schur contribution.
+//
+// All kernels are templated on the storage type of the factor: double (FP64
+// mode) or float (mixed mode, where the factor only preconditions an FP64
+// Krylov solve).  Entries are always formed in FP64 and rounded once.
 #include <math.h>
 
 #include "ahlp_internal.h"
@@ -18,6 +22,7 @@ namespace {
 // --------------------------------------------------------------------------
 // formation: one CTA per 64x64 lower tile, written exactly once
 // --------------------------------------------------------------------------
+template <typename T>
 struct FormArgs {
   const FormTile *tiles;
   const long long *tile_ent;
@@ -27,17 +32,18 @@ struct FormArgs {
   const double *con_coef;
   const double *d;
   const BlkInfo *blk;
-  double *aug;
+  T *aug;
   double *diag0;
   double *cdiag0;
   double delta;
 };
 
-__global__ void __launch_bounds__(kThreads) form_aug_kernel(FormArgs A) {
-  __shared__ double t[NB * NB];   // column-major tile
+template <typename T>
+__global__ void __launch_bounds__(kThreads) form_aug_kernel(FormArgs<T> A) {
+  __shared__ T t[NB * NB];   // column-major tile
   const FormTile ft = A.tiles[blockIdx.x];
   const BlkInfo bi = A.blk[ft.blk];
-  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) t[i] = 0.0;
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) t[i] = T(0);
   __syncthreads();
   const long long e0 = A.tile_ent[blockIdx.x], e1 = A.tile_ent[blockIdx.x + 1];
   for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -56,12 +62,12 @@ __global__ void __launch_bounds__(kThreads) form_aug_kernel(FormArgs A) {
     } else if (pos & (1 << 17)) {   // corner diagonal: reference for link / y_g pivots
       A.cdiag0[bi.cdoff + (long long)ft.I * NB + rt - bi.p] = v;
     }
-    t[ct * NB + rt] = v;
+    t[ct * NB + rt] = T(v);
   }
   __syncthreads();
   const int r0 = ft.I * NB, c0 = ft.J * NB;
   const int nr = min(NB, bi.a - r0), nc = min(NB, bi.a - c0);
-  double *g = A.aug + bi.base + (long long)c0 * bi.lda + r0;
+  T *g = A.aug + bi.base + (long long)c0 * bi.lda + r0;
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
     if (r < nr && c < nc) g[(long long)c * bi.lda + r] = t[i];
@@ -76,32 +82,33 @@ __global__ void dscale_kernel(const double *x, const double *z, double *d, long 
 // --------------------------------------------------------------------------
 // partial Cholesky, step k: diagonal tile
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) pchol_potrf_kernel(double *buf, const BlkInfo *blk,
-                                                               int k, const double *diag0,
-                                                               double tol, int *status) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) pchol_potrf_kernel(T *buf, const BlkInfo *blk, int k,
+                                                               const double *diag0, double tol,
+                                                               int *status) {
   const BlkInfo bi = blk[blockIdx.x];
   if (k >= bi.Tp) return;
-  __shared__ double t[NB][NB + 1];
-  __shared__ double s_inv;
+  __shared__ T t[NB][NB + 1];
+  __shared__ T s_inv;
   const int r0 = k * NB;
   const int nr = min(NB, bi.a - r0);
   const int npiv = min(NB, bi.p - r0);
-  double *g = buf + bi.base + (long long)r0 * bi.lda + r0;
+  T *g = buf + bi.base + (long long)r0 * bi.lda + r0;
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
-    t[r][c] = (r < nr && c < nr && r >= c) ? g[(long long)c * bi.lda + r] : 0.0;
+    t[r][c] = (r < nr && c < nr && r >= c) ? g[(long long)c * bi.lda + r] : T(0);
   }
   __syncthreads();
   for (int c = 0; c < npiv; ++c) {
     if (threadIdx.x == 0) {
-      double piv = t[c][c];
-      pivot_fix(piv, diag0[bi.d0off + r0 + c], tol, status, blockIdx.x, r0 + c);
-      const double l = sqrt(piv);
+      double piv = (double)t[c][c];
+      pivot_fix(piv, diag0[bi.d0off + r0 + c], tol, status, bi.tag + (int)blockIdx.x, r0 + c);
+      const T l = (T)sqrt(piv);
       t[c][c] = l;
-      s_inv = 1.0 / l;
+      s_inv = T(1) / l;
     }
     __syncthreads();
-    const double inv = s_inv;
+    const T inv = s_inv;
     for (int r = c + 1 + threadIdx.x; r < nr; r += blockDim.x) t[r][c] *= inv;
     __syncthreads();
     const int m = nr - c - 1;
@@ -119,30 +126,30 @@ __global__ void __launch_bounds__(kThreads) pchol_potrf_kernel(double *buf, cons
 
 // panel tiles below the diagonal tile: X = A_Ik L_kk^-T on the pivot columns,
 // and the non-pivot (Schur) columns of the tile updated with the new X.
-__global__ void __launch_bounds__(kThreads) pchol_trsm_kernel(double *buf, const BlkInfo *blk,
-                                                              int k) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) pchol_trsm_kernel(T *buf, const BlkInfo *blk, int k) {
   const BlkInfo bi = blk[blockIdx.y];
   if (k >= bi.Tp) return;
   const int I = k + 1 + blockIdx.x;
   if (I >= bi.T) return;
-  extern __shared__ double trsm_sm[];   // two (NB x NB+1) tiles, opt-in size
-  double(*L)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(trsm_sm);
-  double(*X)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(trsm_sm + NB * (NB + 1));
+  extern __shared__ __align__(16) unsigned char trsm_raw[];   // two (NB x NB+1) tiles
+  T(*L)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(trsm_raw);
+  T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(trsm_raw + sizeof(T) * NB * (NB + 1));
   const int r0 = k * NB;
   const int nr = min(NB, bi.a - r0);
   const int npiv = min(NB, bi.p - r0);
   const int ri = I * NB;
   const int nri = min(NB, bi.a - ri);
-  const double *gl = buf + bi.base + (long long)r0 * bi.lda + r0;
-  double *gx = buf + bi.base + (long long)r0 * bi.lda + ri;
+  const T *gl = buf + bi.base + (long long)r0 * bi.lda + r0;
+  T *gx = buf + bi.base + (long long)r0 * bi.lda + ri;
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
-    L[r][c] = (r < nr && c < nr && r >= c) ? gl[(long long)c * bi.lda + r] : 0.0;
-    X[r][c] = (r < nri && c < nr) ? gx[(long long)c * bi.lda + r] : 0.0;
+    L[r][c] = (r < nr && c < nr && r >= c) ? gl[(long long)c * bi.lda + r] : T(0);
+    X[r][c] = (r < nri && c < nr) ? gx[(long long)c * bi.lda + r] : T(0);
   }
   __syncthreads();
   for (int c = 0; c < npiv; ++c) {
-    const double inv = 1.0 / L[c][c];
+    const T inv = T(1) / L[c][c];
     for (int r = threadIdx.x; r < nri; r += blockDim.x) X[r][c] *= inv;
     __syncthreads();
     const int ns = nr - c - 1;
@@ -160,8 +167,8 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_kernel(double *buf, const
 
 // trailing update: C_IJ -= L_Ik L_Jk' over the pivot columns of step k.
 constexpr int KC = 16;
-__global__ void __launch_bounds__(kThreads) pchol_update_kernel(double *buf, const BlkInfo *blk,
-                                                                int k) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) pchol_update_kernel(T *buf, const BlkInfo *blk, int k) {
   const BlkInfo bi = blk[blockIdx.y];
   if (k >= bi.Tp) return;
   const long long t = bi.T - k - 1;
@@ -175,27 +182,27 @@ __global__ void __launch_bounds__(kThreads) pchol_update_kernel(double *buf, con
   const int npiv = min(NB, bi.p - k * NB);
   const int rI = I * NB, rJ = J * NB;
   const int nrI = min(NB, bi.a - rI), nrJ = min(NB, bi.a - rJ);
-  __shared__ double As[KC][NB];
-  __shared__ double Bs[KC][NB];
+  __shared__ T As[KC][NB];
+  __shared__ T Bs[KC][NB];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  const double *colk = buf + bi.base + (long long)(k * NB) * bi.lda;
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  const T *colk = buf + bi.base + (long long)(k * NB) * bi.lda;
   for (int kc = 0; kc < npiv; kc += KC) {
     for (int idx = threadIdx.x; idx < KC * NB; idx += blockDim.x) {
       const int r = idx % NB, kk = idx / NB;
       const bool kin = (kc + kk) < npiv;
-      const double *col = colk + (long long)(kc + kk) * bi.lda;
-      As[kk][r] = (kin && r < nrI) ? col[rI + r] : 0.0;
-      Bs[kk][r] = (kin && r < nrJ) ? col[rJ + r] : 0.0;
+      const T *col = colk + (long long)(kc + kk) * bi.lda;
+      As[kk][r] = (kin && r < nrI) ? col[rI + r] : T(0);
+      Bs[kk][r] = (kin && r < nrJ) ? col[rJ + r] : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
-      double av[4], bv[4];
+      T av[4], bv[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
 #pragma unroll
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) pchol_update_kernel(double *buf, con
     }
     __syncthreads();
   }
-  double *gc = buf + bi.base + (long long)rJ * bi.lda + rI;
+  T *gc = buf + bi.base + (long long)rJ * bi.lda + rI;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = ty + 16 * j;
@@ -223,83 +230,169 @@ __global__ void __launch_bounds__(kThreads) pchol_update_kernel(double *buf, con
 // solves with the partial factor (one CTA per problem, vector in smem)
 // forward : v <- [L11 0; L21 I]^-1 v
 // backward: v_top <- L11^-T (v_top - L21' v_bottom), v_bottom unchanged
+// The arithmetic runs in the factor's precision; the vector in global memory
+// is FP64 either way.  Per 64-column step the diagonal tile and its
+// reciprocal pivots are staged in shared memory (the sequential part runs
+// there), and the panel below it is streamed with eight independent loads
+// per thread in flight so the step is bandwidth-, not latency-bound.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) ptri_fwd_kernel(const double *__restrict__ buf,
-                                                            const BlkInfo *blk, double *vec) {
-  extern __shared__ double v[];
+constexpr int kSolveThreads = 1024;
+
+template <typename T>
+__device__ __forceinline__ void stage_diag_tile(const T *L, long long lda, int c0, int nr,
+                                                int npiv, T (*dt)[NB + 1], T *dinv) {
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    if (r < nr && c < npiv) dt[r][c] = L[(long long)(c0 + c) * lda + c0 + r];
+  }
+  for (int c = threadIdx.x; c < npiv; c += blockDim.x)
+    dinv[c] = T(1) / L[(long long)(c0 + c) * lda + c0 + c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads) ptri_fwd_kernel(const T *__restrict__ buf,
+                                                                 const BlkInfo *blk,
+                                                                 double *vec) {
+  extern __shared__ __align__(16) unsigned char vraw[];
+  __shared__ T dt[NB][NB + 1];   // diagonal tile, dt[r][c]
+  __shared__ T dinv[NB];
+  T *v = reinterpret_cast<T *>(vraw);
   const BlkInfo bi = blk[blockIdx.x];
   double *gv = vec + bi.voff;
-  const double *L = buf + bi.base;
+  const T *__restrict__ L = buf + bi.base;
   const int a = bi.a;
   const long long lda = bi.lda;
-  for (int i = threadIdx.x; i < a; i += blockDim.x) v[i] = gv[i];
-  __syncthreads();
+  for (int i = threadIdx.x; i < a; i += blockDim.x) v[i] = (T)gv[i];
   for (int kt = 0; kt < bi.Tp; ++kt) {
     const int c0 = kt * NB;
     const int npiv = min(NB, bi.p - c0);
     const int rend = min(c0 + NB, a);
+    const int nr = rend - c0;
+    stage_diag_tile(L, lda, c0, nr, npiv, dt, dinv);
+    __syncthreads();
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
-      for (int c = c0; c < c0 + npiv; ++c) {
-        const double *col = L + (long long)c * lda;
-        const double vc = v[c] / col[c];
+      for (int c = 0; c < npiv; ++c) {
+        const T vc = v[c0 + c] * dinv[c];
         __syncwarp();
-        if (lane == 0) v[c] = vc;
-        for (int r = c + 1 + lane; r < rend; r += 32) v[r] -= col[r] * vc;
+        if (lane == 0) v[c0 + c] = vc;
+        for (int r = c + 1 + lane; r < nr; r += 32) v[c0 + r] -= dt[r][c] * vc;
         __syncwarp();
       }
     }
     __syncthreads();
+    const T *__restrict__ P = L + (long long)c0 * lda;   // panel columns c0..c0+npiv
     for (int r = rend + threadIdx.x; r < a; r += blockDim.x) {
-      double s = 0.0;
-      const double *Lr = L + (long long)c0 * lda + r;
-      for (int c = 0; c < npiv; ++c) s = fma(Lr[(long long)c * lda], v[c0 + c], s);
-      v[r] -= s;
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+      int c = 0;
+      for (; c + 8 <= npiv; c += 8) {
+        const T l0 = P[(long long)(c + 0) * lda + r], l1 = P[(long long)(c + 1) * lda + r];
+        const T l2 = P[(long long)(c + 2) * lda + r], l3 = P[(long long)(c + 3) * lda + r];
+        const T l4 = P[(long long)(c + 4) * lda + r], l5 = P[(long long)(c + 5) * lda + r];
+        const T l6 = P[(long long)(c + 6) * lda + r], l7 = P[(long long)(c + 7) * lda + r];
+        s0 = fma(l0, v[c0 + c + 0], s0);
+        s1 = fma(l1, v[c0 + c + 1], s1);
+        s2 = fma(l2, v[c0 + c + 2], s2);
+        s3 = fma(l3, v[c0 + c + 3], s3);
+        s0 = fma(l4, v[c0 + c + 4], s0);
+        s1 = fma(l5, v[c0 + c + 5], s1);
+        s2 = fma(l6, v[c0 + c + 6], s2);
+        s3 = fma(l7, v[c0 + c + 7], s3);
+      }
+      for (; c < npiv; ++c) s0 = fma(P[(long long)c * lda + r], v[c0 + c], s0);
+      v[r] -= (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < a; i += blockDim.x) gv[i] = v[i];
+  for (int i = threadIdx.x; i < a; i += blockDim.x) gv[i] = (double)v[i];
 }
 
-__global__ void __launch_bounds__(kThreads) ptri_bwd_kernel(const double *__restrict__ buf,
-                                                            const BlkInfo *blk, double *vec) {
-  extern __shared__ double v[];
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads) ptri_bwd_kernel(const T *__restrict__ buf,
+                                                                 const BlkInfo *blk,
+                                                                 double *vec) {
+  extern __shared__ __align__(16) unsigned char vraw[];
+  __shared__ T dt[NB][NB + 1];   // diagonal tile, dt[r][c]
+  __shared__ T dinv[NB];
+  T *v = reinterpret_cast<T *>(vraw);
   const BlkInfo bi = blk[blockIdx.x];
   double *gv = vec + bi.voff;
-  const double *L = buf + bi.base;
+  const T *__restrict__ L = buf + bi.base;
   const int a = bi.a;
   const long long lda = bi.lda;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < a; i += blockDim.x) v[i] = gv[i];
+  for (int i = threadIdx.x; i < a; i += blockDim.x) v[i] = (T)gv[i];
   __syncthreads();
   for (int kt = bi.Tp - 1; kt >= 0; --kt) {
     const int c0 = kt * NB;
     const int npiv = min(NB, bi.p - c0);
     const int rend = min(c0 + NB, a);
+    const int nr = rend - c0;
+    stage_diag_tile(L, lda, c0, nr, npiv, dt, dinv);
+    // v[c] -= L(rend:a, c)' v(rend:a): one warp per column, lanes over rows
     for (int cc = warp; cc < npiv; cc += nwarp) {
-      const int c = c0 + cc;
-      const double *col = L + (long long)c * lda;
-      double s = 0.0;
-      for (int r = rend + lane; r < a; r += 32) s = fma(col[r], v[r], s);
+      const T *__restrict__ col = L + (long long)(c0 + cc) * lda;
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+      int r = rend + lane;
+      for (; r + 96 < a; r += 128) {
+        const T l0 = col[r], l1 = col[r + 32], l2 = col[r + 64], l3 = col[r + 96];
+        s0 = fma(l0, v[r], s0);
+        s1 = fma(l1, v[r + 32], s1);
+        s2 = fma(l2, v[r + 64], s2);
+        s3 = fma(l3, v[r + 96], s3);
+      }
+      for (; r < a; r += 32) s0 = fma(col[r], v[r], s0);
+      T s = (s0 + s1) + (s2 + s3);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) v[c] -= s;
+      if (lane == 0) v[c0 + cc] -= s;
     }
     __syncthreads();
     if (warp == 0) {
-      for (int c = c0 + npiv - 1; c >= c0; --c) {
-        const double *col = L + (long long)c * lda;
-        double s = 0.0;
-        for (int r = c + 1 + lane; r < rend; r += 32) s = fma(col[r], v[r], s);
+      for (int c = npiv - 1; c >= 0; --c) {
+        T s = T(0);
+        for (int r = c + 1 + lane; r < nr; r += 32) s = fma(dt[r][c], v[c0 + r], s);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) v[c] = (v[c] - s) / col[c];
+        if (lane == 0) v[c0 + c] = (v[c0 + c] - s) * dinv[c];
         __syncwarp();
       }
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < a; i += blockDim.x) gv[i] = v[i];
+  for (int i = threadIdx.x; i < a; i += blockDim.x) gv[i] = (double)v[i];
+}
+
+template <typename T>
+constexpr size_t trsm_smem() {
+  return 2 * NB * (NB + 1) * sizeof(T);
+}
+
+template <typename T>
+cudaError_t pchol_t(T *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
+                    const double *diag0, double tol, int *status, cudaStream_t s) {
+  int nblk = (int)h.size();
+  if (nblk == 0) return cudaSuccess;
+  int maxTp = 0;
+  for (auto &b : h) maxTp = b.Tp > maxTp ? b.Tp : maxTp;
+  for (int k = 0; k < maxTp; ++k) {
+    long long maxPanel = 0, maxTrail = 0;
+    for (auto &b : h) {
+      if (k >= b.Tp) continue;
+      long long t = b.T - k - 1;
+      if (t > maxPanel) maxPanel = t;
+      if (t * (t + 1) / 2 > maxTrail) maxTrail = t * (t + 1) / 2;
+    }
+    count_launch(), pchol_potrf_kernel<T><<<nblk, kThreads, 0, s>>>(buf, info, k, diag0, tol, status);
+    if (maxPanel > 0)
+      count_launch(), pchol_trsm_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads, trsm_smem<T>(), s>>>(
+          buf, info, k);
+    if (maxTrail > 0)
+      count_launch(), pchol_update_kernel<T><<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(buf, info, k);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -314,37 +407,26 @@ cudaError_t launch_dscale(ahlp_problem *p) {
 
 cudaError_t launch_form(ahlp_problem *p, double delta) {
   if (p->ntiles <= 0) return cudaSuccess;
-  FormArgs A{p->ftiles, p->tile_ent, p->ent_pos, p->ent_cb, p->con_idx, p->con_coef,
-             p->dscale, p->blk, p->aug, p->diag0, p->cdiag0, delta};
-  count_launch(), form_aug_kernel<<<(unsigned)p->ntiles, kThreads, 0, p->stream>>>(A);
+  if (p->fac_prec == kPrecFP32) {
+    FormArgs<float> A{p->ftiles, p->tile_ent, p->ent_pos, p->ent_cb, p->con_idx, p->con_coef,
+                      p->dscale, p->blk, p->aug32, p->diag0, p->cdiag0, delta};
+    count_launch(), form_aug_kernel<float><<<(unsigned)p->ntiles, kThreads, 0, p->stream>>>(A);
+  } else {
+    FormArgs<double> A{p->ftiles, p->tile_ent, p->ent_pos, p->ent_cb, p->con_idx, p->con_coef,
+                       p->dscale, p->blk, p->aug, p->diag0, p->cdiag0, delta};
+    count_launch(), form_aug_kernel<double><<<(unsigned)p->ntiles, kThreads, 0, p->stream>>>(A);
+  }
   return cudaGetLastError();
 }
 
-constexpr size_t kTrsmSmem = 2 * NB * (NB + 1) * sizeof(double);
-
 cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
                          const double *diag0, double tol, int *status, cudaStream_t s) {
-  int nblk = (int)h.size();
-  if (nblk == 0) return cudaSuccess;
-  int maxTp = 0;
-  for (auto &b : h) maxTp = b.Tp > maxTp ? b.Tp : maxTp;
-  for (int k = 0; k < maxTp; ++k) {
-    long long maxPanel = 0, maxTrail = 0;
-    for (auto &b : h) {
-      if (k >= b.Tp) continue;
-      long long t = b.T - k - 1;
-      if (t > maxPanel) maxPanel = t;
-      if (t * (t + 1) / 2 > maxTrail) maxTrail = t * (t + 1) / 2;
-    }
-    count_launch(), pchol_potrf_kernel<<<nblk, kThreads, 0, s>>>(buf, info, k, diag0, tol, status);
-    if (maxPanel > 0)
-      count_launch(), pchol_trsm_kernel<<<dim3((unsigned)maxPanel, nblk), kThreads, kTrsmSmem, s>>>(buf, info, k);
-    if (maxTrail > 0)
-      count_launch(), pchol_update_kernel<<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(buf, info, k);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return pchol_t<double>(buf, info, h, diag0, tol, status, s);
+}
+
+cudaError_t launch_pchol_f32(float *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
+                             const double *diag0, double tol, int *status, cudaStream_t s) {
+  return pchol_t<float>(buf, info, h, diag0, tol, status, s);
 }
 
 cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,
@@ -352,20 +434,42 @@ cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int am
   if (nblk == 0 || amax == 0) return cudaSuccess;
   size_t sm = (size_t)amax * sizeof(double);
   if (forward)
-    count_launch(), ptri_fwd_kernel<<<nblk, kThreads, sm, s>>>(buf, info, vec);
+    count_launch(), ptri_fwd_kernel<double><<<nblk, kSolveThreads, sm, s>>>(buf, info, vec);
   else
-    count_launch(), ptri_bwd_kernel<<<nblk, kThreads, sm, s>>>(buf, info, vec);
+    count_launch(), ptri_bwd_kernel<double><<<nblk, kSolveThreads, sm, s>>>(buf, info, vec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ptri_f32(const float *buf, const BlkInfo *info, int nblk, int amax, double *vec,
+                            bool forward, cudaStream_t s) {
+  if (nblk == 0 || amax == 0) return cudaSuccess;
+  size_t sm = (size_t)amax * sizeof(float);
+  if (forward)
+    count_launch(), ptri_fwd_kernel<float><<<nblk, kSolveThreads, sm, s>>>(buf, info, vec);
+  else
+    count_launch(), ptri_bwd_kernel<float><<<nblk, kSolveThreads, sm, s>>>(buf, info, vec);
   return cudaGetLastError();
 }
 
 cudaError_t set_dense_smem_limits(int bytes) {
-  cudaError_t e = cudaFuncSetAttribute(pchol_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kTrsmSmem);
+  cudaError_t e = cudaFuncSetAttribute(pchol_trsm_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)trsm_smem<double>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(ptri_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       bytes);
+  e = cudaFuncSetAttribute(pchol_trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trsm_smem<float>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(ptri_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(ptri_fwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(ptri_bwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(ptri_fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(ptri_bwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
 }
 
 }  // namespace ahlp

@@ -21,7 +21,9 @@ cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int am
 namespace {
 
 struct SArgs {
-  const double *aug;
+  const double *aug;      // FP64 factors (prec == kPrecFP64)
+  const float *aug32;     // FP32 factors (prec == kPrecFP32)
+  int prec;
   const BlkInfo *blk;
   const SchurBlk *sb;
   int N, n0, mg, B, nl;
@@ -36,9 +38,10 @@ struct SArgs {
 };
 
 // entry (r, c) of block i's Schur contribution, local indices, symmetric
-__device__ __forceinline__ double cget(const double *aug, const BlkInfo &bi, int m, int r, int c) {
+__device__ __forceinline__ double cget(const SArgs &A, const BlkInfo &bi, int m, int r, int c) {
   const int R = m + max(r, c), C = m + min(r, c);
-  return aug[bi.base + (long long)C * bi.lda + R];
+  const long long idx = bi.base + (long long)C * bi.lda + R;
+  return A.prec == kPrecFP32 ? (double)A.aug32[idx] : A.aug[idx];
 }
 
 __device__ __forceinline__ int border_local(const SchurBlk &s, int n0, int rb) {
@@ -53,8 +56,8 @@ __global__ void assemble_T_kernel(SArgs A) {
   const int r = idx % lj, s = idx / lj;
   const BlkInfo b0 = A.blk[j], b1 = A.blk[j + 1];
   const SchurBlk s0 = A.sb[j], s1 = A.sb[j + 1];
-  double v = cget(A.aug, b0, s0.m, A.n0 + s0.lprev + r, A.n0 + s0.lprev + s)   // block j, next
-           + cget(A.aug, b1, s1.m, A.n0 + r, A.n0 + s);                        // block j+1, prev
+  double v = cget(A,b0, s0.m, A.n0 + s0.lprev + r, A.n0 + s0.lprev + s)   // block j, next
+           + cget(A,b1, s1.m, A.n0 + r, A.n0 + s);                        // block j+1, prev
   if (r == s) {
     v += A.delta;
     // pivot reference: the link row's diagonal of the full normal matrix,
@@ -75,7 +78,7 @@ __global__ void assemble_H_kernel(SArgs A) {
   const BlkInfo b1 = A.blk[j + 1];
   const SchurBlk s1 = A.sb[j + 1];
   A.Hd[A.h_off[j] + (long long)s * lr + r] =
-      cget(A.aug, b1, s1.m, A.n0 + s1.lprev + r, A.n0 + s);
+      cget(A,b1, s1.m, A.n0 + s1.lprev + r, A.n0 + s);
 }
 
 __global__ void assemble_E_kernel(SArgs A) {
@@ -86,8 +89,8 @@ __global__ void assemble_E_kernel(SArgs A) {
   const int r = idx % lj, rb = idx / lj;
   const BlkInfo b0 = A.blk[j], b1 = A.blk[j + 1];
   const SchurBlk s0 = A.sb[j], s1 = A.sb[j + 1];
-  const double v = cget(A.aug, b0, s0.m, border_local(s0, A.n0, rb), A.n0 + s0.lprev + r) +
-                   cget(A.aug, b1, s1.m, border_local(s1, A.n0, rb), A.n0 + r);
+  const double v = cget(A,b0, s0.m, border_local(s0, A.n0, rb), A.n0 + s0.lprev + r) +
+                   cget(A,b1, s1.m, border_local(s1, A.n0, rb), A.n0 + r);
   A.Et[(long long)rb * A.nl + A.link_off[j] + r] = v;
 }
 
@@ -98,7 +101,7 @@ __global__ void assemble_SB_kernel(SArgs A) {
   double v = 0.0;
   for (int i = 0; i < A.N; ++i) {   // fixed order over blocks
     const SchurBlk s = A.sb[i];
-    v += cget(A.aug, A.blk[i], s.m, border_local(s, A.n0, rb), border_local(s, A.n0, sb));
+    v += cget(A,A.blk[i], s.m, border_local(s, A.n0, rb), border_local(s, A.n0, sb));
   }
   if (rb == sb) v += (rb < A.n0) ? (-1.0 / A.dscale[A.x0off + rb] - A.rho) : A.delta;
   A.SB[(long long)sb * A.B + rb] = v;
@@ -130,11 +133,18 @@ struct CArgs {
   const double *Td_diag0;
   double tol;
   int *status;
+  // explicit chain operators: Linv_j = L_j^-1 (layout of T_j),
+  // Yf_j = L_j^-1 X_{j-1} (layout of H_{j-1}, ld l_j),
+  // Yb_j = L_j^-T X_j'     (stored at H_j's offset, ld l_j)
+  double *Linv, *Yf, *Yb;
+  double *tmp;             // [nl] scratch of the chain solve
+  const int *link_pair;    // [nl] pair of each link row
 };
 
 __global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
   extern __shared__ double T[];   // lmax * lmax
   __shared__ double s_inv;
+  __shared__ double Tinv[128];
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int j = 0; j < A.N - 1; ++j) {
     const int lj = A.l[j];
@@ -176,34 +186,75 @@ __global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
       const int r = i % lj, s = i / lj;
       Tg[i] = (r >= s) ? T[i] : 0.0;
     }
-    // Z_j = L_j^-1 (E_j' - X_{j-1} Z_{j-1}), one column of Z per thread
-    for (int rb = tid; rb < A.B; rb += bd) {
-      double *zc = A.Et + (long long)rb * A.nl + A.link_off[j];
-      if (lp > 0) {
-        const double *X = A.Hd + A.h_off[j - 1];
+    // Z_j = L_j^-1 (E_j' - X_{j-1} Z_{j-1}): the product one thread per entry,
+    // then one warp per column for the triangular solve
+    if (lp > 0) {
+      const double *X = A.Hd + A.h_off[j - 1];
+      for (int i = tid; i < lj * A.B; i += bd) {
+        const int r = i % lj, rb = i / lj;
         const double *zp = A.Et + (long long)rb * A.nl + A.link_off[j - 1];
-        for (int r = 0; r < lj; ++r) {
-          double acc = 0.0;
-          for (int c = 0; c < lp; ++c) acc = fma(X[r + (long long)c * lj], zp[c], acc);
-          zc[r] -= acc;
-        }
+        double acc = 0.0;
+        for (int c = 0; c < lp; ++c) acc = fma(X[r + (long long)c * lj], zp[c], acc);
+        A.Et[(long long)rb * A.nl + A.link_off[j] + r] -= acc;
       }
-      for (int r = 0; r < lj; ++r) {
-        double acc = zc[r];
-        for (int c = 0; c < r; ++c) acc -= T[r + c * lj] * zc[c];
-        zc[r] = acc / T[r + r * lj];
+      __syncthreads();
+    }
+    // reciprocal pivots (FP64 divides are expensive on this part)
+    for (int c = tid; c < lj; c += bd) Tinv[c] = 1.0 / T[c + c * lj];
+    __syncthreads();
+    // Linv_j = L_j^-1, one thread per column
+    double *Li = A.Linv + A.td_off[j];
+    for (int c = tid; c < lj; c += bd) {
+      for (int r = 0; r < c; ++r) Li[r + c * lj] = 0.0;
+      Li[c + c * lj] = Tinv[c];
+      for (int r = c + 1; r < lj; ++r) {
+        double acc = 0.0;
+        for (int q = c; q < r; ++q) acc = fma(T[r + q * lj], Li[q + c * lj], acc);
+        Li[r + c * lj] = -acc * Tinv[r];
       }
     }
-    // X_j = H_j L_j^-T, one row per thread
+    // one thread per column: every lane of every FP64 instruction is useful
+    for (int rb = tid; rb < A.B; rb += bd) {
+      double *zc = A.Et + (long long)rb * A.nl + A.link_off[j];
+      for (int r = 0; r < lj; ++r) {
+        double acc = zc[r];
+        for (int c = 0; c < r; ++c) acc = fma(-T[r + c * lj], zc[c], acc);
+        zc[r] = acc * Tinv[r];
+      }
+    }
+    // X_j = H_j L_j^-T, one thread per row of H_j
     if (j < A.N - 2) {
       const int ln = A.l[j + 1];
       double *H = A.Hd + A.h_off[j];   // l_{j+1} x l_j, ld l_{j+1}
       for (int r = tid; r < ln; r += bd) {
         for (int c = 0; c < lj; ++c) {
           double acc = H[r + (long long)c * ln];
-          for (int q = 0; q < c; ++q) acc -= H[r + (long long)q * ln] * T[c + q * lj];
-          H[r + (long long)c * ln] = acc / T[c + c * lj];
+          for (int q = 0; q < c; ++q) acc = fma(-H[r + (long long)q * ln], T[c + q * lj], acc);
+          H[r + (long long)c * ln] = acc * Tinv[c];
         }
+      }
+    }
+    __syncthreads();
+    // chain operators for the solves: Yf_j = Linv_j X_{j-1}, Yb_j = Linv_j' X_j'
+    if (lp > 0) {
+      const double *X = A.Hd + A.h_off[j - 1];   // l_j x l_{j-1}
+      double *Y = A.Yf + A.h_off[j - 1];
+      for (int i = tid; i < lj * lp; i += bd) {
+        const int r = i % lj, c = i / lj;
+        double acc = 0.0;
+        for (int q = 0; q <= r; ++q) acc = fma(Li[r + q * lj], X[q + (long long)c * lj], acc);
+        Y[r + (long long)c * lj] = acc;
+      }
+    }
+    if (j < A.N - 2 && A.l[j + 1] > 0) {
+      const int ln = A.l[j + 1];
+      const double *X = A.Hd + A.h_off[j];       // l_{j+1} x l_j
+      double *Y = A.Yb + A.h_off[j];             // l_j x l_{j+1}
+      for (int i = tid; i < lj * ln; i += bd) {
+        const int r = i % lj, c = i / lj;
+        double acc = 0.0;
+        for (int q = r; q < lj; ++q) acc = fma(Li[q + r * lj], X[c + (long long)q * ln], acc);
+        Y[r + (long long)c * lj] = acc;
       }
     }
     __syncthreads();
@@ -295,72 +346,83 @@ __global__ void schur_rhs_kernel(RArgs A) {
   A.svec[q] = v;
 }
 
-// forward (dir = 0) or backward (dir = 1) solve with the block-bidiagonal L_T
+// forward (dir = 0) or backward (dir = 1) solve with the block-bidiagonal L_T,
+// using the operators precomputed by the factor:
+//   forward  u_j = Linv_j r_j  - Yf_j u_{j-1}
+//   backward s_j = Linv_j' v_j - Yb_j s_{j+1}
+// The pre-multiplications are independent across pairs.  The recurrence is
+// sequential: warps 0-3 apply pair j's operator from shared memory while
+// warps 4-7 prefetch pair j+1's operator and sizes into the other buffer, so
+// each step costs one barrier and no global-memory round trip.
+constexpr int kChainMaxL = 96;   // link rows per pair handled by the chain kernels
+constexpr size_t kChainSmem = 2 * kChainMaxL * kChainMaxL * sizeof(double);
+
 __global__ void __launch_bounds__(256) chain_solve_kernel(CArgs A, double *u, int dir) {
-  const int tid = threadIdx.x;
-  if (dir == 0) {
-    for (int j = 0; j < A.N - 1; ++j) {
-      const int lj = A.l[j];
-      if (lj == 0) continue;
-      const int lp = j > 0 ? A.l[j - 1] : 0;
-      double *uj = u + A.link_off[j];
-      if (lp > 0) {
-        const double *X = A.Hd + A.h_off[j - 1];
-        const double *up = u + A.link_off[j - 1];
-        for (int r = tid; r < lj; r += blockDim.x) {
-          double acc = 0.0;
-          for (int c = 0; c < lp; ++c) acc = fma(X[r + (long long)c * lj], up[c], acc);
-          uj[r] -= acc;
-        }
-      }
-      __syncthreads();
-      if (tid == 0) {
-        const double *L = A.Td + A.td_off[j];
-        for (int r = 0; r < lj; ++r) {
-          double acc = uj[r];
-          for (int c = 0; c < r; ++c) acc -= L[r + (long long)c * lj] * uj[c];
-          uj[r] = acc / L[r + (long long)r * lj];
-        }
-      }
-      __syncthreads();
+  extern __shared__ double opbuf[];              // 2 x kChainMaxL^2 operators
+  __shared__ double ubuf[2][kChainMaxL];         // solution of the previous pair
+  __shared__ int meta[2][4];                     // l_j, l_other, has operator, pair
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int npairs = A.N - 1;
+  for (int q = tid; q < A.nl; q += bd) {
+    const int j = A.link_pair[q];
+    const int lj = A.l[j], r = q - (int)A.link_off[j];
+    const double *Li = A.Linv + A.td_off[j];
+    const double *uj = u + A.link_off[j];
+    double acc = 0.0;
+    if (dir == 0)
+      for (int c = 0; c <= r; ++c) acc = fma(Li[r + c * lj], uj[c], acc);
+    else
+      for (int c = r; c < lj; ++c) acc = fma(Li[c + r * lj], uj[c], acc);
+    A.tmp[q] = acc;
+  }
+  // operator of step s (pair order depends on the direction) into buffer b
+  auto fetch = [&](int s, int b, int t0, int nt) {
+    const int j = dir == 0 ? s : npairs - 1 - s;
+    const int lj = A.l[j];
+    const int jo = dir == 0 ? j - 1 : j + 1;           // neighbour pair
+    const bool has = jo >= 0 && jo < npairs;
+    const int lo = has ? A.l[jo] : 0;
+    const double *Y = dir == 0 ? (has ? A.Yf + A.h_off[j - 1] : nullptr)
+                               : (has ? A.Yb + A.h_off[j] : nullptr);
+    double *dst = opbuf + (size_t)b * kChainMaxL * kChainMaxL;
+    for (int i = t0; i < lj * lo; i += nt) dst[i] = Y[i];
+    if (t0 == 0) {
+      meta[b][0] = lj;
+      meta[b][1] = lo;
+      meta[b][3] = j;
     }
-  } else {
-    for (int j = A.N - 2; j >= 0; --j) {
-      const int lj = A.l[j];
-      if (lj == 0) continue;
-      double *uj = u + A.link_off[j];
-      if (j < A.N - 2 && A.l[j + 1] > 0) {
-        const int ln = A.l[j + 1];
-        const double *X = A.Hd + A.h_off[j];   // l_{j+1} x l_j
-        const double *un = u + A.link_off[j + 1];
-        for (int c = tid; c < lj; c += blockDim.x) {
-          double acc = 0.0;
-          for (int r = 0; r < ln; ++r) acc = fma(X[r + (long long)c * ln], un[r], acc);
-          uj[c] -= acc;
-        }
+  };
+  if (npairs > 0) fetch(0, 0, tid, bd);
+  __syncthreads();
+  for (int s = 0; s < npairs; ++s) {
+    const int b = s & 1;
+    const int lj = meta[b][0], lo = meta[b][1], j = meta[b][3];
+    if (tid < 128) {
+      const double *Yop = opbuf + (size_t)b * kChainMaxL * kChainMaxL;
+      for (int r = tid; r < lj; r += 128) {
+        double acc = A.tmp[A.link_off[j] + r];
+        for (int c = 0; c < lo; ++c) acc = fma(-Yop[r + c * lj], ubuf[b][c], acc);
+        u[A.link_off[j] + r] = acc;
+        ubuf[b ^ 1][r] = acc;
       }
-      __syncthreads();
-      if (tid == 0) {
-        const double *L = A.Td + A.td_off[j];
-        for (int r = lj - 1; r >= 0; --r) {
-          double acc = uj[r];
-          for (int c = r + 1; c < lj; ++c) acc -= L[c + (long long)r * lj] * uj[c];
-          uj[r] = acc / L[r + (long long)r * lj];
-        }
-      }
-      __syncthreads();
+    } else if (s + 1 < npairs) {
+      fetch(s + 1, b ^ 1, tid - 128, bd - 128);
     }
+    __syncthreads();
   }
 }
 
-// border rhs: sB -= Z' uT      (one thread per border row)
+// border rhs: sB -= Z' uT      (one warp per border row, lanes over link rows)
 __global__ void border_rhs_kernel(const double *Z, int B, int nl, double *svec) {
-  const int rb = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (rb >= B) return;
   const double *zc = Z + (long long)rb * nl;
   double acc = 0.0;
-  for (int q = 0; q < nl; ++q) acc = fma(zc[q], svec[q], acc);
-  svec[nl + rb] -= acc;
+  for (int q = lane; q < nl; q += 32) acc = fma(zc[q], svec[q], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) svec[nl + rb] -= acc;
 }
 
 // uT -= Z sB      (one thread per link row)
@@ -430,7 +492,7 @@ __global__ void residual_tail_kernel(double *e_d, double *e_c, const double *dx,
 inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 SArgs sargs(ahlp_problem *p, double delta, double rho) {
-  return SArgs{p->aug, p->blk, p->sblk, p->N, p->n0, p->mg, p->B, p->nl,
+  return SArgs{p->aug, p->aug32, p->fac_prec, p->blk, p->sblk, p->N, p->n0, p->mg, p->B, p->nl,
                p->td_off_d, p->h_off_d, p->link_off_d, p->l_d,
                p->Td, p->Hd, p->Et, p->SB, p->Td_diag0, p->dscale,
                p->xoff[p->N], delta, rho, p->cdiag0, p->sb_ref};
@@ -438,7 +500,8 @@ SArgs sargs(ahlp_problem *p, double delta, double rho) {
 
 CArgs cargs(ahlp_problem *p) {
   return CArgs{p->N, p->B, p->nl, p->l_d, p->td_off_d, p->h_off_d, p->link_off_d,
-               p->Td, p->Hd, p->Et, p->Td_diag0, p->fac_pivot_tol, p->status};
+               p->Td, p->Hd, p->Et, p->Td_diag0, p->fac_pivot_tol, p->status,
+               p->Linv, p->Yf, p->Yb, p->chain_tmp, p->link_pair_d};
 }
 
 }  // namespace
@@ -509,7 +572,9 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
   if (e != cudaSuccess) return e;
   count_launch(), pack_rhs_kernel<<<dim3(nb(p->amax, 256), p->N), 256, 0, s>>>(p->blk, p->sblk, p->yoff_d,
                                                                 p->rhat, p->vec);
-  e = launch_ptri(p->aug, p->blk, p->N, p->amax, p->vec, true, s);
+  e = p->fac_prec == kPrecFP32
+          ? launch_ptri_f32(p->aug32, p->blk, p->N, p->amax, p->vec, true, s)
+          : launch_ptri(p->aug, p->blk, p->N, p->amax, p->vec, true, s);
   if (e != cudaSuccess) return e;
   if (p->nS > 0) {
     int lmax = 0;
@@ -520,9 +585,10 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
             p->xoff[p->N], p->svec};
     count_launch(), schur_rhs_kernel<<<nb(p->nS, 256), 256, 0, s>>>(R);
     CArgs C = cargs(p);
-    if (p->nl > 0 && lmax > 0) count_launch(), chain_solve_kernel<<<1, 256, 0, s>>>(C, p->svec, 0);
+    if (p->nl > 0 && lmax > 0)
+      count_launch(), chain_solve_kernel<<<1, 256, kChainSmem, s>>>(C, p->svec, 0);
     if (p->B > 0) {
-      if (p->nl > 0) count_launch(), border_rhs_kernel<<<nb(p->B, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
+      if (p->nl > 0) count_launch(), border_rhs_kernel<<<nb((long long)p->B * 32, 256), 256, 0, s>>>(p->Et, p->B, p->nl, p->svec);
       double *sb = p->svec + p->nl;
       if (p->n0 > 0) {
         e = launch_ptri(p->border, p->bx_info, 1, p->B, sb, true, s);
@@ -541,14 +607,17 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
       }
       if (p->nl > 0) count_launch(), link_back_kernel<<<nb(p->nl, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
     }
-    if (p->nl > 0 && lmax > 0) count_launch(), chain_solve_kernel<<<1, 256, 0, s>>>(C, p->svec, 1);
+    if (p->nl > 0 && lmax > 0)
+      count_launch(), chain_solve_kernel<<<1, 256, kChainSmem, s>>>(C, p->svec, 1);
     int kmax = 0;
     for (int k : p->ki) kmax = std::max(kmax, k);
     if (kmax > 0)
       count_launch(), gather_schur_kernel<<<dim3(nb(kmax, 256), p->N), 256, 0, s>>>(p->blk, p->sblk, p->kmap,
                                                                   p->kmap_off_d, p->svec, p->vec);
   }
-  e = launch_ptri(p->aug, p->blk, p->N, p->amax, p->vec, false, s);
+  e = p->fac_prec == kPrecFP32
+          ? launch_ptri_f32(p->aug32, p->blk, p->N, p->amax, p->vec, false, s)
+          : launch_ptri(p->aug, p->blk, p->N, p->amax, p->vec, false, s);
   if (e != cudaSuccess) return e;
   int mmax = 0;
   for (int v : p->mi) mmax = std::max(mmax, v);
@@ -580,8 +649,11 @@ cudaError_t launch_residual(ahlp_problem *p, const double *r_d, const double *r_
 }
 
 cudaError_t set_schur_smem_limits(int bytes) {
-  return cudaFuncSetAttribute(chain_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              bytes);
+  cudaError_t e = cudaFuncSetAttribute(chain_factor_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(chain_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kChainSmem);
 }
 
 }  // namespace ahlp

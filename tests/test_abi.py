@@ -101,8 +101,8 @@ def test_unsupported_batch_and_precision():
     st, _ = _create_status(lp, batch=2)
     assert st == -3
     L = _lib()
-    st, msg = _create_status(lp, options=L.default_options(precision=1))
-    assert st == -3 and "FP64" in msg
+    st, msg = _create_status(lp, options=L.default_options(precision=7))
+    assert st == -1 and "precision" in msg
 
 
 def test_valid_problem_without_gpu_reports_cuda_error():

@@ -177,7 +177,7 @@ def test_shared_iterates_of_oracle_trajectory(P, seed):
     A, b, c = olp.assemble(lp)
     rec = []
     oipm.solve(A, b, c, record=rec)
-    prob = P.arrowhead_lp_create(lp)
+    prob = P.arrowhead_lp_create(lp, _tight(P))
     checked = 0
     for r in rec:
         if r["mu"] < 1e-6:
