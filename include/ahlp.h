@@ -104,16 +104,22 @@ typedef struct {
   double  delta;        /* dual regularisation of the factor: +delta on the diagonal
                            of M_i, of the link rows and of the global rows (1e-8).
                            Only the preconditioner is regularised: kkt_solve
-                           solves the unregularised Newton system.              */
+                           solves the unregularised Newton system.  ipm_solve
+                           raises it x100 (up to 1e-4) when a NaN persists after
+                           the FP64 and pivot-threshold safeguards            */
   double  rho;          /* primal regularisation of the factor on x_0 (0)        */
-  int32_t refine_max;   /* GMRES iterations per KKT solve, at most 64 (20)        */
+  int32_t refine_max;   /* GMRES iterations per KKT solve, at most 64 (40)        */
   double  refine_tol;   /* target relative Newton residual (1e-10)                */
   double  pivot_tol;    /* a pivot not above pivot_tol * (its diagonal before
                            elimination) has lost its digits to cancellation and
                            is clamped to that value (1e-12); ipm_solve coarsens
                            it x100 (up to 1e-8) when a direction's residual
-                           stays above 1e-6                                      */
+                           stays above 1e-6 or a NaN appears, once the block
+                           factors are FP64                                      */
   int32_t verbose;      /* 0: silent                                              */
+  double  fp32_cond_max;/* mixed precision: the block factors run in FP32 while
+                           max(d)/min(d), d = x/z, stays at or below this value,
+                           and in FP64 beyond it (1e14)                          */
 } ahlp_options;
 
 typedef struct {

@@ -43,7 +43,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("eta", C.c_double), ("delta", C.c_double), ("rho", C.c_double),
                 ("refine_max", C.c_int32), ("refine_tol", C.c_double),
-                ("pivot_tol", C.c_double), ("verbose", C.c_int32)]
+                ("pivot_tol", C.c_double), ("verbose", C.c_int32),
+                ("fp32_cond_max", C.c_double)]
 
 
 class Result(C.Structure):

@@ -14,15 +14,26 @@ namespace ahlp {
 constexpr int NB = 64;            // tile edge of the dense kernels
 constexpr int kPrecFP64 = 0;      // factor storage of the block matrices
 constexpr int kPrecFP32 = 1;
-constexpr double kFp32PivotTol = 1e-6;   // smallest clamp threshold for FP32 pivots
-constexpr long long kSmemVecBytes = 160 * 1024;   // dynamic smem of the block solves
-constexpr double kCondSwitch = 1e10;     // max(d)/min(d) above which FP32 factors give way to FP64
+constexpr double kFp32PivotTol = 1e-6;    // smallest clamp threshold for FP32 pivots
+constexpr long long kSmemVecBytes = 160 * 1024;   // dynamic smem of the border solves
 constexpr int kThreads = 256;     // threads per CTA of the dense kernels
 
 // One dense lower-triangular "partial Cholesky" problem: an a x a matrix
 // (column-major, leading dimension lda, element offset base) whose first p
 // pivots are eliminated.  After the factorisation the (p..a) x (p..a) corner
 // holds the Schur complement of the leading p x p block.
+// CSR matrix on the device with its rows binned by length: rows up to
+// kShortRow nonzeros go to 8-lane groups, the rest (the dense linking-variable
+// rows of A') to one CTA each.
+constexpr int kShortRow = 256;
+struct SpMat {
+  const int *rp = nullptr, *ci = nullptr;
+  const double *v = nullptr;
+  long long rows = 0;
+  const int *long_rows = nullptr;   // [n_long] rows with more than kShortRow nonzeros
+  int n_long = 0;
+};
+
 struct BlkInfo {
   long long base;    // offset of element (0,0) in its buffer
   long long voff;    // offset of this problem's vector segment in solve vectors
@@ -31,6 +42,7 @@ struct BlkInfo {
   int T, Tp;         // tiles of a, tiles holding pivots
   int tag;           // added to the problem index in pivot reports (kTag*)
   long long cdoff;   // offset of the corner (non-pivot) diagonal in cdiag0
+  long long ioff;    // offset of its Tp inverted diagonal tiles (block solves)
 };
 constexpr int kTagBorderX = 1 << 20;   // pivot reports of the border x_0 factor
 constexpr int kTagBorderG = 2 << 20;   // pivot reports of the border y_g factor
@@ -98,11 +110,18 @@ struct ahlp_problem {
   int *AT_rp = nullptr, *AT_ci = nullptr;          // CSR of A' (n x m)
   double *AT_v = nullptr;
   unsigned char *is_x0 = nullptr;                  // [n] 1 for x_0 columns
+  ahlp::SpMat Amat, ATmat;                         // A and A' with their long-row lists
 
   // ---- factor storage -----------------------------------------------------
   double *aug = nullptr;            // all augmented matrices, FP64 (allocated when first used)
   float *aug32 = nullptr;           // the same layout in FP32 (mixed mode)
   long long aug_elems = 0;
+  // per pivot tile of every block, a 64x64 column-major tile: the inverse of
+  // the pivot triangle on its pivot rows, the factor itself on the non-pivot
+  // rows of a block's last pivot tile, zeros elsewhere
+  double *tinv = nullptr;
+  float *tinv32 = nullptr;
+  long long tinv_elems = 0;
   int fac_prec = 0;                 // precision of the current factor (kPrecFP64/kPrecFP32)
   ahlp::BlkInfo *blk = nullptr;     // [N]
   std::vector<ahlp::BlkInfo> h_blk;
@@ -152,6 +171,7 @@ struct ahlp_problem {
   // ---- vectors ------------------------------------------------------------
   double *x = nullptr, *z = nullptr, *dscale = nullptr;   // current point, d = x/z
   double *vec = nullptr;      // block solve segments [sum a_i]
+  float *vec32 = nullptr;     // FP32 copy of the forward solution (FP32 factors)
   double *svec = nullptr;     // Schur vector [nS]
   double *f = nullptr, *g = nullptr, *rhat = nullptr;      // solve scratch
   double *stg[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // staging for host I/O
@@ -166,6 +186,13 @@ struct ahlp_problem {
   double *scal = nullptr;     // device scalars
   double *h_scal = nullptr;   // pinned host scalars
   int *status = nullptr;      // device status words [4]
+  // wavefront block solves: (block, row tile) jobs in ticket order, one ready
+  // flag per tile, then the forward and backward ticket counters
+  int *trsv_fsched = nullptr, *trsv_bsched = nullptr;   // [2 * jobs]
+  int *trsv_flag_off = nullptr;   // [N] first flag of each block
+  int *trsv_flags = nullptr;      // [trsv_nflags + 2]
+  int *trsv_err = nullptr;        // set when a wait timed out
+  int trsv_nf = 0, trsv_nb = 0, trsv_nflags = 0;
   int tiny_pivots = 0;
   bool factored = false;
   bool assembled = false;     // the Schur complement of the last kkt_factor exists
@@ -193,11 +220,15 @@ cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<Blk
                          const double *diag0, double tol, int *status, cudaStream_t s);
 cudaError_t launch_pchol_f32(float *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
                              const double *diag0, double tol, int *status, cudaStream_t s);
-// forward / backward solves with the partial factors (vectors FP64)
+// forward / backward solves with one partial factor per CTA (the border
+// factors; vectors FP64, held in shared memory)
 cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,
                         bool forward, cudaStream_t s);
-cudaError_t launch_ptri_f32(const float *buf, const BlkInfo *info, int nblk, int amax,
-                            double *vec, bool forward, cudaStream_t s);
+// inverted diagonal tiles of the current block factors (p->tinv / tinv32)
+cudaError_t launch_tinv(ahlp_problem *p);
+// forward / backward wavefront solves with all block factors (p->vec, in the
+// precision of the current factor); wait timeouts set p->trsv_err
+cudaError_t launch_trsv(ahlp_problem *p, bool forward);
 cudaError_t launch_schur_assemble(ahlp_problem *p, double delta, double rho);
 cudaError_t launch_schur_factor(ahlp_problem *p);
 cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
@@ -213,9 +244,8 @@ enum RedOp { RED_DOT = 0, RED_MAXABS = 1, RED_MINSTEP = 2, RED_MIN = 3, RED_SUM 
 // device scalar.
 cudaError_t launch_reduce(ahlp_problem *p, int op, const double *a, const double *b,
                           long long len, double *out);
-cudaError_t launch_spmv(const int *rp, const int *ci, const double *v, long long rows,
-                        const double *x, double *y, double alpha, const double *yadd,
-                        cudaStream_t s);   // y = yadd + alpha * A x   (yadd may be null)
+cudaError_t launch_spmv(const SpMat &A, const double *x, double *y, double alpha,
+                        const double *yadd, cudaStream_t s);   // y = yadd + alpha A x (yadd may be null)
 cudaError_t launch_axpby(double *y, const double *x, double a, double b, long long n,
                          cudaStream_t s);  // y = a x + b y
 // generic elementwise kernels for the IPM

@@ -239,10 +239,11 @@ void ahlp_default_options(ahlp_options *o) {
   o->eta = 0.9995;
   o->delta = 1e-8;
   o->rho = 0.0;
-  o->refine_max = 20;
+  o->refine_max = 40;
   o->refine_tol = 1e-10;
   o->pivot_tol = 1e-12;
   o->verbose = 0;
+  o->fp32_cond_max = 1e14;
 }
 
 const char *ahlp_status_string(int s) {
@@ -296,7 +297,8 @@ static int check_options(const ahlp_options &o, std::string &err) {
     return AHLP_ERR_INVALID_ARG;
   }
   if (o.max_iter < 0 || !(o.tol > 0) || !(o.eta > 0 && o.eta < 1) || o.delta < 0 || o.rho < 0 ||
-      o.refine_max < 0 || !(o.refine_tol > 0) || !(o.pivot_tol >= 0)) {
+      o.refine_max < 0 || !(o.refine_tol > 0) || !(o.pivot_tol >= 0) ||
+      !(o.fp32_cond_max >= 1)) {
     err = "invalid option value";
     return AHLP_ERR_INVALID_ARG;
   }
@@ -462,7 +464,7 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     // ---- per-block layout ------------------------------------------------------
     p->h_blk.resize(N);
     p->h_sblk.resize(N);
-    long long base = 0, voff = 0, d0 = 0, cd = 0;
+    long long base = 0, voff = 0, d0 = 0, cd = 0, ioff = 0;
     for (int i = 0; i < N; ++i) {
       const int lp = i > 0 ? l[i - 1] : 0, ln = i + 1 < N ? l[i] : 0;
       const int k = n0 + lp + ln + mg;
@@ -480,6 +482,8 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
       bi.p = m;
       bi.T = (a + NB - 1) / NB;
       bi.Tp = (m + NB - 1) / NB;
+      bi.ioff = ioff;
+      ioff += (long long)bi.Tp * NB * NB;
       p->h_blk[i] = bi;
       base += round_up((long long)bi.lda * a, 32);
       voff += a;
@@ -498,11 +502,12 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
       p->h_sblk[i] = sb;
     }
     p->aug_elems = base;
+    p->tinv_elems = ioff;
     p->vec_elems = voff;
-    // the block solves keep a block's vector in shared memory next to a
+    // the border solves keep the border vector in shared memory next to a
     // staged 64x64 tile; the link-chain kernels keep one l x l block there
-    if ((long long)p->amax * 8 > kSmemVecBytes || (long long)p->B * 8 > kSmemVecBytes)
-      fail(AHLP_ERR_UNSUPPORTED, "a block's augmented order exceeds 20480");
+    if ((long long)p->B * 8 > kSmemVecBytes)
+      fail(AHLP_ERR_UNSUPPORTED, "the border (linking variables + global rows) exceeds 20480");
     for (int v : l)
       if (v > 96) fail(AHLP_ERR_UNSUPPORTED, "more than 96 local link rows per block pair");
     // ---- formation patterns --------------------------------------------------
@@ -589,13 +594,60 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->AT_ci = dupload(p, ATci);
     p->AT_v = dupload(p, ATv);
     p->is_x0 = dupload(p, isx0);
-    if (p->opt.precision == AHLP_PREC_MIXED)
+    auto make_spmat = [&](const std::vector<int> &rp, const int *drp, const int *dci,
+                          const double *dv) {
+      SpMat M;
+      M.rp = drp;
+      M.ci = dci;
+      M.v = dv;
+      M.rows = (long long)rp.size() - 1;
+      std::vector<int> lr;
+      for (long long r = 0; r < M.rows; ++r)
+        if (rp[r + 1] - rp[r] > kShortRow) lr.push_back((int)r);
+      M.n_long = (int)lr.size();
+      if (!lr.empty()) M.long_rows = dupload(p, lr);
+      return M;
+    };
+    p->Amat = make_spmat(Arp, p->A_rp, p->A_ci, p->A_v);
+    p->ATmat = make_spmat(ATrp, p->AT_rp, p->AT_ci, p->AT_v);
+    if (p->opt.precision == AHLP_PREC_MIXED) {
       p->aug32 = dalloc<float>(p, p->aug_elems);
-    else
+      p->tinv32 = dalloc<float>(p, std::max(p->tinv_elems, 1LL));
+      p->vec32 = dalloc<float>(p, std::max(p->vec_elems, 1LL));
+    } else {
       p->aug = dalloc<double>(p, p->aug_elems);
+      p->tinv = dalloc<double>(p, std::max(p->tinv_elems, 1LL));
+    }
     p->fac_prec = p->opt.precision == AHLP_PREC_MIXED ? kPrecFP32 : kPrecFP64;
     p->blk = dupload(p, p->h_blk);
     p->sblk = dupload(p, p->h_sblk);
+    {
+      // wavefront schedules of the block solves: forward in increasing row
+      // tile, backward in decreasing pivot tile, blocks interleaved per wave
+      std::vector<int> fs, bs, foff(N);
+      int nflags = 0, maxT = 0, maxTp = 0;
+      for (int i = 0; i < N; ++i) {
+        foff[i] = nflags;
+        nflags += p->h_blk[i].T;
+        maxT = std::max(maxT, p->h_blk[i].T);
+        maxTp = std::max(maxTp, p->h_blk[i].Tp);
+      }
+      for (int r = 0; r < maxT; ++r)
+        for (int i = 0; i < N; ++i)
+          if (r < p->h_blk[i].T) fs.insert(fs.end(), {i, r});
+      for (int w = 0; w < maxTp; ++w)
+        for (int i = 0; i < N; ++i)
+          if (w < p->h_blk[i].Tp) bs.insert(bs.end(), {i, p->h_blk[i].Tp - 1 - w});
+      p->trsv_nf = (int)fs.size() / 2;
+      p->trsv_nb = (int)bs.size() / 2;
+      p->trsv_nflags = nflags;
+      if (!fs.empty()) p->trsv_fsched = dupload(p, fs);
+      if (!bs.empty()) p->trsv_bsched = dupload(p, bs);
+      if (N > 0) p->trsv_flag_off = dupload(p, foff);
+      p->trsv_flags = dalloc<int>(p, nflags + 2);
+      p->trsv_err = dalloc<int>(p, 1);
+      ck(cudaMemset(p->trsv_err, 0, sizeof(int)), "memset");
+    }
     p->diag0 = dalloc<double>(p, std::max(d0, 1LL));
     p->cdiag0 = dalloc<double>(p, std::max(cd, 1LL));
     p->cdiag_elems = cd;
@@ -722,8 +774,15 @@ void read_scalars(ahlp_problem *p, int k) {
 int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
   // an FP32 pivot that lost six digits is rounding noise
   p->fac_pivot_tol = p->fac_prec == kPrecFP32 ? std::max(pivot_tol, kFp32PivotTol) : pivot_tol;
-  if (p->fac_prec == kPrecFP32 && !p->aug32) p->aug32 = dalloc<float>(p, p->aug_elems);
-  if (p->fac_prec == kPrecFP64 && !p->aug) p->aug = dalloc<double>(p, p->aug_elems);
+  if (p->fac_prec == kPrecFP32 && !p->aug32) {
+    p->aug32 = dalloc<float>(p, p->aug_elems);
+    p->tinv32 = dalloc<float>(p, std::max(p->tinv_elems, 1LL));
+    p->vec32 = dalloc<float>(p, std::max(p->vec_elems, 1LL));
+  }
+  if (p->fac_prec == kPrecFP64 && !p->aug) {
+    p->aug = dalloc<double>(p, p->aug_elems);
+    p->tinv = dalloc<double>(p, std::max(p->tinv_elems, 1LL));
+  }
   cudaStream_t s = p->stream;
   // strictly positive point required (Sec. 2.3: x, z > 0)
   ck(launch_reduce(p, RED_MIN, p->x, nullptr, p->n, p->scal + 0), "reduce");
@@ -739,14 +798,14 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
   ck(cudaMemsetAsync(p->cdiag0, 0, std::max(p->cdiag_elems, 1LL) * sizeof(double), s), "memset");
   ck(launch_dscale(p), "dscale");
   if (p->fac_prec == kPrecFP32 && p->n > 0) {
-    // adaptive precision: once D = X Z^-1 spans more than kCondSwitch the
+    // adaptive precision: once D = X Z^-1 spans more than fp32_cond_max the
     // block normal matrices are too ill-conditioned for FP32 factors
     ck(launch_reduce(p, RED_MAXABS, p->dscale, nullptr, p->n, p->scal + 2), "reduce");
     ck(launch_reduce(p, RED_MIN, p->dscale, nullptr, p->n, p->scal + 3), "reduce");
     ck(cudaMemcpyAsync(p->h_scal + 2, p->scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
        "D2H");
     ck(cudaStreamSynchronize(s), "sync");
-    if (!(p->h_scal[2] <= kCondSwitch * p->h_scal[3])) {
+    if (!(p->h_scal[2] <= p->opt.fp32_cond_max * p->h_scal[3])) {
       p->fac_prec = kPrecFP64;
       return factor_impl(p, delta, rho, pivot_tol);
     }
@@ -758,6 +817,7 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
        "pchol");
   else
     ck(launch_pchol(p->aug, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s), "pchol");
+  ck(launch_tinv(p), "diagonal tile inverses");
   ck(cudaEventRecord(p->ev[2], s), "event");
   ck(launch_schur_assemble(p, delta, rho), "schur assemble");
   p->assembled = true;
@@ -770,10 +830,6 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
   cudaEventElapsedTime(&p->stage_ms[1], p->ev[1], p->ev[2]);
   cudaEventElapsedTime(&p->stage_ms[2], p->ev[2], p->ev[3]);
   p->tiny_pivots = st[1];
-  if (st[0] > 0 && p->fac_prec == kPrecFP32) {   // FP32 range exceeded: redo in FP64
-    p->fac_prec = kPrecFP64;
-    return factor_impl(p, delta, rho, pivot_tol);
-  }
   if (st[0] > 0) {
     char buf[160];
     if (st[2] >= kTagBorderG)
@@ -785,6 +841,11 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
       snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in block %d row %d", st[2], st[3]);
     else
       snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in link pair %d row %d", -1 - st[2], st[3]);
+    if (p->fac_prec == kPrecFP32) {   // FP32 range or accuracy exceeded: redo in FP64
+      if (p->opt.verbose) printf("%s with FP32 block factors; refactoring in FP64\n", buf);
+      p->fac_prec = kPrecFP64;
+      return factor_impl(p, delta, rho, pivot_tol);
+    }
     return set_err(p, AHLP_ERR_NOT_SPD, buf);
   }
   p->factored = true;
@@ -796,6 +857,7 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
                double *dy, double *dz, bool adjoint, ahlp_solve_info *info) {
   cudaStream_t s = p->stream;
   ck(cudaEventRecord(p->ev[4], s), "event");
+  ck(cudaMemsetAsync(p->trsv_err, 0, sizeof(int), s), "memset");
   ck(launch_solve(p, rd, rp, rc, dx, dy, dz, adjoint), "solve");
   ck(launch_reduce(p, RED_DOT, rd, rd, p->n, p->scal + 10), "reduce");
   ck(launch_reduce(p, RED_DOT, rp, rp, p->m, p->scal + 11), "reduce");
@@ -895,8 +957,13 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
     rel = rn > 0 ? en / rn : en;
   }
   ck(cudaEventRecord(p->ev[5], s), "event");
+  int timed_out = 0;
+  ck(cudaMemcpyAsync(&timed_out, p->trsv_err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
   ck(cudaEventSynchronize(p->ev[5]), "sync");
+  ck(cudaStreamSynchronize(s), "sync");
   cudaEventElapsedTime(&p->stage_ms[3], p->ev[4], p->ev[5]);
+  if (timed_out)
+    return set_err(p, AHLP_ERR_TIMEOUT, "kkt_solve: a block-solve wait exceeded its time limit");
   if (info) {
     info->refine_steps = steps;
     info->rel_residual = rel;

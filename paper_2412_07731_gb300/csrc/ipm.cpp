@@ -36,19 +36,27 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     double **v = p->ipmv;
     double *X = v[V_X], *Y = v[V_Y], *Z = v[V_Z];
     const double eta = p->opt.eta;
-    const double delta = p->opt.delta, rho = p->opt.rho;
-    // Pivot clamping threshold.  It starts at pivot_tol; when a direction's
-    // Newton residual stays above kEscalate after the Krylov refinement (the
-    // degenerate end game, where the clamped block factors stop being a good
-    // preconditioner) the factor is redone with a 100x coarser threshold, up
-    // to kMaxPivotTol, and the coarser value is kept for later iterations.
-    constexpr double kEscalate = 1e-6, kMaxPivotTol = 1e-8;
+    const double rho = p->opt.rho;
+    // Safeguards of the factor, all kept for the later iterations once raised:
+    //  - the block factors start in FP32 in mixed precision and switch to FP64
+    //    once D spans more than fp32_cond_max (or an FP32 pivot overflows);
+    //  - the pivot clamping threshold starts at pivot_tol;
+    //  - the regularisation starts at delta.
+    // A direction whose Newton residual stays above kEscalate after the Krylov
+    // refinement (the degenerate end game, where the clamped factors stop
+    // being a good preconditioner) switches FP32 blocks to FP64, else makes
+    // the threshold 100x coarser (up to kMaxPivotTol).  A NaN in the factor or
+    // in the direction does the same and, once those are exhausted, raises
+    // the regularisation 100x (up to kMaxDelta): the Krylov refinement always
+    // solves the unregularised Newton system, so this only weakens the
+    // preconditioner.  A NaN pivot that passed the threshold is one that lost
+    // nearly all its digits to cancellation; its rounding noise is amplified
+    // through the later clamped columns.
+    constexpr double kEscalate = 1e-6, kMaxPivotTol = 1e-8, kMaxDelta = 1e-4;
     double ptol = p->opt.pivot_tol;
+    double delta = p->opt.delta;
     double last_rel = 0.0;
     int cur_iter = 0;
-    // Mixed precision starts with FP32 block factors.  The factor itself
-    // switches to FP64 once D spans more than kCondSwitch (or an FP32 pivot
-    // overflows); a direction whose residual stalls switches too.
     p->fac_prec = p->opt.precision == AHLP_PREC_MIXED ? kPrecFP32 : kPrecFP64;
     R.fp64_switch_iter = p->fac_prec == kPrecFP32 ? -1 : 0;
     auto factor_at = [&](const double *xx, const double *zz) {
@@ -72,21 +80,20 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       last_rel = info.rel_residual;
       return st;
     };
-    // Escalation after a stalled direction: first FP32 -> FP64 factors, then
-    // coarser pivot thresholds.
-    auto can_escalate = [&]() {
-      if (last_rel <= kEscalate) return false;
-      if (p->fac_prec == kPrecFP32) return true;
-      return ptol * 100.0 <= kMaxPivotTol * 1.0001;
-    };
-    auto escalate = [&]() {
+    // next safeguard; false when none is left (allow_delta: NaN recovery only)
+    auto escalate = [&](bool allow_delta) {
       if (p->fac_prec == kPrecFP32) {
         p->fac_prec = kPrecFP64;
         R.fp64_switch_iter = cur_iter;
-      } else {
+      } else if (ptol * 100.0 <= kMaxPivotTol * 1.0001) {
         ptol *= 100.0;
+      } else if (allow_delta && delta > 0 && delta * 100.0 <= kMaxDelta * 1.0001) {
+        delta *= 100.0;
+      } else {
+        return false;
       }
       ++R.escalations;
+      return true;
     };
     const bool warm = x0 && y0 && z0;
     if (warm) {
@@ -130,8 +137,8 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     status = AHLP_ERR_MAX_ITER;
     for (it = 0;; ++it) {
       // residuals r_p = b - Ax, r_d = c - A'y - z
-      ck(launch_spmv(p->A_rp, p->A_ci, p->A_v, m, X, v[V_RP], -1.0, p->b, s), "spmv");
-      ck(launch_spmv(p->AT_rp, p->AT_ci, p->AT_v, n, Y, v[V_RD], -1.0, p->c, s), "spmv");
+      ck(launch_spmv(p->Amat, X, v[V_RP], -1.0, p->b, s), "spmv");
+      ck(launch_spmv(p->ATmat, Y, v[V_RD], -1.0, p->c, s), "spmv");
       ck(launch_axpby(v[V_RD], Z, -1.0, 1.0, n, s), "axpby");
       ck(launch_reduce(p, RED_MAXABS, v[V_RP], nullptr, m, p->scal + 0), "reduce");
       ck(launch_reduce(p, RED_MAXABS, v[V_RD], nullptr, n, p->scal + 1), "reduce");
@@ -175,25 +182,14 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       cur_iter = it;
       for (;;) {
         int st = factor_at(X, Z);
-        // A NaN pivot in an FP64 factor comes from a pivot that lost nearly all
-        // its digits to cancellation yet passed the threshold: the rounding
-        // noise it carries is amplified through the later clamped columns.  A
-        // coarser threshold clamps it instead, so refactor with one.
-        while (st == AHLP_ERR_NOT_SPD && p->fac_prec == kPrecFP64 &&
-               ptol * 100.0 <= kMaxPivotTol * 1.0001) {
-          ptol *= 100.0;
-          ++R.escalations;
-          st = factor_at(X, Z);
-        }
+        if (st == AHLP_ERR_NOT_SPD && escalate(true)) continue;
         if (st != AHLP_OK) throw Fail{st, p->err};
         // predictor: r_c = -XZe
         ck(launch_mul(v[V_RC], X, Z, -1.0, n, s), "mul");
         st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DXA], v[V_DYA], v[V_DZA]);
+        if (st == AHLP_ERR_NOT_SPD && escalate(true)) continue;
         if (st != AHLP_OK) throw Fail{st, p->err};
-        if (can_escalate()) {
-          escalate();
-          continue;
-        }
+        if (last_rel > kEscalate && escalate(false)) continue;
         ck(launch_reduce(p, RED_MINSTEP, X, v[V_DXA], n, p->scal + 0), "reduce");
         ck(launch_reduce(p, RED_MINSTEP, Z, v[V_DZA], n, p->scal + 1), "reduce");
         read_scalars(p, 2);
@@ -206,11 +202,9 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         // corrector: r_c = sigma mu e - XZe - dXa dZa e
         ck(launch_ipm_rc(v[V_RC], X, Z, v[V_DXA], v[V_DZA], sigma * mu, n, s), "rc");
         st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DX], v[V_DY], v[V_DZ]);
+        if (st == AHLP_ERR_NOT_SPD && escalate(true)) continue;
         if (st != AHLP_OK) throw Fail{st, p->err};
-        if (can_escalate()) {
-          escalate();
-          continue;
-        }
+        if (last_rel > kEscalate && escalate(false)) continue;
         break;
       }
       ck(launch_reduce(p, RED_MINSTEP, X, v[V_DX], n, p->scal + 0), "reduce");

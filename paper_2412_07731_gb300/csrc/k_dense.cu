@@ -363,9 +363,348 @@ __global__ void __launch_bounds__(kSolveThreads) ptri_bwd_kernel(const T *__rest
   for (int i = threadIdx.x; i < a; i += blockDim.x) gv[i] = (double)v[i];
 }
 
+// --------------------------------------------------------------------------
+// Wavefront solves with the block partial factors: one CTA per (block, 64-row
+// tile), so every block's factor is streamed by many SMs at once.
+//
+// Each CTA draws a ticket from an atomic counter and takes the job the
+// schedule lists under that ticket.  The schedule is in wavefront order (tile
+// r of every block before tile r+1 of any block; reversed for the backward
+// sweep), so a tile only ever waits for tiles holding smaller tickets, which
+// are already running: the waits cannot deadlock.  A CTA prefetches its part
+// of the factor before it waits for the tile it needs, solves its diagonal
+// tile, writes its solution rows and publishes them with a release store on
+// its ready flag.  Every wait is bounded: after kWaitLimitNs the error word
+// is set, the CTA stops waiting and the host reports AHLP_ERR_TIMEOUT.
+//
+// forward : v <- [L11 0; L21 I]^-1 v     (all a rows; pivot tiles publish)
+// backward: v_top <- L11^-T (v_top - L21' v_bottom), v_bottom unchanged
+// --------------------------------------------------------------------------
+constexpr int kTrsvThreads = 512;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int load_acquire(const int *f) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void store_release(int *f, int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+}
+
+// Thread-level bounded wait until *f != 0.  Gives up at once when another CTA
+// has already timed out, so a failure does not cascade into more waits.
+__device__ void wait_ready(const int *f, int *err) {
+  if (load_acquire(f)) return;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    __nanosleep(128);
+    if (load_acquire(f)) return;
+    if (load_acquire(err)) return;
+    if (global_ns() - t0 > kWaitLimitNs) {
+      atomicExch(err, 1);
+      return;
+    }
+  }
+}
+
+// Inverted diagonal tiles, one CTA (one thread per column) per pivot tile.
+// Column j of X = L_kk^-1 by forward substitution against e_j.  The
+// non-pivot rows of a block's last pivot tile keep the factor entries, so
+// the solves stage one 64x64 tile that covers their whole diagonal step.
+template <typename T>
+__global__ void __launch_bounds__(NB) tinv_kernel(const T *__restrict__ buf, T *__restrict__ tinv,
+                                                  const BlkInfo *__restrict__ blk,
+                                                  const int *__restrict__ sched) {
+  extern __shared__ __align__(16) unsigned char tinv_raw[];   // tinv_smem<T>() bytes
+  T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(tinv_raw);
+  T(*Xs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(tinv_raw + sizeof(T) * NB * (NB + 1));
+  T *rinv = reinterpret_cast<T *>(tinv_raw + 2 * sizeof(T) * NB * (NB + 1));
+  const int b = sched[2 * blockIdx.x], k = sched[2 * blockIdx.x + 1];
+  const BlkInfo bi = blk[b];
+  const T *__restrict__ L = buf + bi.base;
+  const int r0 = k * NB, nr = min(NB, bi.a - r0), npiv = min(NB, bi.p - r0);
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    Ls[r][c] = (r < nr && c < npiv && r >= c) ? L[(long long)(r0 + c) * bi.lda + r0 + r] : T(0);
+    Xs[r][c] = T(0);
+  }
+  __syncthreads();
+  if (threadIdx.x < npiv) rinv[threadIdx.x] = T(1) / Ls[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < npiv) {
+    for (int i = j; i < npiv; ++i) {
+      T s0 = (i == j) ? T(1) : T(0), s1 = T(0);
+      int q = j;
+      for (; q + 1 < i; q += 2) {
+        s0 = fma(-Ls[i][q], Xs[q][j], s0);
+        s1 = fma(-Ls[i][q + 1], Xs[q + 1][j], s1);
+      }
+      if (q < i) s0 = fma(-Ls[i][q], Xs[q][j], s0);
+      Xs[i][j] = (s0 + s1) * rinv[i];
+    }
+  }
+  __syncthreads();
+  T *__restrict__ out = tinv + bi.ioff + (long long)k * NB * NB;
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    out[i] = r < npiv ? Xs[r][c] : Ls[r][c];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_tile(const T *__restrict__ src, T *dst) {
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) dst[i] = src[i];
+}
+
+// Called by all threads when the next needed tile k may not be published.
+// Warp 0 scans up to 32 flags fl[k + dir*i] in one round (tiles publish in
+// order, so the set flags form a run starting at k), waits (bounded) when
+// none is set yet, and the barrier count broadcasts the length of the run.
+__device__ __forceinline__ int published_run(const int *fl, int k, int dir, int limit, int *err) {
+  const int lane = threadIdx.x & 31;
+  int c = 0;
+  if (threadIdx.x < 32) {
+    for (;;) {
+      const int idx = k + dir * lane;
+      const bool in = dir > 0 ? idx < limit : idx > limit;
+      const bool set = in && load_acquire(fl + idx) != 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, set);
+      c = bal == 0xffffffffu ? 32 : __ffs(~bal) - 1;
+      if (c > 0) break;
+      if (lane == 0) wait_ready(fl + k, err);
+      __syncwarp();
+      if (__any_sync(0xffffffffu, load_acquire(err) != 0)) {   // timed out: the host reports it
+        c = 1;
+        break;
+      }
+    }
+  }
+  return __syncthreads_count(threadIdx.x < 32 && lane < c);
+}
+
+// thread = (row rho of a 64-row tile or chunk, column lane q); lane q owns the
+// columns q, q + kQL, ... of a 64-column tile.  The next tile's factor entries
+// are loaded into registers while the current one is used, so every CTA keeps
+// two tiles of the factor in flight.
+constexpr int kQL = kTrsvThreads / NB;   // column lanes
+constexpr int kJC = NB / kQL;            // columns per thread
+
+template <typename T>
+__global__ void __launch_bounds__(kTrsvThreads, sizeof(T) == 4 ? 2 : 1)
+    trsv_fwd_kernel(const T *__restrict__ buf, const T *__restrict__ tinv,
+                    const BlkInfo *__restrict__ blk, const int *__restrict__ sched,
+                    const int *__restrict__ flag_off, int *flags, int *ticket, int *err,
+                    double *vec, T *vecT) {
+  __shared__ T Xs[NB * NB];   // column-major, Xs[c * NB + r]
+  __shared__ T red[kQL][NB];
+  __shared__ T u[NB];
+  __shared__ T xs[NB];
+  __shared__ int s_job;
+  if (threadIdx.x == 0) s_job = atomicAdd(ticket, 1);
+  __syncthreads();
+  const int b = sched[2 * s_job], r = sched[2 * s_job + 1];
+  const BlkInfo bi = blk[b];
+  const T *__restrict__ L = buf + bi.base;
+  const long long lda = bi.lda;
+  double *gv = vec + bi.voff;
+  T *gvT = vecT + bi.voff;   // solution in the factor's precision (gv itself for FP64)
+  int *fl = flags + flag_off[b];
+  const int r0 = r * NB, nr = min(NB, bi.a - r0);
+  const bool pivtile = r < bi.Tp;
+  const int npiv = pivtile ? min(NB, bi.p - r0) : 0;
+  if (pivtile) stage_tile(tinv + bi.ioff + (long long)r * NB * NB, Xs);
+  const int rho = threadIdx.x & (NB - 1), q = threadIdx.x / NB;
+  const bool rok = rho < nr;
+  const T *__restrict__ Lr = L + r0 + rho;
+  const int nct = min(r, bi.Tp);   // pivot column tiles left of this tile
+  T l[kJC], ln[kJC];
+  auto load_tile = [&](int k, T(&dst)[kJC]) {
+    const int c0 = k * NB, nc = min(NB, bi.p - c0);
+#pragma unroll
+    for (int j = 0; j < kJC; ++j) {
+      const int c = q + kQL * j;
+      dst[j] = (rok && c < nc) ? Lr[(long long)(c0 + c) * lda] : T(0);
+    }
+  };
+  if (nct > 0) load_tile(0, l);
+  T acc0 = T(0), acc1 = T(0);
+  int ready = 0;   // column tiles [0, ready) are published
+  for (int k = 0; k < nct; ++k) {
+    const int c0 = k * NB, nc = min(NB, bi.p - c0);
+    if (k + 1 < nct) load_tile(k + 1, ln);
+    if (k >= ready) ready = k + published_run(fl, k, 1, nct, err);
+#pragma unroll
+    for (int j = 0; j < kJC; ++j) {
+      const int c = q + kQL * j;
+      if (c < nc) {
+        const T xv = __ldcg(gvT + c0 + c);
+        if (j & 1)
+          acc1 = fma(l[j], xv, acc1);
+        else
+          acc0 = fma(l[j], xv, acc0);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kJC; ++j) l[j] = ln[j];
+  }
+  auto sum_lanes = [&](int t) {
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < kQL; ++i) s += red[i][t];
+    return s;
+  };
+  red[q][rho] = acc0 + acc1;
+  __syncthreads();
+  if (threadIdx.x < nr) u[threadIdx.x] = (T)gv[r0 + threadIdx.x] - sum_lanes(threadIdx.x);
+  __syncthreads();
+  if (pivtile) {
+    // pivot rows: x = L_rr^-1 u
+    T s = T(0);
+    if (rho < npiv) {
+#pragma unroll
+      for (int j = 0; j < kJC; ++j) {
+        const int c = q + kQL * j;
+        if (c < npiv) s = fma(Xs[c * NB + rho], u[c], s);
+      }
+    }
+    red[q][rho] = s;
+    __syncthreads();
+    if (threadIdx.x < npiv) xs[threadIdx.x] = sum_lanes(threadIdx.x);
+    __syncthreads();
+    if (npiv < nr) {
+      // non-pivot rows of the last pivot tile: u -= L(rows, pivots) x
+      T s2 = T(0);
+      if (rho >= npiv && rok) {
+#pragma unroll
+        for (int j = 0; j < kJC; ++j) {
+          const int c = q + kQL * j;
+          if (c < npiv) s2 = fma(Xs[c * NB + rho], xs[c], s2);
+        }
+      }
+      red[q][rho] = s2;
+      __syncthreads();
+      if (threadIdx.x >= npiv && threadIdx.x < nr) u[threadIdx.x] -= sum_lanes(threadIdx.x);
+    }
+    if (threadIdx.x < npiv) u[threadIdx.x] = xs[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x < nr) {
+    gv[r0 + threadIdx.x] = (double)u[threadIdx.x];
+    if constexpr (sizeof(T) != sizeof(double)) gvT[r0 + threadIdx.x] = u[threadIdx.x];
+  }
+  if (pivtile) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      store_release(fl + r, 1);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTrsvThreads, sizeof(T) == 4 ? 2 : 1)
+    trsv_bwd_kernel(const T *__restrict__ buf, const T *__restrict__ tinv,
+                    const BlkInfo *__restrict__ blk, const int *__restrict__ sched,
+                    const int *__restrict__ flag_off, int *flags, int *ticket, int *err,
+                    double *vec) {
+  __shared__ T Xs[NB * NB];   // column-major, Xs[c * NB + r]
+  __shared__ T red[kTrsvThreads / 32][kJC];
+  __shared__ T u[NB];
+  __shared__ int s_job;
+  if (threadIdx.x == 0) s_job = atomicAdd(ticket, 1);
+  __syncthreads();
+  const int b = sched[2 * s_job], r = sched[2 * s_job + 1];   // r < Tp
+  const BlkInfo bi = blk[b];
+  const T *__restrict__ L = buf + bi.base;
+  const long long lda = bi.lda;
+  double *gv = vec + bi.voff;
+  int *fl = flags + flag_off[b];
+  const int r0 = r * NB, nr = min(NB, bi.a - r0), npiv = min(NB, bi.p - r0);
+  stage_tile(tinv + bi.ioff + (long long)r * NB * NB, Xs);
+  // lane q dots the tile's columns q, q + kQL, ... with the rows of each chunk
+  const int rho = threadIdx.x & (NB - 1), q = threadIdx.x / NB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T *__restrict__ Lc = L + (long long)r0 * lda;
+  // chunks of rows below the pivots, bottom first: non-pivot rows are inputs,
+  // pivot tiles publish upwards.  Chunk r itself holds the non-pivot rows of
+  // the last pivot tile (if any).
+  const int kend = npiv < nr ? r : r + 1;
+  T l[kJC], ln[kJC], acc[kJC];
+  auto load_chunk = [&](int k, T(&dst)[kJC]) {
+    const int row = k * NB + rho;
+    const bool ok = row < bi.a && (k > r || rho >= npiv);
+#pragma unroll
+    for (int j = 0; j < kJC; ++j) {
+      const int c = q + kQL * j;
+      dst[j] = (ok && c < npiv) ? Lc[(long long)c * lda + row] : T(0);
+    }
+  };
+#pragma unroll
+  for (int j = 0; j < kJC; ++j) acc[j] = T(0);
+  if (bi.T - 1 >= kend) load_chunk(bi.T - 1, l);
+  int ready_from = bi.Tp;   // chunks k >= ready_from are final
+  for (int k = bi.T - 1; k >= kend; --k) {
+    if (k - 1 >= kend) load_chunk(k - 1, ln);
+    // tiles publish in decreasing order
+    if (k > r && k < ready_from) ready_from = k + 1 - published_run(fl, k, -1, r, err);
+    const int row = k * NB + rho;
+    const bool ok = row < bi.a && (k > r || rho >= npiv);
+    const T xv = ok ? (T)__ldcg(gv + row) : T(0);
+#pragma unroll
+    for (int j = 0; j < kJC; ++j) acc[j] = fma(l[j], xv, acc[j]);
+#pragma unroll
+    for (int j = 0; j < kJC; ++j) l[j] = ln[j];
+  }
+  // column c = q + kQL j is summed over the two warps of lane q
+  auto col_sum = [&](int c) {
+    const int cq = c % kQL, cj = c / kQL;
+    return red[2 * cq][cj] + red[2 * cq + 1][cj];
+  };
+#pragma unroll
+  for (int j = 0; j < kJC; ++j) {
+    T s = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp][j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < npiv) u[threadIdx.x] = (T)gv[r0 + threadIdx.x] - col_sum(threadIdx.x);
+  __syncthreads();
+  // x = L_rr^-T u: column c = q + kQL j collects X(rho, c) u(rho) over the rows
+  const T uv = rho < npiv ? u[rho] : T(0);
+#pragma unroll
+  for (int j = 0; j < kJC; ++j) {
+    T s = (rho < npiv) ? Xs[(q + kQL * j) * NB + rho] * uv : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp][j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < npiv) gv[r0 + threadIdx.x] = (double)col_sum(threadIdx.x);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    store_release(fl + r, 1);
+  }
+}
+
 template <typename T>
 constexpr size_t trsm_smem() {
   return 2 * NB * (NB + 1) * sizeof(T);
+}
+
+template <typename T>
+constexpr size_t tinv_smem() {
+  return (2 * NB * (NB + 1) + NB) * sizeof(T);
 }
 
 template <typename T>
@@ -440,19 +779,57 @@ cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int am
   return cudaGetLastError();
 }
 
-cudaError_t launch_ptri_f32(const float *buf, const BlkInfo *info, int nblk, int amax, double *vec,
-                            bool forward, cudaStream_t s) {
-  if (nblk == 0 || amax == 0) return cudaSuccess;
-  size_t sm = (size_t)amax * sizeof(float);
-  if (forward)
-    count_launch(), ptri_fwd_kernel<float><<<nblk, kSolveThreads, sm, s>>>(buf, info, vec);
+cudaError_t launch_trsv(ahlp_problem *p, bool forward) {
+  const int njobs = forward ? p->trsv_nf : p->trsv_nb;
+  if (njobs == 0) return cudaSuccess;
+  cudaStream_t s = p->stream;
+  cudaError_t e =
+      cudaMemsetAsync(p->trsv_flags, 0, (size_t)(p->trsv_nflags + 2) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  int *ticket = p->trsv_flags + p->trsv_nflags + (forward ? 0 : 1);
+  const int *sched = forward ? p->trsv_fsched : p->trsv_bsched;
+  if (p->fac_prec == kPrecFP32) {
+    if (forward)
+      count_launch(), trsv_fwd_kernel<float><<<njobs, kTrsvThreads, 0, s>>>(
+          p->aug32, p->tinv32, p->blk, sched, p->trsv_flag_off, p->trsv_flags, ticket,
+          p->trsv_err, p->vec, p->vec32);
+    else
+      count_launch(), trsv_bwd_kernel<float><<<njobs, kTrsvThreads, 0, s>>>(
+          p->aug32, p->tinv32, p->blk, sched, p->trsv_flag_off, p->trsv_flags, ticket,
+          p->trsv_err, p->vec);
+  } else {
+    if (forward)
+      count_launch(), trsv_fwd_kernel<double><<<njobs, kTrsvThreads, 0, s>>>(
+          p->aug, p->tinv, p->blk, sched, p->trsv_flag_off, p->trsv_flags, ticket, p->trsv_err,
+          p->vec, p->vec);
+    else
+      count_launch(), trsv_bwd_kernel<double><<<njobs, kTrsvThreads, 0, s>>>(
+          p->aug, p->tinv, p->blk, sched, p->trsv_flag_off, p->trsv_flags, ticket, p->trsv_err,
+          p->vec);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tinv(ahlp_problem *p) {
+  if (p->trsv_nb == 0) return cudaSuccess;   // one job per pivot tile
+  if (p->fac_prec == kPrecFP32)
+    count_launch(), tinv_kernel<float><<<p->trsv_nb, NB, tinv_smem<float>(), p->stream>>>(
+        p->aug32, p->tinv32, p->blk, p->trsv_bsched);
   else
-    count_launch(), ptri_bwd_kernel<float><<<nblk, kSolveThreads, sm, s>>>(buf, info, vec);
+    count_launch(), tinv_kernel<double><<<p->trsv_nb, NB, tinv_smem<double>(), p->stream>>>(
+        p->aug, p->tinv, p->blk, p->trsv_bsched);
   return cudaGetLastError();
 }
 
 cudaError_t set_dense_smem_limits(int bytes) {
-  cudaError_t e = cudaFuncSetAttribute(pchol_trsm_kernel<double>,
+  cudaError_t e = cudaFuncSetAttribute(tinv_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tinv_smem<double>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tinv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tinv_smem<float>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(pchol_trsm_kernel<double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)trsm_smem<double>());
   if (e != cudaSuccess) return e;
@@ -464,12 +841,7 @@ cudaError_t set_dense_smem_limits(int bytes) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(ptri_bwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(ptri_fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(ptri_bwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              bytes);
+  return e;
 }
 
 }  // namespace ahlp

@@ -15,9 +15,6 @@
 
 namespace ahlp {
 
-cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,
-                        bool forward, cudaStream_t s);
-
 namespace {
 
 struct SArgs {
@@ -351,16 +348,21 @@ __global__ void schur_rhs_kernel(RArgs A) {
 //   forward  u_j = Linv_j r_j  - Yf_j u_{j-1}
 //   backward s_j = Linv_j' v_j - Yb_j s_{j+1}
 // The pre-multiplications are independent across pairs.  The recurrence is
-// sequential: warps 0-3 apply pair j's operator from shared memory while
-// warps 4-7 prefetch pair j+1's operator and sizes into the other buffer, so
-// each step costs one barrier and no global-memory round trip.
-constexpr int kChainMaxL = 96;   // link rows per pair handled by the chain kernels
-constexpr size_t kChainSmem = 2 * kChainMaxL * kChainMaxL * sizeof(double);
+// sequential; its operators lie contiguously in pair order, so they are
+// staged into shared memory in batches of `stages` steps (one burst of
+// loads per batch), and each step then costs one barrier.
+constexpr int kChainMaxL = 96;         // link rows per pair handled by the chain kernels
+constexpr int kChainMaxStages = 512;   // steps staged per batch, at most
+constexpr size_t kChainSmem = 200 * 1024;
 
-__global__ void __launch_bounds__(256) chain_solve_kernel(CArgs A, double *u, int dir) {
-  extern __shared__ double opbuf[];              // 2 x kChainMaxL^2 operators
-  __shared__ double ubuf[2][kChainMaxL];         // solution of the previous pair
-  __shared__ int meta[2][4];                     // l_j, l_other, has operator, pair
+constexpr int kChainSolveThreads = 1024;
+__global__ void __launch_bounds__(kChainSolveThreads) chain_solve_kernel(CArgs A, double *u,
+                                                                         int dir, int stages,
+                                                                         int lmax) {
+  extern __shared__ double opbuf[];               // operators of one batch, then its tmp rows
+  double *tbuf = opbuf + (size_t)stages * lmax * lmax;
+  __shared__ double ubuf[2][kChainMaxL];          // solution of the previous pair
+  __shared__ int meta[kChainMaxStages][4];        // l_j, l_other, operator offset, pair
   const int tid = threadIdx.x, bd = blockDim.x;
   const int npairs = A.N - 1;
   for (int q = tid; q < A.nl; q += bd) {
@@ -375,40 +377,74 @@ __global__ void __launch_bounds__(256) chain_solve_kernel(CArgs A, double *u, in
       for (int c = r; c < lj; ++c) acc = fma(Li[c + r * lj], uj[c], acc);
     A.tmp[q] = acc;
   }
-  // operator of step s (pair order depends on the direction) into buffer b
-  auto fetch = [&](int s, int b, int t0, int nt) {
-    const int j = dir == 0 ? s : npairs - 1 - s;
-    const int lj = A.l[j];
-    const int jo = dir == 0 ? j - 1 : j + 1;           // neighbour pair
-    const bool has = jo >= 0 && jo < npairs;
-    const int lo = has ? A.l[jo] : 0;
-    const double *Y = dir == 0 ? (has ? A.Yf + A.h_off[j - 1] : nullptr)
-                               : (has ? A.Yb + A.h_off[j] : nullptr);
-    double *dst = opbuf + (size_t)b * kChainMaxL * kChainMaxL;
-    for (int i = t0; i < lj * lo; i += nt) dst[i] = Y[i];
-    if (t0 == 0) {
-      meta[b][0] = lj;
-      meta[b][1] = lo;
-      meta[b][3] = j;
-    }
-  };
-  if (npairs > 0) fetch(0, 0, tid, bd);
-  __syncthreads();
-  for (int s = 0; s < npairs; ++s) {
-    const int b = s & 1;
-    const int lj = meta[b][0], lo = meta[b][1], j = meta[b][3];
-    if (tid < 128) {
-      const double *Yop = opbuf + (size_t)b * kChainMaxL * kChainMaxL;
-      for (int r = tid; r < lj; r += 128) {
-        double acc = A.tmp[A.link_off[j] + r];
-        for (int c = 0; c < lo; ++c) acc = fma(-Yop[r + c * lj], ubuf[b][c], acc);
-        u[A.link_off[j] + r] = acc;
-        ubuf[b ^ 1][r] = acc;
+  int b = 0;
+  for (int s0 = 0; s0 < npairs; s0 += stages) {
+    const int ns = min(stages, npairs - s0);
+    // global range [g0, g1) holding the operators of steps s0 .. s0+ns-1
+    long long g0 = 0, g1 = 0;
+    if (dir == 0) {
+      const int a = max(s0, 1), e = s0 + ns - 1;
+      if (e >= a) {
+        g0 = A.h_off[a - 1];
+        g1 = A.h_off[e - 1] + (long long)A.l[e] * A.l[e - 1];
       }
-    } else if (s + 1 < npairs) {
-      fetch(s + 1, b ^ 1, tid - 128, bd - 128);
+    } else {
+      const int jlo = npairs - s0 - ns, jtop = min(npairs - 1 - s0, npairs - 2);
+      if (jtop >= jlo) {
+        g0 = A.h_off[jlo];
+        g1 = A.h_off[jtop] + (long long)A.l[jtop] * A.l[jtop + 1];
+      }
+    }
+    const double *src = (dir == 0 ? A.Yf : A.Yb) + g0;
+    __syncthreads();   // the previous batch is no longer read; tmp is complete
+    const long long cnt = g1 - g0;
+    for (long long i = tid; i < cnt; i += 8LL * bd) {   // eight loads in flight per thread
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = i + k * bd < cnt ? src[i + k * bd] : 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (i + k * bd < cnt) opbuf[i + k * bd] = v[k];
+    }
+    for (int t = tid; t < ns; t += bd) {
+      const int j = dir == 0 ? s0 + t : npairs - 1 - (s0 + t);
+      const int jo = dir == 0 ? j - 1 : j + 1;
+      const bool has = jo >= 0 && jo < npairs;
+      meta[t][0] = A.l[j];
+      meta[t][1] = has ? A.l[jo] : 0;
+      meta[t][2] = has ? (int)((dir == 0 ? A.h_off[j - 1] : A.h_off[j]) - g0) : 0;
+      meta[t][3] = (int)A.link_off[j];
+    }
+    // the pre-multiplied rows of the batch's pairs (a contiguous range of tmp)
+    {
+      const int jf = dir == 0 ? s0 : npairs - s0 - ns;   // first pair in memory order
+      const int jl = dir == 0 ? s0 + ns - 1 : npairs - 1 - s0;
+      const long long t0 = A.link_off[jf], t1 = A.link_off[jl] + A.l[jl];
+      for (long long i = tid; i < t1 - t0; i += bd) tbuf[i] = A.tmp[t0 + i];
+      if (tid == 0) meta[kChainMaxStages - 1][3] = (int)t0;
     }
     __syncthreads();
+    const int tb0 = meta[kChainMaxStages - 1][3];
+    for (int t = 0; t < ns; ++t, b ^= 1) {
+      const int lj = meta[t][0], lo = meta[t][1], off = meta[t][3];
+      const double *Yop = opbuf + meta[t][2];
+      for (int r = tid; r < lj; r += bd) {
+        // four independent partial sums keep the FP64 dependency chain short
+        double a0 = tbuf[off - tb0 + r], a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = 0;
+        for (; c + 4 <= lo; c += 4) {
+          a0 = fma(-Yop[r + (c + 0) * lj], ubuf[b][c + 0], a0);
+          a1 = fma(-Yop[r + (c + 1) * lj], ubuf[b][c + 1], a1);
+          a2 = fma(-Yop[r + (c + 2) * lj], ubuf[b][c + 2], a2);
+          a3 = fma(-Yop[r + (c + 3) * lj], ubuf[b][c + 3], a3);
+        }
+        for (; c < lo; ++c) a0 = fma(-Yop[r + c * lj], ubuf[b][c], a0);
+        const double acc = (a0 + a1) + (a2 + a3);
+        u[off + r] = acc;
+        ubuf[b ^ 1][r] = acc;
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -568,13 +604,11 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
   cudaError_t e;
   count_launch(), prep_f_kernel<<<nb(n, 256), 256, 0, s>>>(p->f, p->g, r_d, r_c, p->x, p->z, p->dscale, p->is_x0,
                                           n, adjoint ? 1 : 0);
-  e = launch_spmv(p->A_rp, p->A_ci, p->A_v, p->m, p->g, p->rhat, 1.0, r_p, s);
+  e = launch_spmv(p->Amat, p->g, p->rhat, 1.0, r_p, s);
   if (e != cudaSuccess) return e;
   count_launch(), pack_rhs_kernel<<<dim3(nb(p->amax, 256), p->N), 256, 0, s>>>(p->blk, p->sblk, p->yoff_d,
                                                                 p->rhat, p->vec);
-  e = p->fac_prec == kPrecFP32
-          ? launch_ptri_f32(p->aug32, p->blk, p->N, p->amax, p->vec, true, s)
-          : launch_ptri(p->aug, p->blk, p->N, p->amax, p->vec, true, s);
+  e = launch_trsv(p, true);
   if (e != cudaSuccess) return e;
   if (p->nS > 0) {
     int lmax = 0;
@@ -585,8 +619,16 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
             p->xoff[p->N], p->svec};
     count_launch(), schur_rhs_kernel<<<nb(p->nS, 256), 256, 0, s>>>(R);
     CArgs C = cargs(p);
+    // one stage = one operator (<= lmax^2) plus one pair's rows (<= lmax); the
+    // last meta slot is reserved
+    const int stages = (int)std::max<long long>(
+        1, std::min<long long>(kChainMaxStages - 1,
+                               (long long)kChainSmem /
+                                   std::max(1LL, 8LL * ((long long)lmax * lmax + lmax))));
+    const size_t csm = (size_t)stages * ((size_t)lmax * lmax + lmax) * sizeof(double);
     if (p->nl > 0 && lmax > 0)
-      count_launch(), chain_solve_kernel<<<1, 256, kChainSmem, s>>>(C, p->svec, 0);
+      count_launch(), chain_solve_kernel<<<1, kChainSolveThreads, csm, s>>>(C, p->svec, 0, stages,
+                                                                             lmax);
     if (p->B > 0) {
       if (p->nl > 0) count_launch(), border_rhs_kernel<<<nb((long long)p->B * 32, 256), 256, 0, s>>>(p->Et, p->B, p->nl, p->svec);
       double *sb = p->svec + p->nl;
@@ -608,16 +650,15 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
       if (p->nl > 0) count_launch(), link_back_kernel<<<nb(p->nl, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
     }
     if (p->nl > 0 && lmax > 0)
-      count_launch(), chain_solve_kernel<<<1, 256, kChainSmem, s>>>(C, p->svec, 1);
+      count_launch(), chain_solve_kernel<<<1, kChainSolveThreads, csm, s>>>(C, p->svec, 1, stages,
+                                                                             lmax);
     int kmax = 0;
     for (int k : p->ki) kmax = std::max(kmax, k);
     if (kmax > 0)
       count_launch(), gather_schur_kernel<<<dim3(nb(kmax, 256), p->N), 256, 0, s>>>(p->blk, p->sblk, p->kmap,
                                                                   p->kmap_off_d, p->svec, p->vec);
   }
-  e = p->fac_prec == kPrecFP32
-          ? launch_ptri_f32(p->aug32, p->blk, p->N, p->amax, p->vec, false, s)
-          : launch_ptri(p->aug, p->blk, p->N, p->amax, p->vec, false, s);
+  e = launch_trsv(p, false);
   if (e != cudaSuccess) return e;
   int mmax = 0;
   for (int v : p->mi) mmax = std::max(mmax, v);
@@ -627,7 +668,7 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
     count_launch(), schur_dy_kernel<<<nb(p->nl + p->mg, 256), 256, 0, s>>>(p->svec, p->nl, p->n0, p->mg, p->msum,
                                                           dy);
   // dx, dz
-  e = launch_spmv(p->AT_rp, p->AT_ci, p->AT_v, n, dy, p->g, 1.0, nullptr, s);
+  e = launch_spmv(p->ATmat, dy, p->g, 1.0, nullptr, s);
   if (e != cudaSuccess) return e;
   count_launch(), finish_kernel<<<nb(n, 256), 256, 0, s>>>(dx, dz, p->g, p->f, p->dscale, p->x, p->z, r_c,
                                           p->is_x0, p->fac_rho, n, adjoint ? 1 : 0);
@@ -639,9 +680,9 @@ cudaError_t launch_residual(ahlp_problem *p, const double *r_d, const double *r_
                             const double *dz, double *e_d, double *e_p, double *e_c,
                             bool adjoint) {
   cudaStream_t s = p->stream;
-  cudaError_t e = launch_spmv(p->AT_rp, p->AT_ci, p->AT_v, p->n, dy, e_d, -1.0, r_d, s);
+  cudaError_t e = launch_spmv(p->ATmat, dy, e_d, -1.0, r_d, s);
   if (e != cudaSuccess) return e;
-  e = launch_spmv(p->A_rp, p->A_ci, p->A_v, p->m, dx, e_p, -1.0, r_p, s);
+  e = launch_spmv(p->Amat, dx, e_p, -1.0, r_p, s);
   if (e != cudaSuccess) return e;
   count_launch(), residual_tail_kernel<<<nb(p->n, 256), 256, 0, s>>>(e_d, e_c, dx, dz, r_c, p->x, p->z, p->n,
                                                     adjoint ? 1 : 0);

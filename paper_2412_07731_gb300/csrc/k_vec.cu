@@ -82,18 +82,63 @@ cudaError_t run_reduce(const RedArgs &r, double *part, double *out, cudaStream_t
   return cudaGetLastError();
 }
 
-// y[r] = yadd[r] + alpha * sum_k v[k] x[ci[k]], one warp per row
-__global__ void spmv_warp(const int *rp, const int *ci, const double *v, long long rows,
-                          const double *x, double *y, double alpha, const double *yadd) {
-  long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (w >= rows) return;
-  int k0 = rp[w], k1 = rp[w + 1];
-  double s = 0.0;
-  for (int k = k0 + lane; k < k1; k += 32) s += v[k] * x[ci[k]];
+// y[r] = yadd[r] + alpha * sum_k v[k] x[ci[k]].  Short rows: one 8-lane group
+// per row (four rows per warp); rows longer than kShortRow are skipped here
+// and done by spmv_long_rows.  Each row is summed in a fixed order.
+constexpr int kRowLanes = 8;
+__global__ void spmv_short_rows(const int *__restrict__ rp, const int *__restrict__ ci,
+                                const double *__restrict__ v, long long rows,
+                                const double *__restrict__ x, double *y, double alpha,
+                                const double *yadd) {
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
+  const int lane = threadIdx.x & (kRowLanes - 1);
+  int k0 = 0, k1 = 0;
+  if (row < rows) {
+    k0 = rp[row];
+    k1 = rp[row + 1];
+    if (k1 - k0 > kShortRow) k1 = k0;   // long row: its own kernel
+  }
+  double s0 = 0.0, s1 = 0.0;
+  int k = k0 + lane;
+  for (; k + kRowLanes < k1; k += 2 * kRowLanes) {
+    s0 = fma(v[k], x[ci[k]], s0);
+    s1 = fma(v[k + kRowLanes], x[ci[k + kRowLanes]], s1);
+  }
+  if (k < k1) s0 = fma(v[k], x[ci[k]], s0);
+  double s = s0 + s1;
+#pragma unroll
+  for (int o = kRowLanes / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, kRowLanes);
+  if (lane == 0 && row < rows && rp[row + 1] - rp[row] <= kShortRow)
+    y[row] = (yadd ? yadd[row] : 0.0) + alpha * s;
+}
+
+// one CTA per long row, fixed-order tree reduction
+__global__ void __launch_bounds__(256) spmv_long_rows(const int *__restrict__ rp,
+                                                      const int *__restrict__ ci,
+                                                      const double *__restrict__ v,
+                                                      const int *__restrict__ long_rows,
+                                                      const double *__restrict__ x, double *y,
+                                                      double alpha, const double *yadd) {
+  __shared__ double part[8];
+  const int row = long_rows[blockIdx.x];
+  const int k0 = rp[row], k1 = rp[row + 1];
+  double s0 = 0.0, s1 = 0.0;
+  int k = k0 + threadIdx.x;
+  for (; k + 256 < k1; k += 512) {
+    s0 = fma(v[k], x[ci[k]], s0);
+    s1 = fma(v[k + 256], x[ci[k + 256]], s1);
+  }
+  if (k < k1) s0 = fma(v[k], x[ci[k]], s0);
+  double s = s0 + s1;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) y[w] = (yadd ? yadd[w] : 0.0) + alpha * s;
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += part[w];
+    y[row] = (yadd ? yadd[row] : 0.0) + alpha * t;
+  }
 }
 
 __global__ void axpby_k(double *y, const double *x, double a, double b, long long n) {
@@ -197,10 +242,9 @@ cudaError_t launch_maxpy(const double *V, long long ld, int k, const double *coe
 cudaError_t launch_jmul(ahlp_problem *p, const double *vx, const double *vy, const double *vz,
                         double *ox, double *oy, double *oz, bool adjoint) {
   cudaStream_t s = p->stream;
-  cudaError_t e = launch_spmv(p->AT_rp, p->AT_ci, p->AT_v, p->n, vy, ox, 1.0,
-                              adjoint ? nullptr : vz, s);
+  cudaError_t e = launch_spmv(p->ATmat, vy, ox, 1.0, adjoint ? nullptr : vz, s);
   if (e != cudaSuccess) return e;
-  e = launch_spmv(p->A_rp, p->A_ci, p->A_v, p->m, vx, oy, 1.0, nullptr, s);
+  e = launch_spmv(p->Amat, vx, oy, 1.0, nullptr, s);
   if (e != cudaSuccess) return e;
   if (p->n > 0)
     count_launch(), jmul_tail_k<<<blocks_for(p->n, 256), 256, 0, s>>>(ox, oz, vx, vz, p->x, p->z, p->n,
@@ -227,11 +271,14 @@ cudaError_t launch_step_dot(const double *x, const double *dx, double ap, const 
   return run_reduce(r, part, out, s);
 }
 
-cudaError_t launch_spmv(const int *rp, const int *ci, const double *v, long long rows,
-                        const double *x, double *y, double alpha, const double *yadd,
-                        cudaStream_t s) {
-  if (rows <= 0) return cudaSuccess;
-  count_launch(), spmv_warp<<<blocks_for(rows * 32, 256), 256, 0, s>>>(rp, ci, v, rows, x, y, alpha, yadd);
+cudaError_t launch_spmv(const SpMat &A, const double *x, double *y, double alpha,
+                        const double *yadd, cudaStream_t s) {
+  if (A.rows <= 0) return cudaSuccess;
+  count_launch(), spmv_short_rows<<<blocks_for(A.rows * kRowLanes, 256), 256, 0, s>>>(
+      A.rp, A.ci, A.v, A.rows, x, y, alpha, yadd);
+  if (A.n_long > 0)
+    count_launch(), spmv_long_rows<<<A.n_long, 256, 0, s>>>(A.rp, A.ci, A.v, A.long_rows, x, y,
+                                                             alpha, yadd);
   return cudaGetLastError();
 }
 
