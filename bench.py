@@ -3,16 +3,21 @@
 Workload (default): the uniform-block arrowhead LP with N = 64 blocks, each
 A_i 2000 x 3000 with 8 nnz/column (N(0,1) values), 50 linking variables with
 5%-dense columns, 20 local link rows per adjacent pair, planted optimum,
-seed 1 -- solved in FP64.  One step = one IPM iteration (residuals, KKT
-factor, predictor solve, corrector solve, step), i.e. every hot-path stage:
-formation, block partial Cholesky (Schur contributions included), Schur
-assembly + factor, and the solves.
+seed 1.  One step = one complete interior-point solve to relative gap 1e-8
+from Mehrotra's starting point (14 iterations; every iteration runs every
+hot-path stage: formation, batched block partial Cholesky with the Schur
+contributions, Schur assembly + link-chain/border factor, and the predictor
+and corrector solves with their Krylov refinement).  The handle (problem
+upload and symbolic analysis) is created before the timed region.
 
-value      iterations/s with every input resident in device memory
-e2e        the same through the C ABI with pinned host buffers: each step copies
-           the iterate (x, y, z) host->device and the new iterate back
-roofline   the batched block partial Cholesky (the dominant stage) against
-           the FP64 ALU peak
+value      IPM iterations/s in mixed precision (FP32 block factors, FP64 Schur
+           complement and refinement), inputs resident in device memory
+fp64       the same LP and metric with FP64 block factors, beside it
+e2e        mixed precision end to end through the C ABI from host memory: each
+           step creates the handle from the host LP (upload + symbolic analysis),
+           solves, copies x, y, z back and destroys the handle
+roofline   the batched block partial Cholesky in the precision that dominates
+           the timed solves, against that ALU's peak
 cpu_baseline  the CPU oracle (monolithic sparse-LU Mehrotra IPM) timed for one
            IPM iteration on the first block of the same LP, scaled to 64 blocks
 
@@ -33,6 +38,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_PEAK_TFLOPS = 1.25       # nominal GB300 FP64 (FMA pipes and DMMA alike)
+FP32_PEAK_TFLOPS = 74.7       # GB300 FP32 FMA, measured by the register-only probe
 METRIC = "IPM iters/s & KKT solve ms at rel. gap 1e-8; mixed vs FP64 GPU path, % peak"
 
 
@@ -160,7 +166,6 @@ def run_reference(args):
 
 
 def run_ours(args):
-    import numpy as np
     import torch
     import paper_2412_07731_gb300 as P
 
@@ -176,111 +181,141 @@ def run_ours(args):
 
     lp, desc = workload(args.workload)
     stream = torch.cuda.current_stream(dev)
-    prob = P.arrowhead_lp_create(lp)
-    P.load().arrowhead_lp_set_stream(prob.handle, torch.cuda.current_stream(dev).cuda_stream)
+    headline = P.PREC_MIXED if args.precision == "mixed" else P.PREC_FP64
+    other = P.PREC_FP64 if headline == P.PREC_MIXED else P.PREC_MIXED
+    prob = P.arrowhead_lp_create(lp, P.default_options(precision=headline))
+    P.load().arrowhead_lp_set_stream(prob.handle, stream.cuda_stream)
     n, m = prob.n, prob.m
     f64 = dict(dtype=torch.float64, device=dev)
     x, y, z = torch.empty(n, **f64), torch.empty(m, **f64), torch.empty(n, **f64)
-    one_iter = P.default_options(max_iter=1)
-    start_opt = P.default_options(max_iter=0)
-    P.set_options(prob, start_opt)
-    P.ipm_solve(prob, out=(x, y, z), check=False)            # Mehrotra starting point
-    x_s, y_s, z_s = x.clone(), y.clone(), z.clone()
-    P.set_options(prob, one_iter)
-    tol = one_iter.tol
-    state = {"converged": False}
-    bf_ms, factor_ms, solve_ms = [], [], []
 
-    def step(xx, yy, zz):
-        if state["converged"]:             # restart the trajectory: every step is a real iteration
-            xx.copy_(x_s if xx.is_cuda else x_s.cpu())
-            yy.copy_(y_s if yy.is_cuda else y_s.cpu())
-            zz.copy_(z_s if zz.is_cuda else z_s.cpu())
-        _, r = P.ipm_solve(prob, xx, yy, zz, out=(xx, yy, zz), check=False)
-        if r["status"] not in (0, -6):
-            raise RuntimeError(f"IPM step failed: {r}")
-        state["converged"] = r["pinf"] <= tol and r["dinf"] <= tol and r["rel_gap"] <= tol
-        bf_ms.append(P.kkt_stage_times(prob)["block_factor_ms"])
-        factor_ms.append(r["ms_factor"])
-        solve_ms.append(r["ms_solve"] / 2.0)
+    def solve():
+        _, r = P.ipm_solve(prob, out=(x, y, z), check=False)
+        if r["status"] != 0:
+            raise RuntimeError(f"IPM solve failed: {r}")
         return r
 
+    def timed(k):
+        """k solves between CUDA events on the handle's stream; returns
+        (ms, results, launches, clocks)."""
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        sampler = ClockSampler(local)
+        l0 = P.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [solve() for _ in range(k)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        launches = P.launch_count() - l0
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms, res, launches, clocks
+
     for _ in range(args.warmup):
-        step(x, y, z)
-    bf_ms.clear(); factor_ms.clear(); solve_ms.clear()
-    # the e2e loop below replays the same K iterations from this snapshot
-    snap = (x.clone(), y.clone(), z.clone(), state["converged"])
-    torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
-    sampler = ClockSampler(local)
-    l0 = P.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step(x, y, z)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    launches = P.launch_count() - l0
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    value = world * args.steps / (ms / 1e3)
-    # roofline of the dominant stage (batched partial Cholesky, FP64 ALU)
+        solve()
+    ms, res, launches, clocks = timed(args.steps)
+    iters = sum(r["iterations"] for r in res)
+    value = world * iters / (ms / 1e3)
+
+    # roofline: the block partial Cholesky in the precision that took longer
+    nf32 = sum(r["factors_fp32"] for r in res)
+    nf64 = sum(r["factors_fp64"] for r in res)
+    t32 = sum(r["ms_block_fp32"] for r in res)
+    t64 = sum(r["ms_block_fp64"] for r in res)
     flops = block_factor_flops(lp)
-    bf = statistics.mean(bf_ms)
-    achieved = flops / (bf / 1e3) / 1e12
-    # end to end through the C ABI with pinned host buffers
+    if t64 >= t32 and nf64 > 0:
+        bf_ms, peak, prec_name, peak_src = t64 / nf64, FP64_PEAK_TFLOPS, "FP64", \
+            "nominal GB300 FP64 rate (profiling recipe table); FMA probe measured 1.009 TFLOP/s"
+    else:
+        bf_ms, peak, prec_name, peak_src = t32 / max(nf32, 1), FP32_PEAK_TFLOPS, "FP32", \
+            "FP32 FMA register-only probe on this GB300 (profiles/fp64_peak_probe.md)"
+    achieved = flops / (bf_ms / 1e3) / 1e12
+    other_line = None
+    if not args.no_compare:
+        P.set_options(prob, P.default_options(precision=other))
+        solve()
+        oms, ores, _, oclocks = timed(args.steps)
+        oit = sum(r["iterations"] for r in ores)
+        other_line = {"precision": "FP64" if other == P.PREC_FP64 else "mixed",
+                      "value": world * oit / (oms / 1e3), "unit": "IPM iters/s",
+                      "ms_per_step": oms / args.steps, "iterations_per_solve": oit / args.steps,
+                      "kkt_factor_ms": sum(r["ms_factor"] for r in ores) / max(oit, 1),
+                      "kkt_solve_ms_per_iteration": sum(r["ms_solve"] for r in ores) / max(oit, 1),
+                      "rel_gap": ores[-1]["rel_gap"], "clocks": oclocks}
+        P.set_options(prob, P.default_options(precision=headline))
+    prob.close()
+
+    # end to end through the C ABI from host memory (mixed precision)
     e2e = None
     if not args.no_e2e:
         xh = torch.empty(n, dtype=torch.float64).pin_memory()
         yh = torch.empty(m, dtype=torch.float64).pin_memory()
         zh = torch.empty(n, dtype=torch.float64).pin_memory()
-        xh.copy_(snap[0]); yh.copy_(snap[1]); zh.copy_(snap[2])
-        state["converged"] = snap[3]
+        h2d = d2h = 0
+        eit = 0
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            step(xh, yh, zh)
+            q = P.arrowhead_lp_create(lp, P.default_options(precision=headline))
+            _, r = P.ipm_solve(q, out=(xh, yh, zh), check=False)
+            if r["status"] != 0:
+                raise RuntimeError(f"IPM solve failed: {r}")
+            eit += r["iterations"]
+            a, b = P.transfer_bytes(q)
+            h2d += a
+            d2h += b
+            q.close()
         torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
         if dist:
             t = torch.tensor([el], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el = float(t.item())
-        e2e = {"value": world * args.steps / el, "unit": "IPM iters/s",
-               "h2d_bytes_per_step": (2 * n + m) * 8, "d2h_bytes_per_step": (2 * n + m) * 8}
+        e2e = {"value": world * eit / el, "unit": "IPM iters/s",
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+               "step": "create from the host LP (upload + symbolic analysis) + solve + "
+                       "x, y, z to pinned host memory + destroy"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(lp, 1)
     if rank == 0:
+        prec = "mixed" if headline == P.PREC_MIXED else "FP64"
         line = {
             "metric": METRIC, "value": value, "unit": "IPM iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if headline == P.PREC_MIXED else "f64", "data": "synthetic",
             "config": {"workload": desc, "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (2.2 GB of block factors per step)",
-                       "precision": "FP64"},
-            "kkt_factor_ms": statistics.median(factor_ms),
-            "kkt_solve_ms": statistics.median(solve_ms),
-            "block_factor_ms": bf,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": None,
-                         "kernel": "batched block partial Cholesky (pchol_potrf/trsm/update), "
-                                   f"{flops:.4g} flop per factor",
-                         "peak_source": "nominal GB300 FP64 rate (profiling recipe table); "
-                                        "FMA probe measured 1.009 TFLOP/s"},
+                       "step": "one IPM solve to rel. gap 1e-8 from Mehrotra's starting point",
+                       "l2": "inputs larger than L2 (1.1-2.2 GB of block factors per iteration)",
+                       "precision": prec},
+            "iterations_per_solve": iters / args.steps,
+            "rel_gap": res[-1]["rel_gap"],
+            "kkt_factor_ms": sum(r["ms_factor"] for r in res) / max(iters, 1),
+            "kkt_solve_ms_per_iteration": sum(r["ms_solve"] for r in res) / max(iters, 1),
+            "factors": {"fp32": nf32 / args.steps, "fp64": nf64 / args.steps},
+            "block_factor_ms": {"fp32": t32 / max(nf32, 1) if nf32 else None,
+                                "fp64": t64 / max(nf64, 1) if nf64 else None},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": f"batched block partial Cholesky ({prec_name}; "
+                                   f"pchol_potrf/trsm/update + tinv), {flops:.4g} flop per factor",
+                         "peak_source": peak_src},
             "clocks": clocks, "gpu_launches": launches,
             "e2e": e2e, "cpu_baseline": cpu,
         }
+        if other_line:
+            line["fp64" if other == P.PREC_FP64 else "mixed"] = other_line
+            line["mixed_over_fp64"] = (value / other_line["value"] if headline == P.PREC_MIXED
+                                       else other_line["value"] / value)
         print(json.dumps(line), flush=True)
-    prob.close()
     if dist:
         dist.destroy_process_group()
 
@@ -288,10 +323,13 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c1", choices=["c1", "c1small", "c0"])
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the other precision's measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--probe-peaks", action="store_true",

@@ -138,6 +138,9 @@ typedef struct {
   int32_t escalations;    /* FP32->FP64 switches plus pivot-threshold coarsenings  */
   int32_t fp64_switch_iter; /* mixed mode: iteration from which the block factors
                              are FP64 (-1: never); FP64 mode: 0                   */
+  int32_t factors_fp32, factors_fp64;   /* block factorisations per precision     */
+  double  ms_block_fp32, ms_block_fp64; /* their summed device time (the batched
+                                           partial Cholesky stage alone)         */
 } ahlp_result;
 
 typedef struct {
@@ -284,6 +287,11 @@ int kkt_stage_times(ahlp_problem *p, double *out4);
  * process so far (all handles).  The difference of two readings is the
  * launch count of the calls made in between. */
 int64_t ahlp_launch_count(void);
+
+/* Diagnostic: bytes this handle has copied host -> device and device -> host
+ * since arrowhead_lp_create (the problem upload included; scalars read back
+ * by the solvers included).  Either pointer may be NULL. */
+int ahlp_transfer_bytes(const ahlp_problem *p, int64_t *h2d, int64_t *d2h);
 
 /*
  * kkt_residual_noalloc -- ||J d - r||_2 / ||r||_2 for a direction

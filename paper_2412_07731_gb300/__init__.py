@@ -20,6 +20,7 @@ from ._lib import (  # noqa: F401
     kkt_solve,
     kkt_stage_times,
     launch_count,
+    transfer_bytes,
     lib_path,
     load,
     set_options,

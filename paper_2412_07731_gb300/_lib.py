@@ -54,7 +54,9 @@ class Result(C.Structure):
                 ("ms_factor", C.c_double), ("ms_solve", C.c_double),
                 ("refine_steps", C.c_int32), ("tiny_pivots", C.c_int32),
                 ("kkt_residual", C.c_double), ("escalations", C.c_int32),
-                ("fp64_switch_iter", C.c_int32)]
+                ("fp64_switch_iter", C.c_int32), ("factors_fp32", C.c_int32),
+                ("factors_fp64", C.c_int32), ("ms_block_fp32", C.c_double),
+                ("ms_block_fp64", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -68,7 +70,8 @@ EXPORTS = ["ahlp_default_options", "ahlp_status_string", "arrowhead_lp_create",
            "arrowhead_lp_destroy", "ahlp_last_error", "arrowhead_lp_sizes",
            "arrowhead_lp_set_stream", "arrowhead_lp_set_options", "kkt_factor", "kkt_solve",
            "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense", "kkt_stage_times",
-           "ahlp_launch_count", "kkt_residual_noalloc", "kkt_block_factor_dense"]
+           "ahlp_launch_count", "kkt_residual_noalloc", "kkt_block_factor_dense",
+           "ahlp_transfer_bytes"]
 
 
 def kkt_block_factor_dense(prob, block: int):
@@ -88,6 +91,13 @@ def kkt_block_factor_dense(prob, block: int):
 def launch_count() -> int:
     """Kernels launched by libahlp.so in this process so far."""
     return int(load().ahlp_launch_count())
+
+
+def transfer_bytes(prob) -> tuple[int, int]:
+    """(host->device, device->host) bytes copied by this handle since create."""
+    h2d, d2h = C.c_int64(0), C.c_int64(0)
+    prob._check(prob._lib.ahlp_transfer_bytes(prob._h, C.byref(h2d), C.byref(d2h)))
+    return int(h2d.value), int(d2h.value)
 
 _lib = None
 
@@ -133,6 +143,8 @@ def load(path: str | None = None):
     L.kkt_residual_noalloc.restype = C.c_int
     L.kkt_block_factor_dense.argtypes = [vp, C.c_int32, vp, C.c_int64, C.POINTER(C.c_int32)]
     L.kkt_block_factor_dense.restype = C.c_int
+    L.ahlp_transfer_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.ahlp_transfer_bytes.restype = C.c_int
     for name in ("arrowhead_lp_sizes", "arrowhead_lp_set_stream", "arrowhead_lp_set_options",
                  "kkt_factor", "kkt_solve", "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense",
                  "kkt_stage_times"):

@@ -198,6 +198,9 @@ struct ahlp_problem {
   bool assembled = false;     // the Schur complement of the last kkt_factor exists
   double fac_delta = 0, fac_rho = 0, fac_pivot_tol = 0;
 
+  // ---- host <-> device traffic since create (ahlp_transfer_bytes) ----------
+  long long bytes_h2d = 0, bytes_d2h = 0;
+
   // ---- timing -------------------------------------------------------------
   cudaEvent_t ev[8] = {};
   float stage_ms[4] = {0, 0, 0, 0};

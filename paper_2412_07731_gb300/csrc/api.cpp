@@ -129,6 +129,7 @@ T *dupload(ahlp_problem *p, const std::vector<T> &h) {
   T *d = dalloc<T>(p, (long long)h.size());
   if (!h.empty()) {
     cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    p->bytes_h2d += (long long)(h.size() * sizeof(T));
     if (e != cudaSuccess) fail(AHLP_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
   }
   return d;
@@ -756,6 +757,7 @@ bool is_device_ptr(const void *ptr) {
 const double *stage_in(ahlp_problem *p, const double *v, long long n, double *staging) {
   if (is_device_ptr(v)) return v;
   if (n > 0) ck(cudaMemcpyAsync(staging, v, n * 8, cudaMemcpyHostToDevice, p->stream), "H2D");
+  p->bytes_h2d += n * 8;
   return staging;
 }
 
@@ -766,6 +768,7 @@ int set_err(ahlp_problem *p, int code, const std::string &msg) {
 
 // read k device scalars into p->h_scal (synchronises the stream)
 void read_scalars(ahlp_problem *p, int k) {
+  p->bytes_d2h += k * (long long)sizeof(double);
   ck(cudaMemcpyAsync(p->h_scal, p->scal, k * sizeof(double), cudaMemcpyDeviceToHost, p->stream),
      "D2H scalars");
   ck(cudaStreamSynchronize(p->stream), "stream sync");
@@ -802,6 +805,7 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
     // block normal matrices are too ill-conditioned for FP32 factors
     ck(launch_reduce(p, RED_MAXABS, p->dscale, nullptr, p->n, p->scal + 2), "reduce");
     ck(launch_reduce(p, RED_MIN, p->dscale, nullptr, p->n, p->scal + 3), "reduce");
+    p->bytes_d2h += 2 * sizeof(double);
     ck(cudaMemcpyAsync(p->h_scal + 2, p->scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
        "D2H");
     ck(cudaStreamSynchronize(s), "sync");
@@ -824,6 +828,7 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
   ck(launch_schur_factor(p), "schur factor");
   ck(cudaEventRecord(p->ev[3], s), "event");
   int st[8];
+  p->bytes_d2h += sizeof(st);
   ck(cudaMemcpyAsync(st, p->status, sizeof(st), cudaMemcpyDeviceToHost, s), "D2H status");
   ck(cudaStreamSynchronize(s), "factor sync");
   cudaEventElapsedTime(&p->stage_ms[0], p->ev[0], p->ev[1]);
@@ -870,6 +875,7 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
     ck(launch_reduce(p, RED_DOT, p->res[0], p->res[0], n, p->scal + 13), "reduce");
     ck(launch_reduce(p, RED_DOT, p->res[1], p->res[1], m, p->scal + 14), "reduce");
     ck(launch_reduce(p, RED_DOT, p->res[2], p->res[2], n, p->scal + 15), "reduce");
+    p->bytes_d2h += 6 * sizeof(double);
     ck(cudaMemcpyAsync(p->h_scal + 10, p->scal + 10, 6 * sizeof(double), cudaMemcpyDeviceToHost, s),
        "D2H");
     ck(cudaStreamSynchronize(s), "sync");
@@ -910,12 +916,14 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
       double *h = &H[(size_t)j * (kmax + 1)];
       for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
         ck(launch_mdot(p, V, L, j + 1, W, L, p->gm_coef), "mdot");
+        p->bytes_d2h += (j + 1) * 8;
         ck(cudaMemcpyAsync(hbuf, p->gm_coef, (j + 1) * 8, cudaMemcpyDeviceToHost, s), "D2H");
         ck(cudaStreamSynchronize(s), "sync");
         for (int i = 0; i <= j; ++i) {
           h[i] += hbuf[i];
           cbuf[i] = -hbuf[i];
         }
+        p->bytes_h2d += (j + 1) * 8;
         ck(cudaMemcpyAsync(p->gm_coef, cbuf, (j + 1) * 8, cudaMemcpyHostToDevice, s), "H2D");
         ck(launch_maxpy(V, L, j + 1, p->gm_coef, W, L, s), "maxpy");
       }
@@ -948,6 +956,7 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
       y[i] = d != 0.0 ? t / d : 0.0;
     }
     for (int i = 0; i < j; ++i) cbuf[i] = y[i];
+    p->bytes_h2d += j * 8;
     ck(cudaMemcpyAsync(p->gm_coef, cbuf, j * 8, cudaMemcpyHostToDevice, s), "H2D");
     ck(launch_maxpy(Z, L, j, p->gm_coef, dx, n, s), "maxpy");
     ck(launch_maxpy(Z + n, L, j, p->gm_coef, dy, m, s), "maxpy");
@@ -958,6 +967,7 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
   }
   ck(cudaEventRecord(p->ev[5], s), "event");
   int timed_out = 0;
+  p->bytes_d2h += sizeof(int);
   ck(cudaMemcpyAsync(&timed_out, p->trsv_err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
   ck(cudaEventSynchronize(p->ev[5]), "sync");
   ck(cudaStreamSynchronize(s), "sync");
@@ -1010,6 +1020,7 @@ static int solve_entry(ahlp_problem *p, const double *a, const double *b, const 
     if (!d1) ck(cudaMemcpyAsync(o1, w1, p->n * 8, cudaMemcpyDeviceToHost, p->stream), "D2H");
     if (!d2) ck(cudaMemcpyAsync(o2, w2, p->m * 8, cudaMemcpyDeviceToHost, p->stream), "D2H");
     if (!d3) ck(cudaMemcpyAsync(o3, w3, p->n * 8, cudaMemcpyDeviceToHost, p->stream), "D2H");
+    p->bytes_d2h += (d1 ? 0 : p->n * 8) + (d2 ? 0 : p->m * 8) + (d3 ? 0 : p->n * 8);
     if (!(d1 && d2 && d3)) ck(cudaStreamSynchronize(p->stream), "sync");
     return st;
   } catch (const Fail &f) {
@@ -1074,6 +1085,13 @@ int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld) {
 }
 
 int64_t ahlp_launch_count(void) { return ahlp::launch_count(); }
+
+int ahlp_transfer_bytes(const ahlp_problem *p, int64_t *h2d, int64_t *d2h) {
+  if (!p) return AHLP_ERR_INVALID_ARG;
+  if (h2d) *h2d = p->bytes_h2d;
+  if (d2h) *d2h = p->bytes_d2h;
+  return AHLP_OK;
+}
 
 int kkt_block_factor_dense(ahlp_problem *p, int32_t block, double *A, int64_t ld,
                            int32_t *order) {

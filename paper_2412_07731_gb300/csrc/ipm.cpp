@@ -68,6 +68,15 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         R.fp64_switch_iter = cur_iter;
       R.ms_factor += p->stage_ms[0] + p->stage_ms[1] + p->stage_ms[2];
       R.tiny_pivots = p->tiny_pivots;
+      if (st == AHLP_OK) {
+        if (p->fac_prec == kPrecFP32) {
+          ++R.factors_fp32;
+          R.ms_block_fp32 += p->stage_ms[1];
+        } else {
+          ++R.factors_fp64;
+          R.ms_block_fp64 += p->stage_ms[1];
+        }
+      }
       return st;
     };
     auto solve = [&](const double *rd, const double *rp, const double *rc, double *dx, double *dy,
@@ -218,6 +227,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     // outputs
     auto put = [&](double *dst, const double *src, long long len) {
       if (!dst || len == 0) return;
+      if (!is_device_ptr(dst)) p->bytes_d2h += len * 8;
       ck(cudaMemcpyAsync(dst, src, len * 8,
                          is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s),
          "copy out");

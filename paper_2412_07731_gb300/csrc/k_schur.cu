@@ -377,7 +377,6 @@ __global__ void __launch_bounds__(kChainSolveThreads) chain_solve_kernel(CArgs A
       for (int c = r; c < lj; ++c) acc = fma(Li[c + r * lj], uj[c], acc);
     A.tmp[q] = acc;
   }
-  int b = 0;
   for (int s0 = 0; s0 < npairs; s0 += stages) {
     const int ns = min(stages, npairs - s0);
     // global range [g0, g1) holding the operators of steps s0 .. s0+ns-1
@@ -424,26 +423,31 @@ __global__ void __launch_bounds__(kChainSolveThreads) chain_solve_kernel(CArgs A
       if (tid == 0) meta[kChainMaxStages - 1][3] = (int)t0;
     }
     __syncthreads();
-    const int tb0 = meta[kChainMaxStages - 1][3];
-    for (int t = 0; t < ns; ++t, b ^= 1) {
-      const int lj = meta[t][0], lo = meta[t][1], off = meta[t][3];
-      const double *Yop = opbuf + meta[t][2];
-      for (int r = tid; r < lj; r += bd) {
-        // four independent partial sums keep the FP64 dependency chain short
-        double a0 = tbuf[off - tb0 + r], a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int c = 0;
-        for (; c + 4 <= lo; c += 4) {
-          a0 = fma(-Yop[r + (c + 0) * lj], ubuf[b][c + 0], a0);
-          a1 = fma(-Yop[r + (c + 1) * lj], ubuf[b][c + 1], a1);
-          a2 = fma(-Yop[r + (c + 2) * lj], ubuf[b][c + 2], a2);
-          a3 = fma(-Yop[r + (c + 3) * lj], ubuf[b][c + 3], a3);
+    // the recurrence itself: one warp, lanes over the rows of a pair, so a
+    // step needs only a warp barrier
+    if (tid < 32) {
+      const int tb0 = meta[kChainMaxStages - 1][3];
+      for (int t = 0; t < ns; ++t) {
+        const int b = (s0 + t) & 1;   // ubuf[b]: the previous pair's solution
+        const int lj = meta[t][0], lo = meta[t][1], off = meta[t][3];
+        const double *Yop = opbuf + meta[t][2];
+        for (int r = tid; r < lj; r += 32) {
+          // four independent partial sums keep the FP64 dependency chain short
+          double a0 = tbuf[off - tb0 + r], a1 = 0.0, a2 = 0.0, a3 = 0.0;
+          int c = 0;
+          for (; c + 4 <= lo; c += 4) {
+            a0 = fma(-Yop[r + (c + 0) * lj], ubuf[b][c + 0], a0);
+            a1 = fma(-Yop[r + (c + 1) * lj], ubuf[b][c + 1], a1);
+            a2 = fma(-Yop[r + (c + 2) * lj], ubuf[b][c + 2], a2);
+            a3 = fma(-Yop[r + (c + 3) * lj], ubuf[b][c + 3], a3);
+          }
+          for (; c < lo; ++c) a0 = fma(-Yop[r + c * lj], ubuf[b][c], a0);
+          const double acc = (a0 + a1) + (a2 + a3);
+          u[off + r] = acc;
+          ubuf[b ^ 1][r] = acc;
         }
-        for (; c < lo; ++c) a0 = fma(-Yop[r + c * lj], ubuf[b][c], a0);
-        const double acc = (a0 + a1) + (a2 + a3);
-        u[off + r] = acc;
-        ubuf[b ^ 1][r] = acc;
+        __syncwarp();
       }
-      __syncthreads();
     }
   }
 }
