@@ -188,6 +188,17 @@ int arrowhead_lp_set_stream(ahlp_problem *p, void *stream);
 int arrowhead_lp_set_options(ahlp_problem *p, const ahlp_options *opt);
 
 /*
+ * arrowhead_lp_set_cb -- replace the objective c and/or the right-hand side b
+ * of the problem (Sec. 3.2 statement) without touching its structure, e.g.
+ * for parametric re-solves or for differentiating the optimum with respect to
+ * (c, b).  c: [n] and b: [m] in the global orderings (x = [x_1..x_N, x_0],
+ * y = [y_1..y_N, y_links, y_g]), host or device memory, copied; NULL keeps
+ * the current vector.  NaN/Inf entries: AHLP_ERR_INVALID_ARG, nothing
+ * replaced for that vector.
+ */
+int arrowhead_lp_set_cb(ahlp_problem *p, const double *c, const double *b);
+
+/*
  * kkt_factor -- factor the Newton system at the interior point (x, z)
  * (Alg. 2 of Sec. 3.2 with the block systems in normal-equation form):
  *   (a) per block, M_i = A_i D_i A_i' + delta I with D_i = X_i Z_i^-1, stacked

@@ -23,6 +23,7 @@ from ._lib import (  # noqa: F401
     transfer_bytes,
     lib_path,
     load,
+    set_cb,
     set_options,
 )
 

@@ -71,7 +71,7 @@ EXPORTS = ["ahlp_default_options", "ahlp_status_string", "arrowhead_lp_create",
            "arrowhead_lp_set_stream", "arrowhead_lp_set_options", "kkt_factor", "kkt_solve",
            "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense", "kkt_stage_times",
            "ahlp_launch_count", "kkt_residual_noalloc", "kkt_block_factor_dense",
-           "ahlp_transfer_bytes"]
+           "ahlp_transfer_bytes", "arrowhead_lp_set_cb"]
 
 
 def kkt_block_factor_dense(prob, block: int):
@@ -91,6 +91,15 @@ def kkt_block_factor_dense(prob, block: int):
 def launch_count() -> int:
     """Kernels launched by libahlp.so in this process so far."""
     return int(load().ahlp_launch_count())
+
+
+def set_cb(prob, c=None, b=None):
+    """Replace the objective c ([n]) and/or right-hand side b ([m]) of the
+    handle; host (numpy) or device (torch) vectors, None keeps the current."""
+    keep = _Keep()
+    prob._stream_for(c, b)
+    prob._check(prob._lib.arrowhead_lp_set_cb(prob._h, _vec_ptr(c, keep, prob.n, "c"),
+                                              _vec_ptr(b, keep, prob.m, "b")))
 
 
 def transfer_bytes(prob) -> tuple[int, int]:
@@ -145,6 +154,8 @@ def load(path: str | None = None):
     L.kkt_block_factor_dense.restype = C.c_int
     L.ahlp_transfer_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.ahlp_transfer_bytes.restype = C.c_int
+    L.arrowhead_lp_set_cb.argtypes = [vp, vp, vp]
+    L.arrowhead_lp_set_cb.restype = C.c_int
     for name in ("arrowhead_lp_sizes", "arrowhead_lp_set_stream", "arrowhead_lp_set_options",
                  "kkt_factor", "kkt_solve", "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense",
                  "kkt_stage_times"):

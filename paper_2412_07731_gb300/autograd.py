@@ -1,0 +1,56 @@
+"""Differentiable LP solve: the optimum (x*, y*, z*) as a function of (c, b).
+
+At a solution w = (x, y, z) of the optimality conditions
+    F(w; c, b) = [A'y + z - c ; Ax - b ; XZe] = 0        (Sec. 2.3)
+the implicit function theorem gives J dw = [dc; db; 0], J the Newton matrix
+[0 A' I; A 0 0; Z 0 X] at w.  A loss L(w) with gradient g = (g_x, g_y, g_z)
+therefore has dL/dc = lam_x and dL/db = lam_y, where J' lam = g: one
+transposed KKT solve (kkt_adjoint_solve) with the block factors of the final
+iterate, refined by FGMRES on the exact J'.  Objective gradients follow from
+the explicit term: d(c'x*)/dc = x* + lam_x with g_x = c (for a nondegenerate
+optimum dx*/dc = 0, so this is x*), d(c'x*)/db = lam_y (= y*).
+
+The handle keeps the structure (A_i, W_i, link rows); forward replaces c and
+b (arrowhead_lp_set_cb), solves, and factors at the returned point.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+
+
+class LPSolve(torch.autograd.Function):
+    """(x, y, z) = LPSolve.apply(c, b, prob): optimum of min c'x s.t. Ax = b,
+    x >= 0 for the handle's structure.  c: [n], b: [m] float64 tensors (CPU or
+    CUDA; the outputs live on the same device).  Backward reuses the factors
+    of the final iterate (the handle must not be refactored in between)."""
+
+    @staticmethod
+    def forward(ctx, c, b, prob):
+        c, b = c.detach().contiguous(), b.detach().contiguous()
+        L.set_cb(prob, c, b)
+        f64 = dict(dtype=torch.float64, device=c.device)
+        x, y, z = torch.empty(prob.n, **f64), torch.empty(prob.m, **f64), torch.empty(prob.n, **f64)
+        L.ipm_solve(prob, out=(x, y, z))
+        L.kkt_factor(prob, x, z)
+        ctx.prob = prob
+        ctx.save_for_backward(x, z)
+        return x, y, z
+
+    @staticmethod
+    def backward(ctx, gx, gy, gz):
+        prob = ctx.prob
+        x, _ = ctx.saved_tensors
+        zeros_n = torch.zeros_like(x)
+        gx = zeros_n if gx is None else gx.contiguous()
+        gy = torch.zeros(prob.m, dtype=x.dtype, device=x.device) if gy is None else gy.contiguous()
+        gz = zeros_n if gz is None else gz.contiguous()
+        (lx, ly, _), _ = L.kkt_adjoint_solve(prob, gx, gy, gz)
+        return lx, ly, None
+
+
+def lp_solve(c, b, prob):
+    """Differentiable optimum (x*, y*, z*) of the handle's LP with objective c
+    and right-hand side b (see LPSolve)."""
+    return LPSolve.apply(c, b, prob)

@@ -314,6 +314,31 @@ int arrowhead_lp_set_options(ahlp_problem *p, const ahlp_options *opt) {
   return AHLP_OK;
 }
 
+int arrowhead_lp_set_cb(ahlp_problem *p, const double *c, const double *b) {
+  if (!p) return AHLP_ERR_INVALID_ARG;
+  try {
+    // stage, check for NaN/Inf, then replace; returns the max norm
+    auto replace = [&](const double *src, double *dst, long long len, double *staging,
+                       double &norm) -> bool {
+      const double *d = stage_in(p, src, len, staging);
+      ck(launch_reduce(p, RED_MAXABS, d, nullptr, len, p->scal + 0), "reduce");
+      read_scalars(p, 1);
+      if (!std::isfinite(p->h_scal[0])) return false;
+      ck(cudaMemcpyAsync(dst, d, len * 8, cudaMemcpyDeviceToDevice, p->stream), "copy");
+      norm = p->h_scal[0];
+      return true;
+    };
+    if (c && p->n > 0 && !replace(c, p->c, p->n, p->stg[0], p->cnorm_inf))
+      return set_err(p, AHLP_ERR_INVALID_ARG, "arrowhead_lp_set_cb: c has NaN or Inf entries");
+    if (b && p->m > 0 && !replace(b, p->b, p->m, p->stg[1], p->bnorm_inf))
+      return set_err(p, AHLP_ERR_INVALID_ARG, "arrowhead_lp_set_cb: b has NaN or Inf entries");
+    ck(cudaStreamSynchronize(p->stream), "sync");
+    return AHLP_OK;
+  } catch (const Fail &f) {
+    return set_err(p, f.code, f.msg);
+  }
+}
+
 int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_options *opt,
                         ahlp_problem **out) {
   if (!out) return AHLP_ERR_INVALID_ARG;
