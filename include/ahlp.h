@@ -117,6 +117,10 @@ typedef struct {
                            stays above 1e-6 or a NaN appears, once the block
                            factors are FP64                                      */
   int32_t verbose;      /* 0: silent                                              */
+  int32_t max_correctors; /* multiple centrality correctors per iteration, each
+                           one more solve with the same factor, tried while the
+                           step length stays below 0.9 and at most (factor time
+                           / solve time) of them (4; 0..8)                      */
   double  fp32_cond_max;/* mixed precision: the block factors run in FP32 while
                            max(d)/min(d), d = x/z, stays at or below this value,
                            and in FP64 beyond it (1e14)                          */
@@ -139,6 +143,7 @@ typedef struct {
   int32_t fp64_switch_iter; /* mixed mode: iteration from which the block factors
                              are FP64 (-1: never); FP64 mode: 0                   */
   int32_t factors_fp32, factors_fp64;   /* block factorisations per precision     */
+  int32_t correctors;     /* accepted centrality correctors                      */
   double  ms_block_fp32, ms_block_fp64; /* their summed device time (the batched
                                            partial Cholesky stage alone)         */
 } ahlp_result;

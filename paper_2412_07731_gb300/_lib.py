@@ -44,7 +44,7 @@ class Options(C.Structure):
                 ("eta", C.c_double), ("delta", C.c_double), ("rho", C.c_double),
                 ("refine_max", C.c_int32), ("refine_tol", C.c_double),
                 ("pivot_tol", C.c_double), ("verbose", C.c_int32),
-                ("fp32_cond_max", C.c_double)]
+                ("max_correctors", C.c_int32), ("fp32_cond_max", C.c_double)]
 
 
 class Result(C.Structure):
@@ -55,8 +55,8 @@ class Result(C.Structure):
                 ("refine_steps", C.c_int32), ("tiny_pivots", C.c_int32),
                 ("kkt_residual", C.c_double), ("escalations", C.c_int32),
                 ("fp64_switch_iter", C.c_int32), ("factors_fp32", C.c_int32),
-                ("factors_fp64", C.c_int32), ("ms_block_fp32", C.c_double),
-                ("ms_block_fp64", C.c_double)]
+                ("factors_fp64", C.c_int32), ("correctors", C.c_int32),
+                ("ms_block_fp32", C.c_double), ("ms_block_fp64", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -177,7 +177,7 @@ struct ahlp_problem {
   double *stg[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // staging for host I/O
   double *res[3] = {nullptr, nullptr, nullptr};            // refinement residual
   double *cor[3] = {nullptr, nullptr, nullptr};            // refinement correction
-  double *ipmv[12] = {};      // IPM work vectors
+  double *ipmv[16] = {};      // IPM work vectors
   double *red_part = nullptr; // reduction partials
   double *mdot_part = nullptr;  // multi-dot partials [kMaxKrylov+1][304]
   double *gm_V = nullptr, *gm_Z = nullptr;   // Krylov bases, allocated on first use
@@ -269,6 +269,11 @@ cudaError_t launch_jmul(ahlp_problem *p, const double *vx, const double *vy, con
                         double *ox, double *oy, double *oz, bool adjoint);
 cudaError_t launch_mul(double *y, const double *a, const double *b, double scale, long long n,
                        cudaStream_t s);   // y = scale * a .* b
+// centrality corrector right-hand side: rc2 = rc + t, where v = (x + ap dx) .* (z + ad dz)
+// is projected onto [lo, hi] and t = proj(v) - v, bounded below by -hi
+cudaError_t launch_centrality_rc(double *rc2, const double *rc, const double *x,
+                                 const double *dx, double ap, const double *z, const double *dz,
+                                 double ad, double lo, double hi, long long n, cudaStream_t s);
 cudaError_t launch_step_dot(const double *x, const double *dx, double ap, const double *z,
                             const double *dz, double ad, long long n, double *part,
                             double *out, cudaStream_t s);  // (x+ap dx)'(z+ad dz)

@@ -244,6 +244,7 @@ void ahlp_default_options(ahlp_options *o) {
   o->refine_tol = 1e-10;
   o->pivot_tol = 1e-12;
   o->verbose = 0;
+  o->max_correctors = 4;
   o->fp32_cond_max = 1e14;
 }
 
@@ -299,7 +300,7 @@ static int check_options(const ahlp_options &o, std::string &err) {
   }
   if (o.max_iter < 0 || !(o.tol > 0) || !(o.eta > 0 && o.eta < 1) || o.delta < 0 || o.rho < 0 ||
       o.refine_max < 0 || !(o.refine_tol > 0) || !(o.pivot_tol >= 0) ||
-      !(o.fp32_cond_max >= 1)) {
+      !(o.fp32_cond_max >= 1) || o.max_correctors < 0 || o.max_correctors > 8) {
     err = "invalid option value";
     return AHLP_ERR_INVALID_ARG;
   }

@@ -14,7 +14,8 @@ using namespace ahlp;
 namespace {
 
 enum {
-  V_X = 0, V_Y, V_Z, V_RP, V_RD, V_RC, V_DXA, V_DYA, V_DZA, V_DX, V_DY, V_DZ
+  V_X = 0, V_Y, V_Z, V_RP, V_RD, V_RC, V_DXA, V_DYA, V_DZA, V_DX, V_DY, V_DZ,
+  V_RC2, V_DX2, V_DY2, V_DZ2
 };
 
 double now_ms() {
@@ -53,6 +54,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     // nearly all its digits to cancellation; its rounding noise is amplified
     // through the later clamped columns.
     constexpr double kEscalate = 1e-6, kMaxPivotTol = 1e-8, kMaxDelta = 1e-4;
+    constexpr double kCorrectorBelow = 0.9;   // correctors only below this step length
     double ptol = p->opt.pivot_tol;
     double delta = p->opt.delta;
     double last_rel = 0.0;
@@ -189,6 +191,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       }
       const double mu = R.mu;
       cur_iter = it;
+      double sigma = 0.0;
       for (;;) {
         int st = factor_at(X, Z);
         if (st == AHLP_ERR_NOT_SPD && escalate(true)) continue;
@@ -207,7 +210,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
            "reduce");
         read_scalars(p, 1);
         const double mu_aff = p->h_scal[0] / n;
-        const double sigma = std::pow(mu_aff / mu, 3.0);
+        sigma = std::pow(mu_aff / mu, 3.0);
         // corrector: r_c = sigma mu e - XZe - dXa dZa e
         ck(launch_ipm_rc(v[V_RC], X, Z, v[V_DXA], v[V_DZA], sigma * mu, n, s), "rc");
         st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DX], v[V_DY], v[V_DZ]);
@@ -215,6 +218,45 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         if (st != AHLP_OK) throw Fail{st, p->err};
         if (last_rel > kEscalate && escalate(false)) continue;
         break;
+      }
+      // Multiple centrality correctors (Gondzio), reusing the factor: the
+      // products (x + a dx)(z + a dz) at an enlarged trial step are pushed into
+      // [0.1 sigma mu, 10 sigma mu]; a corrected direction is kept only while
+      // it lengthens the step.  Tried only when the step is short, and at
+      // most as many as the factorisation costs in solves.
+      if (p->opt.max_correctors > 0) {
+        auto steps = [&](const double *dxv, const double *dzv, double &a_p, double &a_d) {
+          ck(launch_reduce(p, RED_MINSTEP, X, dxv, n, p->scal + 0), "reduce");
+          ck(launch_reduce(p, RED_MINSTEP, Z, dzv, n, p->scal + 1), "reduce");
+          read_scalars(p, 2);
+          a_p = std::min(1.0, p->h_scal[0]);
+          a_d = std::min(1.0, p->h_scal[1]);
+        };
+        double a_p = 1.0, a_d = 1.0;
+        steps(v[V_DX], v[V_DZ], a_p, a_d);
+        // as many as the factorisation is worth in solves (Gondzio's rule)
+        const double fac_ms = p->stage_ms[0] + p->stage_ms[1] + p->stage_ms[2];
+        const double sol_ms = std::max((double)p->stage_ms[3], 1e-3);
+        const int kmax = std::min(p->opt.max_correctors, (int)(fac_ms / sol_ms));
+        for (int k = 0; k < kmax && std::min(a_p, a_d) < kCorrectorBelow; ++k) {
+          const double tp = std::min(1.0, 1.5 * a_p + 0.1), td = std::min(1.0, 1.5 * a_d + 0.1);
+          const double smu = sigma * mu;
+          ck(launch_centrality_rc(v[V_RC2], v[V_RC], X, v[V_DX], tp, Z, v[V_DZ], td, 0.1 * smu,
+                                  10.0 * smu, n, s),
+             "corrector rhs");
+          const int st = solve(v[V_RD], v[V_RP], v[V_RC2], v[V_DX2], v[V_DY2], v[V_DZ2]);
+          if (st != AHLP_OK || last_rel > kEscalate) break;   // keep the previous direction
+          double b_p = 0.0, b_d = 0.0;
+          steps(v[V_DX2], v[V_DZ2], b_p, b_d);
+          if (!(std::min(b_p, b_d) >= 1.01 * std::min(a_p, a_d))) break;
+          std::swap(v[V_DX], v[V_DX2]);
+          std::swap(v[V_DY], v[V_DY2]);
+          std::swap(v[V_DZ], v[V_DZ2]);
+          std::swap(v[V_RC], v[V_RC2]);
+          a_p = b_p;
+          a_d = b_d;
+          ++R.correctors;
+        }
       }
       ck(launch_reduce(p, RED_MINSTEP, X, v[V_DX], n, p->scal + 0), "reduce");
       ck(launch_reduce(p, RED_MINSTEP, Z, v[V_DZ], n, p->scal + 1), "reduce");

@@ -163,6 +163,17 @@ __global__ void ipm_rc_k(double *rc, const double *x, const double *z, const dou
   if (i < n) rc[i] = smu - x[i] * z[i] - (dxa ? dxa[i] * dza[i] : 0.0);
 }
 
+__global__ void centrality_rc_k(double *rc2, const double *rc, const double *x, const double *dx,
+                                double ap, const double *z, const double *dz, double ad,
+                                double lo, double hi, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = (x[i] + ap * dx[i]) * (z[i] + ad * dz[i]);
+  double t = v < lo ? lo - v : (v > hi ? hi - v : 0.0);
+  if (t < -hi) t = -hi;
+  rc2[i] = rc[i] + t;
+}
+
 __global__ void add_scalar_k(double *y, const double *x, double s, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = x[i] + s;
@@ -306,6 +317,15 @@ cudaError_t launch_ipm_rc(double *rc, const double *x, const double *z, const do
                           const double *dza, double sigma_mu, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   count_launch(), ipm_rc_k<<<blocks_for(n, 256), 256, 0, s>>>(rc, x, z, dxa, dza, sigma_mu, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_centrality_rc(double *rc2, const double *rc, const double *x,
+                                 const double *dx, double ap, const double *z, const double *dz,
+                                 double ad, double lo, double hi, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  count_launch(), centrality_rc_k<<<blocks_for(n, 256), 256, 0, s>>>(rc2, rc, x, dx, ap, z, dz, ad,
+                                                                     lo, hi, n);
   return cudaGetLastError();
 }
 

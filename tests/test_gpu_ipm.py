@@ -85,3 +85,25 @@ def test_iteration_cap(P):
     prob = P.arrowhead_lp_create(lp, P.default_options(max_iter=2))
     _, r = P.ipm_solve(prob, check=False)
     assert r["status"] == -6 and r["iterations"] == 2
+
+
+@pytest.mark.parametrize("days", [4, 6])
+def test_centrality_correctors_keep_the_optimum(days):
+    """Multiple centrality correctors change the trajectory, not the optimum:
+    on small energy-system LPs (one block per day, storage chain links, an
+    emissions row) the GPU IPM with and without them reaches the oracle's
+    objective, and with them in fewer iterations."""
+    import paper_2412_07731_gb300 as P
+    from instances import config3
+    from oracle import ipm as oipm
+    lp = config3(days=days, nodes=6, lines=8, n_invest=16)
+    ref = oipm.solve_blocklp(lp)
+    assert ref["status"] == "optimal"
+    its = {}
+    for K in (0, 4):
+        prob = P.arrowhead_lp_create(lp, P.default_options(max_correctors=K))
+        _, r = P.ipm_solve(prob)
+        assert abs(r["pobj"] - ref["pobj"]) <= 1e-8 * (1 + abs(ref["pobj"]))
+        its[K] = r["iterations"]
+        prob.close()
+    assert its[4] <= its[0]
