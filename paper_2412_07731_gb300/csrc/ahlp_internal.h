@@ -221,8 +221,10 @@ cudaError_t launch_dscale(ahlp_problem *p);   // dscale = x / z
 cudaError_t launch_form(ahlp_problem *p, double delta);
 cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
                          const double *diag0, double tol, int *status, cudaStream_t s);
-cudaError_t launch_pchol_f32(float *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
-                             const double *diag0, double tol, int *status, cudaStream_t s);
+// FP32: also writes the inverted diagonal tiles into tinv (see launch_tinv)
+cudaError_t launch_pchol_f32(float *buf, float *tinv, const BlkInfo *info,
+                             const std::vector<BlkInfo> &h, const double *diag0, double tol,
+                             int *status, cudaStream_t s);
 // forward / backward solves with one partial factor per CTA (the border
 // factors; vectors FP64, held in shared memory)
 cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,

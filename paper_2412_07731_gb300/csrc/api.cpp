@@ -843,7 +843,8 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
   ck(launch_form(p, delta), "form");
   ck(cudaEventRecord(p->ev[1], s), "event");
   if (p->fac_prec == kPrecFP32)
-    ck(launch_pchol_f32(p->aug32, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s),
+    ck(launch_pchol_f32(p->aug32, p->tinv32, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol,
+                        p->status, s),
        "pchol");
   else
     ck(launch_pchol(p->aug, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s), "pchol");

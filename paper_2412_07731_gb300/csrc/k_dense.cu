@@ -165,6 +165,153 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_kernel(T *buf, const BlkI
   }
 }
 
+// --------------------------------------------------------------------------
+// FP32 factors: diagonal tile by one warp (warp barriers only; the pivot
+// safeguard in FP32), then the inverse of its pivot triangle, written in the
+// layout the block solves use (inverse on the pivot rows, the factor on the
+// non-pivot rows of a block's last pivot tile).  The panel below then is a
+// product with that inverse instead of a column-by-column substitution.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(NB) pchol_potrf_f32_kernel(float *buf, float *tinv,
+                                                             const BlkInfo *blk, int k,
+                                                             const double *diag0, float tol,
+                                                             int *status) {
+  const BlkInfo bi = blk[blockIdx.x];
+  if (k >= bi.Tp) return;
+  __shared__ float t[NB][NB + 1];
+  __shared__ float X[NB][NB + 1];
+  __shared__ float dref[NB];
+  const int r0 = k * NB;
+  const int nr = min(NB, bi.a - r0);
+  const int npiv = min(NB, bi.p - r0);
+  float *g = buf + bi.base + (long long)r0 * bi.lda + r0;
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    t[r][c] = (r < nr && c < nr && r >= c) ? g[(long long)c * bi.lda + r] : 0.0f;
+    X[r][c] = 0.0f;
+  }
+  for (int c = threadIdx.x; c < npiv; c += blockDim.x) dref[c] = (float)diag0[bi.d0off + r0 + c];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int c = 0; c < npiv; ++c) {
+      float piv = t[c][c];
+      const float lim = tol * dref[c];
+      const float floor_v = lim > 0.0f ? lim : 1.0f;
+      if (!(piv == piv)) {
+        if (lane == 0 && atomicAdd(&status[0], 1) == 0) {
+          status[2] = bi.tag + (int)blockIdx.x;
+          status[3] = r0 + c;
+        }
+        piv = floor_v;
+      } else if (!(piv > lim) || !(piv > 0.0f)) {
+        if (lane == 0) atomicAdd(&status[1], 1);
+        piv = floor_v;
+      }
+      const float lcc = sqrtf(piv), inv = 1.0f / lcc;
+      __syncwarp();
+      if (lane == 0) t[c][c] = lcc;
+      for (int r = c + 1 + lane; r < nr; r += 32) t[r][c] *= inv;
+      __syncwarp();
+      for (int r = c + 1 + lane; r < nr; r += 32) {
+        const float lr = t[r][c];
+        for (int q = c + 1; q <= r; ++q) t[r][q] = fmaf(-lr, t[q][c], t[r][q]);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // inverse of the pivot triangle: thread j substitutes e_j forward
+  const int j = threadIdx.x;
+  if (j < npiv) {
+    for (int i = j; i < npiv; ++i) {
+      float s0 = (i == j) ? 1.0f : 0.0f, s1 = 0.0f;
+      int q = j;
+      for (; q + 1 < i; q += 2) {
+        s0 = fmaf(-t[i][q], X[q][j], s0);
+        s1 = fmaf(-t[i][q + 1], X[q + 1][j], s1);
+      }
+      if (q < i) s0 = fmaf(-t[i][q], X[q][j], s0);
+      X[i][j] = (s0 + s1) / t[i][i];
+    }
+  }
+  __syncthreads();
+  float *out = tinv + bi.ioff + (long long)k * NB * NB;
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    if (r < nr && c < nr && r >= c) g[(long long)c * bi.lda + r] = t[r][c];
+    out[i] = r < npiv ? X[r][c] : (c < npiv ? t[r][c] : 0.0f);
+  }
+}
+
+// Panel tile (I, k) below the diagonal: X = A_Ik L_kk^-T on the pivot columns
+// (a 64x64x64 product with the stored inverse), then the non-pivot columns of
+// a block's last pivot tile: A_Is -= X L_sk'.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) pchol_trsm_inv_kernel(T *buf, const T *tinv,
+                                                                  const BlkInfo *blk, int k) {
+  const BlkInfo bi = blk[blockIdx.y];
+  if (k >= bi.Tp) return;
+  const int I = k + 1 + blockIdx.x;
+  if (I >= bi.T) return;
+  extern __shared__ __align__(16) unsigned char trsm_raw[];   // two (NB x NB+1) tiles
+  T(*A)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(trsm_raw);
+  T(*V)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(trsm_raw + sizeof(T) * NB * (NB + 1));
+  const int r0 = k * NB;
+  const int nr = min(NB, bi.a - r0);
+  const int npiv = min(NB, bi.p - r0);
+  const int ri = I * NB;
+  const int nri = min(NB, bi.a - ri);
+  T *gx = buf + bi.base + (long long)r0 * bi.lda + ri;
+  const T *ti = tinv + bi.ioff + (long long)k * NB * NB;
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    A[r][c] = (r < nri && c < nr) ? gx[(long long)c * bi.lda + r] : T(0);
+    V[r][c] = ti[i];   // V[r][c]: inverse (r < npiv) or factor (r >= npiv) entry (r, c)
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int q = 0; q < npiv; ++q) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = A[tx + 16 * a][q];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = V[ty + 16 * b][q];   // (L^-1)(c, q), zero for q > c
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = ty + 16 * b;
+      if (c < npiv) A[tx + 16 * a][c] = acc[a][b];
+    }
+  __syncthreads();
+  if (npiv < nr) {
+    const int ns = nr - npiv;
+    for (int idx = threadIdx.x; idx < nri * ns; idx += blockDim.x) {
+      const int r = idx % nri, sc = npiv + idx / nri;
+      T u = A[r][sc];
+      for (int c = 0; c < npiv; ++c) u = fma(-A[r][c], V[sc][c], u);
+      A[r][sc] = u;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    if (r < nri && c < nr) gx[(long long)c * bi.lda + r] = A[r][c];
+  }
+}
+
 // trailing update: C_IJ -= L_Ik L_Jk' over the pivot columns of step k.
 constexpr int KC = 16;
 template <typename T>
@@ -708,7 +855,7 @@ constexpr size_t tinv_smem() {
 }
 
 template <typename T>
-cudaError_t pchol_t(T *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
+cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkInfo> &h,
                     const double *diag0, double tol, int *status, cudaStream_t s) {
   int nblk = (int)h.size();
   if (nblk == 0) return cudaSuccess;
@@ -722,10 +869,19 @@ cudaError_t pchol_t(T *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
       if (t > maxPanel) maxPanel = t;
       if (t * (t + 1) / 2 > maxTrail) maxTrail = t * (t + 1) / 2;
     }
-    count_launch(), pchol_potrf_kernel<T><<<nblk, kThreads, 0, s>>>(buf, info, k, diag0, tol, status);
-    if (maxPanel > 0)
-      count_launch(), pchol_trsm_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads, trsm_smem<T>(), s>>>(
-          buf, info, k);
+    if constexpr (sizeof(T) == sizeof(float)) {
+      count_launch(), pchol_potrf_f32_kernel<<<nblk, NB, 0, s>>>(buf, tinv, info, k, diag0,
+                                                                 (float)tol, status);
+      if (maxPanel > 0)
+        count_launch(), pchol_trsm_inv_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads,
+                                                   trsm_smem<T>(), s>>>(buf, tinv, info, k);
+    } else {
+      count_launch(), pchol_potrf_kernel<T><<<nblk, kThreads, 0, s>>>(buf, info, k, diag0, tol,
+                                                                      status);
+      if (maxPanel > 0)
+        count_launch(), pchol_trsm_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads,
+                                               trsm_smem<T>(), s>>>(buf, info, k);
+    }
     if (maxTrail > 0)
       count_launch(), pchol_update_kernel<T><<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(buf, info, k);
     cudaError_t e = cudaGetLastError();
@@ -760,12 +916,13 @@ cudaError_t launch_form(ahlp_problem *p, double delta) {
 
 cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
                          const double *diag0, double tol, int *status, cudaStream_t s) {
-  return pchol_t<double>(buf, info, h, diag0, tol, status, s);
+  return pchol_t<double>(buf, nullptr, info, h, diag0, tol, status, s);
 }
 
-cudaError_t launch_pchol_f32(float *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
-                             const double *diag0, double tol, int *status, cudaStream_t s) {
-  return pchol_t<float>(buf, info, h, diag0, tol, status, s);
+cudaError_t launch_pchol_f32(float *buf, float *tinv, const BlkInfo *info,
+                             const std::vector<BlkInfo> &h, const double *diag0, double tol,
+                             int *status, cudaStream_t s) {
+  return pchol_t<float>(buf, tinv, info, h, diag0, tol, status, s);
 }
 
 cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,
@@ -811,13 +968,10 @@ cudaError_t launch_trsv(ahlp_problem *p, bool forward) {
 }
 
 cudaError_t launch_tinv(ahlp_problem *p) {
-  if (p->trsv_nb == 0) return cudaSuccess;   // one job per pivot tile
-  if (p->fac_prec == kPrecFP32)
-    count_launch(), tinv_kernel<float><<<p->trsv_nb, NB, tinv_smem<float>(), p->stream>>>(
-        p->aug32, p->tinv32, p->blk, p->trsv_bsched);
-  else
-    count_launch(), tinv_kernel<double><<<p->trsv_nb, NB, tinv_smem<double>(), p->stream>>>(
-        p->aug, p->tinv, p->blk, p->trsv_bsched);
+  // FP32 factors write their inverse tiles in pchol_potrf_f32_kernel
+  if (p->trsv_nb == 0 || p->fac_prec == kPrecFP32) return cudaSuccess;
+  count_launch(), tinv_kernel<double><<<p->trsv_nb, NB, tinv_smem<double>(), p->stream>>>(
+      p->aug, p->tinv, p->blk, p->trsv_bsched);
   return cudaGetLastError();
 }
 
@@ -826,15 +980,9 @@ cudaError_t set_dense_smem_limits(int bytes) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tinv_smem<double>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(tinv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)tinv_smem<float>());
-  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(pchol_trsm_kernel<double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)trsm_smem<double>());
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(pchol_trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)trsm_smem<float>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(ptri_fwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            bytes);
