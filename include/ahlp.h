@@ -55,7 +55,7 @@ extern "C" {
 #define AHLP_ERR_TIMEOUT        -10  /* a bounded device wait ran out                          */
 
 #define AHLP_PREC_FP64   0   /* every stage in FP64                                    */
-#define AHLP_PREC_MIXED  1   /* FP32 block factors, FP64 Schur factor and refinement   */
+#define AHLP_PREC_MIXED  1   /* FP32 block factors (float-float near the optimum), FP64 Schur factor and refinement */
 
 /* ---- problem description (host memory, copied at create) --------------- */
 
@@ -123,7 +123,9 @@ typedef struct {
                            / solve time) of them (4; 0..8)                      */
   double  fp32_cond_max;/* mixed precision: the block factors run in FP32 while
                            max(d)/min(d), d = x/z, stays at or below this value,
-                           and in FP64 beyond it (1e14)                          */
+                           and in float-float (two FP32 words, ~46 bits) beyond
+                           it; a float-float factor that fails moves to FP64
+                           (1e14)                                                */
 } ahlp_options;
 
 typedef struct {
@@ -140,12 +142,14 @@ typedef struct {
   int32_t tiny_pivots;    /* pivots clamped in the last factor                    */
   double  kkt_residual;   /* largest relative Newton residual seen                */
   int32_t escalations;    /* FP32->FP64 switches plus pivot-threshold coarsenings  */
-  int32_t fp64_switch_iter; /* mixed mode: iteration from which the block factors
-                             are FP64 (-1: never); FP64 mode: 0                   */
+  int32_t fp64_switch_iter; /* mixed mode: first iteration whose block factors are
+                             no longer FP32 (-1: never); FP64 mode: 0             */
   int32_t factors_fp32, factors_fp64;   /* block factorisations per precision     */
   int32_t correctors;     /* accepted centrality correctors                      */
   double  ms_block_fp32, ms_block_fp64; /* their summed device time (the batched
                                            partial Cholesky stage alone)         */
+  int32_t factors_ff;     /* float-float block factorisations (mixed mode)       */
+  double  ms_block_ff;    /* their summed device time                            */
 } ahlp_result;
 
 typedef struct {

@@ -56,7 +56,8 @@ class Result(C.Structure):
                 ("kkt_residual", C.c_double), ("escalations", C.c_int32),
                 ("fp64_switch_iter", C.c_int32), ("factors_fp32", C.c_int32),
                 ("factors_fp64", C.c_int32), ("correctors", C.c_int32),
-                ("ms_block_fp32", C.c_double), ("ms_block_fp64", C.c_double)]
+                ("ms_block_fp32", C.c_double), ("ms_block_fp64", C.c_double),
+                ("factors_ff", C.c_int32), ("ms_block_ff", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -337,11 +338,13 @@ def arrowhead_lp_create(lp, options: Options | None = None, batch: int = 1) -> P
     L.arrowhead_lp_sizes(h, C.byref(n), C.byref(m))
     prob = Problem(h, L, n.value, m.value)
     prob.schur_dim = int(sum(int(v) for v in lps[0].l)) + lps[0].n0 + lps[0].mg
+    prob.options = Options.from_buffer_copy(options) if options is not None else default_options()
     return prob
 
 
 def set_options(prob: Problem, options: Options):
     prob._check(prob._lib.arrowhead_lp_set_options(prob._h, C.byref(options)))
+    prob.options = Options.from_buffer_copy(options)
 
 
 def kkt_factor(prob: Problem, x, z, delta: float = -1.0, rho: float = -1.0):

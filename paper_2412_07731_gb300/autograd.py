@@ -19,6 +19,8 @@ import torch
 
 from . import _lib as L
 
+_ADJOINT_TOL = 1e-6   # relative residual above which the transposed solve has stalled
+
 
 class LPSolve(torch.autograd.Function):
     """(x, y, z) = LPSolve.apply(c, b, prob): optimum of min c'x s.t. Ax = b,
@@ -46,7 +48,22 @@ class LPSolve(torch.autograd.Function):
         gx = zeros_n if gx is None else gx.contiguous()
         gy = torch.zeros(prob.m, dtype=x.dtype, device=x.device) if gy is None else gy.contiguous()
         gz = zeros_n if gz is None else gz.contiguous()
-        (lx, ly, _), _ = L.kkt_adjoint_solve(prob, gx, gy, gz)
+        (lx, ly, _), info = L.kkt_adjoint_solve(prob, gx, gy, gz)
+        if not info["rel_residual"] <= _ADJOINT_TOL:
+            # the factor of the final iterate is not a good enough
+            # preconditioner (mixed precision at an extreme D): refactor in FP64
+            z = ctx.saved_tensors[1]
+            opts = L.Options.from_buffer_copy(prob.options)
+            fp64 = L.Options.from_buffer_copy(opts)
+            fp64.precision = L.PREC_FP64
+            L.set_options(prob, fp64)
+            try:
+                L.kkt_factor(prob, x, z)
+                (lx, ly, _), info = L.kkt_adjoint_solve(prob, gx, gy, gz)
+            finally:
+                L.set_options(prob, opts)
+            if not info["rel_residual"] <= _ADJOINT_TOL:
+                raise RuntimeError(f"adjoint KKT solve did not converge: {info}")
         return lx, ly, None
 
 

@@ -14,7 +14,13 @@ namespace ahlp {
 constexpr int NB = 64;            // tile edge of the dense kernels
 constexpr int kPrecFP64 = 0;      // factor storage of the block matrices
 constexpr int kPrecFP32 = 1;
+// float-float: value = hi + lo with two FP32 arrays (aug32 = hi, aug_lo = lo);
+// the factorisation runs in double-float arithmetic on the FP32 pipe (about
+// 46 significant bits); the finished factor is expanded into the FP64 buffer,
+// which the Schur assembly and the solves read as for an FP64 factor
+constexpr int kPrecFF = 2;
 constexpr double kFp32PivotTol = 1e-6;    // smallest clamp threshold for FP32 pivots
+constexpr double kFFPivotTol = 1e-12;     // smallest clamp threshold for float-float pivots
 constexpr long long kSmemVecBytes = 160 * 1024;   // dynamic smem of the border solves
 constexpr int kThreads = 256;     // threads per CTA of the dense kernels
 
@@ -114,7 +120,8 @@ struct ahlp_problem {
 
   // ---- factor storage -----------------------------------------------------
   double *aug = nullptr;            // all augmented matrices, FP64 (allocated when first used)
-  float *aug32 = nullptr;           // the same layout in FP32 (mixed mode)
+  float *aug32 = nullptr;           // the same layout in FP32 (mixed mode; hi part of FF)
+  float *aug_lo = nullptr;          // lo part of float-float factors
   long long aug_elems = 0;
   // per pivot tile of every block, a 64x64 column-major tile: the inverse of
   // the pivot triangle on its pivot rows, the factor itself on the non-pivot
@@ -122,7 +129,7 @@ struct ahlp_problem {
   double *tinv = nullptr;
   float *tinv32 = nullptr;
   long long tinv_elems = 0;
-  int fac_prec = 0;                 // precision of the current factor (kPrecFP64/kPrecFP32)
+  int fac_prec = 0;                 // precision of the current factor (kPrec*)
   ahlp::BlkInfo *blk = nullptr;     // [N]
   std::vector<ahlp::BlkInfo> h_blk;
   ahlp::SchurBlk *sblk = nullptr;   // [N]
@@ -221,6 +228,12 @@ cudaError_t launch_dscale(ahlp_problem *p);   // dscale = x / z
 cudaError_t launch_form(ahlp_problem *p, double delta);
 cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
                          const double *diag0, double tol, int *status, cudaStream_t s);
+// float-float (hi = aug32, lo): diagonal tiles and panels in FP64 arithmetic,
+// trailing updates in double-float; then hi + lo is expanded into out (the
+// FP64 factor buffer, elems entries), which the Schur assembly and the solves use
+cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
+                            const BlkInfo *info, const std::vector<BlkInfo> &h,
+                            const double *diag0, double tol, int *status, cudaStream_t s);
 // FP32: also writes the inverted diagonal tiles into tinv (see launch_tinv)
 cudaError_t launch_pchol_f32(float *buf, float *tinv, const BlkInfo *info,
                              const std::vector<BlkInfo> &h, const double *diag0, double tol,

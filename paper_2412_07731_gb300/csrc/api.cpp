@@ -801,14 +801,18 @@ void read_scalars(ahlp_problem *p, int k) {
 }
 
 int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
-  // an FP32 pivot that lost six digits is rounding noise
-  p->fac_pivot_tol = p->fac_prec == kPrecFP32 ? std::max(pivot_tol, kFp32PivotTol) : pivot_tol;
-  if (p->fac_prec == kPrecFP32 && !p->aug32) {
+  // an FP32 pivot that lost six digits, a float-float one that lost eleven,
+  // is rounding noise
+  p->fac_pivot_tol = p->fac_prec == kPrecFP32 ? std::max(pivot_tol, kFp32PivotTol)
+                     : p->fac_prec == kPrecFF ? std::max(pivot_tol, kFFPivotTol)
+                                              : pivot_tol;
+  if (p->fac_prec != kPrecFP64 && !p->aug32) {
     p->aug32 = dalloc<float>(p, p->aug_elems);
     p->tinv32 = dalloc<float>(p, std::max(p->tinv_elems, 1LL));
     p->vec32 = dalloc<float>(p, std::max(p->vec_elems, 1LL));
   }
-  if (p->fac_prec == kPrecFP64 && !p->aug) {
+  if (p->fac_prec == kPrecFF && !p->aug_lo) p->aug_lo = dalloc<float>(p, p->aug_elems);
+  if (p->fac_prec != kPrecFP32 && !p->aug) {
     p->aug = dalloc<double>(p, p->aug_elems);
     p->tinv = dalloc<double>(p, std::max(p->tinv_elems, 1LL));
   }
@@ -828,7 +832,8 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
   ck(launch_dscale(p), "dscale");
   if (p->fac_prec == kPrecFP32 && p->n > 0) {
     // adaptive precision: once D = X Z^-1 spans more than fp32_cond_max the
-    // block normal matrices are too ill-conditioned for FP32 factors
+    // block normal matrices are too ill-conditioned for FP32 factors, and the
+    // factor moves to float-float
     ck(launch_reduce(p, RED_MAXABS, p->dscale, nullptr, p->n, p->scal + 2), "reduce");
     ck(launch_reduce(p, RED_MIN, p->dscale, nullptr, p->n, p->scal + 3), "reduce");
     p->bytes_d2h += 2 * sizeof(double);
@@ -836,7 +841,7 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
        "D2H");
     ck(cudaStreamSynchronize(s), "sync");
     if (!(p->h_scal[2] <= p->opt.fp32_cond_max * p->h_scal[3])) {
-      p->fac_prec = kPrecFP64;
+      p->fac_prec = kPrecFF;
       return factor_impl(p, delta, rho, pivot_tol);
     }
   }
@@ -845,6 +850,10 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
   if (p->fac_prec == kPrecFP32)
     ck(launch_pchol_f32(p->aug32, p->tinv32, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol,
                         p->status, s),
+       "pchol");
+  else if (p->fac_prec == kPrecFF)
+    ck(launch_pchol_ff(p->aug32, p->aug_lo, p->aug, p->aug_elems, p->blk, p->h_blk, p->diag0,
+                       p->fac_pivot_tol, p->status, s),
        "pchol");
   else
     ck(launch_pchol(p->aug, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s), "pchol");
@@ -873,9 +882,12 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
       snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in block %d row %d", st[2], st[3]);
     else
       snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in link pair %d row %d", -1 - st[2], st[3]);
-    if (p->fac_prec == kPrecFP32) {   // FP32 range or accuracy exceeded: redo in FP64
-      if (p->opt.verbose) printf("%s with FP32 block factors; refactoring in FP64\n", buf);
-      p->fac_prec = kPrecFP64;
+    if (p->fac_prec != kPrecFP64) {   // range or accuracy exceeded: one precision up
+      const int up = p->fac_prec == kPrecFP32 ? kPrecFF : kPrecFP64;
+      if (p->opt.verbose)
+        printf("%s with %s block factors; refactoring in %s\n", buf,
+               p->fac_prec == kPrecFP32 ? "FP32" : "float-float", up == kPrecFF ? "float-float" : "FP64");
+      p->fac_prec = up;
       return factor_impl(p, delta, rho, pivot_tol);
     }
     return set_err(p, AHLP_ERR_NOT_SPD, buf);
@@ -1137,7 +1149,7 @@ int kkt_block_factor_dense(ahlp_problem *p, int32_t block, double *A, int64_t ld
       std::vector<float> hf(cnt);
       if (cnt) ck(cudaMemcpy(hf.data(), p->aug32 + bi.base, cnt * 4, cudaMemcpyDeviceToHost), "D2H");
       for (size_t i = 0; i < cnt; ++i) h[i] = hf[i];
-    } else if (cnt) {
+    } else if (cnt) {   // FP64, or the FP64 copy of a float-float factor
       ck(cudaMemcpy(h.data(), p->aug + bi.base, cnt * 8, cudaMemcpyDeviceToHost), "D2H");
     }
     for (long long c = 0; c < bi.a; ++c)

@@ -39,13 +39,14 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     const double eta = p->opt.eta;
     const double rho = p->opt.rho;
     // Safeguards of the factor, all kept for the later iterations once raised:
-    //  - the block factors start in FP32 in mixed precision and switch to FP64
-    //    once D spans more than fp32_cond_max (or an FP32 pivot overflows);
+    //  - the block factors start in FP32 in mixed precision and move to
+    //    float-float once D spans more than fp32_cond_max (or an FP32 factor
+    //    produces a NaN), and to FP64 when float-float fails in turn;
     //  - the pivot clamping threshold starts at pivot_tol;
     //  - the regularisation starts at delta.
     // A direction whose Newton residual stays above kEscalate after the Krylov
     // refinement (the degenerate end game, where the clamped factors stop
-    // being a good preconditioner) switches FP32 blocks to FP64, else makes
+    // being a good preconditioner) moves the blocks one precision up, else makes
     // the threshold 100x coarser (up to kMaxPivotTol).  A NaN in the factor or
     // in the direction does the same and, once those are exhausted, raises
     // the regularisation 100x (up to kMaxDelta): the Krylov refinement always
@@ -66,7 +67,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       ck(cudaMemcpyAsync(p->z, zz, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
       const int before = p->fac_prec;
       int st = factor_impl(p, delta, rho, ptol);
-      if (before == kPrecFP32 && p->fac_prec == kPrecFP64 && R.fp64_switch_iter < 0)
+      if (before == kPrecFP32 && p->fac_prec != kPrecFP32 && R.fp64_switch_iter < 0)
         R.fp64_switch_iter = cur_iter;
       R.ms_factor += p->stage_ms[0] + p->stage_ms[1] + p->stage_ms[2];
       R.tiny_pivots = p->tiny_pivots;
@@ -74,6 +75,9 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         if (p->fac_prec == kPrecFP32) {
           ++R.factors_fp32;
           R.ms_block_fp32 += p->stage_ms[1];
+        } else if (p->fac_prec == kPrecFF) {
+          ++R.factors_ff;
+          R.ms_block_ff += p->stage_ms[1];
         } else {
           ++R.factors_fp64;
           R.ms_block_fp64 += p->stage_ms[1];
@@ -93,9 +97,9 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     };
     // next safeguard; false when none is left (allow_delta: NaN recovery only)
     auto escalate = [&](bool allow_delta) {
-      if (p->fac_prec == kPrecFP32) {
-        p->fac_prec = kPrecFP64;
-        R.fp64_switch_iter = cur_iter;
+      if (p->fac_prec != kPrecFP64) {   // FP32 -> float-float -> FP64
+        if (p->fac_prec == kPrecFP32 && R.fp64_switch_iter < 0) R.fp64_switch_iter = cur_iter;
+        p->fac_prec = p->fac_prec == kPrecFP32 ? kPrecFF : kPrecFP64;
       } else if (ptol * 100.0 <= kMaxPivotTol * 1.0001) {
         ptol *= 100.0;
       } else if (allow_delta && delta > 0 && delta * 100.0 <= kMaxDelta * 1.0001) {

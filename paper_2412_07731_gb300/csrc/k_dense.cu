@@ -24,6 +24,7 @@ namespace {
 // --------------------------------------------------------------------------
 template <typename T>
 struct FormArgs {
+  float *lo;   // float-float: receives v - (double)(float)v (nullptr otherwise)
   const FormTile *tiles;
   const long long *tile_ent;
   const int *ent_pos;
@@ -38,12 +39,16 @@ struct FormArgs {
   double delta;
 };
 
-template <typename T>
+template <typename T, bool kLo>
 __global__ void __launch_bounds__(kThreads) form_aug_kernel(FormArgs<T> A) {
   __shared__ T t[NB * NB];   // column-major tile
+  __shared__ float tl[kLo ? NB * NB : 1];
   const FormTile ft = A.tiles[blockIdx.x];
   const BlkInfo bi = A.blk[ft.blk];
-  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) t[i] = T(0);
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    t[i] = T(0);
+    if constexpr (kLo) tl[i] = 0.0f;
+  }
   __syncthreads();
   const long long e0 = A.tile_ent[blockIdx.x], e1 = A.tile_ent[blockIdx.x + 1];
   for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -63,14 +68,18 @@ __global__ void __launch_bounds__(kThreads) form_aug_kernel(FormArgs<T> A) {
       A.cdiag0[bi.cdoff + (long long)ft.I * NB + rt - bi.p] = v;
     }
     t[ct * NB + rt] = T(v);
+    if constexpr (kLo) tl[ct * NB + rt] = (float)(v - (double)(float)v);
   }
   __syncthreads();
   const int r0 = ft.I * NB, c0 = ft.J * NB;
   const int nr = min(NB, bi.a - r0), nc = min(NB, bi.a - c0);
-  T *g = A.aug + bi.base + (long long)c0 * bi.lda + r0;
+  const long long g0 = bi.base + (long long)c0 * bi.lda + r0;
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
-    if (r < nr && c < nc) g[(long long)c * bi.lda + r] = t[i];
+    if (r < nr && c < nc) {
+      A.aug[g0 + (long long)c * bi.lda + r] = t[i];
+      if constexpr (kLo) A.lo[g0 + (long long)c * bi.lda + r] = tl[i];
+    }
   }
 }
 
@@ -309,6 +318,217 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_inv_kernel(T *buf, const 
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
     if (r < nri && c < nr) gx[(long long)c * bi.lda + r] = A[r][c];
+  }
+}
+
+// --------------------------------------------------------------------------
+// float-float factors (hi + lo, both FP32).  The diagonal tile and the panel
+// run in FP64 arithmetic on the converted values (a small share of the work);
+// the trailing update -- nearly all the flops -- runs in double-float
+// arithmetic on the FP32 pipe: each product by an FMA-based exact product, the
+// sum by error-free two-sum, the low parts in FP32, renormalised per chunk.
+// The __f*_rn intrinsics keep the compiler from contracting the error-free
+// transformations into FMAs.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double ff_get(const float *hi, const float *lo, long long i) {
+  return (double)hi[i] + (double)lo[i];
+}
+
+__device__ __forceinline__ void ff_put(float *hi, float *lo, long long i, double v) {
+  const float h = (float)v;
+  hi[i] = h;
+  lo[i] = (float)(v - (double)h);
+}
+
+// (sh, sl) += (ah + al)(bh + bl), al*bl dropped
+__device__ __forceinline__ void ff_mac(float &sh, float &sl, float ah, float al, float bh,
+                                       float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);   // exact rounding error of ah*bh
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = __fadd_rn(sh, p);
+  const float bv = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ void ff_renorm(float &sh, float &sl) {
+  const float h = __fadd_rn(sh, sl);
+  sl = __fsub_rn(sl, __fsub_rn(h, sh));
+  sh = h;
+}
+
+// hi + lo -> FP64 copy of the float-float factor, used by the solves
+__global__ void ff_expand_kernel(const float *__restrict__ hi, const float *__restrict__ lo,
+                                 double *__restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)hi[i] + (double)lo[i];
+}
+
+__global__ void __launch_bounds__(kThreads) pchol_potrf_ff_kernel(float *hi, float *lo,
+                                                                  const BlkInfo *blk, int k,
+                                                                  const double *diag0, double tol,
+                                                                  int *status) {
+  const BlkInfo bi = blk[blockIdx.x];
+  if (k >= bi.Tp) return;
+  __shared__ double t[NB][NB + 1];
+  __shared__ double s_inv;
+  const int r0 = k * NB;
+  const int nr = min(NB, bi.a - r0);
+  const int npiv = min(NB, bi.p - r0);
+  const long long g0 = bi.base + (long long)r0 * bi.lda + r0;
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    t[r][c] = (r < nr && c < nr && r >= c) ? ff_get(hi, lo, g0 + (long long)c * bi.lda + r) : 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < npiv; ++c) {
+    if (threadIdx.x == 0) {
+      double piv = t[c][c];
+      pivot_fix(piv, diag0[bi.d0off + r0 + c], tol, status, bi.tag + (int)blockIdx.x, r0 + c);
+      const double l = sqrt(piv);
+      t[c][c] = l;
+      s_inv = 1.0 / l;
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    for (int r = c + 1 + threadIdx.x; r < nr; r += blockDim.x) t[r][c] *= inv;
+    __syncthreads();
+    const int m = nr - c - 1;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int rr = idx % m, ss = idx / m;
+      if (rr >= ss) t[c + 1 + rr][c + 1 + ss] -= t[c + 1 + rr][c] * t[c + 1 + ss][c];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    if (r < nr && c < nr && r >= c) ff_put(hi, lo, g0 + (long long)c * bi.lda + r, t[r][c]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, float *lo,
+                                                                 const BlkInfo *blk, int k) {
+  const BlkInfo bi = blk[blockIdx.y];
+  if (k >= bi.Tp) return;
+  const int I = k + 1 + blockIdx.x;
+  if (I >= bi.T) return;
+  extern __shared__ __align__(16) unsigned char trsm_raw[];   // two (NB x NB+1) FP64 tiles
+  double(*L)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(trsm_raw);
+  double(*X)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(trsm_raw + sizeof(double) * NB * (NB + 1));
+  const int r0 = k * NB;
+  const int nr = min(NB, bi.a - r0);
+  const int npiv = min(NB, bi.p - r0);
+  const int ri = I * NB;
+  const int nri = min(NB, bi.a - ri);
+  const long long gl = bi.base + (long long)r0 * bi.lda + r0;
+  const long long gx = bi.base + (long long)r0 * bi.lda + ri;
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    L[r][c] = (r < nr && c < nr && r >= c) ? ff_get(hi, lo, gl + (long long)c * bi.lda + r) : 0.0;
+    X[r][c] = (r < nri && c < nr) ? ff_get(hi, lo, gx + (long long)c * bi.lda + r) : 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < npiv; ++c) {
+    const double inv = 1.0 / L[c][c];
+    for (int r = threadIdx.x; r < nri; r += blockDim.x) X[r][c] *= inv;
+    __syncthreads();
+    const int ns = nr - c - 1;
+    for (int idx = threadIdx.x; idx < nri * ns; idx += blockDim.x) {
+      const int r = idx % nri, sc = c + 1 + idx / nri;
+      X[r][sc] -= X[r][c] * L[sc][c];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
+    const int r = i % NB, c = i / NB;
+    if (r < nri && c < nr) ff_put(hi, lo, gx + (long long)c * bi.lda + r, X[r][c]);
+  }
+}
+
+constexpr int KCF = 16;   // pivot columns per staged chunk of the float-float update
+__global__ void __launch_bounds__(kThreads) pchol_update_ff_kernel(float *hi, float *lo,
+                                                                   const BlkInfo *blk, int k) {
+  const BlkInfo bi = blk[blockIdx.y];
+  if (k >= bi.Tp) return;
+  const long long t = bi.T - k - 1;
+  const long long q = blockIdx.x;
+  if (q >= t * (t + 1) / 2) return;
+  long long ii = (long long)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  while (ii * (ii + 1) / 2 > q) --ii;
+  while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
+  const long long jj = q - ii * (ii + 1) / 2;
+  const int I = k + 1 + (int)ii, J = k + 1 + (int)jj;
+  const int npiv = min(NB, bi.p - k * NB);
+  const int rI = I * NB, rJ = J * NB;
+  const int nrI = min(NB, bi.a - rI), nrJ = min(NB, bi.a - rJ);
+  __shared__ float Ah[KCF][NB], Al[KCF][NB], Bh[KCF][NB], Bl[KCF][NB];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.0f;
+  const long long colk = bi.base + (long long)(k * NB) * bi.lda;
+  for (int kc = 0; kc < npiv; kc += KCF) {
+    for (int idx = threadIdx.x; idx < KCF * NB; idx += blockDim.x) {
+      const int r = idx % NB, kk = idx / NB;
+      const bool kin = (kc + kk) < npiv;
+      const long long col = colk + (long long)(kc + kk) * bi.lda;
+      const bool aok = kin && r < nrI, bok = kin && r < nrJ;
+      Ah[kk][r] = aok ? hi[col + rI + r] : 0.0f;
+      Al[kk][r] = aok ? lo[col + rI + r] : 0.0f;
+      Bh[kk][r] = bok ? hi[col + rJ + r] : 0.0f;
+      Bl[kk][r] = bok ? lo[col + rJ + r] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KCF; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ah[i] = Ah[kk][tx + 16 * i];
+        al[i] = Al[kk][tx + 16 * i];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        bh[j] = Bh[kk][ty + 16 * j];
+        bl[j] = Bl[kk][ty + 16 * j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ff_mac(sh[i][j], sl[i][j], ah[i], al[i], bh[j], bl[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) ff_renorm(sh[i][j], sl[i][j]);
+    __syncthreads();
+  }
+  const long long g = bi.base + (long long)rJ * bi.lda + rI;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = ty + 16 * j;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = tx + 16 * i;
+      if (r < nrI && c < nrJ && (I != J || r >= c)) {
+        const long long e = g + (long long)c * bi.lda + r;
+        // (ch + cl) - (sh + sl): two-sum of the high parts, low parts added
+        const float ch = hi[e], cl = lo[e], s = sh[i][j];
+        const float tt = __fsub_rn(ch, s);
+        const float bv = __fsub_rn(tt, ch);
+        const float err = __fadd_rn(__fsub_rn(ch, __fsub_rn(tt, bv)), __fsub_rn(-s, bv));
+        const float el = __fadd_rn(err, __fsub_rn(cl, sl[i][j]));
+        const float h = __fadd_rn(tt, el);
+        hi[e] = h;
+        lo[e] = __fsub_rn(el, __fsub_rn(h, tt));
+      }
+    }
   }
 }
 
@@ -903,14 +1123,49 @@ cudaError_t launch_dscale(ahlp_problem *p) {
 cudaError_t launch_form(ahlp_problem *p, double delta) {
   if (p->ntiles <= 0) return cudaSuccess;
   if (p->fac_prec == kPrecFP32) {
-    FormArgs<float> A{p->ftiles, p->tile_ent, p->ent_pos, p->ent_cb, p->con_idx, p->con_coef,
-                      p->dscale, p->blk, p->aug32, p->diag0, p->cdiag0, delta};
-    count_launch(), form_aug_kernel<float><<<(unsigned)p->ntiles, kThreads, 0, p->stream>>>(A);
+    FormArgs<float> A{nullptr, p->ftiles, p->tile_ent, p->ent_pos, p->ent_cb, p->con_idx,
+                      p->con_coef, p->dscale, p->blk, p->aug32, p->diag0, p->cdiag0, delta};
+    count_launch(), form_aug_kernel<float, false><<<(unsigned)p->ntiles, kThreads, 0, p->stream>>>(A);
+  } else if (p->fac_prec == kPrecFF) {
+    FormArgs<float> A{p->aug_lo, p->ftiles, p->tile_ent, p->ent_pos, p->ent_cb, p->con_idx,
+                      p->con_coef, p->dscale, p->blk, p->aug32, p->diag0, p->cdiag0, delta};
+    count_launch(), form_aug_kernel<float, true><<<(unsigned)p->ntiles, kThreads, 0, p->stream>>>(A);
   } else {
-    FormArgs<double> A{p->ftiles, p->tile_ent, p->ent_pos, p->ent_cb, p->con_idx, p->con_coef,
-                       p->dscale, p->blk, p->aug, p->diag0, p->cdiag0, delta};
-    count_launch(), form_aug_kernel<double><<<(unsigned)p->ntiles, kThreads, 0, p->stream>>>(A);
+    FormArgs<double> A{nullptr, p->ftiles, p->tile_ent, p->ent_pos, p->ent_cb, p->con_idx,
+                       p->con_coef, p->dscale, p->blk, p->aug, p->diag0, p->cdiag0, delta};
+    count_launch(), form_aug_kernel<double, false><<<(unsigned)p->ntiles, kThreads, 0, p->stream>>>(A);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
+                            const BlkInfo *info, const std::vector<BlkInfo> &h,
+                            const double *diag0, double tol, int *status, cudaStream_t s) {
+  int nblk = (int)h.size();
+  if (nblk == 0) return cudaSuccess;
+  int maxTp = 0;
+  for (auto &b : h) maxTp = b.Tp > maxTp ? b.Tp : maxTp;
+  for (int k = 0; k < maxTp; ++k) {
+    long long maxPanel = 0, maxTrail = 0;
+    for (auto &b : h) {
+      if (k >= b.Tp) continue;
+      long long t = b.T - k - 1;
+      if (t > maxPanel) maxPanel = t;
+      if (t * (t + 1) / 2 > maxTrail) maxTrail = t * (t + 1) / 2;
+    }
+    count_launch(), pchol_potrf_ff_kernel<<<nblk, kThreads, 0, s>>>(hi, lo, info, k, diag0, tol,
+                                                                    status);
+    if (maxPanel > 0)
+      count_launch(), pchol_trsm_ff_kernel<<<dim3((unsigned)maxPanel, nblk), kThreads,
+                                             trsm_smem<double>(), s>>>(hi, lo, info, k);
+    if (maxTrail > 0)
+      count_launch(), pchol_update_ff_kernel<<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(
+          hi, lo, info, k);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (elems > 0)
+    count_launch(), ff_expand_kernel<<<152 * 8, 256, 0, s>>>(hi, lo, out, elems);
   return cudaGetLastError();
 }
 
@@ -968,7 +1223,8 @@ cudaError_t launch_trsv(ahlp_problem *p, bool forward) {
 }
 
 cudaError_t launch_tinv(ahlp_problem *p) {
-  // FP32 factors write their inverse tiles in pchol_potrf_f32_kernel
+  // FP32 factors write their inverse tiles in pchol_potrf_f32_kernel; FP64 and
+  // float-float factors (through their FP64 copy) get them here
   if (p->trsv_nb == 0 || p->fac_prec == kPrecFP32) return cudaSuccess;
   count_launch(), tinv_kernel<double><<<p->trsv_nb, NB, tinv_smem<double>(), p->stream>>>(
       p->aug, p->tinv, p->blk, p->trsv_bsched);
@@ -979,6 +1235,9 @@ cudaError_t set_dense_smem_limits(int bytes) {
   cudaError_t e = cudaFuncSetAttribute(tinv_kernel<double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tinv_smem<double>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(pchol_trsm_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trsm_smem<double>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(pchol_trsm_kernel<double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,

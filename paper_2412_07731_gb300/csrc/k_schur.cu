@@ -18,7 +18,7 @@ namespace ahlp {
 namespace {
 
 struct SArgs {
-  const double *aug;      // FP64 factors (prec == kPrecFP64)
+  const double *aug;      // FP64 factors (prec kPrecFP64 / kPrecFF)
   const float *aug32;     // FP32 factors (prec == kPrecFP32)
   int prec;
   const BlkInfo *blk;
@@ -38,6 +38,7 @@ struct SArgs {
 __device__ __forceinline__ double cget(const SArgs &A, const BlkInfo &bi, int m, int r, int c) {
   const int R = m + max(r, c), C = m + min(r, c);
   const long long idx = bi.base + (long long)C * bi.lda + R;
+  // FP64 factors, or the FP64 copy of float-float ones
   return A.prec == kPrecFP32 ? (double)A.aug32[idx] : A.aug[idx];
 }
 

@@ -91,3 +91,42 @@ def test_mixed_ipm_structured_shape(P):
     (x, y, z), r = P.ipm_solve(prob)
     assert r["status"] == 0
     assert abs(r["pobj"] - ref["pobj"]) / (1 + abs(ref["pobj"])) <= 1e-8
+
+
+def test_float_float_schur_matches_fp64(P):
+    """Float-float block factors (two FP32 words, double-float trailing
+    updates) give the Schur complement to nearly FP64 accuracy: at a point
+    where D spans ~1e10, within 1e-10 of the FP64 one (relative to its
+    scale), where FP32 factors reach only ~1e-5."""
+    lp = random_block_lp(4, **SHAPE)
+    A, b, c = olp.assemble(lp)
+    rng = np.random.default_rng(5)
+    n = A.shape[1]
+    x, z = np.exp(3 * rng.standard_normal(n)), np.exp(3 * rng.standard_normal(n))
+    p64 = P.arrowhead_lp_create(lp)
+    P.kkt_factor(p64, x, z)
+    S64 = P.kkt_schur_dense(p64)
+    pff = P.arrowhead_lp_create(lp, _mixed(P, fp32_cond_max=1.0))
+    P.kkt_factor(pff, x, z)
+    Sff = P.kkt_schur_dense(pff)
+    scale = np.abs(S64).max()
+    assert np.abs(Sff - S64).max() <= 1e-10 * scale
+    p32 = P.arrowhead_lp_create(lp, _mixed(P, fp32_cond_max=1e300))
+    P.kkt_factor(p32, x, z)
+    S32 = P.kkt_schur_dense(p32)
+    assert np.abs(S32 - S64).max() > 1e3 * np.abs(Sff - S64).max()   # the test can tell them apart
+    for p in (p64, pff, p32):
+        p.close()
+
+
+@pytest.mark.parametrize("seed", [0, 4, 8])
+def test_float_float_ipm_matches_oracle(P, seed):
+    """Mixed IPM with every factor past the starting point in float-float
+    reaches the oracle's optimum."""
+    lp = config0(seed)
+    ref = oipm.solve_blocklp(lp)
+    prob = P.arrowhead_lp_create(lp, _mixed(P, fp32_cond_max=1.0))
+    _, r = P.ipm_solve(prob)
+    assert r["factors_ff"] > 0
+    assert abs(r["pobj"] - ref["pobj"]) <= 1e-8 * (1 + abs(ref["pobj"]))
+    prob.close()
