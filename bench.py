@@ -335,6 +335,52 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_kkt(args):
+    """KKT factor and solve alone: one factorisation at a seeded interior point
+    (x, z = exp(N(0,1)), seed 0) of the first --blocks blocks of the workload,
+    then --steps solves (the block solve, Schur solve and back-substitution,
+    without Krylov refinement).  Reports the stage times measured with CUDA
+    events inside the library."""
+    import numpy as np
+    import torch
+    import paper_2412_07731_gb300 as P
+    from instances import prefix
+    lp, desc = workload(args.workload)
+    if args.blocks and args.blocks < lp.N:
+        lp = prefix(lp, args.blocks)
+    prec = P.PREC_MIXED if args.precision == "mixed" else P.PREC_FP64
+    opts = dict(refine_max=0)
+    if args.force_fp32:
+        opts["fp32_cond_max"] = 1e300
+    prob = P.arrowhead_lp_create(lp, P.default_options(precision=prec, **opts))
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(0)
+    f64 = dict(dtype=torch.float64, device=dev)
+    x = torch.tensor(np.exp(rng.standard_normal(prob.n)), **f64)
+    z = torch.tensor(np.exp(rng.standard_normal(prob.n)), **f64)
+    rp = torch.tensor(rng.standard_normal(prob.m), **f64)
+    zero = torch.zeros(prob.n, **f64)
+    fac, sol = [], []
+    for _ in range(args.warmup + args.steps):
+        P.kkt_factor(prob, x, z)
+        fac.append(P.kkt_stage_times(prob))
+    for _ in range(args.warmup + args.steps):
+        P.kkt_solve(prob, zero, rp, zero)
+        sol.append(P.kkt_stage_times(prob)["last_solve_ms"])
+    fac, sol = fac[args.warmup:], sol[args.warmup:]
+    med = lambda v: statistics.median(v)
+    line = {"metric": "KKT factor and solve ms", "unit": "ms", "higher_is_better": False,
+            "config": {"workload": desc, "blocks": lp.N, "precision": args.precision,
+                       "fp32_forced": bool(args.force_fp32), "steps": args.steps,
+                       "warmup": args.warmup},
+            "form_ms": med([f["form_ms"] for f in fac]),
+            "block_factor_ms": med([f["block_factor_ms"] for f in fac]),
+            "schur_ms": med([f["schur_ms"] for f in fac]),
+            "kkt_solve_ms": med(sol)}
+    print(json.dumps(line), flush=True)
+    prob.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,6 +391,12 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other precision's measurement")
+    ap.add_argument("--kkt-only", action="store_true",
+                    help="time one KKT factorisation and --steps solves at a seeded point")
+    ap.add_argument("--blocks", type=int, default=0,
+                    help="--kkt-only: use the first BLOCKS blocks of the workload")
+    ap.add_argument("--force-fp32", action="store_true",
+                    help="--kkt-only, mixed: keep FP32 block factors at any conditioning")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--probe-peaks", action="store_true",
@@ -357,7 +409,9 @@ def main():
         subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
                         src], check=True)
         sys.exit(subprocess.run([exe]).returncode)
-    if args.impl == "reference":
+    if args.kkt_only:
+        run_kkt(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
