@@ -107,7 +107,11 @@ typedef struct {
                            solves the unregularised Newton system.  ipm_solve
                            raises it x100 (up to 1e-4) when a NaN persists after
                            the FP64 and pivot-threshold safeguards            */
-  double  rho;          /* primal regularisation of the factor on x_0 (0)        */
+  double  rho;          /* primal regularisation of the factor: D^-1 + rho on every
+                           primal variable (block variables through
+                           d = x / (z + rho x)) (0); ipm_solve raises it from
+                           1e-10 up to 1e-6 when a NaN persists after the other
+                           safeguards                                           */
   int32_t refine_max;   /* GMRES iterations per KKT solve, at most 64 (40)        */
   double  refine_tol;   /* target relative Newton residual (1e-10)                */
   double  pivot_tol;    /* a pivot not above pivot_tol * (its diagonal before
@@ -170,7 +174,15 @@ const char *ahlp_status_string(int status);
  * and run the symbolic analysis (storage layout of the per-block augmented
  * matrices, formation patterns, Schur-complement index maps).
  *   descs : [batch] problem descriptions (host memory)
- *   batch : must be 1 in this version (else AHLP_ERR_UNSUPPORTED)
+ *   batch : number of independent LPs in descs (>= 1).  A batch is solved as
+ *           their direct sum, one arrowhead LP whose blocks are all the LPs'
+ *           blocks in order (consecutive blocks of different LPs share no link
+ *           rows), so every stage runs all LPs in the same launches.  The
+ *           global vectors of the handle follow the direct sum's ordering:
+ *           x = [blocks of LP 0, blocks of LP 1, ..., x_0 of LP 0, x_0 of LP 1,
+ *           ...]; y = [block rows of all LPs, link rows of all LPs, global rows
+ *           of all LPs], each part in LP order.  ipm_solve stops when every LP
+ *           meets the tolerances on its own and reports the worst LP.
  *   opt   : options, or NULL for defaults
  *   out   : receives the handle; *out is NULL on error
  * The structure follows Sec. 3.2 (blocks, linking variables and rows) and

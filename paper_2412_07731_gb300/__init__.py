@@ -12,6 +12,7 @@ from ._lib import (  # noqa: F401
     Problem,
     STATUS,
     arrowhead_lp_create,
+    batch_layout,
     default_options,
     ipm_solve,
     kkt_adjoint_solve,

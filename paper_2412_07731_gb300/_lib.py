@@ -94,6 +94,29 @@ def launch_count() -> int:
     return int(load().ahlp_launch_count())
 
 
+def batch_layout(lps):
+    """For a batch of LPs: per LP, the index arrays (ix, iy) that place its own
+    global vectors -- x = [x_1..x_N, x_0], y = [y_1..y_N, y_links, y_g] -- in
+    the direct sum's vectors: x = [blocks of every LP, x_0 of every LP],
+    y = [block rows of every LP, link rows of every LP, global rows of every
+    LP].  combined[ix] = own_x, own_x = combined[ix]."""
+    nxb = [int(sum(A.shape[1] for A in q.A)) for q in lps]
+    nyb = [int(sum(A.shape[0] for A in q.A)) for q in lps]
+    nl = [int(sum(int(v) for v in q.l)) for q in lps]
+    xb0 = np.concatenate([[0], np.cumsum(nxb)]).astype(np.int64)
+    x00 = xb0[-1] + np.concatenate([[0], np.cumsum([q.n0 for q in lps])]).astype(np.int64)
+    yb0 = np.concatenate([[0], np.cumsum(nyb)]).astype(np.int64)
+    yl0 = yb0[-1] + np.concatenate([[0], np.cumsum(nl)]).astype(np.int64)
+    yg0 = yl0[-1] + np.concatenate([[0], np.cumsum([q.mg for q in lps])]).astype(np.int64)
+    out = []
+    for k, q in enumerate(lps):
+        ix = np.concatenate([np.arange(xb0[k], xb0[k + 1]), np.arange(x00[k], x00[k + 1])])
+        iy = np.concatenate([np.arange(yb0[k], yb0[k + 1]), np.arange(yl0[k], yl0[k + 1]),
+                             np.arange(yg0[k], yg0[k + 1])])
+        out.append((ix, iy))
+    return out
+
+
 def set_cb(prob, c=None, b=None):
     """Replace the objective c ([n]) and/or right-hand side b ([m]) of the
     handle; host (numpy) or device (torch) vectors, None keeps the current."""
@@ -322,13 +345,18 @@ class Problem:
                 return
 
 
-def arrowhead_lp_create(lp, options: Options | None = None, batch: int = 1) -> Problem:
+def arrowhead_lp_create(lp, options: Options | None = None, batch: int | None = None) -> Problem:
+    """Handle for one LP, or for a batch (a list of LPs, solved as their direct
+    sum; see batch_layout for the ordering of its vectors)."""
     L = load()
     keep = _Keep()
+    lps = list(lp) if isinstance(lp, (list, tuple)) else [lp]
+    if batch is None:
+        batch = len(lps)
+    lps = [lps[min(k, len(lps) - 1)] for k in range(batch)]
     descs = (Desc * batch)()
-    lps = lp if isinstance(lp, (list, tuple)) else [lp]
     for k in range(batch):
-        descs[k] = make_desc(lps[min(k, len(lps) - 1)], keep)
+        descs[k] = make_desc(lps[k], keep)
     h = C.c_void_p()
     st = L.arrowhead_lp_create(descs, batch, C.byref(options) if options is not None else None,
                                C.byref(h))
@@ -337,7 +365,8 @@ def arrowhead_lp_create(lp, options: Options | None = None, batch: int = 1) -> P
     n, m = C.c_int64(), C.c_int64()
     L.arrowhead_lp_sizes(h, C.byref(n), C.byref(m))
     prob = Problem(h, L, n.value, m.value)
-    prob.schur_dim = int(sum(int(v) for v in lps[0].l)) + lps[0].n0 + lps[0].mg
+    prob.schur_dim = sum(int(sum(int(v) for v in q.l)) + q.n0 + q.mg for q in lps)
+    prob.batch = batch
     prob.options = Options.from_buffer_copy(options) if options is not None else default_options()
     return prob
 

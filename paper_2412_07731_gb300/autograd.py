@@ -22,6 +22,41 @@ from . import _lib as L
 _ADJOINT_TOL = 1e-6   # relative residual above which the transposed solve has stalled
 
 
+def _factor_chain(prob, x, z):
+    """kkt_factor at (x, z), answering a NaN pivot with more regularisation
+    (dual delta, primal rho); True on success."""
+    for delta, rho in ((-1.0, -1.0), (1e-6, 1e-8), (1e-4, 1e-6)):
+        try:
+            L.kkt_factor(prob, x, z, delta, rho)
+            return True
+        except L.AHLPError as e:
+            if e.status != -4:   # AHLP_ERR_NOT_SPD
+                raise
+    return False
+
+
+def _factor_fp64(prob, x, z):
+    """The same chain with FP64 block factors, the handle's options restored."""
+    opts = L.Options.from_buffer_copy(prob.options)
+    fp64 = L.Options.from_buffer_copy(opts)
+    fp64.precision = L.PREC_FP64
+    L.set_options(prob, fp64)
+    try:
+        if not _factor_chain(prob, x, z):
+            raise RuntimeError("no usable factor at the returned point")
+    finally:
+        L.set_options(prob, opts)
+
+
+def _factor_at_optimum(prob, x, z):
+    """Factor at the returned point for the transposed solves of backward.  The
+    point is extremely ill-conditioned (complementarity ~ the tolerance); the
+    factor only preconditions an FGMRES solve of the exact transposed system,
+    so a NaN pivot is answered with more regularisation, then an FP64 factor."""
+    if not _factor_chain(prob, x, z):
+        _factor_fp64(prob, x, z)
+
+
 class LPSolve(torch.autograd.Function):
     """(x, y, z) = LPSolve.apply(c, b, prob): optimum of min c'x s.t. Ax = b,
     x >= 0 for the handle's structure.  c: [n], b: [m] float64 tensors (CPU or
@@ -35,7 +70,7 @@ class LPSolve(torch.autograd.Function):
         f64 = dict(dtype=torch.float64, device=c.device)
         x, y, z = torch.empty(prob.n, **f64), torch.empty(prob.m, **f64), torch.empty(prob.n, **f64)
         L.ipm_solve(prob, out=(x, y, z))
-        L.kkt_factor(prob, x, z)
+        _factor_at_optimum(prob, x, z)
         ctx.prob = prob
         ctx.save_for_backward(x, z)
         return x, y, z
@@ -52,16 +87,8 @@ class LPSolve(torch.autograd.Function):
         if not info["rel_residual"] <= _ADJOINT_TOL:
             # the factor of the final iterate is not a good enough
             # preconditioner (mixed precision at an extreme D): refactor in FP64
-            z = ctx.saved_tensors[1]
-            opts = L.Options.from_buffer_copy(prob.options)
-            fp64 = L.Options.from_buffer_copy(opts)
-            fp64.precision = L.PREC_FP64
-            L.set_options(prob, fp64)
-            try:
-                L.kkt_factor(prob, x, z)
-                (lx, ly, _), info = L.kkt_adjoint_solve(prob, gx, gy, gz)
-            finally:
-                L.set_options(prob, opts)
+            _factor_fp64(prob, x, ctx.saved_tensors[1])
+            (lx, ly, _), info = L.kkt_adjoint_solve(prob, gx, gy, gz)
             if not info["rel_residual"] <= _ADJOINT_TOL:
                 raise RuntimeError(f"adjoint KKT solve did not converge: {info}")
         return lx, ly, None

@@ -84,9 +84,11 @@ struct FormTile {
 // Per-block layout of the local Schur columns k_i = n0 + lprev + lnext + mg.
 struct SchurBlk {
   int m;       // pivots (rows of A_i)
-  int k;       // local Schur columns
+  int k;       // local Schur columns: [x_0 slice | links i-1 | links i | global-row slice]
   int lprev, lnext;
   int link_prev_off, link_next_off;   // offsets of pairs i-1 and i in the link block
+  int x0lo, x0n;   // the block's slice of the linking variables (all of them for one LP;
+  int glo, gn;     // its LP's ones in a batch) and of the global rows
 };
 
 struct DeviceBuf {
@@ -99,6 +101,16 @@ struct DeviceBuf {
 struct ahlp_problem {
   // ---- sizes -------------------------------------------------------------
   int N = 0, n0 = 0, mg = 0, B = 0, nl = 0, nS = 0;
+  // batch > 1: the direct sum of independent LPs; per LP its first block and
+  // the offsets of its slices of x_0 and of the global rows
+  int batch = 1;
+  std::vector<long long> lp_blk0, lp_x0off, lp_goff;
+  struct LpRange {   // index ranges of one LP of a batch in the global vectors
+    long long xb0, xb1, x00, x01;            // x: its blocks, its linking variables
+    long long yb0, yb1, yl0, yl1, yg0, yg1;  // y: block rows, link rows, global rows
+    double bnorm, cnorm;                      // its ||b||_inf and ||c||_inf
+  };
+  std::vector<LpRange> lp_rng;
   long long n = 0, m = 0, msum = 0;   // n_total, m_total, sum of m_i
   std::vector<int> mi, ni, ki, lprev, lnext;
   std::vector<long long> xoff, yoff, link_off;   // link_off has N entries (pairs + 1)
@@ -164,6 +176,9 @@ struct ahlp_problem {
   long long *link_off_d = nullptr;   // [N]
   int *kmap = nullptr;               // local Schur index -> global S index
   int *link_pair_d = nullptr;        // [nl] pair of each link row
+  int *chain_seg = nullptr;          // [2 nchain_seg] pair ranges with link rows throughout
+  int nchain_seg = 0;
+  int *zlo = nullptr, *zhi = nullptr;   // [B] link rows a border column of Z can touch
   long long *yoff_d = nullptr;       // [N] start of y_i
   long long *kmap_off_d = nullptr;   // [N]
   std::vector<long long> kmap_off;
@@ -204,6 +219,7 @@ struct ahlp_problem {
   bool factored = false;
   bool assembled = false;     // the Schur complement of the last kkt_factor exists
   double fac_delta = 0, fac_rho = 0, fac_pivot_tol = 0;
+  double fac_rho_x = 0;   // primal regularisation of the preconditioner's D (ipm_solve's last safeguard)
 
   // ---- host <-> device traffic since create (ahlp_transfer_bytes) ----------
   long long bytes_h2d = 0, bytes_d2h = 0;
@@ -224,7 +240,7 @@ long long launch_count();
 
 // ---- kernels (launch wrappers) --------------------------------------------
 // All wrappers enqueue on p->stream and return the cudaError_t of the launch.
-cudaError_t launch_dscale(ahlp_problem *p);   // dscale = x / z
+cudaError_t launch_dscale(ahlp_problem *p);   // dscale = x / (z + fac_rho_x x)
 cudaError_t launch_form(ahlp_problem *p, double delta);
 cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
                          const double *diag0, double tol, int *status, cudaStream_t s);

@@ -1,6 +1,7 @@
 // Host runtime of the C ABI: validation, symbolic analysis, device memory,
 // and the kkt_factor / kkt_solve / kkt_adjoint_solve entry points.
 #include <algorithm>
+#include <deque>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -160,7 +161,7 @@ struct URow {   // one link / global row restricted to the block's columns
 };
 
 void build_block_pattern(int blk, const Csc &A, const Csc &W, const std::vector<URow> &urows,
-                         int n0, int m, int k, long long xoff, Pattern &P) {
+                         int x0lo, int x0n, int m, int k, long long xoff, Pattern &P) {
   const int a = m + k;
   const int T = (a + NB - 1) / NB;
   auto tile_id = [T](long long It, long long Jt) { return Jt * T - Jt * (Jt - 1) / 2 + (It - Jt); };
@@ -177,13 +178,13 @@ void build_block_pattern(int blk, const Csc &A, const Csc &W, const std::vector<
       for (int q = A.cp[j]; q <= p; ++q)
         add(A.ri[p], A.ri[q], (int)(xoff + j), A.v[p] * A.v[q]);
   for (int r = 0; r < m; ++r) add(r, r, -1, 0.0);   // every diagonal entry exists
-  // G_i' rows: W_i part (constant) ...
-  for (int t = 0; t < n0; ++t)
-    for (int q = W.cp[t]; q < W.cp[t + 1]; ++q) add(m + t, W.ri[q], -1, W.v[q]);
+  // G_i' rows: W_i part (constant, the block's slice of the linking variables) ...
+  for (int t = 0; t < x0n; ++t)
+    for (int q = W.cp[x0lo + t]; q < W.cp[x0lo + t + 1]; ++q) add(m + t, W.ri[q], -1, W.v[q]);
   // ... and A_i D_i u' for every link / global row u touching the block
   std::vector<std::vector<std::pair<int, double>>> ucol(A.n);
   for (size_t tt = 0; tt < urows.size(); ++tt) {
-    const int t = n0 + (int)tt;
+    const int t = x0n + (int)tt;
     const URow &u = urows[tt];
     for (size_t e = 0; e < u.j.size(); ++e) {
       const int j = u.j[e];
@@ -340,6 +341,170 @@ int arrowhead_lp_set_cb(ahlp_problem *p, const double *c, const double *b) {
   }
 }
 
+namespace {
+
+// A batch of independent arrowhead LPs solved as one: their direct sum is an
+// arrowhead LP whose blocks are all the LPs' blocks in order, whose linking
+// variables and global rows are the LPs' ones stacked, and in which a pair of
+// consecutive blocks of different LPs has no link rows.  W, F0 and Fg0 get
+// their columns moved to the LP's slice of x_0, Fg and Fg0 their rows to the
+// LP's slice of the global rows; everything else is reused as given.
+struct BatchDesc {
+  ahlp_desc d{};
+  std::vector<ahlp_csc> A, W, Fg, FL, FR, F0;
+  ahlp_csc Fg0{};
+  std::vector<const double *> b, c, blink, lb, ub;
+  std::vector<int32_t> l;
+  std::vector<double> c0, bg, lb0, ub0;
+  std::deque<std::vector<int32_t>> ints;   // owned index arrays (stable addresses)
+  std::deque<std::vector<double>> dbls;
+  std::vector<long long> blk0, x0off, goff;   // per LP: first block, x_0 and row offsets
+
+  const int32_t *zeros(int n) {
+    ints.emplace_back(n + 1, 0);
+    return ints.back().data();
+  }
+  // columns [0, n) of M become columns [off, off + n) of an ncols-wide matrix
+  ahlp_csc shift_cols(const ahlp_csc *M, int m, int n, int off, int ncols) {
+    if (M && (M->m != m || M->n != n)) fail(AHLP_ERR_DIM_MISMATCH, "batch: W or F0 shape");
+    ahlp_csc o{m, ncols, nullptr, nullptr, nullptr};
+    ints.emplace_back(ncols + 1, 0);
+    std::vector<int32_t> &cp = ints.back();
+    const int nnz = (M && n > 0 && M->colptr) ? M->colptr[n] : 0;
+    for (int j = 0; j <= ncols; ++j) {
+      const int jj = j - off;
+      cp[j] = jj <= 0 ? 0 : (jj >= n ? nnz : M->colptr[jj]);
+    }
+    o.colptr = cp.data();
+    o.rowidx = nnz ? M->rowidx : nullptr;
+    o.val = nnz ? M->val : nullptr;
+    return o;
+  }
+  // rows [0, m) of M become rows [off, off + m) of an nrows-high matrix
+  ahlp_csc shift_rows(const ahlp_csc *M, int m, int n, int off, int nrows) {
+    if (M && (M->m != m || M->n != n)) fail(AHLP_ERR_DIM_MISMATCH, "batch: Fg shape");
+    ahlp_csc o{nrows, n, nullptr, nullptr, nullptr};
+    if (!M || n == 0 || !M->colptr) {
+      o.colptr = zeros(n);
+      return o;
+    }
+    const int nnz = M->colptr[n];
+    ints.emplace_back(M->rowidx, M->rowidx + nnz);
+    for (auto &r : ints.back()) r += off;
+    o.colptr = M->colptr;
+    o.rowidx = ints.back().data();
+    o.val = M->val;
+    return o;
+  }
+};
+
+void compose_batch(const ahlp_desc *D, int B, BatchDesc &S) {
+  int N = 0, n0 = 0, mg = 0;
+  for (int b = 0; b < B; ++b) {
+    if (D[b].N < 1 || D[b].n0 < 0 || D[b].mg < 0)
+      fail(AHLP_ERR_INVALID_ARG, "batch item " + std::to_string(b) + ": N >= 1, n0 >= 0, mg >= 0 required");
+    if (!D[b].A || !D[b].W || !D[b].b || !D[b].c)
+      fail(AHLP_ERR_INVALID_ARG, "batch item " + std::to_string(b) + ": A, W, b, c must be given");
+    S.blk0.push_back(N);
+    S.x0off.push_back(n0);
+    S.goff.push_back(mg);
+    N += D[b].N;
+    n0 += D[b].n0;
+    mg += D[b].mg;
+  }
+  bool bounds = false, bounds0 = false;
+  for (int b = 0; b < B; ++b) {
+    const ahlp_desc &d = D[b];
+    const std::string tag = "batch item " + std::to_string(b);
+    if (d.N > 1 && !d.l) fail(AHLP_ERR_INVALID_ARG, tag + ": l must be given when N > 1");
+    for (int i = 0; i < d.N; ++i) {
+      const int mi = d.A[i].m, ni = d.A[i].n;
+      S.A.push_back(d.A[i]);
+      S.W.push_back(S.shift_cols(&d.W[i], mi, d.n0, (int)S.x0off[b], n0));
+      S.Fg.push_back(S.shift_rows(d.Fg ? &d.Fg[i] : nullptr, d.mg, ni, (int)S.goff[b], mg));
+      S.b.push_back(d.b[i]);
+      S.c.push_back(d.c[i]);
+      S.lb.push_back(d.lb ? d.lb[i] : nullptr);
+      S.ub.push_back(d.ub ? d.ub[i] : nullptr);
+      bounds = bounds || d.lb || d.ub;
+      if (i + 1 < d.N) {
+        const int l = d.l[i];
+        S.l.push_back(l);
+        const ahlp_csc empty_l{l, d.A[i].n, S.zeros(d.A[i].n), nullptr, nullptr};
+        const ahlp_csc empty_r{l, d.A[i + 1].n, S.zeros(d.A[i + 1].n), nullptr, nullptr};
+        S.FL.push_back(d.FL ? d.FL[i] : empty_l);
+        S.FR.push_back(d.FR ? d.FR[i] : empty_r);
+        S.F0.push_back(S.shift_cols(d.F0 ? &d.F0[i] : nullptr, l, d.n0, (int)S.x0off[b], n0));
+        S.blink.push_back(d.blink ? d.blink[i] : nullptr);
+      } else if (b + 1 < B) {   // between LPs: no link rows
+        S.l.push_back(0);
+        S.FL.push_back(ahlp_csc{0, d.A[i].n, S.zeros(d.A[i].n), nullptr, nullptr});
+        S.FR.push_back(ahlp_csc{0, D[b + 1].A[0].n, S.zeros(D[b + 1].A[0].n), nullptr, nullptr});
+        S.F0.push_back(ahlp_csc{0, n0, S.zeros(n0), nullptr, nullptr});
+        S.blink.push_back(nullptr);
+      }
+    }
+    for (int k = 0; k < d.n0; ++k) S.c0.push_back(d.c0 ? d.c0[k] : 0.0);
+    for (int k = 0; k < d.mg; ++k) S.bg.push_back(d.bg ? d.bg[k] : 0.0);
+    bounds0 = bounds0 || d.lb0 || d.ub0;
+  }
+  if (bounds0)
+    for (int b = 0; b < B; ++b)
+      for (int k = 0; k < D[b].n0; ++k) {
+        S.lb0.push_back(D[b].lb0 ? D[b].lb0[k] : 0.0);
+        S.ub0.push_back(D[b].ub0 ? D[b].ub0[k] : INFINITY);
+      }
+  // Fg0: block diagonal over the LPs
+  {
+    std::vector<int32_t> cp(n0 + 1, 0), ri;
+    std::vector<double> v;
+    for (int b = 0; b < B; ++b) {
+      const ahlp_desc &d = D[b];
+      for (int j = 0; j < d.n0; ++j) {
+        const int col = (int)S.x0off[b] + j;
+        if (d.Fg0 && d.Fg0->colptr && d.Fg0->n == d.n0 && d.Fg0->m == d.mg)
+          for (int q = d.Fg0->colptr[j]; q < d.Fg0->colptr[j + 1]; ++q) {
+            ri.push_back(d.Fg0->rowidx[q] + (int)S.goff[b]);
+            v.push_back(d.Fg0->val[q]);
+          }
+        else if (d.Fg0 && (d.Fg0->n != d.n0 || d.Fg0->m != d.mg))
+          fail(AHLP_ERR_DIM_MISMATCH, "batch item " + std::to_string(b) + " Fg0: wrong shape");
+        cp[col + 1] = (int32_t)ri.size();
+      }
+    }
+    for (int j = 0; j < n0; ++j) cp[j + 1] = std::max(cp[j + 1], cp[j]);
+    S.ints.push_back(std::move(cp));
+    const int32_t *cpp = S.ints.back().data();
+    S.ints.push_back(std::move(ri));
+    const int32_t *rip = S.ints.back().data();
+    S.dbls.push_back(std::move(v));
+    S.Fg0 = ahlp_csc{mg, n0, cpp, rip, S.dbls.back().data()};
+  }
+  ahlp_desc &o = S.d;
+  o.N = N;
+  o.n0 = n0;
+  o.mg = mg;
+  o.c0 = S.c0.data();
+  o.A = S.A.data();
+  o.W = S.W.data();
+  o.b = S.b.data();
+  o.c = S.c.data();
+  o.l = S.l.data();
+  o.FL = S.FL.data();
+  o.FR = S.FR.data();
+  o.F0 = S.F0.data();
+  o.blink = S.blink.data();
+  o.Fg = S.Fg.data();
+  o.Fg0 = &S.Fg0;
+  o.bg = S.bg.data();
+  o.lb = bounds ? S.lb.data() : nullptr;
+  o.ub = bounds ? S.ub.data() : nullptr;
+  o.lb0 = bounds0 ? S.lb0.data() : nullptr;
+  o.ub0 = bounds0 ? S.ub0.data() : nullptr;
+}
+
+}  // namespace
+
 int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_options *opt,
                         ahlp_problem **out) {
   if (!out) return AHLP_ERR_INVALID_ARG;
@@ -349,11 +514,27 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     g_create_err = "descs is NULL";
     return AHLP_ERR_INVALID_ARG;
   }
-  if (batch != 1) {
-    g_create_err = "batch != 1 is not supported in this build";
-    return AHLP_ERR_UNSUPPORTED;
+  if (batch < 1) {
+    g_create_err = "batch must be >= 1";
+    return AHLP_ERR_INVALID_ARG;
+  }
+  BatchDesc composed;
+  if (batch > 1) {
+    try {
+      compose_batch(descs, batch, composed);
+    } catch (const Fail &f) {
+      g_create_err = f.msg;
+      return f.code;
+    }
+    descs = &composed.d;
   }
   ahlp_problem *p = new ahlp_problem();
+  p->batch = batch;
+  if (batch > 1) {
+    p->lp_blk0 = composed.blk0;
+    p->lp_x0off = composed.x0off;
+    p->lp_goff = composed.goff;
+  }
   ahlp_default_options(&p->opt);
   if (opt) {
     int s = check_options(*opt, g_create_err);
@@ -486,15 +667,53 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     cgl.insert(cgl.end(), c0.begin(), c0.end());
     for (double v : bgl) p->bnorm_inf = std::max(p->bnorm_inf, std::fabs(v));
     for (double v : cgl) p->cnorm_inf = std::max(p->cnorm_inf, std::fabs(v));
+    for (int b = 0; b < p->batch && p->batch > 1; ++b) {
+      ahlp_problem::LpRange r{};
+      const long long blo = p->lp_blk0[b], bhi = b + 1 < p->batch ? p->lp_blk0[b + 1] : N;
+      const long long x0hi = b + 1 < p->batch ? p->lp_x0off[b + 1] : n0;
+      const long long ghi = b + 1 < p->batch ? p->lp_goff[b + 1] : mg;
+      r.xb0 = p->xoff[blo];
+      r.xb1 = p->xoff[bhi];
+      r.x00 = p->xoff[N] + p->lp_x0off[b];
+      r.x01 = p->xoff[N] + x0hi;
+      r.yb0 = p->yoff[blo];
+      r.yb1 = bhi < N ? p->yoff[bhi] : p->msum;
+      r.yl0 = p->msum + p->link_off[blo];
+      r.yl1 = p->msum + p->link_off[bhi - 1];
+      r.yg0 = p->msum + p->nl + p->lp_goff[b];
+      r.yg1 = p->msum + p->nl + ghi;
+      r.bnorm = r.cnorm = 0.0;
+      for (long long k : {0, 1, 2})
+        for (long long q = (k == 0 ? r.yb0 : k == 1 ? r.yl0 : r.yg0);
+             q < (k == 0 ? r.yb1 : k == 1 ? r.yl1 : r.yg1); ++q)
+          r.bnorm = std::max(r.bnorm, std::fabs(bgl[q]));
+      for (long long q = r.xb0; q < r.xb1; ++q) r.cnorm = std::max(r.cnorm, std::fabs(cgl[q]));
+      for (long long q = r.x00; q < r.x01; ++q) r.cnorm = std::max(r.cnorm, std::fabs(cgl[q]));
+      p->lp_rng.push_back(r);
+    }
     std::vector<unsigned char> isx0(p->n, 0);
     for (long long k = p->xoff[N]; k < p->n; ++k) isx0[k] = 1;
     // ---- per-block layout ------------------------------------------------------
     p->h_blk.resize(N);
     p->h_sblk.resize(N);
     long long base = 0, voff = 0, d0 = 0, cd = 0, ioff = 0;
+    // each block's slice of the linking variables and global rows: all of
+    // them for one LP, its own LP's ones in a batch (W_i, Fg_i are zero elsewhere)
+    std::vector<int> bx0lo(N, 0), bx0n(N, n0), bglo(N, 0), bgn(N, mg);
+    for (int b = 0; b < p->batch && p->batch > 1; ++b) {
+      const long long blo = p->lp_blk0[b], bhi = b + 1 < p->batch ? p->lp_blk0[b + 1] : N;
+      const long long x0hi = b + 1 < p->batch ? p->lp_x0off[b + 1] : n0;
+      const long long ghi = b + 1 < p->batch ? p->lp_goff[b + 1] : mg;
+      for (long long i = blo; i < bhi; ++i) {
+        bx0lo[i] = (int)p->lp_x0off[b];
+        bx0n[i] = (int)(x0hi - p->lp_x0off[b]);
+        bglo[i] = (int)p->lp_goff[b];
+        bgn[i] = (int)(ghi - p->lp_goff[b]);
+      }
+    }
     for (int i = 0; i < N; ++i) {
       const int lp = i > 0 ? l[i - 1] : 0, ln = i + 1 < N ? l[i] : 0;
-      const int k = n0 + lp + ln + mg;
+      const int k = bx0n[i] + lp + ln + bgn[i];
       const int m = A[i].m, a = m + k;
       p->ki.push_back(k);
       p->lprev.push_back(lp);
@@ -526,6 +745,10 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
       sb.lnext = ln;
       sb.link_prev_off = i > 0 ? (int)p->link_off[i - 1] : 0;
       sb.link_next_off = i + 1 < N ? (int)p->link_off[i] : 0;
+      sb.x0lo = bx0lo[i];
+      sb.x0n = bx0n[i];
+      sb.glo = bglo[i];
+      sb.gn = bgn[i];
       p->h_sblk[i] = sb;
     }
     p->aug_elems = base;
@@ -540,20 +763,24 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     // ---- formation patterns --------------------------------------------------
     Pattern P;
     for (int i = 0; i < N; ++i) {
-      std::vector<URow> urows(p->ki[i] - n0);
-      auto rows_of = [&](const Csc &F, int off) {
+      std::vector<URow> urows(p->ki[i] - bx0n[i]);
+      auto rows_of = [&](const Csc &F, int off, int shift, int nrows) {
         for (int j = 0; j < F.n; ++j)
           for (int q = F.cp[j]; q < F.cp[j + 1]; ++q) {
-            urows[off + F.ri[q]].j.push_back(j);
-            urows[off + F.ri[q]].u.push_back(F.v[q]);
+            const int r = F.ri[q] - shift;
+            if (r < 0 || r >= nrows)
+              fail(AHLP_ERR_INVALID_ARG, "block " + std::to_string(i) + ": a global row outside its LP");
+            urows[off + r].j.push_back(j);
+            urows[off + r].u.push_back(F.v[q]);
           }
       };
-      if (i > 0) rows_of(FR[i - 1], 0);
-      if (i + 1 < N) rows_of(FL[i], p->lprev[i]);
-      rows_of(Fg[i], p->lprev[i] + p->lnext[i]);
-      const long long t0 = (long long)P.tiles.size();
-      build_block_pattern(i, A[i], W[i], urows, n0, A[i].m, p->ki[i], p->xoff[i], P);
-      (void)t0;
+      if (i > 0) rows_of(FR[i - 1], 0, 0, p->lprev[i]);
+      if (i + 1 < N) rows_of(FL[i], p->lprev[i], 0, p->lnext[i]);
+      rows_of(Fg[i], p->lprev[i] + p->lnext[i], bglo[i], bgn[i]);
+      for (int t = 0; t < n0; ++t)
+        if ((t < bx0lo[i] || t >= bx0lo[i] + bx0n[i]) && W[i].cp[t + 1] > W[i].cp[t])
+          fail(AHLP_ERR_INVALID_ARG, "block " + std::to_string(i) + ": a linking variable outside its LP");
+      build_block_pattern(i, A[i], W[i], urows, bx0lo[i], bx0n[i], A[i].m, p->ki[i], p->xoff[i], P);
     }
     P.tile_ent.push_back((long long)P.ent_pos.size());
     P.ent_cb.push_back((long long)P.con_idx.size());
@@ -564,12 +791,13 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     std::vector<int> kmap;
     for (int i = 0; i < N; ++i) {
       p->kmap_off.push_back((long long)kmap.size());
+      const int xn = bx0n[i], lpv = p->lprev[i], lnx = p->lnext[i];
       for (int t = 0; t < p->ki[i]; ++t) {
         int s;
-        if (t < n0) s = p->nl + t;
-        else if (t < n0 + p->lprev[i]) s = (int)p->link_off[i - 1] + (t - n0);
-        else if (t < n0 + p->lprev[i] + p->lnext[i]) s = (int)p->link_off[i] + (t - n0 - p->lprev[i]);
-        else s = p->nl + n0 + (t - n0 - p->lprev[i] - p->lnext[i]);
+        if (t < xn) s = p->nl + bx0lo[i] + t;
+        else if (t < xn + lpv) s = (int)p->link_off[i - 1] + (t - xn);
+        else if (t < xn + lpv + lnx) s = (int)p->link_off[i] + (t - xn - lpv);
+        else s = p->nl + n0 + bglo[i] + (t - xn - lpv - lnx);
         kmap.push_back(s);
       }
     }
@@ -700,6 +928,42 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->chain_tmp = dalloc<double>(p, p->nl);
     p->td_off_d = dupload(p, p->td_off);
     p->h_off_d = dupload(p, p->h_off);
+    {
+      // chain segments: maximal runs of pairs that all have link rows
+      std::vector<int> seg;
+      for (int j = 0; j + 1 < N;) {
+        if (l[j] == 0) {
+          ++j;
+          continue;
+        }
+        int e = j;
+        while (e + 1 < N && l[e] > 0) ++e;
+        seg.push_back(j);
+        seg.push_back(e);
+        j = e;
+      }
+      p->nchain_seg = (int)seg.size() / 2;
+      if (!seg.empty()) p->chain_seg = dupload(p, seg);
+      // link-row range of each border column of Z = L_T^-1 E': all links for one
+      // LP; in a batch, the links of the LP that owns the linking variable or
+      // global row
+      std::vector<int> zl(std::max(p->B, 1), 0), zh(std::max(p->B, 1), p->nl);
+      if (p->batch > 1) {
+        const int Bt = p->batch;
+        for (int b = 0; b < Bt; ++b) {
+          const long long blo = p->lp_blk0[b];
+          const long long bhi = b + 1 < Bt ? p->lp_blk0[b + 1] : N;
+          const int lo = (int)p->link_off[blo];
+          const int hi = (int)(bhi - 1 < N - 1 ? p->link_off[bhi - 1] : p->nl);
+          const long long x0hi = b + 1 < Bt ? p->lp_x0off[b + 1] : n0;
+          const long long ghi = b + 1 < Bt ? p->lp_goff[b + 1] : mg;
+          for (long long k = p->lp_x0off[b]; k < x0hi; ++k) zl[k] = lo, zh[k] = hi;
+          for (long long k = p->lp_goff[b]; k < ghi; ++k) zl[n0 + k] = lo, zh[n0 + k] = hi;
+        }
+      }
+      p->zlo = dupload(p, zl);
+      p->zhi = dupload(p, zh);
+    }
     p->l_d = dupload(p, l);
     p->link_off_d = dupload(p, p->link_off);
     p->kmap = dupload(p, kmap);
@@ -1031,6 +1295,10 @@ int kkt_factor(ahlp_problem *p, const double *x, const double *z, double delta, 
   try {
     const double *dx = stage_in(p, x, p->n, p->stg[0]);
     const double *dz = stage_in(p, z, p->n, p->stg[1]);
+    // rho regularises every primal variable: D^-1 + rho on the blocks (through
+    // d = x / (z + rho x)) and on the linking variables (in the Schur border)
+    const double r = rho < 0 ? p->opt.rho : rho;
+    p->fac_rho_x = r > 0 ? r : 0.0;
     if (p->n > 0) {
       ck(cudaMemcpyAsync(p->x, dx, p->n * 8, cudaMemcpyDeviceToDevice, p->stream), "copy x");
       ck(cudaMemcpyAsync(p->z, dz, p->n * 8, cudaMemcpyDeviceToDevice, p->stream), "copy z");

@@ -49,12 +49,16 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     // being a good preconditioner) moves the blocks one precision up, else makes
     // the threshold 100x coarser (up to kMaxPivotTol).  A NaN in the factor or
     // in the direction does the same and, once those are exhausted, raises
-    // the regularisation 100x (up to kMaxDelta): the Krylov refinement always
-    // solves the unregularised Newton system, so this only weakens the
-    // preconditioner.  A NaN pivot that passed the threshold is one that lost
+    // the regularisation 100x (up to kMaxDelta) and then regularises D itself,
+    // d = x / (z + rho_x x) with rho_x from kMinRhoX up to kMaxRhoX, which bounds
+    // the factor's conditioning when complementarity products collapse.  The
+    // Krylov refinement always solves the unregularised Newton system, so all
+    // this only weakens the preconditioner.  A NaN pivot that passed the threshold is one that lost
     // nearly all its digits to cancellation; its rounding noise is amplified
     // through the later clamped columns.
     constexpr double kEscalate = 1e-6, kMaxPivotTol = 1e-8, kMaxDelta = 1e-4;
+    constexpr double kMinRhoX = 1e-10, kMaxRhoX = 1e-6;
+    p->fac_rho_x = rho > 0 ? rho : 0.0;
     constexpr double kCorrectorBelow = 0.9;   // correctors only below this step length
     double ptol = p->opt.pivot_tol;
     double delta = p->opt.delta;
@@ -62,9 +66,33 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     int cur_iter = 0;
     p->fac_prec = p->opt.precision == AHLP_PREC_MIXED ? kPrecFP32 : kPrecFP64;
     R.fp64_switch_iter = p->fac_prec == kPrecFP32 ? -1 : 0;
+    // batch: LPs that already meet the tolerances stop moving (see below)
+    const int nlp = p->batch > 1 ? (int)p->lp_rng.size() : 0;
+    std::vector<char> frozen(nlp, 0);
+    // set the x ranges (or y ranges) of the frozen LPs of vec to val
+    auto fill_frozen = [&](double *vec, double val, bool on_y) {
+      for (int b = 0; b < nlp; ++b) {
+        if (!frozen[b]) continue;
+        const auto &r = p->lp_rng[b];
+        if (on_y) {
+          ck(launch_fill(vec + r.yb0, val, r.yb1 - r.yb0, s), "fill");
+          ck(launch_fill(vec + r.yl0, val, r.yl1 - r.yl0, s), "fill");
+          ck(launch_fill(vec + r.yg0, val, r.yg1 - r.yg0, s), "fill");
+        } else {
+          ck(launch_fill(vec + r.xb0, val, r.xb1 - r.xb0, s), "fill");
+          ck(launch_fill(vec + r.x00, val, r.x01 - r.x00, s), "fill");
+        }
+      }
+    };
     auto factor_at = [&](const double *xx, const double *zz) {
       ck(cudaMemcpyAsync(p->x, xx, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
       ck(cudaMemcpyAsync(p->z, zz, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+      // a frozen LP of a batch sits at its converged, extremely ill-conditioned
+      // point; its direction is zero (its right-hand sides are zeroed), so its
+      // blocks are factored at x = z = 1 instead -- the LPs share no rows or
+      // columns, so nothing else changes
+      fill_frozen(p->x, 1.0, false);
+      fill_frozen(p->z, 1.0, false);
       const int before = p->fac_prec;
       int st = factor_impl(p, delta, rho, ptol);
       if (before == kPrecFP32 && p->fac_prec != kPrecFP32 && R.fp64_switch_iter < 0)
@@ -104,11 +132,97 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         ptol *= 100.0;
       } else if (allow_delta && delta > 0 && delta * 100.0 <= kMaxDelta * 1.0001) {
         delta *= 100.0;
+      } else if (allow_delta && p->fac_rho_x * 100.0 <= kMaxRhoX * 1.0001) {
+        // primal regularisation of the preconditioner: d = x / (z + rho_x x)
+        p->fac_rho_x = p->fac_rho_x > 0.0 ? p->fac_rho_x * 100.0 : kMinRhoX;
       } else {
         return false;
       }
       ++R.escalations;
       return true;
+    };
+    // Batch (a direct sum of independent LPs).  Each LP runs its own IPM on
+    // the shared factorisations: its own mu, sigma and primal / dual step
+    // lengths, computed over its index ranges, and it stops moving once it
+    // meets the tolerances on its own (its D then stays fixed and well
+    // conditioned while the others converge).  The reported measures are the
+    // worst LP's.  Reductions over the LPs' ranges go through scalar slots
+    // 20..51, sixteen LPs per host read.
+    std::vector<double> lp_mu(nlp, 0.0), lp_ap(nlp, 0.0), lp_ad(nlp, 0.0);
+    auto lp_nx = [&](const ahlp_problem::LpRange &r) {
+      return (double)((r.xb1 - r.xb0) + (r.x01 - r.x00));
+    };
+    // out[b] = op over LP b's x ranges (min for step lengths, sum for dots)
+    auto lp_xreduce = [&](int op, const double *a, const double *bv, std::vector<double> &out) {
+      for (int c0 = 0; c0 < nlp; c0 += 16) {
+        const int cn = std::min(16, nlp - c0);
+        for (int k = 0; k < cn; ++k) {
+          const auto &r = p->lp_rng[c0 + k];
+          ck(launch_reduce(p, op, a + r.xb0, bv ? bv + r.xb0 : nullptr, r.xb1 - r.xb0,
+                           p->scal + 20 + 2 * k),
+             "reduce");
+          ck(launch_reduce(p, op, a + r.x00, bv ? bv + r.x00 : nullptr, r.x01 - r.x00,
+                           p->scal + 21 + 2 * k),
+             "reduce");
+        }
+        read_scalars(p, 20 + 2 * cn);
+        for (int k = 0; k < cn; ++k) {
+          const double u = p->h_scal[20 + 2 * k], w = p->h_scal[21 + 2 * k];
+          out[c0 + k] = op == RED_MINSTEP ? std::min(u, w) : u + w;
+        }
+      }
+    };
+    // per-LP measures; freezes the LPs that meet the tolerances; true when all do
+    auto batch_measures = [&]() {
+      double wp = 0.0, wd = 0.0, wg = 0.0;
+      for (int b = 0; b < nlp; ++b) {
+        const auto &r = p->lp_rng[b];
+        double *sc = p->scal + 20;
+        ck(launch_reduce(p, RED_MAXABS, v[V_RP] + r.yb0, nullptr, r.yb1 - r.yb0, sc + 0), "reduce");
+        ck(launch_reduce(p, RED_MAXABS, v[V_RP] + r.yl0, nullptr, r.yl1 - r.yl0, sc + 1), "reduce");
+        ck(launch_reduce(p, RED_MAXABS, v[V_RP] + r.yg0, nullptr, r.yg1 - r.yg0, sc + 2), "reduce");
+        ck(launch_reduce(p, RED_MAXABS, v[V_RD] + r.xb0, nullptr, r.xb1 - r.xb0, sc + 3), "reduce");
+        ck(launch_reduce(p, RED_MAXABS, v[V_RD] + r.x00, nullptr, r.x01 - r.x00, sc + 4), "reduce");
+        ck(launch_reduce(p, RED_DOT, p->c + r.xb0, X + r.xb0, r.xb1 - r.xb0, sc + 5), "reduce");
+        ck(launch_reduce(p, RED_DOT, p->c + r.x00, X + r.x00, r.x01 - r.x00, sc + 6), "reduce");
+        ck(launch_reduce(p, RED_DOT, p->b + r.yb0, Y + r.yb0, r.yb1 - r.yb0, sc + 7), "reduce");
+        ck(launch_reduce(p, RED_DOT, p->b + r.yl0, Y + r.yl0, r.yl1 - r.yl0, sc + 8), "reduce");
+        ck(launch_reduce(p, RED_DOT, p->b + r.yg0, Y + r.yg0, r.yg1 - r.yg0, sc + 9), "reduce");
+        ck(launch_reduce(p, RED_DOT, X + r.xb0, Z + r.xb0, r.xb1 - r.xb0, sc + 10), "reduce");
+        ck(launch_reduce(p, RED_DOT, X + r.x00, Z + r.x00, r.x01 - r.x00, sc + 11), "reduce");
+        read_scalars(p, 32);
+        const double *h = p->h_scal + 20;
+        const double pinf = std::max({h[0], h[1], h[2]}) / (1.0 + r.bnorm);
+        const double dinf = std::max(h[3], h[4]) / (1.0 + r.cnorm);
+        const double pobj = h[5] + h[6], dobj = h[7] + h[8] + h[9];
+        const double gap = std::fabs(pobj - dobj) / (1.0 + std::fabs(pobj));
+        lp_mu[b] = (h[10] + h[11]) / std::max(lp_nx(r), 1.0);
+        if (pinf <= p->opt.tol && dinf <= p->opt.tol && gap <= p->opt.tol) frozen[b] = 1;
+        wp = std::max(wp, pinf);
+        wd = std::max(wd, dinf);
+        wg = std::max(wg, gap);
+      }
+      R.pinf = wp;
+      R.dinf = wd;
+      R.rel_gap = wg;
+      for (int b = 0; b < nlp; ++b)
+        if (!frozen[b]) return false;
+      return true;
+    };
+    // LP-wise axpby over its x ranges (y ranges when on_y): y += a_b x
+    auto lp_axpy = [&](double *yv, const double *xv, const std::vector<double> &a, bool on_y) {
+      for (int b = 0; b < nlp; ++b) {
+        const auto &r = p->lp_rng[b];
+        if (a[b] == 0.0) continue;
+        if (on_y) {
+          ck(launch_axpby(yv + r.yb0, xv + r.yb0, a[b], 1.0, r.yb1 - r.yb0, s), "update");
+          ck(launch_axpby(yv + r.yl0, xv + r.yl0, a[b], 1.0, r.yl1 - r.yl0, s), "update");
+          ck(launch_axpby(yv + r.yg0, xv + r.yg0, a[b], 1.0, r.yg1 - r.yg0, s), "update");
+        } else {
+          ck(launch_axpby(yv + r.xb0, xv + r.xb0, a[b], 1.0, r.xb1 - r.xb0, s), "update");
+          ck(launch_axpby(yv + r.x00, xv + r.x00, a[b], 1.0, r.x01 - r.x00, s), "update");
+        }
+      }
     };
     const bool warm = x0 && y0 && z0;
     if (warm) {
@@ -179,7 +293,14 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         p->err = "ipm_solve: NaN in the iterate";
         break;
       }
-      if (R.pinf <= p->opt.tol && R.dinf <= p->opt.tol && R.rel_gap <= p->opt.tol) {
+      if (nlp > 0) {
+        if (batch_measures()) {
+          status = AHLP_OK;
+          break;
+        }
+        fill_frozen(v[V_RD], 0.0, false);
+        fill_frozen(v[V_RP], 0.0, true);
+      } else if (R.pinf <= p->opt.tol && R.dinf <= p->opt.tol && R.rel_gap <= p->opt.tol) {
         status = AHLP_OK;
         break;
       }
@@ -202,21 +323,56 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         if (st != AHLP_OK) throw Fail{st, p->err};
         // predictor: r_c = -XZe
         ck(launch_mul(v[V_RC], X, Z, -1.0, n, s), "mul");
+        fill_frozen(v[V_RC], 0.0, false);
         st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DXA], v[V_DYA], v[V_DZA]);
         if (st == AHLP_ERR_NOT_SPD && escalate(true)) continue;
         if (st != AHLP_OK) throw Fail{st, p->err};
         if (last_rel > kEscalate && escalate(false)) continue;
-        ck(launch_reduce(p, RED_MINSTEP, X, v[V_DXA], n, p->scal + 0), "reduce");
-        ck(launch_reduce(p, RED_MINSTEP, Z, v[V_DZA], n, p->scal + 1), "reduce");
-        read_scalars(p, 2);
-        const double apa = std::min(1.0, p->h_scal[0]), ada = std::min(1.0, p->h_scal[1]);
-        ck(launch_step_dot(X, v[V_DXA], apa, Z, v[V_DZA], ada, n, p->red_part, p->scal + 0, s),
-           "reduce");
-        read_scalars(p, 1);
-        const double mu_aff = p->h_scal[0] / n;
-        sigma = std::pow(mu_aff / mu, 3.0);
-        // corrector: r_c = sigma mu e - XZe - dXa dZa e
-        ck(launch_ipm_rc(v[V_RC], X, Z, v[V_DXA], v[V_DZA], sigma * mu, n, s), "rc");
+        if (nlp > 0) {
+          // each LP's affine step, mu_aff and sigma, and its corrector rhs
+          lp_xreduce(RED_MINSTEP, X, v[V_DXA], lp_ap);
+          lp_xreduce(RED_MINSTEP, Z, v[V_DZA], lp_ad);
+          for (int c0 = 0; c0 < nlp; c0 += 16) {
+            const int cn = std::min(16, nlp - c0);
+            for (int k = 0; k < cn; ++k) {
+              const auto &r = p->lp_rng[c0 + k];
+              const double a1 = std::min(1.0, lp_ap[c0 + k]), a2 = std::min(1.0, lp_ad[c0 + k]);
+              ck(launch_step_dot(X + r.xb0, v[V_DXA] + r.xb0, a1, Z + r.xb0, v[V_DZA] + r.xb0, a2,
+                                 r.xb1 - r.xb0, p->red_part, p->scal + 20 + 2 * k, s),
+                 "reduce");
+              ck(launch_step_dot(X + r.x00, v[V_DXA] + r.x00, a1, Z + r.x00, v[V_DZA] + r.x00, a2,
+                                 r.x01 - r.x00, p->red_part, p->scal + 21 + 2 * k, s),
+                 "reduce");
+            }
+            read_scalars(p, 20 + 2 * cn);
+            for (int k = 0; k < cn; ++k) {
+              if (frozen[c0 + k]) continue;   // its r_c stays zero
+              const auto &r = p->lp_rng[c0 + k];
+              const double mua = (p->h_scal[20 + 2 * k] + p->h_scal[21 + 2 * k]) /
+                                 std::max(lp_nx(r), 1.0);
+              const double mub = lp_mu[c0 + k];
+              const double sig = mub > 0.0 ? std::pow(mua / mub, 3.0) : 0.0;
+              ck(launch_ipm_rc(v[V_RC] + r.xb0, X + r.xb0, Z + r.xb0, v[V_DXA] + r.xb0,
+                               v[V_DZA] + r.xb0, sig * mub, r.xb1 - r.xb0, s),
+                 "rc");
+              ck(launch_ipm_rc(v[V_RC] + r.x00, X + r.x00, Z + r.x00, v[V_DXA] + r.x00,
+                               v[V_DZA] + r.x00, sig * mub, r.x01 - r.x00, s),
+                 "rc");
+            }
+          }
+        } else {
+          ck(launch_reduce(p, RED_MINSTEP, X, v[V_DXA], n, p->scal + 0), "reduce");
+          ck(launch_reduce(p, RED_MINSTEP, Z, v[V_DZA], n, p->scal + 1), "reduce");
+          read_scalars(p, 2);
+          const double apa = std::min(1.0, p->h_scal[0]), ada = std::min(1.0, p->h_scal[1]);
+          ck(launch_step_dot(X, v[V_DXA], apa, Z, v[V_DZA], ada, n, p->red_part, p->scal + 0, s),
+             "reduce");
+          read_scalars(p, 1);
+          const double mu_aff = p->h_scal[0] / n;
+          sigma = std::pow(mu_aff / mu, 3.0);
+          // corrector: r_c = sigma mu e - XZe - dXa dZa e
+          ck(launch_ipm_rc(v[V_RC], X, Z, v[V_DXA], v[V_DZA], sigma * mu, n, s), "rc");
+        }
         st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DX], v[V_DY], v[V_DZ]);
         if (st == AHLP_ERR_NOT_SPD && escalate(true)) continue;
         if (st != AHLP_OK) throw Fail{st, p->err};
@@ -228,7 +384,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       // [0.1 sigma mu, 10 sigma mu]; a corrected direction is kept only while
       // it lengthens the step.  Tried only when the step is short, and at
       // most as many as the factorisation costs in solves.
-      if (p->opt.max_correctors > 0) {
+      if (p->opt.max_correctors > 0 && nlp == 0) {
         auto steps = [&](const double *dxv, const double *dzv, double &a_p, double &a_d) {
           ck(launch_reduce(p, RED_MINSTEP, X, dxv, n, p->scal + 0), "reduce");
           ck(launch_reduce(p, RED_MINSTEP, Z, dzv, n, p->scal + 1), "reduce");
@@ -261,6 +417,18 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
           a_d = b_d;
           ++R.correctors;
         }
+      }
+      if (nlp > 0) {
+        lp_xreduce(RED_MINSTEP, X, v[V_DX], lp_ap);
+        lp_xreduce(RED_MINSTEP, Z, v[V_DZ], lp_ad);
+        for (int b = 0; b < nlp; ++b) {
+          lp_ap[b] = frozen[b] ? 0.0 : std::min(1.0, eta * lp_ap[b]);
+          lp_ad[b] = frozen[b] ? 0.0 : std::min(1.0, eta * lp_ad[b]);
+        }
+        lp_axpy(X, v[V_DX], lp_ap, false);
+        lp_axpy(Y, v[V_DY], lp_ad, true);
+        lp_axpy(Z, v[V_DZ], lp_ad, false);
+        continue;
       }
       ck(launch_reduce(p, RED_MINSTEP, X, v[V_DX], n, p->scal + 0), "reduce");
       ck(launch_reduce(p, RED_MINSTEP, Z, v[V_DZ], n, p->scal + 1), "reduce");

@@ -83,9 +83,13 @@ __global__ void __launch_bounds__(kThreads) form_aug_kernel(FormArgs<T> A) {
   }
 }
 
-__global__ void dscale_kernel(const double *x, const double *z, double *d, long long n) {
+// d = x / z; on the block variables x / (z + rho_x x) with the factor's primal
+// regularisation, i.e. D^-1 + rho_x (caps d at 1 / rho_x).  The linking
+// variables get theirs in the Schur border (-D_0^-1 - rho).
+__global__ void dscale_kernel(const double *x, const double *z, double *d, long long n,
+                              double rho_x, const unsigned char *is_x0) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) d[i] = x[i] / z[i];
+  if (i < n) d[i] = (rho_x > 0.0 && !is_x0[i]) ? x[i] / (z[i] + rho_x * x[i]) : x[i] / z[i];
 }
 
 // --------------------------------------------------------------------------
@@ -1115,8 +1119,8 @@ cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkI
 // ---------------------------------------------------------------------------
 cudaError_t launch_dscale(ahlp_problem *p) {
   if (p->n <= 0) return cudaSuccess;
-  count_launch(), dscale_kernel<<<(unsigned)((p->n + 255) / 256), 256, 0, p->stream>>>(p->x, p->z, p->dscale,
-                                                                       p->n);
+  count_launch(), dscale_kernel<<<(unsigned)((p->n + 255) / 256), 256, 0, p->stream>>>(
+      p->x, p->z, p->dscale, p->n, p->fac_rho_x, p->is_x0);
   return cudaGetLastError();
 }
 

@@ -42,8 +42,15 @@ __device__ __forceinline__ double cget(const SArgs &A, const BlkInfo &bi, int m,
   return A.prec == kPrecFP32 ? (double)A.aug32[idx] : A.aug[idx];
 }
 
+// local Schur column of border index rb (linking variable rb < n0, else global
+// row rb - n0) in block s, or -1 when the block does not touch it
 __device__ __forceinline__ int border_local(const SchurBlk &s, int n0, int rb) {
-  return rb < n0 ? rb : n0 + s.lprev + s.lnext + (rb - n0);
+  if (rb < n0) {
+    const int t = rb - s.x0lo;
+    return (t >= 0 && t < s.x0n) ? t : -1;
+  }
+  const int g = rb - n0 - s.glo;
+  return (g >= 0 && g < s.gn) ? s.x0n + s.lprev + s.lnext + g : -1;
 }
 
 __global__ void assemble_T_kernel(SArgs A) {
@@ -54,15 +61,15 @@ __global__ void assemble_T_kernel(SArgs A) {
   const int r = idx % lj, s = idx / lj;
   const BlkInfo b0 = A.blk[j], b1 = A.blk[j + 1];
   const SchurBlk s0 = A.sb[j], s1 = A.sb[j + 1];
-  double v = cget(A,b0, s0.m, A.n0 + s0.lprev + r, A.n0 + s0.lprev + s)   // block j, next
-           + cget(A,b1, s1.m, A.n0 + r, A.n0 + s);                        // block j+1, prev
+  double v = cget(A,b0, s0.m, s0.x0n + s0.lprev + r, s0.x0n + s0.lprev + s)   // block j, next
+           + cget(A,b1, s1.m, s1.x0n + r, s1.x0n + s);                          // block j+1, prev
   if (r == s) {
     v += A.delta;
     // pivot reference: the link row's diagonal of the full normal matrix,
     // sum_i (U_i D_i U_i')_qq + delta, i.e. before the block eliminations
     // cancel most of it
-    A.Td_diag0[A.link_off[j] + r] = A.cdiag0[b0.cdoff + A.n0 + s0.lprev + r] +
-                                    A.cdiag0[b1.cdoff + A.n0 + r] + A.delta;
+    A.Td_diag0[A.link_off[j] + r] = A.cdiag0[b0.cdoff + s0.x0n + s0.lprev + r] +
+                                    A.cdiag0[b1.cdoff + s1.x0n + r] + A.delta;
   }
   A.Td[A.td_off[j] + (long long)s * lj + r] = v;
 }
@@ -76,7 +83,7 @@ __global__ void assemble_H_kernel(SArgs A) {
   const BlkInfo b1 = A.blk[j + 1];
   const SchurBlk s1 = A.sb[j + 1];
   A.Hd[A.h_off[j] + (long long)s * lr + r] =
-      cget(A,b1, s1.m, A.n0 + s1.lprev + r, A.n0 + s);
+      cget(A,b1, s1.m, s1.x0n + s1.lprev + r, s1.x0n + s);
 }
 
 __global__ void assemble_E_kernel(SArgs A) {
@@ -87,8 +94,9 @@ __global__ void assemble_E_kernel(SArgs A) {
   const int r = idx % lj, rb = idx / lj;
   const BlkInfo b0 = A.blk[j], b1 = A.blk[j + 1];
   const SchurBlk s0 = A.sb[j], s1 = A.sb[j + 1];
-  const double v = cget(A,b0, s0.m, border_local(s0, A.n0, rb), A.n0 + s0.lprev + r) +
-                   cget(A,b1, s1.m, border_local(s1, A.n0, rb), A.n0 + r);
+  const int t0 = border_local(s0, A.n0, rb), t1 = border_local(s1, A.n0, rb);
+  const double v = (t0 >= 0 ? cget(A,b0, s0.m, t0, s0.x0n + s0.lprev + r) : 0.0) +
+                   (t1 >= 0 ? cget(A,b1, s1.m, t1, s1.x0n + r) : 0.0);
   A.Et[(long long)rb * A.nl + A.link_off[j] + r] = v;
 }
 
@@ -99,7 +107,8 @@ __global__ void assemble_SB_kernel(SArgs A) {
   double v = 0.0;
   for (int i = 0; i < A.N; ++i) {   // fixed order over blocks
     const SchurBlk s = A.sb[i];
-    v += cget(A,A.blk[i], s.m, border_local(s, A.n0, rb), border_local(s, A.n0, sb));
+    const int tr = border_local(s, A.n0, rb), ts = border_local(s, A.n0, sb);
+    if (tr >= 0 && ts >= 0) v += cget(A,A.blk[i], s.m, tr, ts);
   }
   if (rb == sb) v += (rb < A.n0) ? (-1.0 / A.dscale[A.x0off + rb] - A.rho) : A.delta;
   A.SB[(long long)sb * A.B + rb] = v;
@@ -107,7 +116,8 @@ __global__ void assemble_SB_kernel(SArgs A) {
     double ref = A.delta;
     for (int i = 0; i < A.N; ++i) {
       const SchurBlk s = A.sb[i];
-      ref += A.cdiag0[A.blk[i].cdoff + border_local(s, A.n0, rb)];
+      const int t = border_local(s, A.n0, rb);
+      if (t >= 0) ref += A.cdiag0[A.blk[i].cdoff + t];
     }
     A.sb_ref[rb] = ref;
   }
@@ -137,6 +147,10 @@ struct CArgs {
   double *Linv, *Yf, *Yb;
   double *tmp;             // [nl] scratch of the chain solve
   const int *link_pair;    // [nl] pair of each link row
+  // the chain falls apart at pairs without link rows: segment s covers pairs
+  // [seg[2s], seg[2s+1]) and runs in CTA s (one per LP of a batch)
+  const int *seg;
+  int nseg;
 };
 
 __global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
@@ -144,10 +158,11 @@ __global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
   __shared__ double s_inv;
   __shared__ double Tinv[128];
   const int tid = threadIdx.x, bd = blockDim.x;
-  for (int j = 0; j < A.N - 1; ++j) {
+  const int jb = A.seg[2 * blockIdx.x], je = A.seg[2 * blockIdx.x + 1];
+  for (int j = jb; j < je; ++j) {
     const int lj = A.l[j];
     if (lj == 0) continue;
-    const int lp = (j > 0) ? A.l[j - 1] : 0;
+    const int lp = (j > jb) ? A.l[j - 1] : 0;
     double *Tg = A.Td + A.td_off[j];
     for (int i = tid; i < lj * lj; i += bd) T[i] = Tg[i];
     __syncthreads();
@@ -221,7 +236,7 @@ __global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
       }
     }
     // X_j = H_j L_j^-T, one thread per row of H_j
-    if (j < A.N - 2) {
+    if (j + 1 < je) {
       const int ln = A.l[j + 1];
       double *H = A.Hd + A.h_off[j];   // l_{j+1} x l_j, ld l_{j+1}
       for (int r = tid; r < ln; r += bd) {
@@ -244,7 +259,7 @@ __global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
         Y[r + (long long)c * lj] = acc;
       }
     }
-    if (j < A.N - 2 && A.l[j + 1] > 0) {
+    if (j + 1 < je && A.l[j + 1] > 0) {
       const int ln = A.l[j + 1];
       const double *X = A.Hd + A.h_off[j];       // l_{j+1} x l_j
       double *Y = A.Yb + A.h_off[j];             // l_j x l_{j+1}
@@ -259,16 +274,28 @@ __global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
   }
 }
 
-// SB' = SB - Z'Z, written negated into the lower part of the border buffer
+// SB' = SB - Z'Z, written negated into the lower part of the border buffer.
+// Column rb of Z can be nonzero only on the link rows [zlo[rb], zhi[rb]) (its
+// LP's links in a batch), so each dot product runs over the overlap, in four
+// independent partial sums.
 __global__ void border_prep_kernel(const double *SB, const double *Z, int B, int nl, double *bd,
-                                   int ld, double *bdiag0) {
+                                   int ld, double *bdiag0, const int *zlo, const int *zhi) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= B * B) return;
   const int rb = idx % B, sb = idx / B;
   if (rb < sb) return;
-  double acc = SB[(long long)sb * B + rb];
+  double a0 = SB[(long long)sb * B + rb], a1 = 0.0, a2 = 0.0, a3 = 0.0;
   const double *zr = Z + (long long)rb * nl, *zs = Z + (long long)sb * nl;
-  for (int q = 0; q < nl; ++q) acc -= zr[q] * zs[q];
+  const int q0 = max(zlo[rb], zlo[sb]), q1 = min(zhi[rb], zhi[sb]);
+  int q = q0;
+  for (; q + 4 <= q1; q += 4) {
+    a0 -= zr[q] * zs[q];
+    a1 -= zr[q + 1] * zs[q + 1];
+    a2 -= zr[q + 2] * zs[q + 2];
+    a3 -= zr[q + 3] * zs[q + 3];
+  }
+  for (; q < q1; ++q) a0 -= zr[q] * zs[q];
+  const double acc = (a0 + a1) + (a2 + a3);
   bd[(long long)sb * ld + rb] = -acc;
   if (rb == sb) bdiag0[rb] = -acc;
 }
@@ -331,14 +358,15 @@ __global__ void schur_rhs_kernel(RArgs A) {
     const SchurBlk s0 = A.sb[j], s1 = A.sb[j + 1];
     const int r = q - s0.link_next_off;
     v = A.rhat[A.msum + q];
-    v += A.vec[A.blk[j].voff + s0.m + A.n0 + s0.lprev + r];
-    v += A.vec[A.blk[j + 1].voff + s1.m + A.n0 + r];
+    v += A.vec[A.blk[j].voff + s0.m + s0.x0n + s0.lprev + r];
+    v += A.vec[A.blk[j + 1].voff + s1.m + s1.x0n + r];
   } else {
     const int rb = q - A.nl;
     v = (rb < A.n0) ? A.f[A.x0off + rb] : A.rhat[A.msum + A.nl + (rb - A.n0)];
     for (int i = 0; i < A.N; ++i) {
       const SchurBlk s = A.sb[i];
-      v += A.vec[A.blk[i].voff + s.m + border_local(s, A.n0, rb)];
+      const int t = border_local(s, A.n0, rb);
+      if (t >= 0) v += A.vec[A.blk[i].voff + s.m + t];
     }
   }
   A.svec[q] = v;
@@ -365,8 +393,10 @@ __global__ void __launch_bounds__(kChainSolveThreads) chain_solve_kernel(CArgs A
   __shared__ double ubuf[2][kChainMaxL];          // solution of the previous pair
   __shared__ int meta[kChainMaxStages][4];        // l_j, l_other, operator offset, pair
   const int tid = threadIdx.x, bd = blockDim.x;
-  const int npairs = A.N - 1;
-  for (int q = tid; q < A.nl; q += bd) {
+  const int jb = A.seg[2 * blockIdx.x], je = A.seg[2 * blockIdx.x + 1];
+  const int npairs = je - jb;   // steps of this segment
+  const long long q0 = A.link_off[jb], q1 = A.link_off[je - 1] + A.l[je - 1];
+  for (long long q = q0 + tid; q < q1; q += bd) {
     const int j = A.link_pair[q];
     const int lj = A.l[j], r = q - (int)A.link_off[j];
     const double *Li = A.Linv + A.td_off[j];
@@ -382,14 +412,14 @@ __global__ void __launch_bounds__(kChainSolveThreads) chain_solve_kernel(CArgs A
     const int ns = min(stages, npairs - s0);
     // global range [g0, g1) holding the operators of steps s0 .. s0+ns-1
     long long g0 = 0, g1 = 0;
-    if (dir == 0) {
-      const int a = max(s0, 1), e = s0 + ns - 1;
+    if (dir == 0) {   // operators of pairs jb+1 .. : at h_off[j-1]
+      const int a = jb + max(s0, 1), e = jb + s0 + ns - 1;
       if (e >= a) {
         g0 = A.h_off[a - 1];
         g1 = A.h_off[e - 1] + (long long)A.l[e] * A.l[e - 1];
       }
-    } else {
-      const int jlo = npairs - s0 - ns, jtop = min(npairs - 1 - s0, npairs - 2);
+    } else {          // operators of pairs .. je-2: at h_off[j]
+      const int jlo = je - s0 - ns, jtop = min(je - 1 - s0, je - 2);
       if (jtop >= jlo) {
         g0 = A.h_off[jlo];
         g1 = A.h_off[jtop] + (long long)A.l[jtop] * A.l[jtop + 1];
@@ -407,9 +437,9 @@ __global__ void __launch_bounds__(kChainSolveThreads) chain_solve_kernel(CArgs A
         if (i + k * bd < cnt) opbuf[i + k * bd] = v[k];
     }
     for (int t = tid; t < ns; t += bd) {
-      const int j = dir == 0 ? s0 + t : npairs - 1 - (s0 + t);
+      const int j = dir == 0 ? jb + s0 + t : je - 1 - (s0 + t);
       const int jo = dir == 0 ? j - 1 : j + 1;
-      const bool has = jo >= 0 && jo < npairs;
+      const bool has = jo >= jb && jo < je;
       meta[t][0] = A.l[j];
       meta[t][1] = has ? A.l[jo] : 0;
       meta[t][2] = has ? (int)((dir == 0 ? A.h_off[j - 1] : A.h_off[j]) - g0) : 0;
@@ -417,8 +447,8 @@ __global__ void __launch_bounds__(kChainSolveThreads) chain_solve_kernel(CArgs A
     }
     // the pre-multiplied rows of the batch's pairs (a contiguous range of tmp)
     {
-      const int jf = dir == 0 ? s0 : npairs - s0 - ns;   // first pair in memory order
-      const int jl = dir == 0 ? s0 + ns - 1 : npairs - 1 - s0;
+      const int jf = dir == 0 ? jb + s0 : je - s0 - ns;   // first pair in memory order
+      const int jl = dir == 0 ? jb + s0 + ns - 1 : je - 1 - s0;
       const long long t0 = A.link_off[jf], t1 = A.link_off[jl] + A.l[jl];
       for (long long i = tid; i < t1 - t0; i += bd) tbuf[i] = A.tmp[t0 + i];
       if (tid == 0) meta[kChainMaxStages - 1][3] = (int)t0;
@@ -542,7 +572,7 @@ SArgs sargs(ahlp_problem *p, double delta, double rho) {
 CArgs cargs(ahlp_problem *p) {
   return CArgs{p->N, p->B, p->nl, p->l_d, p->td_off_d, p->h_off_d, p->link_off_d,
                p->Td, p->Hd, p->Et, p->Td_diag0, p->fac_pivot_tol, p->status,
-               p->Linv, p->Yf, p->Yb, p->chain_tmp, p->link_pair_d};
+               p->Linv, p->Yf, p->Yb, p->chain_tmp, p->link_pair_d, p->chain_seg, p->nchain_seg};
 }
 
 }  // namespace
@@ -579,11 +609,13 @@ cudaError_t launch_schur_factor(ahlp_problem *p) {
   int lmax = 0;
   for (int j = 0; j + 1 < p->N; ++j) lmax = std::max(lmax, (int)(p->link_off[j + 1] - p->link_off[j]));
   if (p->N > 1 && lmax > 0) {
-    count_launch(), chain_factor_kernel<<<1, 512, (size_t)lmax * lmax * 8, s>>>(cargs(p));
+    if (p->nchain_seg > 0)
+      count_launch(), chain_factor_kernel<<<p->nchain_seg, 512, (size_t)lmax * lmax * 8, s>>>(
+          cargs(p));
   }
   if (p->B > 0) {
     count_launch(), border_prep_kernel<<<nb((long long)p->B * p->B, 256), 256, 0, s>>>(
-        p->SB, p->Et, p->B, p->nl, p->border, p->Bld, p->border_diag0);
+        p->SB, p->Et, p->B, p->nl, p->border, p->Bld, p->border_diag0, p->zlo, p->zhi);
     std::vector<BlkInfo> hx(1, p->h_bx);
     if (p->n0 > 0) {
       cudaError_t e = launch_pchol(p->border, p->bx_info, hx, p->border_diag0, p->fac_pivot_tol,
@@ -631,9 +663,9 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
                                (long long)kChainSmem /
                                    std::max(1LL, 8LL * ((long long)lmax * lmax + lmax))));
     const size_t csm = (size_t)stages * ((size_t)lmax * lmax + lmax) * sizeof(double);
-    if (p->nl > 0 && lmax > 0)
-      count_launch(), chain_solve_kernel<<<1, kChainSolveThreads, csm, s>>>(C, p->svec, 0, stages,
-                                                                             lmax);
+    if (p->nl > 0 && lmax > 0 && p->nchain_seg > 0)
+      count_launch(), chain_solve_kernel<<<p->nchain_seg, kChainSolveThreads, csm, s>>>(
+          C, p->svec, 0, stages, lmax);
     if (p->B > 0) {
       if (p->nl > 0) count_launch(), border_rhs_kernel<<<nb((long long)p->B * 32, 256), 256, 0, s>>>(p->Et, p->B, p->nl, p->svec);
       double *sb = p->svec + p->nl;
@@ -654,9 +686,9 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
       }
       if (p->nl > 0) count_launch(), link_back_kernel<<<nb(p->nl, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
     }
-    if (p->nl > 0 && lmax > 0)
-      count_launch(), chain_solve_kernel<<<1, kChainSolveThreads, csm, s>>>(C, p->svec, 1, stages,
-                                                                             lmax);
+    if (p->nl > 0 && lmax > 0 && p->nchain_seg > 0)
+      count_launch(), chain_solve_kernel<<<p->nchain_seg, kChainSolveThreads, csm, s>>>(
+          C, p->svec, 1, stages, lmax);
     int kmax = 0;
     for (int k : p->ki) kmax = std::max(kmax, k);
     if (kmax > 0)

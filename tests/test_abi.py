@@ -60,9 +60,10 @@ def _create_status(lp, batch=1, options=None):
     L = _lib()
     lib = L.load()
     keep = L._Keep()
-    descs = (L.Desc * batch)()
-    for k in range(batch):
-        descs[k] = L.make_desc(lp, keep)
+    lps = lp if isinstance(lp, list) else [lp] * max(batch, 1)
+    descs = (L.Desc * max(batch, 1))()
+    for k in range(max(batch, 1)):
+        descs[k] = L.make_desc(lps[k], keep)
     h = ctypes.c_void_p()
     st = lib.arrowhead_lp_create(descs, batch, ctypes.byref(options) if options else None,
                                  ctypes.byref(h))
@@ -96,10 +97,14 @@ def test_validation_row_index_out_of_range():
     assert st == -1 and "out of range" in msg
 
 
-def test_unsupported_batch_and_precision():
+def test_batch_validation_and_bad_precision():
     lp = _small_lp()
-    st, _ = _create_status(lp, batch=2)
-    assert st == -3
+    st, msg = _create_status(lp, batch=0)
+    assert st == -1 and "batch" in msg
+    bad = _small_lp()
+    bad.W[1] = sp.csc_matrix(np.ones((bad.A[1].shape[0], bad.n0 + 1)))
+    st, msg = _create_status([lp, bad], batch=2)   # composing the batch checks shapes
+    assert st == -2 and "batch" in msg
     L = _lib()
     st, msg = _create_status(lp, options=L.default_options(precision=7))
     assert st == -1 and "precision" in msg
@@ -110,4 +115,6 @@ def test_valid_problem_without_gpu_reports_cuda_error():
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
     st, msg = _create_status(_small_lp())
+    assert st == -8
+    st, msg = _create_status(_small_lp(), batch=3)   # a valid batch also gets that far
     assert st == -8
