@@ -261,6 +261,7 @@ def run_ours(args):
                       "ms_per_step": oms / args.steps, "iterations_per_solve": oit / args.steps,
                       "kkt_factor_ms": sum(r["ms_factor"] for r in ores) / max(oit, 1),
                       "kkt_solve_ms_per_iteration": sum(r["ms_solve"] for r in ores) / max(oit, 1),
+                      "refine_steps_per_iteration": sum(r["refine_steps"] for r in ores) / max(oit, 1),
                       "rel_gap": ores[-1]["rel_gap"], "clocks": oclocks}
         P.set_options(prob, P.default_options(precision=headline, **opts))
     prob.close()
@@ -313,6 +314,7 @@ def run_ours(args):
             "rel_gap": res[-1]["rel_gap"],
             "kkt_factor_ms": sum(r["ms_factor"] for r in res) / max(iters, 1),
             "kkt_solve_ms_per_iteration": sum(r["ms_solve"] for r in res) / max(iters, 1),
+            "refine_steps_per_iteration": sum(r["refine_steps"] for r in res) / max(iters, 1),
             "factors": {"fp32": nf32 / args.steps, "float_float": nff / args.steps,
                         "fp64": nf64 / args.steps},
             "block_factor_ms": {"fp32": t32 / nf32 if nf32 else None,

@@ -130,6 +130,11 @@ typedef struct {
                            and in float-float (two FP32 words, ~46 bits) beyond
                            it; a float-float factor that fails moves to FP64
                            (1e14)                                                */
+  double  ipm_refine_tol; /* target relative Newton residual of the directions
+                           inside ipm_solve (1e-6): an inexact-Newton forcing
+                           term, the residual is ~1e-6 of |r| >= mu sqrt(n).
+                           The larger of it and refine_tol applies; kkt_solve
+                           and kkt_adjoint_solve always use refine_tol        */
 } ahlp_options;
 
 typedef struct {

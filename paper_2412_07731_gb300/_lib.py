@@ -44,7 +44,8 @@ class Options(C.Structure):
                 ("eta", C.c_double), ("delta", C.c_double), ("rho", C.c_double),
                 ("refine_max", C.c_int32), ("refine_tol", C.c_double),
                 ("pivot_tol", C.c_double), ("verbose", C.c_int32),
-                ("max_correctors", C.c_int32), ("fp32_cond_max", C.c_double)]
+                ("max_correctors", C.c_int32), ("fp32_cond_max", C.c_double),
+                ("ipm_refine_tol", C.c_double)]
 
 
 class Result(C.Structure):

@@ -314,9 +314,14 @@ bool is_device_ptr(const void *ptr);
 const double *stage_in(ahlp_problem *p, const double *v, long long n, double *staging);
 int set_err(ahlp_problem *p, int code, const std::string &msg);
 void read_scalars(ahlp_problem *p, int k);
-int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol);
+// ff_nan_up: a NaN pivot of a float-float factor refactors in FP64 (else the
+// call returns AHLP_ERR_NOT_SPD and the caller picks the next safeguard)
+int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol,
+                bool ff_nan_up = true);
+// tol_override > 0 replaces refine_tol as the FGMRES target
 int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double *rc, double *dx,
-               double *dy, double *dz, bool adjoint, ahlp_solve_info *info);
+               double *dy, double *dz, bool adjoint, ahlp_solve_info *info,
+               double tol_override = 0.0);
 void ck(cudaError_t e, const char *what);   // throws on error
 
 struct Fail {

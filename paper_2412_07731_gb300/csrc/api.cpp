@@ -247,6 +247,7 @@ void ahlp_default_options(ahlp_options *o) {
   o->verbose = 0;
   o->max_correctors = 4;
   o->fp32_cond_max = 1e14;
+  o->ipm_refine_tol = 1e-6;
 }
 
 const char *ahlp_status_string(int s) {
@@ -301,7 +302,8 @@ static int check_options(const ahlp_options &o, std::string &err) {
   }
   if (o.max_iter < 0 || !(o.tol > 0) || !(o.eta > 0 && o.eta < 1) || o.delta < 0 || o.rho < 0 ||
       o.refine_max < 0 || !(o.refine_tol > 0) || !(o.pivot_tol >= 0) ||
-      !(o.fp32_cond_max >= 1) || o.max_correctors < 0 || o.max_correctors > 8) {
+      !(o.fp32_cond_max >= 1) || o.max_correctors < 0 || o.max_correctors > 8 ||
+      !(o.ipm_refine_tol >= 0 && o.ipm_refine_tol < 1)) {
     err = "invalid option value";
     return AHLP_ERR_INVALID_ARG;
   }
@@ -1064,7 +1066,7 @@ void read_scalars(ahlp_problem *p, int k) {
   ck(cudaStreamSynchronize(p->stream), "stream sync");
 }
 
-int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
+int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol, bool ff_nan_up) {
   // an FP32 pivot that lost six digits, a float-float one that lost eleven,
   // is rounding noise
   p->fac_pivot_tol = p->fac_prec == kPrecFP32 ? std::max(pivot_tol, kFp32PivotTol)
@@ -1105,8 +1107,11 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
        "D2H");
     ck(cudaStreamSynchronize(s), "sync");
     if (!(p->h_scal[2] <= p->opt.fp32_cond_max * p->h_scal[3])) {
+      if (p->opt.verbose)
+        printf("D spans %.2e > fp32_cond_max: block factors move to float-float\n",
+               p->h_scal[2] / p->h_scal[3]);
       p->fac_prec = kPrecFF;
-      return factor_impl(p, delta, rho, pivot_tol);
+      return factor_impl(p, delta, rho, pivot_tol, ff_nan_up);
     }
   }
   ck(launch_form(p, delta), "form");
@@ -1146,13 +1151,14 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
       snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in block %d row %d", st[2], st[3]);
     else
       snprintf(buf, sizeof buf, "kkt_factor: NaN pivot in link pair %d row %d", -1 - st[2], st[3]);
-    if (p->fac_prec != kPrecFP64) {   // range or accuracy exceeded: one precision up
+    if (p->fac_prec == kPrecFP32 || (p->fac_prec == kPrecFF && ff_nan_up)) {
+      // range or accuracy exceeded: one precision up
       const int up = p->fac_prec == kPrecFP32 ? kPrecFF : kPrecFP64;
       if (p->opt.verbose)
         printf("%s with %s block factors; refactoring in %s\n", buf,
                p->fac_prec == kPrecFP32 ? "FP32" : "float-float", up == kPrecFF ? "float-float" : "FP64");
       p->fac_prec = up;
-      return factor_impl(p, delta, rho, pivot_tol);
+      return factor_impl(p, delta, rho, pivot_tol, ff_nan_up);
     }
     return set_err(p, AHLP_ERR_NOT_SPD, buf);
   }
@@ -1162,7 +1168,7 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol) {
 
 // one solve + refinement, all arguments device pointers
 int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double *rc, double *dx,
-               double *dy, double *dz, bool adjoint, ahlp_solve_info *info) {
+               double *dy, double *dz, bool adjoint, ahlp_solve_info *info, double tol_override) {
   cudaStream_t s = p->stream;
   ck(cudaEventRecord(p->ev[4], s), "event");
   ck(cudaMemsetAsync(p->trsv_err, 0, sizeof(int), s), "memset");
@@ -1188,12 +1194,18 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
   auto [en, rn] = residual_norms();
   double rel = rn > 0 ? en / rn : en;
   int steps = 0;
-  const double tol = p->opt.refine_tol;
+  const double tol = tol_override > 0 ? tol_override : p->opt.refine_tol;
   const int kmax = std::min(p->opt.refine_max, kMaxKrylov);
-  if (rel > tol && kmax > 0 && en > 0 && std::isfinite(en)) {
-    // Right-preconditioned FGMRES on the unregularised Newton system: the
-    // (regularised) block factorisation is the preconditioner, so the result
-    // solves J d = r itself, not the regularised system.
+  // Right-preconditioned FGMRES on the unregularised Newton system: the
+  // (regularised) block factorisation is the preconditioner, so the result
+  // solves J d = r itself, not the regularised system.  The cycle's own
+  // residual estimate can run ahead of the true residual when the
+  // preconditioned vectors are badly scaled; the true residual is then
+  // recomputed and, while it is above the target, another cycle starts from
+  // it (restarted FGMRES, refine_max steps in all), as long as each cycle at
+  // least halves it.
+  for (double prev = rel; rel > tol && steps < kmax && en > 0 && std::isfinite(en);) {
+    const int kc = kmax - steps;
     if (p->gm_cap < kmax) {
       if (p->gm_V) cudaFree(p->gm_V);
       if (p->gm_Z) cudaFree(p->gm_Z);
@@ -1209,14 +1221,14 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
     ck(cudaMemcpyAsync(V + n, p->res[1], m * 8, cudaMemcpyDeviceToDevice, s), "copy");
     ck(cudaMemcpyAsync(V + n + m, p->res[2], n * 8, cudaMemcpyDeviceToDevice, s), "copy");
     ck(launch_axpby(V, V, 1.0 / en, 0.0, L, s), "scale");
-    std::vector<double> H((size_t)(kmax + 1) * kmax, 0.0), cs(kmax), sn(kmax), g(kmax + 1, 0.0);
+    std::vector<double> H((size_t)(kc + 1) * kc, 0.0), cs(kc), sn(kc), g(kc + 1, 0.0);
     g[0] = en;
     int j = 0;
-    for (; j < kmax;) {
+    for (; j < kc;) {
       double *Vj = V + (long long)j * L, *Zj = Z + (long long)j * L, *W = V + (long long)(j + 1) * L;
       ck(launch_solve(p, Vj, Vj + n, Vj + n + m, Zj, Zj + n, Zj + n + m, adjoint), "precond");
       ck(launch_jmul(p, Zj, Zj + n, Zj + n + m, W, W + n, W + n + m, adjoint), "jmul");
-      double *h = &H[(size_t)j * (kmax + 1)];
+      double *h = &H[(size_t)j * (kc + 1)];
       for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
         ck(launch_mdot(p, V, L, j + 1, W, L, p->gm_coef), "mdot");
         p->bytes_d2h += (j + 1) * 8;
@@ -1254,8 +1266,8 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
     std::vector<double> y(j, 0.0);
     for (int i = j - 1; i >= 0; --i) {
       double t = g[i];
-      for (int k = i + 1; k < j; ++k) t -= H[(size_t)k * (kmax + 1) + i] * y[k];
-      const double d = H[(size_t)i * (kmax + 1) + i];
+      for (int k = i + 1; k < j; ++k) t -= H[(size_t)k * (kc + 1) + i] * y[k];
+      const double d = H[(size_t)i * (kc + 1) + i];
       y[i] = d != 0.0 ? t / d : 0.0;
     }
     for (int i = 0; i < j; ++i) cbuf[i] = y[i];
@@ -1264,9 +1276,11 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
     ck(launch_maxpy(Z, L, j, p->gm_coef, dx, n, s), "maxpy");
     ck(launch_maxpy(Z + n, L, j, p->gm_coef, dy, m, s), "maxpy");
     ck(launch_maxpy(Z + n + m, L, j, p->gm_coef, dz, n, s), "maxpy");
-    steps = j;
+    steps += j;
     std::tie(en, rn) = residual_norms();
     rel = rn > 0 ? en / rn : en;
+    if (!(rel <= 0.5 * prev)) break;
+    prev = rel;
   }
   ck(cudaEventRecord(p->ev[5], s), "event");
   int timed_out = 0;

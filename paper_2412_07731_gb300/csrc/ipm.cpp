@@ -44,7 +44,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     //    produces a NaN), and to FP64 when float-float fails in turn;
     //  - the pivot clamping threshold starts at pivot_tol;
     //  - the regularisation starts at delta.
-    // A direction whose Newton residual stays above kEscalate after the Krylov
+    // A direction whose Newton residual stays above `stalled` after the Krylov
     // refinement (the degenerate end game, where the clamped factors stop
     // being a good preconditioner) moves the blocks one precision up, else makes
     // the threshold 100x coarser (up to kMaxPivotTol).  A NaN in the factor or
@@ -58,11 +58,22 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     // through the later clamped columns.
     constexpr double kEscalate = 1e-6, kMaxPivotTol = 1e-8, kMaxDelta = 1e-4;
     constexpr double kMinRhoX = 1e-10, kMaxRhoX = 1e-6;
+    // a float-float factor that breaks down (its FP32 exponent range is
+    // exceeded behind clamped pivots) first gets more regularisation, up to
+    // kFFMaxDelta, before the blocks move to FP64 at ~3x its cost
+    constexpr double kFFMaxDelta = 1e-6;
+    // inexact Newton: the IPM's directions are solved to a relative residual
+    // of ipm_refine_tol, not the refine_tol of kkt_solve
+    const double ipm_tol = std::max(p->opt.refine_tol, p->opt.ipm_refine_tol);
+    // a direction counts as stalled above this (well clear of the target, so
+    // that the Krylov estimate and the recomputed residual cannot straddle it)
+    const double stalled = std::max(kEscalate, 10.0 * ipm_tol);
     p->fac_rho_x = rho > 0 ? rho : 0.0;
     constexpr double kCorrectorBelow = 0.9;   // correctors only below this step length
     double ptol = p->opt.pivot_tol;
     double delta = p->opt.delta;
     double last_rel = 0.0;
+    int last_steps = 0;
     int cur_iter = 0;
     p->fac_prec = p->opt.precision == AHLP_PREC_MIXED ? kPrecFP32 : kPrecFP64;
     R.fp64_switch_iter = p->fac_prec == kPrecFP32 ? -1 : 0;
@@ -94,7 +105,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       fill_frozen(p->x, 1.0, false);
       fill_frozen(p->z, 1.0, false);
       const int before = p->fac_prec;
-      int st = factor_impl(p, delta, rho, ptol);
+      int st = factor_impl(p, delta, rho, ptol, false);
       if (before == kPrecFP32 && p->fac_prec != kPrecFP32 && R.fp64_switch_iter < 0)
         R.fp64_switch_iter = cur_iter;
       R.ms_factor += p->stage_ms[0] + p->stage_ms[1] + p->stage_ms[2];
@@ -116,16 +127,24 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     auto solve = [&](const double *rd, const double *rp, const double *rc, double *dx, double *dy,
                      double *dz) {
       ahlp_solve_info info{};
-      int st = solve_impl(p, rd, rp, rc, dx, dy, dz, false, &info);
+      int st = solve_impl(p, rd, rp, rc, dx, dy, dz, false, &info, ipm_tol);
       R.ms_solve += p->stage_ms[3];
       R.refine_steps += info.refine_steps;
       R.kkt_residual = std::max(R.kkt_residual, info.rel_residual);
       last_rel = info.rel_residual;
+      last_steps = info.refine_steps;
       return st;
     };
+    static const char *kPrecName[] = {"FP64", "FP32", "float-float"};
     // next safeguard; false when none is left (allow_delta: NaN recovery only)
-    auto escalate = [&](bool allow_delta) {
-      if (p->fac_prec != kPrecFP64) {   // FP32 -> float-float -> FP64
+    auto escalate = [&](bool allow_delta, const char *why) {
+      if (p->opt.verbose)
+        printf("       safeguard after %s (%s factor, residual %.2e)\n", why,
+               kPrecName[p->fac_prec], last_rel);
+      if (allow_delta && p->fac_prec == kPrecFF && delta > 0 &&
+          delta * 100.0 <= kFFMaxDelta * 1.0001) {
+        delta *= 100.0;
+      } else if (p->fac_prec != kPrecFP64) {   // FP32 -> float-float -> FP64
         if (p->fac_prec == kPrecFP32 && R.fp64_switch_iter < 0) R.fp64_switch_iter = cur_iter;
         p->fac_prec = p->fac_prec == kPrecFP32 ? kPrecFF : kPrecFP64;
       } else if (ptol * 100.0 <= kMaxPivotTol * 1.0001) {
@@ -319,15 +338,17 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       double sigma = 0.0;
       for (;;) {
         int st = factor_at(X, Z);
-        if (st == AHLP_ERR_NOT_SPD && escalate(true)) continue;
+        if (st == AHLP_ERR_NOT_SPD && escalate(true, "a NaN pivot")) continue;
         if (st != AHLP_OK) throw Fail{st, p->err};
         // predictor: r_c = -XZe
         ck(launch_mul(v[V_RC], X, Z, -1.0, n, s), "mul");
         fill_frozen(v[V_RC], 0.0, false);
         st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DXA], v[V_DYA], v[V_DZA]);
-        if (st == AHLP_ERR_NOT_SPD && escalate(true)) continue;
+        if (st == AHLP_ERR_NOT_SPD && escalate(true, "a NaN predictor")) continue;
         if (st != AHLP_OK) throw Fail{st, p->err};
-        if (last_rel > kEscalate && escalate(false)) continue;
+        if (last_rel > stalled && escalate(false, "a stalled predictor")) continue;
+        const int pred_steps = last_steps;
+        const double pred_rel = last_rel;
         if (nlp > 0) {
           // each LP's affine step, mu_aff and sigma, and its corrector rhs
           lp_xreduce(RED_MINSTEP, X, v[V_DXA], lp_ap);
@@ -374,9 +395,13 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
           ck(launch_ipm_rc(v[V_RC], X, Z, v[V_DXA], v[V_DZA], sigma * mu, n, s), "rc");
         }
         st = solve(v[V_RD], v[V_RP], v[V_RC], v[V_DX], v[V_DY], v[V_DZ]);
-        if (st == AHLP_ERR_NOT_SPD && escalate(true)) continue;
+        if (st == AHLP_ERR_NOT_SPD && escalate(true, "a NaN corrector")) continue;
         if (st != AHLP_OK) throw Fail{st, p->err};
-        if (last_rel > kEscalate && escalate(false)) continue;
+        if (last_rel > stalled && escalate(false, "a stalled corrector")) continue;
+        if (p->opt.verbose)
+          printf("       %s factor %.1f ms; predictor %d steps (%.1e), corrector %d steps (%.1e)\n",
+                 kPrecName[p->fac_prec], p->stage_ms[0] + p->stage_ms[1] + p->stage_ms[2],
+                 pred_steps, pred_rel, last_steps, last_rel);
         break;
       }
       // Multiple centrality correctors (Gondzio), reusing the factor: the
@@ -405,7 +430,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
                                   10.0 * smu, n, s),
              "corrector rhs");
           const int st = solve(v[V_RD], v[V_RP], v[V_RC2], v[V_DX2], v[V_DY2], v[V_DZ2]);
-          if (st != AHLP_OK || last_rel > kEscalate) break;   // keep the previous direction
+          if (st != AHLP_OK || last_rel > stalled) break;   // keep the previous direction
           double b_p = 0.0, b_d = 0.0;
           steps(v[V_DX2], v[V_DZ2], b_p, b_d);
           if (!(std::min(b_p, b_d) >= 1.01 * std::min(a_p, a_d))) break;

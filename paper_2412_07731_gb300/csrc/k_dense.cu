@@ -179,21 +179,32 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_kernel(T *buf, const BlkI
 }
 
 // --------------------------------------------------------------------------
-// FP32 factors: diagonal tile by one warp (warp barriers only; the pivot
-// safeguard in FP32), then the inverse of its pivot triangle, written in the
-// layout the block solves use (inverse on the pivot rows, the factor on the
-// non-pivot rows of a block's last pivot tile).  The panel below then is a
-// product with that inverse instead of a column-by-column substitution.
+// FP32 factors: diagonal tile, then the inverse of its pivot triangle,
+// written in the layout the block solves use (inverse on the pivot rows, the
+// factor on the non-pivot rows of a block's last pivot tile).  The panel
+// below then is a product with that inverse instead of a column-by-column
+// substitution.
+//
+// The 64x64 tile sits in shared memory and is factored in four 16-column
+// panels.  Warp 0 factors a panel in registers: lane l holds rows l and
+// l + 32 of the panel's 16 columns, the pivot and the scaled column entries
+// are broadcast with shuffles, so the sequential path has no shared-memory
+// round trip.  All 256 threads then apply the panel to the columns right of
+// it (a rank-16 update).  The code of a panel step is small and runs four
+// times; a fully unrolled 64-column version was bound by instruction fetch.
+// The inverse is column-oriented: thread j forward-substitutes e_j, reading
+// the factor as broadcasts.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(NB) pchol_potrf_f32_kernel(float *buf, float *tinv,
-                                                             const BlkInfo *blk, int k,
-                                                             const double *diag0, float tol,
-                                                             int *status) {
+constexpr int kPotrf32Threads = 256;
+constexpr int kPW = 16;   // panel width
+
+__global__ void __launch_bounds__(kPotrf32Threads) pchol_potrf_f32_kernel(
+    float *buf, float *tinv, const BlkInfo *blk, int k, const double *diag0, float tol,
+    int *status) {
   const BlkInfo bi = blk[blockIdx.x];
   if (k >= bi.Tp) return;
   __shared__ float t[NB][NB + 1];
   __shared__ float X[NB][NB + 1];
-  __shared__ float dref[NB];
   const int r0 = k * NB;
   const int nr = min(NB, bi.a - r0);
   const int npiv = min(NB, bi.p - r0);
@@ -201,51 +212,104 @@ __global__ void __launch_bounds__(NB) pchol_potrf_f32_kernel(float *buf, float *
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
     t[r][c] = (r < nr && c < nr && r >= c) ? g[(long long)c * bi.lda + r] : 0.0f;
-    X[r][c] = 0.0f;
   }
-  for (int c = threadIdx.x; c < npiv; c += blockDim.x) dref[c] = (float)diag0[bi.d0off + r0 + c];
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int c = 0; c < npiv; ++c) {
-      float piv = t[c][c];
-      const float lim = tol * dref[c];
-      const float floor_v = lim > 0.0f ? lim : 1.0f;
-      if (!(piv == piv)) {
-        if (lane == 0 && atomicAdd(&status[0], 1) == 0) {
-          status[2] = bi.tag + (int)blockIdx.x;
-          status[3] = r0 + c;
+  const double *d0 = diag0 + bi.d0off + r0;
+  for (int c0 = 0; c0 < npiv; c0 += kPW) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      float ra[kPW], rb[kPW];   // rows lane and lane + 32, columns c0 .. c0 + 15
+#pragma unroll
+      for (int u = 0; u < kPW; ++u) {
+        ra[u] = t[lane][c0 + u];
+        rb[u] = t[lane + 32][c0 + u];
+      }
+      const float dref_a = lane < npiv ? (float)d0[lane] : 0.0f;
+      const float dref_b = lane + 32 < npiv ? (float)d0[lane + 32] : 0.0f;
+#pragma unroll
+      for (int u = 0; u < kPW; ++u) {
+        const int c = c0 + u;
+        if (c < npiv) {   // uniform over the warp
+          // values, not array elements, are selected (a select of two
+          // array elements would force the arrays into local memory)
+          const float va = ra[u], vb = rb[u];
+          const bool hi = c >= 32;
+          float piv = __shfl_sync(0xffffffffu, hi ? vb : va, c & 31);
+          const float lim = tol * __shfl_sync(0xffffffffu, hi ? dref_b : dref_a, c & 31);
+          const float floor_v = lim > 0.0f ? lim : 1.0f;
+          if (!(piv == piv)) {
+            if (lane == 0 && atomicAdd(&status[0], 1) == 0) {
+              status[2] = bi.tag + (int)blockIdx.x;
+              status[3] = r0 + c;
+            }
+            piv = floor_v;
+          } else if (!(piv > lim) || !(piv > 0.0f)) {
+            if (lane == 0) atomicAdd(&status[1], 1);
+            piv = floor_v;
+          }
+          const float lcc = sqrtf(piv), inv = 1.0f / lcc;
+          const float la = lane == c ? lcc : va * inv;
+          const float lb = lane + 32 == c ? lcc : vb * inv;
+          ra[u] = la;
+          rb[u] = lb;
+#pragma unroll
+          for (int w = u + 1; w < kPW; ++w) {
+            const int q = c0 + w;
+            const float lq = __shfl_sync(0xffffffffu, q >= 32 ? lb : la, q & 31);
+            ra[w] = fmaf(-la, lq, ra[w]);
+            rb[w] = fmaf(-lb, lq, rb[w]);
+          }
         }
-        piv = floor_v;
-      } else if (!(piv > lim) || !(piv > 0.0f)) {
-        if (lane == 0) atomicAdd(&status[1], 1);
-        piv = floor_v;
       }
-      const float lcc = sqrtf(piv), inv = 1.0f / lcc;
-      __syncwarp();
-      if (lane == 0) t[c][c] = lcc;
-      for (int r = c + 1 + lane; r < nr; r += 32) t[r][c] *= inv;
-      __syncwarp();
-      for (int r = c + 1 + lane; r < nr; r += 32) {
-        const float lr = t[r][c];
-        for (int q = c + 1; q <= r; ++q) t[r][q] = fmaf(-lr, t[q][c], t[r][q]);
+      // write the panel back (entries above the diagonal stay zero)
+#pragma unroll
+      for (int u = 0; u < kPW; ++u) {
+        const int c = c0 + u;
+        if (lane >= c) t[lane][c] = ra[u];
+        if (lane + 32 >= c) t[lane + 32][c] = rb[u];
       }
-      __syncwarp();
     }
-  }
-  __syncthreads();
-  // inverse of the pivot triangle: thread j substitutes e_j forward
-  const int j = threadIdx.x;
-  if (j < npiv) {
-    for (int i = j; i < npiv; ++i) {
-      float s0 = (i == j) ? 1.0f : 0.0f, s1 = 0.0f;
-      int q = j;
-      for (; q + 1 < i; q += 2) {
-        s0 = fmaf(-t[i][q], X[q][j], s0);
-        s1 = fmaf(-t[i][q + 1], X[q + 1][j], s1);
+    __syncthreads();
+    // rank-16 update of the lower triangle right of the panel:
+    // t[r][q] -= sum_c t[r][c] t[q][c], c0 + 16 <= q <= r < nr, c < npiv
+    const int q0 = c0 + kPW;
+    const int cend = min(c0 + kPW, npiv);
+    if (q0 < nr) {
+      const int w = nr - q0;
+      for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+        const int rr = idx % w, qq = idx / w;
+        if (rr < qq) continue;
+        const int r = q0 + rr, q = q0 + qq;
+        float s0 = 0.0f, s1 = 0.0f;
+        int c = c0;
+        for (; c + 1 < cend; c += 2) {
+          s0 = fmaf(t[r][c], t[q][c], s0);
+          s1 = fmaf(t[r][c + 1], t[q][c + 1], s1);
+        }
+        if (c < cend) s0 = fmaf(t[r][c], t[q][c], s0);
+        t[r][q] -= s0 + s1;
       }
-      if (q < i) s0 = fmaf(-t[i][q], X[q][j], s0);
-      X[i][j] = (s0 + s1) / t[i][i];
+    }
+    __syncthreads();
+  }
+  // inverse of the pivot triangle: column j = threadIdx.x; X[i][j] = 0 for i < j
+  if (threadIdx.x < NB) {
+    const int j = threadIdx.x;
+    for (int i = 0; i < NB; ++i) {
+      float v = 0.0f;
+      if (i < npiv && i >= j) {
+        float s0 = i == j ? 1.0f : 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        int q = j;
+        for (; q + 3 < i; q += 4) {
+          s0 = fmaf(-t[i][q], X[q][j], s0);
+          s1 = fmaf(-t[i][q + 1], X[q + 1][j], s1);
+          s2 = fmaf(-t[i][q + 2], X[q + 2][j], s2);
+          s3 = fmaf(-t[i][q + 3], X[q + 3][j], s3);
+        }
+        for (; q < i; ++q) s0 = fmaf(-t[i][q], X[q][j], s0);
+        v = ((s0 + s1) + (s2 + s3)) / t[i][i];
+      }
+      X[i][j] = v;
     }
   }
   __syncthreads();
@@ -593,6 +657,126 @@ __global__ void __launch_bounds__(kThreads) pchol_update_kernel(T *buf, const Bl
     for (int i = 0; i < 4; ++i) {
       const int r = tx + 16 * i;
       if (r < nrI && c < nrJ && (I != J || r >= c)) gc[(long long)c * bi.lda + r] -= acc[i][j];
+    }
+  }
+}
+
+// FP32 trailing update.  The 4x4-per-thread tile above leaves the FP32 pipe
+// waiting on shared-memory issue (8 scalar loads per 16 FMAs); here 64
+// threads cover the 64x64 tile with an 8x8 register tile each, reading it
+// with four 16-byte shared loads per 64 FMAs.  Rows 4tx..4tx+3 and
+// 32+4tx..35+4tx, columns likewise with ty, so that the 16-byte loads of a
+// quarter warp cover 128 contiguous bytes.  The next chunk of the panel is
+// prefetched into registers while the current one is in use (double-buffered
+// shared memory, one barrier per chunk).
+constexpr int kUpdF32Threads = 64;
+constexpr int KC32 = 16;   // pivot columns per staged chunk
+
+__device__ __forceinline__ float4 ld_col4(const float *col, int r, int nr) {
+  if (r + 4 <= nr) return *reinterpret_cast<const float4 *>(col + r);
+  float4 v;
+  v.x = r < nr ? col[r] : 0.0f;
+  v.y = r + 1 < nr ? col[r + 1] : 0.0f;
+  v.z = r + 2 < nr ? col[r + 2] : 0.0f;
+  v.w = r + 3 < nr ? col[r + 3] : 0.0f;
+  return v;
+}
+
+__global__ void __launch_bounds__(kUpdF32Threads) pchol_update_f32_kernel(float *buf,
+                                                                         const BlkInfo *blk,
+                                                                         int k) {
+  const BlkInfo bi = blk[blockIdx.y];
+  if (k >= bi.Tp) return;
+  const long long t = bi.T - k - 1;
+  const long long q = blockIdx.x;
+  if (q >= t * (t + 1) / 2) return;
+  long long ii = (long long)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  while (ii * (ii + 1) / 2 > q) --ii;
+  while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
+  const long long jj = q - ii * (ii + 1) / 2;
+  const int I = k + 1 + (int)ii, J = k + 1 + (int)jj;
+  const int npiv = min(NB, bi.p - k * NB);
+  const int rI = I * NB, rJ = J * NB;
+  const int nrI = min(NB, bi.a - rI), nrJ = min(NB, bi.a - rJ);
+  __shared__ __align__(16) float As[2][KC32][NB];
+  __shared__ __align__(16) float Bs[2][KC32][NB];
+  const int tid = threadIdx.x;
+  const int tx = tid & 7, ty = tid >> 3;
+  // staging: thread loads float4 number (tid & 15) of columns (tid >> 4) + 4u
+  const int lv = (tid & 15) * 4, lk = tid >> 4;
+  const float *colk = buf + bi.base + (long long)(k * NB) * bi.lda;
+  const int nchunk = (npiv + KC32 - 1) / KC32;
+  float4 pa[4], pb[4];
+  auto fetch = [&](int kc) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = lk + 4 * u;
+      if (kc + kk < npiv) {
+        const float *col = colk + (long long)(kc + kk) * bi.lda;
+        pa[u] = ld_col4(col + rI, lv, nrI);
+        pb[u] = ld_col4(col + rJ, lv, nrJ);
+      } else {
+        pa[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        pb[u] = pa[u];
+      }
+    }
+  };
+  auto stash = [&](int b) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      *reinterpret_cast<float4 *>(&As[b][lk + 4 * u][lv]) = pa[u];
+      *reinterpret_cast<float4 *>(&Bs[b][lk + 4 * u][lv]) = pb[u];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+  fetch(0);
+  stash(0);
+  __syncthreads();
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int b = ch & 1;
+    if (ch + 1 < nchunk) fetch((ch + 1) * KC32);
+#pragma unroll
+    for (int kk = 0; kk < KC32; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[b][kk][4 * tx]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[b][kk][32 + 4 * tx]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[b][kk][4 * ty]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[b][kk][32 + 4 * ty]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (ch + 1 < nchunk) stash(b ^ 1);
+    __syncthreads();
+  }
+  float *gc = buf + bi.base + (long long)rJ * bi.lda + rI;
+  const bool diag = I == J;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c = (j < 4 ? 4 * ty : 32 + 4 * ty) + (j & 3);
+    if (c >= nrJ) continue;
+    float *col = gc + (long long)c * bi.lda;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = (h == 0 ? 4 * tx : 32 + 4 * tx);
+      if (!diag && r + 4 <= nrI) {
+        float4 v = *reinterpret_cast<float4 *>(col + r);
+        v.x -= acc[4 * h][j];
+        v.y -= acc[4 * h + 1][j];
+        v.z -= acc[4 * h + 2][j];
+        v.w -= acc[4 * h + 3][j];
+        *reinterpret_cast<float4 *>(col + r) = v;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (r + e < nrI && (!diag || r + e >= c)) col[r + e] -= acc[4 * h + e][j];
+      }
     }
   }
 }
@@ -1094,7 +1278,7 @@ cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkI
       if (t * (t + 1) / 2 > maxTrail) maxTrail = t * (t + 1) / 2;
     }
     if constexpr (sizeof(T) == sizeof(float)) {
-      count_launch(), pchol_potrf_f32_kernel<<<nblk, NB, 0, s>>>(buf, tinv, info, k, diag0,
+      count_launch(), pchol_potrf_f32_kernel<<<nblk, kPotrf32Threads, 0, s>>>(buf, tinv, info, k, diag0,
                                                                  (float)tol, status);
       if (maxPanel > 0)
         count_launch(), pchol_trsm_inv_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads,
@@ -1106,8 +1290,14 @@ cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkI
         count_launch(), pchol_trsm_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads,
                                                trsm_smem<T>(), s>>>(buf, info, k);
     }
-    if (maxTrail > 0)
-      count_launch(), pchol_update_kernel<T><<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(buf, info, k);
+    if (maxTrail > 0) {
+      if constexpr (sizeof(T) == sizeof(float))
+        count_launch(), pchol_update_f32_kernel<<<dim3((unsigned)maxTrail, nblk), kUpdF32Threads, 0,
+                                                  s>>>(buf, info, k);
+      else
+        count_launch(), pchol_update_kernel<T><<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(
+                            buf, info, k);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -46,6 +46,7 @@ def test_default_options_and_status_strings():
     o = L.default_options()
     assert o.precision == 0 and o.max_iter == 200
     assert o.tol == 1e-8 and o.refine_tol == 1e-10 and o.eta == 0.9995
+    assert o.ipm_refine_tol == 1e-6 and o.fp32_cond_max == 1e14
     lib = L.load()
     assert lib.ahlp_status_string(-4) == b"NOT_SPD"
     assert lib.ahlp_status_string(0) == b"OK"
@@ -108,6 +109,8 @@ def test_batch_validation_and_bad_precision():
     L = _lib()
     st, msg = _create_status(lp, options=L.default_options(precision=7))
     assert st == -1 and "precision" in msg
+    st, msg = _create_status(lp, options=L.default_options(ipm_refine_tol=1.5))
+    assert st == -1 and "option" in msg
 
 
 def test_valid_problem_without_gpu_reports_cuda_error():
