@@ -192,8 +192,9 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_kernel(T *buf, const BlkI
 // round trip.  All 256 threads then apply the panel to the columns right of
 // it (a rank-16 update).  The code of a panel step is small and runs four
 // times; a fully unrolled 64-column version was bound by instruction fetch.
-// The inverse is column-oriented: thread j forward-substitutes e_j, reading
-// the factor as broadcasts.
+// The inverse goes by 16x16 blocks: the diagonal blocks by substitution in
+// parallel, then each block row below as two small products with the rows
+// above it, so its sequential depth is 16 rows rather than 64.
 // --------------------------------------------------------------------------
 constexpr int kPotrf32Threads = 256;
 constexpr int kPW = 16;   // panel width
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(kPotrf32Threads) pchol_potrf_f32_kernel(
   if (k >= bi.Tp) return;
   __shared__ float t[NB][NB + 1];
   __shared__ float X[NB][NB + 1];
+  __shared__ float Tm[kPW][NB];
   const int r0 = k * NB;
   const int nr = min(NB, bi.a - r0);
   const int npiv = min(NB, bi.p - r0);
@@ -212,6 +214,7 @@ __global__ void __launch_bounds__(kPotrf32Threads) pchol_potrf_f32_kernel(
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
     t[r][c] = (r < nr && c < nr && r >= c) ? g[(long long)c * bi.lda + r] : 0.0f;
+    X[r][c] = 0.0f;
   }
   __syncthreads();
   const double *d0 = diag0 + bi.d0off + r0;
@@ -292,27 +295,54 @@ __global__ void __launch_bounds__(kPotrf32Threads) pchol_potrf_f32_kernel(
     }
     __syncthreads();
   }
-  // inverse of the pivot triangle: column j = threadIdx.x; X[i][j] = 0 for i < j
-  if (threadIdx.x < NB) {
-    const int j = threadIdx.x;
-    for (int i = 0; i < NB; ++i) {
-      float v = 0.0f;
-      if (i < npiv && i >= j) {
-        float s0 = i == j ? 1.0f : 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-        int q = j;
-        for (; q + 3 < i; q += 4) {
-          s0 = fmaf(-t[i][q], X[q][j], s0);
-          s1 = fmaf(-t[i][q + 1], X[q + 1][j], s1);
-          s2 = fmaf(-t[i][q + 2], X[q + 2][j], s2);
-          s3 = fmaf(-t[i][q + 3], X[q + 3][j], s3);
+  // inverse of the pivot triangle by 16x16 blocks: warp w inverts diagonal
+  // block w by substitution (lane = column); then block rows 1..3 in turn,
+  // X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj, all threads on the entries.
+  // Rows at or past npiv are zero.
+  const int nbk = (npiv + kPW - 1) / kPW;
+  {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < 4 && lane < kPW) {
+      const int b0 = w * kPW, j = b0 + lane;
+      for (int i = b0; i < b0 + kPW; ++i) {
+        float v = 0.0f;
+        if (i < npiv && i >= j) {
+          float s0 = i == j ? 1.0f : 0.0f, s1 = 0.0f;
+          int q = j;
+          for (; q + 1 < i; q += 2) {
+            s0 = fmaf(-t[i][q], X[q][j], s0);
+            s1 = fmaf(-t[i][q + 1], X[q + 1][j], s1);
+          }
+          if (q < i) s0 = fmaf(-t[i][q], X[q][j], s0);
+          v = (s0 + s1) / t[i][i];
         }
-        for (; q < i; ++q) s0 = fmaf(-t[i][q], X[q][j], s0);
-        v = ((s0 + s1) + (s2 + s3)) / t[i][i];
+        X[i][j] = v;
       }
-      X[i][j] = v;
     }
   }
   __syncthreads();
+  for (int bi2 = 1; bi2 < nbk; ++bi2) {
+    const int i0 = bi2 * kPW, wc = i0;   // columns 0 .. i0-1 of block row bi2
+    for (int e = threadIdx.x; e < kPW * wc; e += blockDim.x) {
+      const int r = e % kPW, c = e / kPW;
+      float s0 = 0.0f, s1 = 0.0f;
+      int q = (c / kPW) * kPW;
+      for (; q + 1 < i0; q += 2) {
+        s0 = fmaf(t[i0 + r][q], X[q][c], s0);
+        s1 = fmaf(t[i0 + r][q + 1], X[q + 1][c], s1);
+      }
+      if (q < i0) s0 = fmaf(t[i0 + r][q], X[q][c], s0);
+      Tm[r][c] = s0 + s1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kPW * wc; e += blockDim.x) {
+      const int r = e % kPW, c = e / kPW;
+      float s = 0.0f;
+      for (int q = 0; q <= r; ++q) s = fmaf(X[i0 + r][i0 + q], Tm[q][c], s);
+      X[i0 + r][c] = i0 + r < npiv ? -s : 0.0f;
+    }
+    __syncthreads();
+  }
   float *out = tinv + bi.ioff + (long long)k * NB * NB;
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
@@ -666,20 +696,25 @@ __global__ void __launch_bounds__(kThreads) pchol_update_kernel(T *buf, const Bl
 // threads cover the 64x64 tile with an 8x8 register tile each, reading it
 // with four 16-byte shared loads per 64 FMAs.  Rows 4tx..4tx+3 and
 // 32+4tx..35+4tx, columns likewise with ty, so that the 16-byte loads of a
-// quarter warp cover 128 contiguous bytes.  The next chunk of the panel is
-// prefetched into registers while the current one is in use (double-buffered
-// shared memory, one barrier per chunk).
+// quarter warp cover 128 contiguous bytes.  The whole 64-column panel is
+// requested up front with cp.async, in four 16-column groups, and the
+// arithmetic on a group starts as soon as it has landed, so the later groups
+// arrive behind the arithmetic; ragged rows and columns past the pivots are
+// zero-filled by the copy itself.
 constexpr int kUpdF32Threads = 64;
-constexpr int KC32 = 16;   // pivot columns per staged chunk
 
-__device__ __forceinline__ float4 ld_col4(const float *col, int r, int nr) {
-  if (r + 4 <= nr) return *reinterpret_cast<const float4 *>(col + r);
-  float4 v;
-  v.x = r < nr ? col[r] : 0.0f;
-  v.y = r + 1 < nr ? col[r + 1] : 0.0f;
-  v.z = r + 2 < nr ? col[r + 2] : 0.0f;
-  v.w = r + 3 < nr ? col[r + 3] : 0.0f;
-  return v;
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 __global__ void __launch_bounds__(kUpdF32Threads) pchol_update_f32_kernel(float *buf,
@@ -698,53 +733,48 @@ __global__ void __launch_bounds__(kUpdF32Threads) pchol_update_f32_kernel(float 
   const int npiv = min(NB, bi.p - k * NB);
   const int rI = I * NB, rJ = J * NB;
   const int nrI = min(NB, bi.a - rI), nrJ = min(NB, bi.a - rJ);
-  __shared__ __align__(16) float As[2][KC32][NB];
-  __shared__ __align__(16) float Bs[2][KC32][NB];
+  __shared__ __align__(16) float As[NB][NB];   // [pivot column][row]
+  __shared__ __align__(16) float Bs[NB][NB];
   const int tid = threadIdx.x;
   const int tx = tid & 7, ty = tid >> 3;
-  // staging: thread loads float4 number (tid & 15) of columns (tid >> 4) + 4u
+  // copies: thread moves float4 number (tid & 15) of columns (tid >> 4) + 4u
   const int lv = (tid & 15) * 4, lk = tid >> 4;
   const float *colk = buf + bi.base + (long long)(k * NB) * bi.lda;
-  const int nchunk = (npiv + KC32 - 1) / KC32;
-  float4 pa[4], pb[4];
-  auto fetch = [&](int kc) {
+  const int nchunk = (npiv + 15) / 16;
+  const int na = 4 * max(0, min(4, nrI - lv)), nb = 4 * max(0, min(4, nrJ - lv));
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int kk = lk + 4 * u;
-      if (kc + kk < npiv) {
-        const float *col = colk + (long long)(kc + kk) * bi.lda;
-        pa[u] = ld_col4(col + rI, lv, nrI);
-        pb[u] = ld_col4(col + rJ, lv, nrJ);
-      } else {
-        pa[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        pb[u] = pa[u];
+  for (int ch = 0; ch < 4; ++ch) {
+    if (ch < nchunk) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int kk = ch * 16 + lk + 4 * u;
+        const bool kin = kk < npiv;
+        // a zero-byte copy still names a valid address: row rI / rJ of a pivot column
+        const float *col = colk + (long long)(kin ? kk : 0) * bi.lda;
+        cp_async16(&As[kk][lv], col + rI + (kin && na ? lv : 0), kin ? na : 0);
+        cp_async16(&Bs[kk][lv], col + rJ + (kin && nb ? lv : 0), kin ? nb : 0);
       }
     }
-  };
-  auto stash = [&](int b) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      *reinterpret_cast<float4 *>(&As[b][lk + 4 * u][lv]) = pa[u];
-      *reinterpret_cast<float4 *>(&Bs[b][lk + 4 * u][lv]) = pb[u];
-    }
-  };
+    cp_async_commit();
+  }
   float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-  fetch(0);
-  stash(0);
-  __syncthreads();
   for (int ch = 0; ch < nchunk; ++ch) {
-    const int b = ch & 1;
-    if (ch + 1 < nchunk) fetch((ch + 1) * KC32);
+    if (ch == 0) cp_async_wait<3>();
+    else if (ch == 1) cp_async_wait<2>();
+    else if (ch == 2) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < KC32; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4 *>(&As[b][kk][4 * tx]);
-      const float4 a1 = *reinterpret_cast<const float4 *>(&As[b][kk][32 + 4 * tx]);
-      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[b][kk][4 * ty]);
-      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[b][kk][32 + 4 * ty]);
+    for (int kq = 0; kq < 16; ++kq) {
+      const int kk = ch * 16 + kq;
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][4 * tx]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][32 + 4 * tx]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][4 * ty]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][32 + 4 * ty]);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -752,11 +782,32 @@ __global__ void __launch_bounds__(kUpdF32Threads) pchol_update_f32_kernel(float 
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    if (ch + 1 < nchunk) stash(b ^ 1);
-    __syncthreads();
   }
   float *gc = buf + bi.base + (long long)rJ * bi.lda + rI;
   const bool diag = I == J;
+  if (!diag && nrI == NB && nrJ == NB) {
+    // interior tile: the eight loads of a row quad are issued before any store
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = h == 0 ? 4 * tx : 32 + 4 * tx;
+      float4 cv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = (j < 4 ? 4 * ty : 32 + 4 * ty) + (j & 3);
+        cv[j] = *reinterpret_cast<const float4 *>(gc + (long long)c * bi.lda + r);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = (j < 4 ? 4 * ty : 32 + 4 * ty) + (j & 3);
+        cv[j].x -= acc[4 * h][j];
+        cv[j].y -= acc[4 * h + 1][j];
+        cv[j].z -= acc[4 * h + 2][j];
+        cv[j].w -= acc[4 * h + 3][j];
+        *reinterpret_cast<float4 *>(gc + (long long)c * bi.lda + r) = cv[j];
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int c = (j < 4 ? 4 * ty : 32 + 4 * ty) + (j & 3);
@@ -765,18 +816,9 @@ __global__ void __launch_bounds__(kUpdF32Threads) pchol_update_f32_kernel(float 
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int r = (h == 0 ? 4 * tx : 32 + 4 * tx);
-      if (!diag && r + 4 <= nrI) {
-        float4 v = *reinterpret_cast<float4 *>(col + r);
-        v.x -= acc[4 * h][j];
-        v.y -= acc[4 * h + 1][j];
-        v.z -= acc[4 * h + 2][j];
-        v.w -= acc[4 * h + 3][j];
-        *reinterpret_cast<float4 *>(col + r) = v;
-      } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (r + e < nrI && (!diag || r + e >= c)) col[r + e] -= acc[4 * h + e][j];
-      }
+      for (int e = 0; e < 4; ++e)
+        if (r + e < nrI && (!diag || r + e >= c)) col[r + e] -= acc[4 * h + e][j];
     }
   }
 }
