@@ -153,6 +153,28 @@ struct CArgs {
   int nseg;
 };
 
+// Forward substitution z <- L^-1 z for one right-hand side of at most 32 rows
+// held in registers.  Axpy order: once z_q is final, every later row takes its
+// update from it at once, so the dependent chain is two operations per row
+// rather than the length of a dot product (FP64 latency dominates these
+// small solves on this part).  L: column-major, ld lj; Tinv: its reciprocal
+// pivots.
+constexpr int kChainRegL = 32;
+
+__device__ __forceinline__ void fwd_subst_regs(double (&z)[kChainRegL], int lj, const double *L,
+                                               const double *Tinv) {
+#pragma unroll
+  for (int q = 0; q < kChainRegL; ++q) {
+    if (q < lj) {
+      const double zq = z[q] * Tinv[q];
+      z[q] = zq;
+#pragma unroll
+      for (int r = q + 1; r < kChainRegL; ++r)
+        if (r < lj) z[r] = fma(-L[r + q * lj], zq, z[r]);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
   extern __shared__ double T[];   // lmax * lmax
   __shared__ double s_inv;
@@ -163,82 +185,161 @@ __global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
     const int lj = A.l[j];
     if (lj == 0) continue;
     const int lp = (j > jb) ? A.l[j - 1] : 0;
+    const int ln = (j + 1 < je) ? A.l[j + 1] : 0;
+    const bool small = lj <= kChainRegL;
     double *Tg = A.Td + A.td_off[j];
     for (int i = tid; i < lj * lj; i += bd) T[i] = Tg[i];
     __syncthreads();
+    // T_j -= X_{j-1} X_{j-1}' (lower part), four partial sums per entry
     if (lp > 0) {
       const double *X = A.Hd + A.h_off[j - 1];   // l_j x l_{j-1}, ld l_j
       for (int i = tid; i < lj * lj; i += bd) {
         const int r = i % lj, s = i / lj;
         if (r < s) continue;
-        double acc = 0.0;
-        for (int c = 0; c < lp; ++c) acc = fma(X[r + (long long)c * lj], X[s + (long long)c * lj], acc);
-        T[i] -= acc;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = 0;
+        for (; c + 4 <= lp; c += 4) {
+          a0 = fma(X[r + (long long)c * lj], X[s + (long long)c * lj], a0);
+          a1 = fma(X[r + (long long)(c + 1) * lj], X[s + (long long)(c + 1) * lj], a1);
+          a2 = fma(X[r + (long long)(c + 2) * lj], X[s + (long long)(c + 2) * lj], a2);
+          a3 = fma(X[r + (long long)(c + 3) * lj], X[s + (long long)(c + 3) * lj], a3);
+        }
+        for (; c < lp; ++c) a0 = fma(X[r + (long long)c * lj], X[s + (long long)c * lj], a0);
+        T[i] -= (a0 + a1) + (a2 + a3);
       }
     }
     __syncthreads();
-    for (int c = 0; c < lj; ++c) {
-      if (tid == 0) {
-        double piv = T[c + c * lj];
-        pivot_fix(piv, A.Td_diag0[A.link_off[j] + c], A.tol, A.status, -1 - j, c);
-        const double lcc = sqrt(piv);
-        T[c + c * lj] = lcc;
-        s_inv = 1.0 / lcc;
+    if (small) {
+      // Cholesky of T_j by warp 0, lane r owning row r; every lane takes the
+      // pivot from shared memory, so no barrier or shuffle sits between the
+      // pivot and its reciprocal square root
+      if (tid < 32) {
+        const int lane = tid;
+        for (int c = 0; c < lj; ++c) {
+          double piv = T[c + c * lj];
+          const double orig = A.Td_diag0[A.link_off[j] + c];
+          const double lim = A.tol * orig, floor_v = lim > 0.0 ? lim : 1.0;
+          if (!(piv == piv)) {
+            if (lane == 0 && atomicAdd(&A.status[0], 1) == 0) {
+              A.status[2] = -1 - j;
+              A.status[3] = c;
+            }
+            piv = floor_v;
+          } else if (!(piv > lim) || !(piv > 0.0)) {
+            if (lane == 0) atomicAdd(&A.status[1], 1);
+            piv = floor_v;
+          }
+          const double inv = rsqrt(piv);
+          __syncwarp();
+          if (lane == c) {
+            T[c + c * lj] = piv * inv;
+            Tinv[c] = inv;
+          } else if (lane > c && lane < lj) {
+            T[lane + c * lj] *= inv;
+          }
+          __syncwarp();
+          if (lane > c && lane < lj) {
+            const double lr = T[lane + c * lj];
+            for (int q = c + 1; q <= lane; ++q)
+              T[lane + q * lj] = fma(-lr, T[q + c * lj], T[lane + q * lj]);
+          }
+          __syncwarp();
+        }
       }
-      __syncthreads();
-      for (int r = c + 1 + tid; r < lj; r += bd) T[r + c * lj] *= s_inv;
-      __syncthreads();
-      const int m = lj - c - 1;
-      for (int i = tid; i < m * m; i += bd) {
-        const int rr = i % m, ss = i / m;
-        if (rr >= ss) T[(c + 1 + rr) + (c + 1 + ss) * lj] -= T[(c + 1 + rr) + c * lj] * T[(c + 1 + ss) + c * lj];
+    } else {
+      for (int c = 0; c < lj; ++c) {
+        if (tid == 0) {
+          double piv = T[c + c * lj];
+          pivot_fix(piv, A.Td_diag0[A.link_off[j] + c], A.tol, A.status, -1 - j, c);
+          const double lcc = sqrt(piv);
+          T[c + c * lj] = lcc;
+          s_inv = 1.0 / lcc;
+        }
+        __syncthreads();
+        for (int r = c + 1 + tid; r < lj; r += bd) T[r + c * lj] *= s_inv;
+        __syncthreads();
+        const int m = lj - c - 1;
+        for (int i = tid; i < m * m; i += bd) {
+          const int rr = i % m, ss = i / m;
+          if (rr >= ss) T[(c + 1 + rr) + (c + 1 + ss) * lj] -= T[(c + 1 + rr) + c * lj] * T[(c + 1 + ss) + c * lj];
+        }
+        __syncthreads();
       }
-      __syncthreads();
+      // reciprocal pivots (FP64 divides are expensive on this part)
+      for (int c = tid; c < lj; c += bd) Tinv[c] = 1.0 / T[c + c * lj];
     }
+    __syncthreads();
     for (int i = tid; i < lj * lj; i += bd) {
       const int r = i % lj, s = i / lj;
       Tg[i] = (r >= s) ? T[i] : 0.0;
     }
-    // Z_j = L_j^-1 (E_j' - X_{j-1} Z_{j-1}): the product one thread per entry,
-    // then one warp per column for the triangular solve
+    // E_j' -= X_{j-1} Z_{j-1}, one thread per entry, four partial sums
     if (lp > 0) {
       const double *X = A.Hd + A.h_off[j - 1];
       for (int i = tid; i < lj * A.B; i += bd) {
         const int r = i % lj, rb = i / lj;
         const double *zp = A.Et + (long long)rb * A.nl + A.link_off[j - 1];
-        double acc = 0.0;
-        for (int c = 0; c < lp; ++c) acc = fma(X[r + (long long)c * lj], zp[c], acc);
-        A.Et[(long long)rb * A.nl + A.link_off[j] + r] -= acc;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = 0;
+        for (; c + 4 <= lp; c += 4) {
+          a0 = fma(X[r + (long long)c * lj], zp[c], a0);
+          a1 = fma(X[r + (long long)(c + 1) * lj], zp[c + 1], a1);
+          a2 = fma(X[r + (long long)(c + 2) * lj], zp[c + 2], a2);
+          a3 = fma(X[r + (long long)(c + 3) * lj], zp[c + 3], a3);
+        }
+        for (; c < lp; ++c) a0 = fma(X[r + (long long)c * lj], zp[c], a0);
+        A.Et[(long long)rb * A.nl + A.link_off[j] + r] -= (a0 + a1) + (a2 + a3);
       }
       __syncthreads();
     }
-    // reciprocal pivots (FP64 divides are expensive on this part)
-    for (int c = tid; c < lj; c += bd) Tinv[c] = 1.0 / T[c + c * lj];
-    __syncthreads();
-    // Linv_j = L_j^-1, one thread per column
     double *Li = A.Linv + A.td_off[j];
-    for (int c = tid; c < lj; c += bd) {
-      for (int r = 0; r < c; ++r) Li[r + c * lj] = 0.0;
-      Li[c + c * lj] = Tinv[c];
-      for (int r = c + 1; r < lj; ++r) {
-        double acc = 0.0;
-        for (int q = c; q < r; ++q) acc = fma(T[r + q * lj], Li[q + c * lj], acc);
-        Li[r + c * lj] = -acc * Tinv[r];
+    double *H = A.Hd + A.h_off[j];   // l_{j+1} x l_j, ld l_{j+1}; becomes X_j = H_j L_j^-T
+    if (small) {
+      // three families of forward substitutions with L_j, all at once:
+      // columns of Linv_j (e_c), rows of X_j (rows of H_j) and the columns
+      // of Z_j (E_j' after the update above)
+      const int nrhs = lj + ln + A.B;
+      for (int w = tid; w < nrhs; w += bd) {
+        double z[kChainRegL];
+        double *dst;
+        long long stride;
+        if (w < lj) {
+          dst = Li + (long long)w * lj;
+          stride = 1;
+        } else if (w < lj + ln) {
+          dst = H + (w - lj);
+          stride = ln;
+        } else {
+          dst = A.Et + (long long)(w - lj - ln) * A.nl + A.link_off[j];
+          stride = 1;
+        }
+#pragma unroll
+        for (int q = 0; q < kChainRegL; ++q)
+          z[q] = q < lj ? (w < lj ? (q == w ? 1.0 : 0.0) : dst[q * stride]) : 0.0;
+        fwd_subst_regs(z, lj, T, Tinv);
+#pragma unroll
+        for (int q = 0; q < kChainRegL; ++q)
+          if (q < lj) dst[q * stride] = z[q];
       }
-    }
-    // one thread per column: every lane of every FP64 instruction is useful
-    for (int rb = tid; rb < A.B; rb += bd) {
-      double *zc = A.Et + (long long)rb * A.nl + A.link_off[j];
-      for (int r = 0; r < lj; ++r) {
-        double acc = zc[r];
-        for (int c = 0; c < r; ++c) acc = fma(-T[r + c * lj], zc[c], acc);
-        zc[r] = acc * Tinv[r];
+    } else {
+      // Linv_j = L_j^-1, one thread per column
+      for (int c = tid; c < lj; c += bd) {
+        for (int r = 0; r < c; ++r) Li[r + c * lj] = 0.0;
+        Li[c + c * lj] = Tinv[c];
+        for (int r = c + 1; r < lj; ++r) {
+          double acc = 0.0;
+          for (int q = c; q < r; ++q) acc = fma(T[r + q * lj], Li[q + c * lj], acc);
+          Li[r + c * lj] = -acc * Tinv[r];
+        }
       }
-    }
-    // X_j = H_j L_j^-T, one thread per row of H_j
-    if (j + 1 < je) {
-      const int ln = A.l[j + 1];
-      double *H = A.Hd + A.h_off[j];   // l_{j+1} x l_j, ld l_{j+1}
+      for (int rb = tid; rb < A.B; rb += bd) {
+        double *zc = A.Et + (long long)rb * A.nl + A.link_off[j];
+        for (int r = 0; r < lj; ++r) {
+          double acc = zc[r];
+          for (int c = 0; c < r; ++c) acc = fma(-T[r + c * lj], zc[c], acc);
+          zc[r] = acc * Tinv[r];
+        }
+      }
       for (int r = tid; r < ln; r += bd) {
         for (int c = 0; c < lj; ++c) {
           double acc = H[r + (long long)c * ln];
@@ -254,23 +355,246 @@ __global__ void __launch_bounds__(512) chain_factor_kernel(CArgs A) {
       double *Y = A.Yf + A.h_off[j - 1];
       for (int i = tid; i < lj * lp; i += bd) {
         const int r = i % lj, c = i / lj;
-        double acc = 0.0;
-        for (int q = 0; q <= r; ++q) acc = fma(Li[r + q * lj], X[q + (long long)c * lj], acc);
-        Y[r + (long long)c * lj] = acc;
+        double a0 = 0.0, a1 = 0.0;
+        int q = 0;
+        for (; q + 1 <= r; q += 2) {
+          a0 = fma(Li[r + q * lj], X[q + (long long)c * lj], a0);
+          a1 = fma(Li[r + (q + 1) * lj], X[q + 1 + (long long)c * lj], a1);
+        }
+        if (q <= r) a0 = fma(Li[r + q * lj], X[q + (long long)c * lj], a0);
+        Y[r + (long long)c * lj] = a0 + a1;
       }
     }
-    if (j + 1 < je && A.l[j + 1] > 0) {
-      const int ln = A.l[j + 1];
+    if (ln > 0) {
       const double *X = A.Hd + A.h_off[j];       // l_{j+1} x l_j
       double *Y = A.Yb + A.h_off[j];             // l_j x l_{j+1}
       for (int i = tid; i < lj * ln; i += bd) {
         const int r = i % lj, c = i / lj;
-        double acc = 0.0;
-        for (int q = r; q < lj; ++q) acc = fma(Li[q + r * lj], X[c + (long long)q * ln], acc);
-        Y[r + (long long)c * lj] = acc;
+        double a0 = 0.0, a1 = 0.0;
+        int q = r;
+        for (; q + 1 < lj; q += 2) {
+          a0 = fma(Li[q + r * lj], X[c + (long long)q * ln], a0);
+          a1 = fma(Li[q + 1 + r * lj], X[c + (long long)(q + 1) * ln], a1);
+        }
+        if (q < lj) a0 = fma(Li[q + r * lj], X[c + (long long)q * ln], a0);
+        Y[r + (long long)c * lj] = a0 + a1;
       }
     }
     __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// Link chain for link blocks of at most 32 rows, in three launches.  Only the
+// block Cholesky of T and X_j = H_j L_j^-T are sequential along the chain;
+// the solve operators (Linv_j, Yf_j, Yb_j) and Z = L_T^-1 E' hang off it.
+// On one SM the FP64 pipe (about two FMA lanes per clock here) would carry
+// all of that work; split this way the chain's CTA does the sequential part
+// only, the operators take one CTA per pair, and Z one warp per border column.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) chain_critical_kernel(CArgs A) {
+  extern __shared__ double T[];   // lmax * lmax
+  __shared__ double Tinv[kChainRegL], Dg[kChainRegL];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int jb = A.seg[2 * blockIdx.x], je = A.seg[2 * blockIdx.x + 1];
+  for (int j = jb; j < je; ++j) {
+    const int lj = A.l[j];
+    if (lj == 0) continue;
+    const int lp = (j > jb) ? A.l[j - 1] : 0;
+    const int ln = (j + 1 < je) ? A.l[j + 1] : 0;
+    double *Tg = A.Td + A.td_off[j];
+    for (int i = tid; i < lj * lj; i += bd) T[i] = Tg[i];
+    if (tid < lj) Dg[tid] = A.Td_diag0[A.link_off[j] + tid];
+    __syncthreads();
+    if (lp > 0) {   // T_j -= X_{j-1} X_{j-1}', four partial sums per entry
+      const double *X = A.Hd + A.h_off[j - 1];   // l_j x l_{j-1}, ld l_j
+      for (int i = tid; i < lj * lj; i += bd) {
+        const int r = i % lj, s = i / lj;
+        if (r < s) continue;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = 0;
+        for (; c + 4 <= lp; c += 4) {
+          a0 = fma(X[r + (long long)c * lj], X[s + (long long)c * lj], a0);
+          a1 = fma(X[r + (long long)(c + 1) * lj], X[s + (long long)(c + 1) * lj], a1);
+          a2 = fma(X[r + (long long)(c + 2) * lj], X[s + (long long)(c + 2) * lj], a2);
+          a3 = fma(X[r + (long long)(c + 3) * lj], X[s + (long long)(c + 3) * lj], a3);
+        }
+        for (; c < lp; ++c) a0 = fma(X[r + (long long)c * lj], X[s + (long long)c * lj], a0);
+        T[i] -= (a0 + a1) + (a2 + a3);
+      }
+    }
+    __syncthreads();
+    // Cholesky of T_j by warp 0, lane r owning row r; every lane reads the
+    // pivot from shared memory, so no barrier or shuffle sits between the
+    // pivot and its reciprocal square root
+    if (tid < 32) {
+      const int lane = tid;
+      for (int c = 0; c < lj; ++c) {
+        double piv = T[c + c * lj];
+        const double lim = A.tol * Dg[c], floor_v = lim > 0.0 ? lim : 1.0;
+        if (!(piv == piv)) {
+          if (lane == 0 && atomicAdd(&A.status[0], 1) == 0) {
+            A.status[2] = -1 - j;
+            A.status[3] = c;
+          }
+          piv = floor_v;
+        } else if (!(piv > lim) || !(piv > 0.0)) {
+          if (lane == 0) atomicAdd(&A.status[1], 1);
+          piv = floor_v;
+        }
+        const double inv = rsqrt(piv);
+        __syncwarp();
+        if (lane == c) {
+          T[c + c * lj] = piv * inv;
+          Tinv[c] = inv;
+        } else if (lane > c && lane < lj) {
+          T[lane + c * lj] *= inv;
+        }
+        __syncwarp();
+        if (lane > c && lane < lj) {
+          const double lr = T[lane + c * lj];
+          for (int q = c + 1; q <= lane; ++q)
+            T[lane + q * lj] = fma(-lr, T[q + c * lj], T[lane + q * lj]);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < lj * lj; i += bd) {
+      const int r = i % lj, s = i / lj;
+      Tg[i] = (r >= s) ? T[i] : 0.0;
+    }
+    // X_j = H_j L_j^-T in place: row w of H_j is a forward substitution with L_j
+    if (tid < ln) {
+      double *H = A.Hd + A.h_off[j] + tid;   // l_{j+1} x l_j, ld l_{j+1}
+      double z[kChainRegL];
+#pragma unroll
+      for (int q = 0; q < kChainRegL; ++q) z[q] = q < lj ? H[(long long)q * ln] : 0.0;
+      fwd_subst_regs(z, lj, T, Tinv);
+#pragma unroll
+      for (int q = 0; q < kChainRegL; ++q)
+        if (q < lj) H[(long long)q * ln] = z[q];
+    }
+    __syncthreads();
+  }
+}
+
+// Linv_j = L_j^-1, Yf_j = Linv_j X_{j-1}, Yb_j = Linv_j' X_j': one CTA per pair
+__global__ void __launch_bounds__(128) chain_ops_kernel(CArgs A) {
+  extern __shared__ double Ls[];   // L_j then Linv_j, lmax * lmax each
+  __shared__ double Tinv[kChainRegL];
+  const int j = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  int jb = -1, je = -1;
+  for (int s = 0; s < A.nseg; ++s)
+    if (A.seg[2 * s] <= j && j < A.seg[2 * s + 1]) {
+      jb = A.seg[2 * s];
+      je = A.seg[2 * s + 1];
+    }
+  const int lj = A.l[j];
+  if (jb < 0 || lj == 0) return;
+  const int lp = (j > jb) ? A.l[j - 1] : 0;
+  const int ln = (j + 1 < je) ? A.l[j + 1] : 0;
+  double *L = Ls, *Li = Ls + lj * lj;
+  const double *Tg = A.Td + A.td_off[j];
+  for (int i = tid; i < lj * lj; i += bd) L[i] = Tg[i];
+  __syncthreads();
+  if (tid < lj) Tinv[tid] = 1.0 / L[tid + tid * lj];
+  __syncthreads();
+  double *Lg = A.Linv + A.td_off[j];
+  if (tid < lj) {   // column tid of Linv_j
+    double z[kChainRegL];
+#pragma unroll
+    for (int q = 0; q < kChainRegL; ++q) z[q] = q == tid ? 1.0 : 0.0;
+    fwd_subst_regs(z, lj, L, Tinv);
+#pragma unroll
+    for (int q = 0; q < kChainRegL; ++q)
+      if (q < lj) {
+        Li[q + tid * lj] = z[q];
+        Lg[q + tid * lj] = z[q];
+      }
+  }
+  __syncthreads();
+  if (lp > 0) {
+    const double *X = A.Hd + A.h_off[j - 1];   // l_j x l_{j-1}
+    double *Y = A.Yf + A.h_off[j - 1];
+    for (int i = tid; i < lj * lp; i += bd) {
+      const int r = i % lj, c = i / lj;
+      double a0 = 0.0, a1 = 0.0;
+      int q = 0;
+      for (; q + 1 <= r; q += 2) {
+        a0 = fma(Li[r + q * lj], X[q + (long long)c * lj], a0);
+        a1 = fma(Li[r + (q + 1) * lj], X[q + 1 + (long long)c * lj], a1);
+      }
+      if (q <= r) a0 = fma(Li[r + q * lj], X[q + (long long)c * lj], a0);
+      Y[r + (long long)c * lj] = a0 + a1;
+    }
+  }
+  if (ln > 0) {
+    const double *X = A.Hd + A.h_off[j];   // l_{j+1} x l_j
+    double *Y = A.Yb + A.h_off[j];         // l_j x l_{j+1}
+    for (int i = tid; i < lj * ln; i += bd) {
+      const int r = i % lj, c = i / lj;
+      double a0 = 0.0, a1 = 0.0;
+      int q = r;
+      for (; q + 1 < lj; q += 2) {
+        a0 = fma(Li[q + r * lj], X[c + (long long)q * ln], a0);
+        a1 = fma(Li[q + 1 + r * lj], X[c + (long long)(q + 1) * ln], a1);
+      }
+      if (q < lj) a0 = fma(Li[q + r * lj], X[c + (long long)q * ln], a0);
+      Y[r + (long long)c * lj] = a0 + a1;
+    }
+  }
+}
+
+// Z = L_T^-1 E' along the chain, one warp per border column rb (lane r holds
+// row r of the current link block): Z_j = Linv_j (E_j' - X_{j-1} Z_{j-1}).
+// Segments outside the column's link rows [zlo, zhi) hold zeros and are skipped.
+__global__ void __launch_bounds__(256) chain_z_kernel(CArgs A, const int *zlo, const int *zhi) {
+  const int rb = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (rb >= A.B) return;   // whole warps leave together
+  const int lo = zlo[rb], hi = zhi[rb];
+  for (int s = 0; s < A.nseg; ++s) {
+    const int jb = A.seg[2 * s], je = A.seg[2 * s + 1];
+    if (A.link_off[je] <= lo || A.link_off[jb] >= hi) continue;
+    double zprev = 0.0;
+    int lp = 0;
+    for (int j = jb; j < je; ++j) {
+      const int lj = A.l[j];
+      if (lj == 0) {
+        lp = 0;
+        continue;
+      }
+      double *zc = A.Et + (long long)rb * A.nl + A.link_off[j];
+      double e = lane < lj ? zc[lane] : 0.0;
+      if (lp > 0) {
+        const double *X = A.Hd + A.h_off[j - 1];   // l_j x l_{j-1}, ld l_j
+        double a0 = 0.0, a1 = 0.0;
+        for (int c = 0; c < lp; c += 2) {
+          const double z0 = __shfl_sync(0xffffffffu, zprev, c);
+          const double z1 = __shfl_sync(0xffffffffu, zprev, c + 1 < 32 ? c + 1 : 31);
+          if (lane < lj) {
+            a0 = fma(X[lane + (long long)c * lj], z0, a0);
+            if (c + 1 < lp) a1 = fma(X[lane + (long long)(c + 1) * lj], z1, a1);
+          }
+        }
+        e -= a0 + a1;
+      }
+      const double *Li = A.Linv + A.td_off[j];
+      double a0 = 0.0, a1 = 0.0;
+      for (int q = 0; q < lj; q += 2) {
+        const double e0 = __shfl_sync(0xffffffffu, e, q);
+        const double e1 = __shfl_sync(0xffffffffu, e, q + 1 < 32 ? q + 1 : 31);
+        if (lane < lj) {
+          if (q <= lane) a0 = fma(Li[lane + q * lj], e0, a0);
+          if (q + 1 <= lane && q + 1 < lj) a1 = fma(Li[lane + (q + 1) * lj], e1, a1);
+        }
+      }
+      const double z = a0 + a1;
+      if (lane < lj) zc[lane] = z;
+      zprev = z;
+      lp = lj;
+    }
   }
 }
 
@@ -609,9 +933,17 @@ cudaError_t launch_schur_factor(ahlp_problem *p) {
   int lmax = 0;
   for (int j = 0; j + 1 < p->N; ++j) lmax = std::max(lmax, (int)(p->link_off[j + 1] - p->link_off[j]));
   if (p->N > 1 && lmax > 0) {
-    if (p->nchain_seg > 0)
+    if (p->nchain_seg > 0 && lmax <= kChainRegL) {
+      const CArgs A = cargs(p);
+      count_launch(), chain_critical_kernel<<<p->nchain_seg, 256, (size_t)lmax * lmax * 8, s>>>(A);
+      count_launch(), chain_ops_kernel<<<p->N - 1, 128, (size_t)2 * lmax * lmax * 8, s>>>(A);
+      if (p->B > 0)
+        count_launch(), chain_z_kernel<<<(unsigned)((p->B + 7) / 8), 256, 0, s>>>(A, p->zlo,
+                                                                                   p->zhi);
+    } else if (p->nchain_seg > 0) {
       count_launch(), chain_factor_kernel<<<p->nchain_seg, 512, (size_t)lmax * lmax * 8, s>>>(
           cargs(p));
+    }
   }
   if (p->B > 0) {
     count_launch(), border_prep_kernel<<<nb((long long)p->B * p->B, 256), 256, 0, s>>>(
