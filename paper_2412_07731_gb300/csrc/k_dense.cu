@@ -548,88 +548,6 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, floa
 }
 
 constexpr int KCF = 16;   // pivot columns per staged chunk of the float-float update
-__global__ void __launch_bounds__(kThreads) pchol_update_ff_kernel(float *hi, float *lo,
-                                                                   const BlkInfo *blk, int k) {
-  const BlkInfo bi = blk[blockIdx.y];
-  if (k >= bi.Tp) return;
-  const long long t = bi.T - k - 1;
-  const long long q = blockIdx.x;
-  if (q >= t * (t + 1) / 2) return;
-  long long ii = (long long)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
-  while (ii * (ii + 1) / 2 > q) --ii;
-  while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
-  const long long jj = q - ii * (ii + 1) / 2;
-  const int I = k + 1 + (int)ii, J = k + 1 + (int)jj;
-  const int npiv = min(NB, bi.p - k * NB);
-  const int rI = I * NB, rJ = J * NB;
-  const int nrI = min(NB, bi.a - rI), nrJ = min(NB, bi.a - rJ);
-  __shared__ float Ah[KCF][NB], Al[KCF][NB], Bh[KCF][NB], Bl[KCF][NB];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float sh[4][4], sl[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.0f;
-  const long long colk = bi.base + (long long)(k * NB) * bi.lda;
-  for (int kc = 0; kc < npiv; kc += KCF) {
-    for (int idx = threadIdx.x; idx < KCF * NB; idx += blockDim.x) {
-      const int r = idx % NB, kk = idx / NB;
-      const bool kin = (kc + kk) < npiv;
-      const long long col = colk + (long long)(kc + kk) * bi.lda;
-      const bool aok = kin && r < nrI, bok = kin && r < nrJ;
-      Ah[kk][r] = aok ? hi[col + rI + r] : 0.0f;
-      Al[kk][r] = aok ? lo[col + rI + r] : 0.0f;
-      Bh[kk][r] = bok ? hi[col + rJ + r] : 0.0f;
-      Bl[kk][r] = bok ? lo[col + rJ + r] : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < KCF; ++kk) {
-      float ah[4], al[4], bh[4], bl[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        ah[i] = Ah[kk][tx + 16 * i];
-        al[i] = Al[kk][tx + 16 * i];
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        bh[j] = Bh[kk][ty + 16 * j];
-        bl[j] = Bl[kk][ty + 16 * j];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) ff_mac(sh[i][j], sl[i][j], ah[i], al[i], bh[j], bl[j]);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) ff_renorm(sh[i][j], sl[i][j]);
-    __syncthreads();
-  }
-  const long long g = bi.base + (long long)rJ * bi.lda + rI;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int c = ty + 16 * j;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = tx + 16 * i;
-      if (r < nrI && c < nrJ && (I != J || r >= c)) {
-        const long long e = g + (long long)c * bi.lda + r;
-        // (ch + cl) - (sh + sl): two-sum of the high parts, low parts added
-        const float ch = hi[e], cl = lo[e], s = sh[i][j];
-        const float tt = __fsub_rn(ch, s);
-        const float bv = __fsub_rn(tt, ch);
-        const float err = __fadd_rn(__fsub_rn(ch, __fsub_rn(tt, bv)), __fsub_rn(-s, bv));
-        const float el = __fadd_rn(err, __fsub_rn(cl, sl[i][j]));
-        const float h = __fadd_rn(tt, el);
-        hi[e] = h;
-        lo[e] = __fsub_rn(el, __fsub_rn(h, tt));
-      }
-    }
-  }
-}
-
 // trailing update: C_IJ -= L_Ik L_Jk' over the pivot columns of step k.
 constexpr int KC = 16;
 template <typename T>
@@ -819,6 +737,118 @@ __global__ void __launch_bounds__(kUpdF32Threads) pchol_update_f32_kernel(float 
 #pragma unroll
       for (int e = 0; e < 4; ++e)
         if (r + e < nrI && (!diag || r + e >= c)) col[r + e] -= acc[4 * h + e][j];
+    }
+  }
+}
+
+// Float-float trailing update with an 8x4 register tile per thread (128
+// threads per 64x64 tile): rows 4tx..4tx+3 and 32+4tx..35+4tx, columns
+// 4ty..4ty+3, read with six 16-byte shared loads per 32 multiply-adds of 12
+// FP32 operations each.  The whole panel (high and low words of both tile
+// rows, 64 KB) is requested up front with cp.async in four 16-column groups.
+constexpr int kUpdFFThreads = 128;
+constexpr size_t kUpdFFSmem = 4 * NB * NB * sizeof(float);
+
+__global__ void __launch_bounds__(kUpdFFThreads) pchol_update_ff8_kernel(float *hi, float *lo,
+                                                                        const BlkInfo *blk,
+                                                                        int k) {
+  const BlkInfo bi = blk[blockIdx.y];
+  if (k >= bi.Tp) return;
+  const long long t = bi.T - k - 1;
+  const long long q = blockIdx.x;
+  if (q >= t * (t + 1) / 2) return;
+  long long ii = (long long)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  while (ii * (ii + 1) / 2 > q) --ii;
+  while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
+  const long long jj = q - ii * (ii + 1) / 2;
+  const int I = k + 1 + (int)ii, J = k + 1 + (int)jj;
+  const int npiv = min(NB, bi.p - k * NB);
+  const int rI = I * NB, rJ = J * NB;
+  const int nrI = min(NB, bi.a - rI), nrJ = min(NB, bi.a - rJ);
+  extern __shared__ __align__(16) float ffsm[];
+  float(*Ah)[NB] = reinterpret_cast<float(*)[NB]>(ffsm);
+  float(*Al)[NB] = reinterpret_cast<float(*)[NB]>(ffsm + NB * NB);
+  float(*Bh)[NB] = reinterpret_cast<float(*)[NB]>(ffsm + 2 * NB * NB);
+  float(*Bl)[NB] = reinterpret_cast<float(*)[NB]>(ffsm + 3 * NB * NB);
+  const int tid = threadIdx.x;
+  const int tx = tid & 7, ty = tid >> 3;
+  // copies: thread moves float4 number (tid & 15) of column (tid >> 4) of a
+  // chunk, for both words of both tile rows (8 x 16-byte copies per chunk)
+  const int lv = (tid & 15) * 4, lk = tid >> 4;
+  const long long colk = bi.base + (long long)(k * NB) * bi.lda;
+  const int nchunk = (npiv + 15) / 16;
+  const int na = 4 * max(0, min(4, nrI - lv)), nb = 4 * max(0, min(4, nrJ - lv));
+#pragma unroll
+  for (int ch = 0; ch < 4; ++ch) {
+    if (ch < nchunk) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int kk = ch * 16 + lk + 8 * u;
+        const bool kin = kk < npiv;
+        const long long col = colk + (long long)(kin ? kk : 0) * bi.lda;
+        const long long oa = col + rI + (kin && na ? lv : 0);
+        const long long ob = col + rJ + (kin && nb ? lv : 0);
+        cp_async16(&Ah[kk][lv], hi + oa, kin ? na : 0);
+        cp_async16(&Al[kk][lv], lo + oa, kin ? na : 0);
+        cp_async16(&Bh[kk][lv], hi + ob, kin ? nb : 0);
+        cp_async16(&Bl[kk][lv], lo + ob, kin ? nb : 0);
+      }
+    }
+    cp_async_commit();
+  }
+  float sh[8][4], sl[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.0f;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    if (ch == 0) cp_async_wait<3>();
+    else if (ch == 1) cp_async_wait<2>();
+    else if (ch == 2) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncthreads();
+#pragma unroll 4
+    for (int kq = 0; kq < 16; ++kq) {
+      const int kk = ch * 16 + kq;
+      const float4 h0 = *reinterpret_cast<const float4 *>(&Ah[kk][4 * tx]);
+      const float4 h1 = *reinterpret_cast<const float4 *>(&Ah[kk][32 + 4 * tx]);
+      const float4 l0 = *reinterpret_cast<const float4 *>(&Al[kk][4 * tx]);
+      const float4 l1 = *reinterpret_cast<const float4 *>(&Al[kk][32 + 4 * tx]);
+      const float4 bh4 = *reinterpret_cast<const float4 *>(&Bh[kk][4 * ty]);
+      const float4 bl4 = *reinterpret_cast<const float4 *>(&Bl[kk][4 * ty]);
+      const float ah[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+      const float al[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+      const float bh[4] = {bh4.x, bh4.y, bh4.z, bh4.w};
+      const float bl[4] = {bl4.x, bl4.y, bl4.z, bl4.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ff_mac(sh[i][j], sl[i][j], ah[i], al[i], bh[j], bl[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) ff_renorm(sh[i][j], sl[i][j]);
+  }
+  const long long g = bi.base + (long long)rJ * bi.lda + rI;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = 4 * ty + j;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = (i < 4 ? 4 * tx : 32 + 4 * tx) + (i & 3);
+      if (r < nrI && c < nrJ && (I != J || r >= c)) {
+        const long long e = g + (long long)c * bi.lda + r;
+        // (ch + cl) - (sh + sl): two-sum of the high parts, low parts added
+        const float chv = hi[e], clv = lo[e], s = sh[i][j];
+        const float tt = __fsub_rn(chv, s);
+        const float bv = __fsub_rn(tt, chv);
+        const float err = __fadd_rn(__fsub_rn(chv, __fsub_rn(tt, bv)), __fsub_rn(-s, bv));
+        const float el = __fadd_rn(err, __fsub_rn(clv, sl[i][j]));
+        const float h = __fadd_rn(tt, el);
+        hi[e] = h;
+        lo[e] = __fsub_rn(el, __fsub_rn(h, tt));
+      }
     }
   }
 }
@@ -1395,8 +1425,8 @@ cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
       count_launch(), pchol_trsm_ff_kernel<<<dim3((unsigned)maxPanel, nblk), kThreads,
                                              trsm_smem<double>(), s>>>(hi, lo, info, k);
     if (maxTrail > 0)
-      count_launch(), pchol_update_ff_kernel<<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(
-          hi, lo, info, k);
+      count_launch(), pchol_update_ff8_kernel<<<dim3((unsigned)maxTrail, nblk), kUpdFFThreads,
+                                                kUpdFFSmem, s>>>(hi, lo, info, k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1471,6 +1501,9 @@ cudaError_t set_dense_smem_limits(int bytes) {
   cudaError_t e = cudaFuncSetAttribute(tinv_kernel<double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tinv_smem<double>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(pchol_update_ff8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kUpdFFSmem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(pchol_trsm_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trsm_smem<double>());
