@@ -40,6 +40,18 @@ sys.path.insert(0, ROOT)
 
 FP64_PEAK_TFLOPS = 1.25       # nominal GB300 FP64 (FMA pipes and DMMA alike)
 FP32_PEAK_TFLOPS = 74.7       # GB300 FP32 FMA, measured by the register-only probe
+HBM_FALLBACK_GBS = 6800.0     # GB300 copy bandwidth when no measured figure is present
+
+
+def measured_hbm_gbs() -> float:
+    """Copy bandwidth measured on this machine type (MEASURED_PEAKS.json beside
+    this file, key hbm_gbs), else the fallback figure."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return HBM_FALLBACK_GBS
 METRIC = "IPM iters/s & KKT solve ms at rel. gap 1e-8; mixed vs FP64 GPU path, % peak"
 
 
@@ -73,6 +85,76 @@ def block_factor_flops(lp) -> float:
             s += r + r * (r + 1)
         tot += s
     return tot
+
+
+def stage_rooflines(P, prob, lp, hbm_gbs: float):
+    """Per-stage times of one KKT factor and one preconditioner application
+    (the block solves, the Schur solve and the back-substitution, no Krylov
+    refinement) at a seeded interior point (x, z = exp(N(0,1)), seed 0), with
+    CUDA events inside the library; median of three after one warm-up.  Each
+    stage against the bound that limits it:
+      form   -- HBM: the FP32 lower tiles written (pattern reads not counted);
+      block  -- FP32 pipe: block_factor_flops against the FP32 FMA probe;
+      schur  -- FP64 latency: the link chain is sequential over the link pairs
+                and the border is small, so no throughput fraction is claimed;
+      apply  -- HBM: the FP32 block factors read twice (forward and backward
+                wavefront solves)."""
+    import numpy as np
+    import torch
+    from paper_2412_07731_gb300 import _lib as L
+    rng = np.random.default_rng(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f64 = dict(dtype=torch.float64, device=dev)
+    x = torch.tensor(np.exp(rng.standard_normal(prob.n)), **f64)
+    z = torch.tensor(np.exp(rng.standard_normal(prob.n)), **f64)
+    rp = torch.tensor(rng.standard_normal(prob.m), **f64)
+    zero = torch.zeros(prob.n, **f64)
+    saved = L.Options.from_buffer_copy(prob.options)
+    once = L.Options.from_buffer_copy(saved)
+    once.refine_max = 0
+    P.set_options(prob, once)
+    fac, sol = [], []
+    try:
+        for _ in range(4):
+            P.kkt_factor(prob, x, z)
+            fac.append(P.kkt_stage_times(prob))
+        for _ in range(4):
+            P.kkt_solve(prob, zero, rp, zero)
+            sol.append(P.kkt_stage_times(prob)["last_solve_ms"])
+    finally:
+        P.set_options(prob, saved)
+    med = lambda v: statistics.median(v[1:])
+    form_ms = med([f["form_ms"] for f in fac])
+    block_ms = med([f["block_factor_ms"] for f in fac])
+    schur_ms = med([f["schur_ms"] for f in fac])
+    apply_ms = med(sol)
+    NB = 64
+    tiles = 0
+    tri = 0
+    for i, A in enumerate(lp.A):
+        k = lp.n0 + lp.mg + (int(lp.l[i - 1]) if i > 0 else 0) + (int(lp.l[i]) if i < lp.N - 1 else 0)
+        a = A.shape[0] + k
+        t = (a + NB - 1) // NB
+        tiles += t * (t + 1) // 2
+        tri += a * (a + 1) // 2
+    form_bytes = tiles * NB * NB * 4
+    apply_bytes = 2 * tri * 4
+    flops = block_factor_flops(lp)
+    gbs = lambda b, ms: b / (ms / 1e3) / 1e9
+    return {
+        "point": "x, z = exp(N(0,1)) (seed 0); FP32 block factors",
+        "form": {"ms": form_ms, "bound": "hbm", "bytes": form_bytes,
+                 "achieved_gbs": gbs(form_bytes, form_ms),
+                 "frac": gbs(form_bytes, form_ms) / hbm_gbs},
+        "block_factor": {"ms": block_ms, "bound": "alu (FP32)", "flop": flops,
+                         "achieved_tflops": flops / (block_ms / 1e3) / 1e12,
+                         "frac": flops / (block_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
+        "schur_factor": {"ms": schur_ms, "bound": "FP64 latency (sequential link chain)"},
+        "apply": {"ms": apply_ms, "bound": "hbm", "bytes": apply_bytes,
+                  "achieved_gbs": gbs(apply_bytes, apply_ms),
+                  "frac": gbs(apply_bytes, apply_ms) / hbm_gbs},
+        "peaks": {"hbm_gbs": hbm_gbs, "fp32_tflops": FP32_PEAK_TFLOPS},
+    }
 
 
 class ClockSampler:
@@ -264,6 +346,9 @@ def run_ours(args):
                       "refine_steps_per_iteration": sum(r["refine_steps"] for r in ores) / max(oit, 1),
                       "rel_gap": ores[-1]["rel_gap"], "clocks": oclocks}
         P.set_options(prob, P.default_options(precision=headline, **opts))
+    stages = None
+    if rank == 0 and headline == P.PREC_MIXED:
+        stages = stage_rooflines(P, prob, lp, measured_hbm_gbs())
     prob.close()
 
     # end to end through the C ABI from host memory (mixed precision)
@@ -325,6 +410,7 @@ def run_ours(args):
                          "kernel": f"batched block partial Cholesky ({prec_name}; "
                                    f"pchol_potrf/trsm/update + tinv), {flops:.4g} flop per factor",
                          "peak_source": peak_src},
+            "stages": stages,
             "clocks": clocks, "gpu_launches": launches,
             "e2e": e2e, "cpu_baseline": cpu,
         }
