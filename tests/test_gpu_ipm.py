@@ -107,3 +107,29 @@ def test_centrality_correctors_keep_the_optimum(days):
         its[K] = r["iterations"]
         prob.close()
     assert its[4] <= its[0]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_inexact_directions_reach_the_same_optimum(P, prec):
+    """Directions solved to ipm_refine_tol (1e-6, the default) or to
+    refine_tol (ipm_refine_tol = 0): the same optimum, and not more Krylov
+    steps for the inexact ones."""
+    lp = random_block_lp(21, N=6, m_sizes=[90, 130, 70, 64, 100, 150],
+                         n_sizes=[135, 195, 105, 96, 150, 225], nnz_per_col=6, n0=8,
+                         w_density=0.1, l=[4, 5, 3, 6, 2], mg=2, global_nnz=6,
+                         x0_link_nnz=2, x0_global_nnz=2)
+    A, b, c = olp.assemble(lp)
+    obj = float(c @ lp.xstar)
+    pr = P.PREC_MIXED if prec == "mixed" else P.PREC_FP64
+    runs = {}
+    for tol in (0.0, 1e-6):
+        prob = P.arrowhead_lp_create(lp, P.default_options(precision=pr, ipm_refine_tol=tol))
+        (x, y, z), r = P.ipm_solve(prob)
+        assert r["status"] == 0
+        assert _rel(r["pobj"], obj) <= 1e-8
+        m = olp.measures(A, b, c, x, y, z)
+        assert m["pinf"] <= 1e-8 and m["dinf"] <= 1e-8 and m["gap"] <= 1e-8
+        runs[tol] = r
+        prob.close()
+    # the iterates differ slightly, so the step counts are compared with slack
+    assert runs[1e-6]["refine_steps"] <= 1.1 * runs[0.0]["refine_steps"] + 2
