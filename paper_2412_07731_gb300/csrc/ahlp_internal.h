@@ -204,6 +204,7 @@ struct ahlp_problem {
   double *mdot_part = nullptr;  // multi-dot partials [kMaxKrylov+1][304]
   double *gm_V = nullptr, *gm_Z = nullptr;   // Krylov bases, allocated on first use
   double *gm_coef = nullptr;    // device coefficients for multi-axpy
+  double *gm_h = nullptr;       // Arnoldi column on the device: both Gram-Schmidt passes and |w|^2
   int gm_cap = 0;               // vectors allocated in gm_Z (gm_V has one more)
   double *scal = nullptr;     // device scalars
   double *h_scal = nullptr;   // pinned host scalars
@@ -293,8 +294,11 @@ constexpr int kMaxKrylov = 64;   // cap on GMRES iterations per solve
 cudaError_t launch_mdot(ahlp_problem *p, const double *V, long long ld, int k, const double *w,
                         long long len, double *out);
 // w += sum_i coef[i] V_i   (coef in device memory)
+// w += sign * sum_i coef[i] V_i (coef on the device, fixed order over i)
 cudaError_t launch_maxpy(const double *V, long long ld, int k, const double *coef, double *w,
-                         long long len, cudaStream_t s);
+                         long long len, cudaStream_t s, double sign = 1.0);
+// w *= 1 / sqrt(*nrm2) when *nrm2 > 0, nrm2 a device scalar
+cudaError_t launch_scale_inv_norm(double *w, long long len, const double *nrm2, cudaStream_t s);
 // o = J v (Newton matrix of Sec. 2.3) or J' v
 cudaError_t launch_jmul(ahlp_problem *p, const double *vx, const double *vy, const double *vz,
                         double *ox, double *oy, double *oz, bool adjoint);

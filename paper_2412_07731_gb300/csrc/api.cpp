@@ -996,9 +996,10 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->red_part = dalloc<double>(p, 1024);
     p->mdot_part = dalloc<double>(p, (long long)(kMaxKrylov + 1) * 304);
     p->gm_coef = dalloc<double>(p, kMaxKrylov + 1);
+    p->gm_h = dalloc<double>(p, 2 * (kMaxKrylov + 1) + 1);
     p->scal = dalloc<double>(p, 64);
     p->status = dalloc<int>(p, 8);
-    ck(cudaMallocHost(&p->h_scal, 256 * sizeof(double)), "cudaMallocHost");
+    ck(cudaMallocHost(&p->h_scal, 512 * sizeof(double)), "cudaMallocHost");
     for (auto &e : p->ev) ck(cudaEventCreate(&e), "cudaEventCreate");
     ck(set_dense_smem_limits((int)kSmemVecBytes), "smem limit");
     ck(set_schur_smem_limits(128 * 128 * 8), "smem limit");
@@ -1216,7 +1217,7 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
       p->gm_cap = kmax;
     }
     double *V = p->gm_V, *Z = p->gm_Z;
-    double *hbuf = p->h_scal + 64, *cbuf = p->h_scal + 64 + kMaxKrylov + 1;
+    double *cbuf = p->h_scal + 64, *hcol = p->h_scal + 256;
     ck(cudaMemcpyAsync(V, p->res[0], n * 8, cudaMemcpyDeviceToDevice, s), "copy");
     ck(cudaMemcpyAsync(V + n, p->res[1], m * 8, cudaMemcpyDeviceToDevice, s), "copy");
     ck(cudaMemcpyAsync(V + n + m, p->res[2], n * 8, cudaMemcpyDeviceToDevice, s), "copy");
@@ -1229,24 +1230,23 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
       ck(launch_solve(p, Vj, Vj + n, Vj + n + m, Zj, Zj + n, Zj + n + m, adjoint), "precond");
       ck(launch_jmul(p, Zj, Zj + n, Zj + n + m, W, W + n, W + n + m, adjoint), "jmul");
       double *h = &H[(size_t)j * (kc + 1)];
-      for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
-        ck(launch_mdot(p, V, L, j + 1, W, L, p->gm_coef), "mdot");
-        p->bytes_d2h += (j + 1) * 8;
-        ck(cudaMemcpyAsync(hbuf, p->gm_coef, (j + 1) * 8, cudaMemcpyDeviceToHost, s), "D2H");
-        ck(cudaStreamSynchronize(s), "sync");
-        for (int i = 0; i <= j; ++i) {
-          h[i] += hbuf[i];
-          cbuf[i] = -hbuf[i];
-        }
-        p->bytes_h2d += (j + 1) * 8;
-        ck(cudaMemcpyAsync(p->gm_coef, cbuf, (j + 1) * 8, cudaMemcpyHostToDevice, s), "H2D");
-        ck(launch_maxpy(V, L, j + 1, p->gm_coef, W, L, s), "maxpy");
-      }
-      ck(launch_reduce(p, RED_DOT, W, W, L, p->scal + 16), "reduce");
-      read_scalars(p, 17);
-      const double hn = std::sqrt(p->h_scal[16]);
+      // classical Gram-Schmidt, twice, and the normalisation, all on the
+      // device (the coefficients never leave it in between); the host reads
+      // the column once per step, for the Givens update and the stopping test
+      const int nh = j + 1;
+      double *gh = p->gm_h;
+      ck(launch_mdot(p, V, L, nh, W, L, gh), "mdot");
+      ck(launch_maxpy(V, L, nh, gh, W, L, s, -1.0), "maxpy");
+      ck(launch_mdot(p, V, L, nh, W, L, gh + nh), "mdot");
+      ck(launch_maxpy(V, L, nh, gh + nh, W, L, s, -1.0), "maxpy");
+      ck(launch_reduce(p, RED_DOT, W, W, L, gh + 2 * nh), "reduce");
+      ck(launch_scale_inv_norm(W, L, gh + 2 * nh, s), "scale");
+      p->bytes_d2h += (2 * nh + 1) * 8;
+      ck(cudaMemcpyAsync(hcol, gh, (2 * nh + 1) * 8, cudaMemcpyDeviceToHost, s), "D2H");
+      ck(cudaStreamSynchronize(s), "sync");
+      for (int i = 0; i <= j; ++i) h[i] = (h[i] + hcol[i]) + hcol[nh + i];
+      const double hn = std::sqrt(hcol[2 * nh]);
       h[j + 1] = hn;
-      if (hn > 0) ck(launch_axpby(W, W, 1.0 / hn, 0.0, L, s), "scale");
       for (int i = 0; i < j; ++i) {   // previous Givens rotations
         const double t = cs[i] * h[i] + sn[i] * h[i + 1];
         h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];

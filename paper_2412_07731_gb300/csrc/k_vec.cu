@@ -208,13 +208,21 @@ __global__ void __launch_bounds__(kRedThreads) mdot_stage2(const double *part, i
 }
 
 // w[e] += sum_i coef[i] V_i[e], fixed order over i
-__global__ void maxpy_k(const double *V, long long ld, int k, const double *coef, double *w,
-                        long long len) {
+__global__ void maxpy_k(const double *V, long long ld, int k, const double *coef, double sc,
+                        double *w, long long len) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= len) return;
   double acc = w[e];
-  for (int i = 0; i < k; ++i) acc = fma(coef[i], V[(long long)i * ld + e], acc);
+  for (int i = 0; i < k; ++i) acc = fma(sc * coef[i], V[(long long)i * ld + e], acc);
   w[e] = acc;
+}
+
+// w *= 1 / sqrt(*nrm2) when *nrm2 > 0 (the norm stays on the device)
+__global__ void scale_inv_norm_k(double *w, long long len, const double *nrm2) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double q = *nrm2;
+  if (e >= len || !(q > 0.0)) return;
+  w[e] = (1.0 / sqrt(q)) * w[e];
 }
 
 // J v tail: oz = z vx + x vz (Newton), oz = vx + x vz (transposed); ox += z vz (transposed)
@@ -243,9 +251,15 @@ cudaError_t launch_mdot(ahlp_problem *p, const double *V, long long ld, int k, c
 }
 
 cudaError_t launch_maxpy(const double *V, long long ld, int k, const double *coef, double *w,
-                         long long len, cudaStream_t s) {
+                         long long len, cudaStream_t s, double sign) {
   if (k <= 0 || len <= 0) return cudaSuccess;
-  count_launch(), maxpy_k<<<blocks_for(len, 256), 256, 0, s>>>(V, ld, k, coef, w, len);
+  count_launch(), maxpy_k<<<blocks_for(len, 256), 256, 0, s>>>(V, ld, k, coef, sign, w, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_inv_norm(double *w, long long len, const double *nrm2, cudaStream_t s) {
+  if (len <= 0) return cudaSuccess;
+  count_launch(), scale_inv_norm_k<<<blocks_for(len, 256), 256, 0, s>>>(w, len, nrm2);
   return cudaGetLastError();
 }
 
