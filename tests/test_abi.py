@@ -121,3 +121,38 @@ def test_valid_problem_without_gpu_reports_cuda_error():
     assert st == -8
     st, msg = _create_status(_small_lp(), batch=3)   # a valid batch also gets that far
     assert st == -8
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of the C structs have the header's sizes
+    and field offsets (a C program compiled against include/ahlp.h prints
+    them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    L = _lib()
+    pairs = [("ahlp_csc", L.CSC), ("ahlp_desc", L.Desc), ("ahlp_options", L.Options),
+             ("ahlp_result", L.Result), ("ahlp_solve_info", L.SolveInfo)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ahlp.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in pairs:
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
