@@ -233,12 +233,12 @@ int arrowhead_lp_set_cb(ahlp_problem *p, const double *c, const double *b);
  *   (b) one batched partial Cholesky of all augmented matrices over their
  *       first m_i pivots, which leaves Y_i' = (L_i^-1 G_i)' below the factor
  *       and the Schur contribution C_i - G_i' M_i^-1 G_i in the corner
- *       (Alg. 1 / Alg. 2 lines 1-2; the partial-factorisation idea of
- *       Sec. 3.2);
+ *       (Alg. 1, and the block factorisation and Schur-contribution steps
+ *       of Alg. 2; the partial-factorisation idea of Sec. 3.2);
  *   (c) fixed-order summation of the contributions into the block-
  *       tridiagonal-plus-border Schur complement of App. A, its block
  *       Cholesky along the link chain and the quasi-definite border factor
- *       (Alg. 2 lines 3-4).
+ *       (the Schur-complement assembly and factorisation of Alg. 2).
  *   x, z : [n_total], strictly positive (host or device)
  *   delta, rho : regularisation for this factor (negative = use options)
  * Returns AHLP_ERR_INVALID_ARG if some x or z is not > 0, AHLP_ERR_NOT_SPD if
@@ -304,7 +304,7 @@ int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld);
  * kkt_block_factor_dense -- diagnostic: copy block i's augmented matrix after
  * the last kkt_factor (its partial Cholesky over the first m_i pivots:
  * L_i on top, Y_i' below it, the Schur contribution C_i - G_i' M_i^-1 G_i in
- * the corner; Alg. 2 lines 1-2) into host memory as a dense column-major
+ * the corner; the block steps of Alg. 2) into host memory as a dense column-major
  * a x a lower triangle, a = m_i + k_i (the upper triangle is zeroed).
  *   block : 0 <= block < N;  A : host buffer of ld * a doubles;  ld >= a
  *   order : receives a (may be NULL)

@@ -137,7 +137,7 @@ T *dupload(ahlp_problem *p, const std::vector<T> &h) {
 }
 
 // ---------------------------------------------------------------------------
-// formation pattern of one block (Alg. 2 line 1 in normal-equation form):
+// formation pattern of one block (the block step of Alg. 2 in normal-equation form):
 // entries of M_i, G_i' and C_i as sums coef * d[j] (j = -1: constant 1)
 // ---------------------------------------------------------------------------
 struct Con {

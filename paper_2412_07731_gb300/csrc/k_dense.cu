@@ -4,13 +4,16 @@
 // Every block i owns an augmented lower-triangular matrix
 //     [ M_i   .  ]        M_i = A_i D_i A_i' + delta I      (m_i x m_i)
 //     [ G_i'  C_i]        G_i = [W_i | A_i D_i U_i' | A_i D_i Fg_i']
-// stored column-major.  Eliminating its first m_i pivots (Alg. 2 lines 1-2
-// in normal-equation form) leaves L_i on top, Y_i' = (L_i^-1 G_i)' below it
-// and C_i - G_i' M_i^-1 G_i in the corner -- the block's Schur contribution.
+// stored column-major.  Eliminating its first m_i pivots (the block factor and
+// Schur-contribution steps of Alg. 2 in normal-equation form) leaves L_i on
+// top, Y_i' = (L_i^-1 G_i)' below it and C_i - G_i' M_i^-1 G_i in the corner
+// -- the block's Schur contribution.
 //
-// All kernels are templated on the storage type of the factor: double (FP64
-// mode) or float (mixed mode, where the factor only preconditions an FP64
-// Krylov solve).  Entries are always formed in FP64 and rounded once.
+// The factor is stored in FP64, FP32 or float-float (two FP32 words); in the
+// mixed modes it only preconditions an FP64 Krylov solve.  Kernels shared by
+// FP64 and FP32 are templated on the storage type; the FP32 and float-float
+// trailing updates and the FP32 diagonal tile have their own kernels.
+// Entries are always formed in FP64 and rounded once.
 #include <math.h>
 
 #include "ahlp_internal.h"
