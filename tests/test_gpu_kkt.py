@@ -60,6 +60,9 @@ SHAPES = {
     # link blocks above 32 rows take the general one-CTA link chain
     "long_links": dict(N=3, m_sizes=[90, 80, 100], n_sizes=[140, 130, 150], nnz_per_col=5,
                        n0=6, w_density=0.1, l=[40, 33], mg=2, global_nnz=5),
+    # a small link block inside a chain that takes the general kernel
+    "mixed_links": dict(N=4, m_sizes=[90, 60, 80, 100], n_sizes=[140, 95, 130, 150],
+                        nnz_per_col=5, n0=6, w_density=0.1, l=[40, 8, 33], mg=2, global_nnz=5),
     # link blocks of exactly 32 rows (the register path's limit) next to a 1-row one
     "links_32": dict(N=4, m_sizes=[70, 64, 75, 66], n_sizes=[110, 100, 120, 100],
                      nnz_per_col=5, n0=5, w_density=0.1, l=[32, 1, 32], mg=1, global_nnz=4),
