@@ -112,7 +112,8 @@ typedef struct {
                            d = x / (z + rho x)) (0); ipm_solve raises it from
                            1e-10 up to 1e-6 when a NaN persists after the other
                            safeguards                                           */
-  int32_t refine_max;   /* GMRES iterations per KKT solve, at most 64 (40)        */
+  int32_t refine_max;   /* FGMRES iterations per KKT solve, at most 64, counted
+                           over restarts (40)                                     */
   double  refine_tol;   /* target relative Newton residual (1e-10)                */
   double  pivot_tol;    /* a pivot not above pivot_tol * (its diagonal before
                            elimination) has lost its digits to cancellation and
@@ -255,7 +256,10 @@ int kkt_factor(ahlp_problem *p, const double *x, const double *z, double delta, 
  * dz = X^-1 (r_c - Z dx) (the elimination of Sec. 2.3).  When the relative
  * residual of the unregularised Newton system is still above refine_tol,
  * right-preconditioned FGMRES on that system (the block solve above as the
- * preconditioner) runs for at most refine_max iterations.
+ * preconditioner) runs for at most refine_max iterations; when the true
+ * residual after a cycle is still above refine_tol (the cycle's own estimate
+ * can run ahead of it), the method restarts from it while each cycle at
+ * least halves it.
  *   r_d [n_total], r_p [m_total], r_c [n_total] : right-hand side
  *   dx [n_total], dy [m_total], dz [n_total]    : output (caller-allocated)
  *   info : optional (NULL allowed)

@@ -48,14 +48,16 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     // refinement (the degenerate end game, where the clamped factors stop
     // being a good preconditioner) moves the blocks one precision up, else makes
     // the threshold 100x coarser (up to kMaxPivotTol).  A NaN in the factor or
-    // in the direction does the same and, once those are exhausted, raises
-    // the regularisation 100x (up to kMaxDelta) and then regularises D itself,
-    // d = x / (z + rho_x x) with rho_x from kMinRhoX up to kMaxRhoX, which bounds
-    // the factor's conditioning when complementarity products collapse.  The
-    // Krylov refinement always solves the unregularised Newton system, so all
-    // this only weakens the preconditioner.  A NaN pivot that passed the threshold is one that lost
-    // nearly all its digits to cancellation; its rounding noise is amplified
-    // through the later clamped columns.
+    // in the direction does the same, except that a float-float factor first
+    // gets delta 100x larger (up to kFFMaxDelta); once those are exhausted it
+    // raises the regularisation 100x (up to kMaxDelta) and then regularises D
+    // itself, d = x / (z + rho_x x) with rho_x from kMinRhoX up to kMaxRhoX,
+    // which bounds the factor's conditioning when complementarity products
+    // collapse.  The Krylov refinement always solves the unregularised Newton
+    // system, so all this only weakens the preconditioner.  A NaN pivot that
+    // passed the threshold is one that lost nearly all its digits to
+    // cancellation; its rounding noise is amplified through the later clamped
+    // columns.
     constexpr double kEscalate = 1e-6, kMaxPivotTol = 1e-8, kMaxDelta = 1e-4;
     constexpr double kMinRhoX = 1e-10, kMaxRhoX = 1e-6;
     // a float-float factor that breaks down (its FP32 exponent range is
