@@ -9,6 +9,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <utility>
 #include <vector>
@@ -763,26 +764,67 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     for (int v : l)
       if (v > 96) fail(AHLP_ERR_UNSUPPORTED, "more than 96 local link rows per block pair");
     // ---- formation patterns --------------------------------------------------
+    // Independent per block: built on host threads into block-local patterns,
+    // then concatenated in block order, so the result does not depend on the
+    // thread count.  A failure reports the first failing block, as a
+    // sequential pass would.
+    std::vector<Pattern> part(N);
+    std::vector<int> pcode(N, 0);
+    std::vector<std::string> pmsg(N);
+    auto one_block = [&](int i) {
+      try {
+        std::vector<URow> urows(p->ki[i] - bx0n[i]);
+        auto rows_of = [&](const Csc &F, int off, int shift, int nrows) {
+          for (int j = 0; j < F.n; ++j)
+            for (int q = F.cp[j]; q < F.cp[j + 1]; ++q) {
+              const int r = F.ri[q] - shift;
+              if (r < 0 || r >= nrows)
+                fail(AHLP_ERR_INVALID_ARG, "block " + std::to_string(i) + ": a global row outside its LP");
+              urows[off + r].j.push_back(j);
+              urows[off + r].u.push_back(F.v[q]);
+            }
+        };
+        if (i > 0) rows_of(FR[i - 1], 0, 0, p->lprev[i]);
+        if (i + 1 < N) rows_of(FL[i], p->lprev[i], 0, p->lnext[i]);
+        rows_of(Fg[i], p->lprev[i] + p->lnext[i], bglo[i], bgn[i]);
+        for (int t = 0; t < n0; ++t)
+          if ((t < bx0lo[i] || t >= bx0lo[i] + bx0n[i]) && W[i].cp[t + 1] > W[i].cp[t])
+            fail(AHLP_ERR_INVALID_ARG, "block " + std::to_string(i) + ": a linking variable outside its LP");
+        build_block_pattern(i, A[i], W[i], urows, bx0lo[i], bx0n[i], A[i].m, p->ki[i], p->xoff[i],
+                            part[i]);
+      } catch (const Fail &f) {
+        pcode[i] = f.code;
+        pmsg[i] = f.msg;
+      } catch (const std::bad_alloc &) {
+        pcode[i] = AHLP_ERR_OOM;
+        pmsg[i] = "host memory exhausted while building the formation pattern";
+      }
+    };
+    {
+      const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+      const int nthr = (int)std::min<long long>(N, std::min(16u, hw));
+      std::atomic<int> next{0};
+      auto worker = [&]() {
+        for (int i = next++; i < N; i = next++) one_block(i);
+      };
+      std::vector<std::thread> pool;
+      for (int t = 1; t < nthr; ++t) pool.emplace_back(worker);
+      worker();
+      for (auto &th : pool) th.join();
+    }
+    for (int i = 0; i < N; ++i)
+      if (pcode[i]) fail(pcode[i], pmsg[i]);
     Pattern P;
     for (int i = 0; i < N; ++i) {
-      std::vector<URow> urows(p->ki[i] - bx0n[i]);
-      auto rows_of = [&](const Csc &F, int off, int shift, int nrows) {
-        for (int j = 0; j < F.n; ++j)
-          for (int q = F.cp[j]; q < F.cp[j + 1]; ++q) {
-            const int r = F.ri[q] - shift;
-            if (r < 0 || r >= nrows)
-              fail(AHLP_ERR_INVALID_ARG, "block " + std::to_string(i) + ": a global row outside its LP");
-            urows[off + r].j.push_back(j);
-            urows[off + r].u.push_back(F.v[q]);
-          }
-      };
-      if (i > 0) rows_of(FR[i - 1], 0, 0, p->lprev[i]);
-      if (i + 1 < N) rows_of(FL[i], p->lprev[i], 0, p->lnext[i]);
-      rows_of(Fg[i], p->lprev[i] + p->lnext[i], bglo[i], bgn[i]);
-      for (int t = 0; t < n0; ++t)
-        if ((t < bx0lo[i] || t >= bx0lo[i] + bx0n[i]) && W[i].cp[t + 1] > W[i].cp[t])
-          fail(AHLP_ERR_INVALID_ARG, "block " + std::to_string(i) + ": a linking variable outside its LP");
-      build_block_pattern(i, A[i], W[i], urows, bx0lo[i], bx0n[i], A[i].m, p->ki[i], p->xoff[i], P);
+      Pattern &q = part[i];
+      const long long eb = (long long)P.ent_pos.size(), cb = (long long)P.con_idx.size();
+      P.tiles.insert(P.tiles.end(), q.tiles.begin(), q.tiles.end());
+      for (long long v : q.tile_ent) P.tile_ent.push_back(v + eb);
+      P.ent_pos.insert(P.ent_pos.end(), q.ent_pos.begin(), q.ent_pos.end());
+      for (long long v : q.ent_cb) P.ent_cb.push_back(v + cb);
+      P.con_idx.insert(P.con_idx.end(), q.con_idx.begin(), q.con_idx.end());
+      P.con_coef.insert(P.con_coef.end(), q.con_coef.begin(), q.con_coef.end());
+      q = Pattern();
     }
     P.tile_ent.push_back((long long)P.ent_pos.size());
     P.ent_cb.push_back((long long)P.con_idx.size());
