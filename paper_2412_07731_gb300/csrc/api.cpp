@@ -645,8 +645,9 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
         vv[pos] = V[k];
       }
       // sort columns within rows (sum order of the mat-vec is then fixed)
+      std::vector<std::pair<int, double>> row;
       for (long long r = 0; r < rows; ++r) {
-        std::vector<std::pair<int, double>> row;
+        row.clear();
         for (int q = rp[r]; q < rp[r + 1]; ++q) row.push_back({ci[q], vv[q]});
         std::sort(row.begin(), row.end(),
                   [](const std::pair<int, double> &x, const std::pair<int, double> &y) {
