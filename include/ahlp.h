@@ -45,7 +45,7 @@ extern "C" {
 #define AHLP_OK                   0
 #define AHLP_ERR_INVALID_ARG     -1  /* NaN/Inf, negative size, bad index, NULL where required */
 #define AHLP_ERR_DIM_MISMATCH    -2  /* block sizes disagree with each other                 */
-#define AHLP_ERR_UNSUPPORTED     -3  /* finite upper bounds, lower bounds != 0, batch > 1 ... */
+#define AHLP_ERR_UNSUPPORTED     -3  /* finite upper bounds, lower bounds != 0, size limits  */
 #define AHLP_ERR_NOT_SPD         -4  /* a pivot became NaN / negative beyond repair            */
 #define AHLP_ERR_REFINE_FAIL     -5  /* refinement did not reach refine_tol                    */
 #define AHLP_ERR_MAX_ITER        -6  /* ipm_solve hit max_iter                                 */
