@@ -156,6 +156,21 @@ struct Pattern {
   std::vector<double> con_coef;
 };
 
+// fn(i) for i in [0, n) on up to 16 host threads (work taken in index order)
+template <class F>
+void parallel_for(int n, F fn) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nthr = (int)std::min<long long>(n, std::min(16u, hw));
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (int i = next++; i < n; i = next++) fn(i);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nthr; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto &th : pool) th.join();
+}
+
 struct URow {   // one link / global row restricted to the block's columns
   std::vector<int> j;
   std::vector<double> u;
@@ -200,7 +215,22 @@ void build_block_pattern(int blk, const Csc &A, const Csc &W, const std::vector<
       for (size_t y = 0; y <= x; ++y)
         add(m + ucol[j][x].first, m + ucol[j][y].first, (int)(xoff + j),
             ucol[j][x].second * ucol[j][y].second);
-  std::stable_sort(cons.begin(), cons.end(), [](const Con &x, const Con &y) { return x.key < y.key; });
+  // stable sort by key = tile id * NB*NB + position in the tile: two stable
+  // counting passes (position, then tile), the same order as a stable
+  // comparison sort in linear time
+  {
+    const long long ntile = (long long)T * (T + 1) / 2;
+    std::vector<Con> tmp(cons.size());
+    std::vector<long long> cnt((size_t)std::max<long long>(ntile, NB * NB) + 1);
+    auto pass = [&](std::vector<Con> &src, std::vector<Con> &dst, long long nb, auto digit) {
+      std::fill(cnt.begin(), cnt.begin() + nb + 1, 0);
+      for (const Con &x : src) ++cnt[digit(x) + 1];
+      for (long long d = 0; d < nb; ++d) cnt[d + 1] += cnt[d];
+      for (const Con &x : src) dst[cnt[digit(x)]++] = x;
+    };
+    pass(cons, tmp, NB * NB, [](const Con &x) { return x.key % (NB * NB); });
+    pass(tmp, cons, ntile, [](const Con &x) { return x.key / (NB * NB); });
+  }
   // tiles in id order (J-major lower), entries grouped by key
   size_t c = 0;
   for (int Jt = 0; Jt < T; ++Jt)
@@ -801,32 +831,33 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
         pmsg[i] = "host memory exhausted while building the formation pattern";
       }
     };
-    {
-      const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-      const int nthr = (int)std::min<long long>(N, std::min(16u, hw));
-      std::atomic<int> next{0};
-      auto worker = [&]() {
-        for (int i = next++; i < N; i = next++) one_block(i);
-      };
-      std::vector<std::thread> pool;
-      for (int t = 1; t < nthr; ++t) pool.emplace_back(worker);
-      worker();
-      for (auto &th : pool) th.join();
-    }
+    parallel_for(N, one_block);
     for (int i = 0; i < N; ++i)
       if (pcode[i]) fail(pcode[i], pmsg[i]);
-    Pattern P;
+    // concatenation at precomputed offsets, also on the threads
+    std::vector<long long> tb(N + 1, 0), eb(N + 1, 0), cb(N + 1, 0);
     for (int i = 0; i < N; ++i) {
-      Pattern &q = part[i];
-      const long long eb = (long long)P.ent_pos.size(), cb = (long long)P.con_idx.size();
-      P.tiles.insert(P.tiles.end(), q.tiles.begin(), q.tiles.end());
-      for (long long v : q.tile_ent) P.tile_ent.push_back(v + eb);
-      P.ent_pos.insert(P.ent_pos.end(), q.ent_pos.begin(), q.ent_pos.end());
-      for (long long v : q.ent_cb) P.ent_cb.push_back(v + cb);
-      P.con_idx.insert(P.con_idx.end(), q.con_idx.begin(), q.con_idx.end());
-      P.con_coef.insert(P.con_coef.end(), q.con_coef.begin(), q.con_coef.end());
-      q = Pattern();
+      tb[i + 1] = tb[i] + (long long)part[i].tiles.size();
+      eb[i + 1] = eb[i] + (long long)part[i].ent_pos.size();
+      cb[i + 1] = cb[i] + (long long)part[i].con_idx.size();
     }
+    Pattern P;
+    P.tiles.resize(tb[N]);
+    P.tile_ent.resize(tb[N]);
+    P.ent_pos.resize(eb[N]);
+    P.ent_cb.resize(eb[N]);
+    P.con_idx.resize(cb[N]);
+    P.con_coef.resize(cb[N]);
+    parallel_for(N, [&](int i) {
+      Pattern &q = part[i];
+      std::copy(q.tiles.begin(), q.tiles.end(), P.tiles.begin() + tb[i]);
+      for (size_t t = 0; t < q.tile_ent.size(); ++t) P.tile_ent[tb[i] + t] = q.tile_ent[t] + eb[i];
+      std::copy(q.ent_pos.begin(), q.ent_pos.end(), P.ent_pos.begin() + eb[i]);
+      for (size_t t = 0; t < q.ent_cb.size(); ++t) P.ent_cb[eb[i] + t] = q.ent_cb[t] + cb[i];
+      std::copy(q.con_idx.begin(), q.con_idx.end(), P.con_idx.begin() + cb[i]);
+      std::copy(q.con_coef.begin(), q.con_coef.end(), P.con_coef.begin() + cb[i]);
+      q = Pattern();
+    });
     P.tile_ent.push_back((long long)P.ent_pos.size());
     P.ent_cb.push_back((long long)P.con_idx.size());
     p->ntiles = (long long)P.tiles.size();
