@@ -182,6 +182,20 @@ void build_block_pattern(int blk, const Csc &A, const Csc &W, const std::vector<
   const int T = (a + NB - 1) / NB;
   auto tile_id = [T](long long It, long long Jt) { return Jt * T - Jt * (Jt - 1) / 2 + (It - Jt); };
   std::vector<Con> cons;
+  {   // exact count of the contributions below, so the buffer is allocated once
+    long long nc = m + (long long)(W.cp[x0lo + x0n] - W.cp[x0lo]);
+    std::vector<int> uc(A.n, 0);
+    for (const URow &u : urows)
+      for (int j : u.j) {
+        nc += A.cp[j + 1] - A.cp[j];
+        ++uc[j];
+      }
+    for (int j = 0; j < A.n; ++j) {
+      const long long d = A.cp[j + 1] - A.cp[j];
+      nc += d * (d + 1) / 2 + (long long)uc[j] * (uc[j] + 1) / 2;
+    }
+    cons.reserve((size_t)nc);
+  }
   auto add = [&](int R, int C, int didx, double coef) {
     if (R < C) std::swap(R, C);
     const long long key = tile_id(R / NB, C / NB) * (long long)(NB * NB) + (long long)(C % NB) * NB +
@@ -674,20 +688,26 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
         ci[pos] = (int)cc[k];
         vv[pos] = V[k];
       }
-      // sort columns within rows (sum order of the mat-vec is then fixed)
-      std::vector<std::pair<int, double>> row;
-      for (long long r = 0; r < rows; ++r) {
-        row.clear();
-        for (int q = rp[r]; q < rp[r + 1]; ++q) row.push_back({ci[q], vv[q]});
-        std::sort(row.begin(), row.end(),
-                  [](const std::pair<int, double> &x, const std::pair<int, double> &y) {
-                    return x.first < y.first;
-                  });
-        for (int q = rp[r]; q < rp[r + 1]; ++q) {
-          ci[q] = row[q - rp[r]].first;
-          vv[q] = row[q - rp[r]].second;
+      // sort columns within rows (sum order of the mat-vec is then fixed);
+      // rows are independent, so chunks of them go to the host threads
+      constexpr long long kChunk = 4096;
+      const int nchunk = (int)((rows + kChunk - 1) / kChunk);
+      parallel_for(nchunk, [&](int ch) {
+        std::vector<std::pair<int, double>> row;
+        const long long r1 = std::min(rows, (ch + 1) * kChunk);
+        for (long long r = ch * kChunk; r < r1; ++r) {
+          row.clear();
+          for (int q = rp[r]; q < rp[r + 1]; ++q) row.push_back({ci[q], vv[q]});
+          std::sort(row.begin(), row.end(),
+                    [](const std::pair<int, double> &x, const std::pair<int, double> &y) {
+                      return x.first < y.first;
+                    });
+          for (int q = rp[r]; q < rp[r + 1]; ++q) {
+            ci[q] = row[q - rp[r]].first;
+            vv[q] = row[q - rp[r]].second;
+          }
         }
-      }
+      });
     };
     std::vector<int> Arp, Aci, ATrp, ATci;
     std::vector<double> Av, ATv;
