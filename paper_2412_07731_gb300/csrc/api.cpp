@@ -126,6 +126,25 @@ T *dalloc(ahlp_problem *p, long long count) {
   return reinterpret_cast<T *>(ptr);
 }
 
+// the concatenation of member `f` of every part, uploaded part by part
+template <class P, class T>
+T *dupload_parts(ahlp_problem *p, const std::vector<P> &parts, std::vector<T> P::*f) {
+  long long total = 0;
+  for (const P &q : parts) total += (long long)(q.*f).size();
+  T *d = dalloc<T>(p, total);
+  long long off = 0;
+  for (const P &q : parts) {
+    const std::vector<T> &h = q.*f;
+    if (!h.empty()) {
+      cudaError_t e = cudaMemcpy(d + off, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+      p->bytes_h2d += (long long)(h.size() * sizeof(T));
+      if (e != cudaSuccess) fail(AHLP_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+    off += (long long)h.size();
+  }
+  return d;
+}
+
 template <class T>
 T *dupload(ahlp_problem *p, const std::vector<T> &h) {
   T *d = dalloc<T>(p, (long long)h.size());
@@ -604,17 +623,34 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     // ---- blocks -----------------------------------------------------------
     std::vector<Csc> A(N), W(N), Fg(N), FL(N > 1 ? N - 1 : 0), FR(FL.size()), F0(FL.size());
     std::vector<std::vector<double>> b(N), c(N), blink(FL.size());
-    for (int i = 0; i < N; ++i) {
-      const std::string tag = "block " + std::to_string(i);
-      if (D.A[i].m < 0 || D.A[i].n < 0) fail(AHLP_ERR_INVALID_ARG, tag + ": negative size");
-      A[i] = canon(&D.A[i], D.A[i].m, D.A[i].n, tag + " A");
-      W[i] = canon(&D.W[i], A[i].m, n0, tag + " W");
-      Fg[i] = canon(D.Fg ? &D.Fg[i] : nullptr, mg, A[i].n, tag + " Fg");
-      b[i] = vec_in(D.b[i], A[i].m, tag + " b");
-      c[i] = vec_in(D.c[i], A[i].n, tag + " c");
-      check_bounds(D.lb ? D.lb[i] : nullptr, D.ub ? D.ub[i] : nullptr, A[i].n, tag);
-      p->mi.push_back(A[i].m);
-      p->ni.push_back(A[i].n);
+    {   // blocks are independent: validated on host threads, the first failing
+        // block reported (as a sequential pass would)
+      std::vector<int> vcode(N, 0);
+      std::vector<std::string> vmsg(N);
+      parallel_for(N, [&](int i) {
+        try {
+          const std::string tag = "block " + std::to_string(i);
+          if (D.A[i].m < 0 || D.A[i].n < 0) fail(AHLP_ERR_INVALID_ARG, tag + ": negative size");
+          A[i] = canon(&D.A[i], D.A[i].m, D.A[i].n, tag + " A");
+          W[i] = canon(&D.W[i], A[i].m, n0, tag + " W");
+          Fg[i] = canon(D.Fg ? &D.Fg[i] : nullptr, mg, A[i].n, tag + " Fg");
+          b[i] = vec_in(D.b[i], A[i].m, tag + " b");
+          c[i] = vec_in(D.c[i], A[i].n, tag + " c");
+          check_bounds(D.lb ? D.lb[i] : nullptr, D.ub ? D.ub[i] : nullptr, A[i].n, tag);
+        } catch (const Fail &f) {
+          vcode[i] = f.code;
+          vmsg[i] = f.msg;
+        } catch (const std::bad_alloc &) {
+          vcode[i] = AHLP_ERR_OOM;
+          vmsg[i] = "host memory exhausted while reading block " + std::to_string(i);
+        }
+      });
+      for (int i = 0; i < N; ++i)
+        if (vcode[i]) fail(vcode[i], vmsg[i]);
+      for (int i = 0; i < N; ++i) {
+        p->mi.push_back(A[i].m);
+        p->ni.push_back(A[i].n);
+      }
     }
     check_bounds(D.lb0, D.ub0, n0, "x0");
     std::vector<int> l(FL.size());
@@ -650,69 +686,84 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->m = p->msum + p->nl + mg;
     p->nS = p->nl + p->B;
     // ---- monolithic A (CSR) and A' (CSR) for residuals ------------------------
-    std::vector<long long> R, C;
-    std::vector<double> V;
-    auto put = [&](const Csc &M, long long r0, long long c0_) {
-      for (int j = 0; j < M.n; ++j)
-        for (int q = M.cp[j]; q < M.cp[j + 1]; ++q) {
-          R.push_back(r0 + M.ri[q]);
-          C.push_back(c0_ + j);
-          V.push_back(M.v[q]);
-        }
-    };
+    // A's rows are counted, then filled, visiting the blocks in a fixed order
+    // in which every row receives its columns in increasing order (block
+    // columns, then linking variables), so its rows come out sorted.  A' is
+    // A's transpose by one more counting pass, sorted by construction.
     const long long grow0 = p->msum + p->nl;
-    for (int i = 0; i < N; ++i) {
-      put(A[i], p->yoff[i], p->xoff[i]);
-      put(W[i], p->yoff[i], p->xoff[N]);
-      put(Fg[i], grow0, p->xoff[i]);
-    }
-    for (size_t j = 0; j < FL.size(); ++j) {
-      put(FL[j], p->msum + p->link_off[j], p->xoff[j]);
-      put(FR[j], p->msum + p->link_off[j], p->xoff[j + 1]);
-      put(F0[j], p->msum + p->link_off[j], p->xoff[N]);
-    }
-    put(Fg0, grow0, p->xoff[N]);
-    const long long nnz = (long long)V.size();
-    if (nnz >= (1LL << 31)) fail(AHLP_ERR_UNSUPPORTED, "more than 2^31 nonzeros");
-    auto to_csr = [&](const std::vector<long long> &rr, const std::vector<long long> &cc,
-                      long long rows, std::vector<int> &rp, std::vector<int> &ci,
-                      std::vector<double> &vv) {
-      rp.assign(rows + 1, 0);
-      for (long long k = 0; k < nnz; ++k) rp[rr[k] + 1]++;
-      for (long long r = 0; r < rows; ++r) rp[r + 1] += rp[r];
-      std::vector<int> fill(rp.begin(), rp.end() - 1);
-      ci.resize(nnz);
-      vv.resize(nnz);
-      for (long long k = 0; k < nnz; ++k) {   // stable: keeps input order within a row
-        const int pos = fill[rr[k]]++;
-        ci[pos] = (int)cc[k];
-        vv[pos] = V[k];
+    auto visit = [&](auto &&f) {
+      auto put = [&](const Csc &M, long long r0, long long c0_) {
+        for (int j = 0; j < M.n; ++j)
+          for (int q = M.cp[j]; q < M.cp[j + 1]; ++q) f(r0 + M.ri[q], c0_ + j, M.v[q]);
+      };
+      for (int i = 0; i < N; ++i) {
+        put(A[i], p->yoff[i], p->xoff[i]);
+        put(W[i], p->yoff[i], p->xoff[N]);
+        put(Fg[i], grow0, p->xoff[i]);
       }
-      // sort columns within rows (sum order of the mat-vec is then fixed);
-      // rows are independent, so chunks of them go to the host threads
+      for (size_t j = 0; j < FL.size(); ++j) {
+        put(FL[j], p->msum + p->link_off[j], p->xoff[j]);
+        put(FR[j], p->msum + p->link_off[j], p->xoff[j + 1]);
+        put(F0[j], p->msum + p->link_off[j], p->xoff[N]);
+      }
+      put(Fg0, grow0, p->xoff[N]);
+    };
+    std::vector<int> Arp(p->m + 1, 0), Aci, ATrp(p->n + 1, 0), ATci;
+    std::vector<double> Av, ATv;
+    long long nnz = 0;
+    visit([&](long long r, long long, double) {
+      ++Arp[r + 1];
+      ++nnz;
+    });
+    if (nnz >= (1LL << 31)) fail(AHLP_ERR_UNSUPPORTED, "more than 2^31 nonzeros");
+    for (long long r = 0; r < p->m; ++r) Arp[r + 1] += Arp[r];
+    Aci.resize(nnz);
+    Av.resize(nnz);
+    {
+      std::vector<int> fill(Arp.begin(), Arp.end() - 1);
+      visit([&](long long r, long long cc, double v) {
+        const int pos = fill[r]++;
+        Aci[pos] = (int)cc;
+        Av[pos] = v;
+      });
+    }
+    // the rows are sorted by construction; sort any that are not (kept as a
+    // guard: the mat-vec's summation order depends on it)
+    {
       constexpr long long kChunk = 4096;
-      const int nchunk = (int)((rows + kChunk - 1) / kChunk);
-      parallel_for(nchunk, [&](int ch) {
+      const long long rows = p->m;
+      parallel_for((int)((rows + kChunk - 1) / kChunk), [&](int ch) {
         std::vector<std::pair<int, double>> row;
-        const long long r1 = std::min(rows, (ch + 1) * kChunk);
-        for (long long r = ch * kChunk; r < r1; ++r) {
+        for (long long r = ch * kChunk; r < std::min(rows, (ch + 1) * kChunk); ++r) {
+          bool sorted = true;
+          for (int q = Arp[r] + 1; q < Arp[r + 1] && sorted; ++q) sorted = Aci[q - 1] < Aci[q];
+          if (sorted) continue;
           row.clear();
-          for (int q = rp[r]; q < rp[r + 1]; ++q) row.push_back({ci[q], vv[q]});
+          for (int q = Arp[r]; q < Arp[r + 1]; ++q) row.push_back({Aci[q], Av[q]});
           std::sort(row.begin(), row.end(),
                     [](const std::pair<int, double> &x, const std::pair<int, double> &y) {
                       return x.first < y.first;
                     });
-          for (int q = rp[r]; q < rp[r + 1]; ++q) {
-            ci[q] = row[q - rp[r]].first;
-            vv[q] = row[q - rp[r]].second;
+          for (int q = Arp[r]; q < Arp[r + 1]; ++q) {
+            Aci[q] = row[q - Arp[r]].first;
+            Av[q] = row[q - Arp[r]].second;
           }
         }
       });
-    };
-    std::vector<int> Arp, Aci, ATrp, ATci;
-    std::vector<double> Av, ATv;
-    to_csr(R, C, p->m, Arp, Aci, Av);
-    to_csr(C, R, p->n, ATrp, ATci, ATv);
+    }
+    for (long long k = 0; k < nnz; ++k) ++ATrp[Aci[k] + 1];
+    for (long long c2 = 0; c2 < p->n; ++c2) ATrp[c2 + 1] += ATrp[c2];
+    ATci.resize(nnz);
+    ATv.resize(nnz);
+    {
+      std::vector<int> fill(ATrp.begin(), ATrp.end() - 1);
+      for (long long r = 0; r < p->m; ++r)
+        for (int q = Arp[r]; q < Arp[r + 1]; ++q) {
+          const int pos = fill[Aci[q]]++;
+          ATci[pos] = (int)r;
+          ATv[pos] = Av[q];
+        }
+    }
     std::vector<double> bgl, cgl;
     for (int i = 0; i < N; ++i) bgl.insert(bgl.end(), b[i].begin(), b[i].end());
     for (auto &v : blink) bgl.insert(bgl.end(), v.begin(), v.end());
@@ -854,35 +905,23 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     parallel_for(N, one_block);
     for (int i = 0; i < N; ++i)
       if (pcode[i]) fail(pcode[i], pmsg[i]);
-    // concatenation at precomputed offsets, also on the threads
+    // the block patterns stay separate: their entry and contribution offsets
+    // are made absolute here and each part is uploaded at its offset
     std::vector<long long> tb(N + 1, 0), eb(N + 1, 0), cb(N + 1, 0);
     for (int i = 0; i < N; ++i) {
       tb[i + 1] = tb[i] + (long long)part[i].tiles.size();
       eb[i + 1] = eb[i] + (long long)part[i].ent_pos.size();
       cb[i + 1] = cb[i] + (long long)part[i].con_idx.size();
     }
-    Pattern P;
-    P.tiles.resize(tb[N]);
-    P.tile_ent.resize(tb[N]);
-    P.ent_pos.resize(eb[N]);
-    P.ent_cb.resize(eb[N]);
-    P.con_idx.resize(cb[N]);
-    P.con_coef.resize(cb[N]);
     parallel_for(N, [&](int i) {
-      Pattern &q = part[i];
-      std::copy(q.tiles.begin(), q.tiles.end(), P.tiles.begin() + tb[i]);
-      for (size_t t = 0; t < q.tile_ent.size(); ++t) P.tile_ent[tb[i] + t] = q.tile_ent[t] + eb[i];
-      std::copy(q.ent_pos.begin(), q.ent_pos.end(), P.ent_pos.begin() + eb[i]);
-      for (size_t t = 0; t < q.ent_cb.size(); ++t) P.ent_cb[eb[i] + t] = q.ent_cb[t] + cb[i];
-      std::copy(q.con_idx.begin(), q.con_idx.end(), P.con_idx.begin() + cb[i]);
-      std::copy(q.con_coef.begin(), q.con_coef.end(), P.con_coef.begin() + cb[i]);
-      q = Pattern();
+      for (long long &v : part[i].tile_ent) v += eb[i];
+      for (long long &v : part[i].ent_cb) v += cb[i];
     });
-    P.tile_ent.push_back((long long)P.ent_pos.size());
-    P.ent_cb.push_back((long long)P.con_idx.size());
-    p->ntiles = (long long)P.tiles.size();
-    p->nent = (long long)P.ent_pos.size();
-    p->ncon = (long long)P.con_idx.size();
+    part[N - 1].tile_ent.push_back(eb[N]);   // end sentinels
+    part[N - 1].ent_cb.push_back(cb[N]);
+    p->ntiles = tb[N];
+    p->nent = eb[N];
+    p->ncon = cb[N];
     // ---- Schur maps ---------------------------------------------------------------
     std::vector<int> kmap;
     for (int i = 0; i < N; ++i) {
@@ -1003,12 +1042,13 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->cdiag0 = dalloc<double>(p, std::max(cd, 1LL));
     p->cdiag_elems = cd;
     p->sb_ref = dalloc<double>(p, p->B);
-    p->ftiles = dupload(p, P.tiles);
-    p->tile_ent = dupload(p, P.tile_ent);
-    p->ent_pos = dupload(p, P.ent_pos);
-    p->ent_cb = dupload(p, P.ent_cb);
-    p->con_idx = dupload(p, P.con_idx);
-    p->con_coef = dupload(p, P.con_coef);
+    p->ftiles = dupload_parts(p, part, &Pattern::tiles);
+    p->tile_ent = dupload_parts(p, part, &Pattern::tile_ent);
+    p->ent_pos = dupload_parts(p, part, &Pattern::ent_pos);
+    p->ent_cb = dupload_parts(p, part, &Pattern::ent_cb);
+    p->con_idx = dupload_parts(p, part, &Pattern::con_idx);
+    p->con_coef = dupload_parts(p, part, &Pattern::con_coef);
+    std::vector<Pattern>().swap(part);
     p->Td = dalloc<double>(p, te);
     p->Hd = dalloc<double>(p, he);
     p->Et = dalloc<double>(p, (long long)p->nl * p->B);
