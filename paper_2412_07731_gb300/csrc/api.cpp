@@ -2,6 +2,8 @@
 // and the kkt_factor / kkt_solve / kkt_adjoint_solve entry points.
 #include <algorithm>
 #include <deque>
+#include <exception>
+#include <mutex>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -175,19 +177,31 @@ struct Pattern {
   std::vector<double> con_coef;
 };
 
-// fn(i) for i in [0, n) on up to 16 host threads (work taken in index order)
+// fn(i) for i in [0, n) on up to 16 host threads (work taken in index order).
+// An exception thrown by fn stops no other index; the first one caught is
+// rethrown on the calling thread once every thread has joined.
 template <class F>
 void parallel_for(int n, F fn) {
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
   const int nthr = (int)std::min<long long>(n, std::min(16u, hw));
   std::atomic<int> next{0};
+  std::exception_ptr err;
+  std::mutex mu;
   auto worker = [&]() {
-    for (int i = next++; i < n; i = next++) fn(i);
+    for (int i = next++; i < n; i = next++) {
+      try {
+        fn(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> g(mu);
+        if (!err) err = std::current_exception();
+      }
+    }
   };
   std::vector<std::thread> pool;
   for (int t = 1; t < nthr; ++t) pool.emplace_back(worker);
   worker();
   for (auto &th : pool) th.join();
+  if (err) std::rethrow_exception(err);
 }
 
 struct URow {   // one link / global row restricted to the block's columns
@@ -643,6 +657,9 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
         } catch (const std::bad_alloc &) {
           vcode[i] = AHLP_ERR_OOM;
           vmsg[i] = "host memory exhausted while reading block " + std::to_string(i);
+        } catch (...) {   // nothing may leave a host thread
+          vcode[i] = AHLP_ERR_INVALID_ARG;
+          vmsg[i] = "block " + std::to_string(i) + ": could not be read";
         }
       });
       for (int i = 0; i < N; ++i)
@@ -900,6 +917,9 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
       } catch (const std::bad_alloc &) {
         pcode[i] = AHLP_ERR_OOM;
         pmsg[i] = "host memory exhausted while building the formation pattern";
+      } catch (...) {   // nothing may leave a host thread
+        pcode[i] = AHLP_ERR_INVALID_ARG;
+        pmsg[i] = "block " + std::to_string(i) + ": formation pattern could not be built";
       }
     };
     parallel_for(N, one_block);
@@ -1146,6 +1166,10 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     g_create_err = "host allocation failed";
     arrowhead_lp_destroy(p);
     return AHLP_ERR_OOM;
+  } catch (const std::exception &e) {
+    g_create_err = std::string("create: ") + e.what();
+    arrowhead_lp_destroy(p);
+    return AHLP_ERR_INVALID_ARG;
   }
   *out = p;
   return AHLP_OK;
