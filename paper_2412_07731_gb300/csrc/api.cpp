@@ -703,83 +703,113 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->m = p->msum + p->nl + mg;
     p->nS = p->nl + p->B;
     // ---- monolithic A (CSR) and A' (CSR) for residuals ------------------------
-    // A's rows are counted, then filled, visiting the blocks in a fixed order
-    // in which every row receives its columns in increasing order (block
-    // columns, then linking variables), so its rows come out sorted.  A' is
-    // A's transpose by one more counting pass, sorted by construction.
+    // Built by counting and filling, block by block (and pair by pair) on host
+    // threads.  A block's rows hold its A_i columns then its linking-variable
+    // columns; a pair's link rows its FL, FR, F0 columns; global rows take the
+    // blocks in order, then Fg0 -- so every row of A is sorted.  In A', a
+    // block's columns hold its own rows, then the previous pair's link rows,
+    // the next pair's, then the global rows; a linking variable's column the
+    // blocks' rows, the link rows, the global rows -- sorted as well.
     const long long grow0 = p->msum + p->nl;
-    auto visit = [&](auto &&f) {
-      auto put = [&](const Csc &M, long long r0, long long c0_) {
-        for (int j = 0; j < M.n; ++j)
-          for (int q = M.cp[j]; q < M.cp[j + 1]; ++q) f(r0 + M.ri[q], c0_ + j, M.v[q]);
-      };
-      for (int i = 0; i < N; ++i) {
-        put(A[i], p->yoff[i], p->xoff[i]);
-        put(W[i], p->yoff[i], p->xoff[N]);
-        put(Fg[i], grow0, p->xoff[i]);
-      }
-      for (size_t j = 0; j < FL.size(); ++j) {
-        put(FL[j], p->msum + p->link_off[j], p->xoff[j]);
-        put(FR[j], p->msum + p->link_off[j], p->xoff[j + 1]);
-        put(F0[j], p->msum + p->link_off[j], p->xoff[N]);
-      }
-      put(Fg0, grow0, p->xoff[N]);
+    const int nP = (int)FL.size();
+    auto each = [](const Csc &M, auto &&f) {   // f(row, col, value), column-major order
+      for (int j = 0; j < M.n; ++j)
+        for (int q = M.cp[j]; q < M.cp[j + 1]; ++q) f(M.ri[q], j, M.v[q]);
     };
     std::vector<int> Arp(p->m + 1, 0), Aci, ATrp(p->n + 1, 0), ATci;
     std::vector<double> Av, ATv;
-    long long nnz = 0;
-    visit([&](long long r, long long, double) {
-      ++Arp[r + 1];
-      ++nnz;
+    parallel_for(N, [&](int i) {
+      int *cnt = Arp.data() + 1 + p->yoff[i];
+      each(A[i], [&](int r, int, double) { ++cnt[r]; });
+      each(W[i], [&](int r, int, double) { ++cnt[r]; });
     });
-    if (nnz >= (1LL << 31)) fail(AHLP_ERR_UNSUPPORTED, "more than 2^31 nonzeros");
-    for (long long r = 0; r < p->m; ++r) Arp[r + 1] += Arp[r];
+    parallel_for(nP, [&](int j) {
+      int *cnt = Arp.data() + 1 + p->msum + p->link_off[j];
+      each(FL[j], [&](int r, int, double) { ++cnt[r]; });
+      each(FR[j], [&](int r, int, double) { ++cnt[r]; });
+      each(F0[j], [&](int r, int, double) { ++cnt[r]; });
+    });
+    {
+      int *cnt = Arp.data() + 1 + grow0;
+      for (int i = 0; i < N; ++i) each(Fg[i], [&](int r, int, double) { ++cnt[r]; });
+      each(Fg0, [&](int r, int, double) { ++cnt[r]; });
+    }
+    for (long long r = 0; r < p->m; ++r) {
+      if ((long long)Arp[r] + Arp[r + 1] >= (1LL << 31))
+        fail(AHLP_ERR_UNSUPPORTED, "more than 2^31 nonzeros");
+      Arp[r + 1] += Arp[r];
+    }
+    const long long nnz = Arp[p->m];
     Aci.resize(nnz);
     Av.resize(nnz);
-    {
-      std::vector<int> fill(Arp.begin(), Arp.end() - 1);
-      visit([&](long long r, long long cc, double v) {
+    // fill: the row starts of the rows M's local row indices refer to
+    auto put_rows = [&](std::vector<int> &fill, const Csc &M, long long c0_) {
+      each(M, [&](int r, int j, double v) {
         const int pos = fill[r]++;
-        Aci[pos] = (int)cc;
+        Aci[pos] = (int)(c0_ + j);
         Av[pos] = v;
       });
-    }
-    // the rows are sorted by construction; sort any that are not (kept as a
-    // guard: the mat-vec's summation order depends on it)
+    };
+    parallel_for(N, [&](int i) {
+      std::vector<int> fill(Arp.begin() + p->yoff[i], Arp.begin() + p->yoff[i] + A[i].m);
+      put_rows(fill, A[i], p->xoff[i]);
+      put_rows(fill, W[i], p->xoff[N]);
+    });
+    parallel_for(nP, [&](int j) {
+      const long long r0 = p->msum + p->link_off[j];
+      std::vector<int> fill(Arp.begin() + r0, Arp.begin() + r0 + l[j]);
+      put_rows(fill, FL[j], p->xoff[j]);
+      put_rows(fill, FR[j], p->xoff[j + 1]);
+      put_rows(fill, F0[j], p->xoff[N]);
+    });
     {
-      constexpr long long kChunk = 4096;
-      const long long rows = p->m;
-      parallel_for((int)((rows + kChunk - 1) / kChunk), [&](int ch) {
-        std::vector<std::pair<int, double>> row;
-        for (long long r = ch * kChunk; r < std::min(rows, (ch + 1) * kChunk); ++r) {
-          bool sorted = true;
-          for (int q = Arp[r] + 1; q < Arp[r + 1] && sorted; ++q) sorted = Aci[q - 1] < Aci[q];
-          if (sorted) continue;
-          row.clear();
-          for (int q = Arp[r]; q < Arp[r + 1]; ++q) row.push_back({Aci[q], Av[q]});
-          std::sort(row.begin(), row.end(),
-                    [](const std::pair<int, double> &x, const std::pair<int, double> &y) {
-                      return x.first < y.first;
-                    });
-          for (int q = Arp[r]; q < Arp[r + 1]; ++q) {
-            Aci[q] = row[q - Arp[r]].first;
-            Av[q] = row[q - Arp[r]].second;
-          }
-        }
-      });
+      std::vector<int> fill(Arp.begin() + grow0, Arp.begin() + grow0 + mg);
+      for (int i = 0; i < N; ++i) put_rows(fill, Fg[i], p->xoff[i]);
+      put_rows(fill, Fg0, p->xoff[N]);
     }
-    for (long long k = 0; k < nnz; ++k) ++ATrp[Aci[k] + 1];
+    // A': column counts, then each column's rows in increasing order
+    parallel_for(N, [&](int i) {
+      int *cnt = ATrp.data() + 1 + p->xoff[i];
+      for (int j = 0; j < A[i].n; ++j) {
+        int c = (A[i].cp[j + 1] - A[i].cp[j]) + (Fg[i].cp[j + 1] - Fg[i].cp[j]);
+        if (i > 0) c += FR[i - 1].cp[j + 1] - FR[i - 1].cp[j];
+        if (i + 1 < N) c += FL[i].cp[j + 1] - FL[i].cp[j];
+        cnt[j] = c;
+      }
+    });
+    {
+      int *cnt = ATrp.data() + 1 + p->xoff[N];
+      for (int t = 0; t < n0; ++t) {
+        int c = Fg0.cp[t + 1] - Fg0.cp[t];
+        for (int i = 0; i < N; ++i) c += W[i].cp[t + 1] - W[i].cp[t];
+        for (int j = 0; j < nP; ++j) c += F0[j].cp[t + 1] - F0[j].cp[t];
+        cnt[t] = c;
+      }
+    }
     for (long long c2 = 0; c2 < p->n; ++c2) ATrp[c2 + 1] += ATrp[c2];
     ATci.resize(nnz);
     ATv.resize(nnz);
-    {
-      std::vector<int> fill(ATrp.begin(), ATrp.end() - 1);
-      for (long long r = 0; r < p->m; ++r)
-        for (int q = Arp[r]; q < Arp[r + 1]; ++q) {
-          const int pos = fill[Aci[q]]++;
-          ATci[pos] = (int)r;
-          ATv[pos] = Av[q];
-        }
+    auto put_col = [&](int &pos, const Csc &M, int j, long long r0) {
+      for (int q = M.cp[j]; q < M.cp[j + 1]; ++q) {
+        ATci[pos] = (int)(r0 + M.ri[q]);
+        ATv[pos] = M.v[q];
+        ++pos;
+      }
+    };
+    parallel_for(N, [&](int i) {
+      for (int j = 0; j < A[i].n; ++j) {
+        int pos = ATrp[p->xoff[i] + j];
+        put_col(pos, A[i], j, p->yoff[i]);
+        if (i > 0) put_col(pos, FR[i - 1], j, p->msum + p->link_off[i - 1]);
+        if (i + 1 < N) put_col(pos, FL[i], j, p->msum + p->link_off[i]);
+        put_col(pos, Fg[i], j, grow0);
+      }
+    });
+    for (int t = 0; t < n0; ++t) {
+      int pos = ATrp[p->xoff[N] + t];
+      for (int i = 0; i < N; ++i) put_col(pos, W[i], t, p->yoff[i]);
+      for (int j = 0; j < nP; ++j) put_col(pos, F0[j], t, p->msum + p->link_off[j]);
+      put_col(pos, Fg0, t, grow0);
     }
     std::vector<double> bgl, cgl;
     for (int i = 0; i < N; ++i) bgl.insert(bgl.end(), b[i].begin(), b[i].end());
