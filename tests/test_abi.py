@@ -156,3 +156,18 @@ def test_ctypes_structures_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_validation_reports_the_first_failing_block():
+    """Blocks are validated concurrently; the error is still the one of the
+    lowest-numbered bad block, whatever the thread timing."""
+    from instances import random_block_lp
+    lp = random_block_lp(2, N=12, m_sizes=[30] * 12, n_sizes=[45] * 12, nnz_per_col=3, n0=2,
+                         w_density=0.3, l=[2] * 11, mg=1, global_nnz=3)
+    lp.A[3] = lp.A[3].copy()
+    lp.A[3].data[0] = np.nan
+    lp.A[9] = lp.A[9].copy()
+    lp.A[9].data[0] = np.inf
+    for _ in range(5):
+        st, msg = _create_status(lp)
+        assert st == -1 and "block 3" in msg and "non-finite" in msg, msg
