@@ -550,7 +550,6 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, floa
   }
 }
 
-constexpr int KCF = 16;   // pivot columns per staged chunk of the float-float update
 // trailing update: C_IJ -= L_Ik L_Jk' over the pivot columns of step k.
 constexpr int KC = 16;
 template <typename T>

@@ -922,7 +922,7 @@ cudaError_t launch_schur_assemble(ahlp_problem *p, double delta, double rho) {
   // keep the assembled matrix for diagnostics
   if (p->td_elems) cudaMemcpyAsync(p->Td_asm, p->Td, p->td_elems * 8, cudaMemcpyDeviceToDevice, s);
   if (p->h_elems) cudaMemcpyAsync(p->Hd_asm, p->Hd, p->h_elems * 8, cudaMemcpyDeviceToDevice, s);
-  if ((long long)p->nl * p->B)
+  if ((long long)p->nl * p->B != 0)
     cudaMemcpyAsync(p->Et_asm, p->Et, (size_t)p->nl * p->B * 8, cudaMemcpyDeviceToDevice, s);
   if (p->B) cudaMemcpyAsync(p->SB_asm, p->SB, (size_t)p->B * p->B * 8, cudaMemcpyDeviceToDevice, s);
   return cudaGetLastError();
