@@ -550,7 +550,8 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, floa
   }
 }
 
-// trailing update: C_IJ -= L_Ik L_Jk' over the pivot columns of step k.
+// trailing update: C_IJ -= L_Ik L_Jk' over the pivot columns of step k (the
+// FP64 factor; FP32 and float-float have their own kernels below).
 constexpr int KC = 16;
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pchol_update_kernel(T *buf, const BlkInfo *blk, int k) {
@@ -611,8 +612,9 @@ __global__ void __launch_bounds__(kThreads) pchol_update_kernel(T *buf, const Bl
   }
 }
 
-// FP32 trailing update.  The 4x4-per-thread tile above leaves the FP32 pipe
-// waiting on shared-memory issue (8 scalar loads per 16 FMAs); here 64
+// FP32 trailing update.  The FP64 kernel's 4x4-per-thread tile above, run in
+// FP32, leaves the FP32 pipe waiting on shared-memory issue (8 scalar loads
+// per 16 FMAs); here 64
 // threads cover the 64x64 tile with an 8x8 register tile each, reading it
 // with four 16-byte shared loads per 64 FMAs.  Rows 4tx..4tx+3 and
 // 32+4tx..35+4tx, columns likewise with ty, so that the 16-byte loads of a
