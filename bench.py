@@ -1,33 +1,48 @@
 """Benchmark: interior-point iterations per second on one GB300.
 
-Workload (default): the uniform-block arrowhead LP with N = 64 blocks, each
-A_i 2000 x 3000 with 8 nnz/column (N(0,1) values), 50 linking variables with
-5%-dense columns, 20 local link rows per adjacent pair, planted optimum,
-seed 1.  One step = one complete interior-point solve to relative gap 1e-8
-from Mehrotra's starting point (14 iterations; every iteration runs every
-hot-path stage: formation, batched block partial Cholesky with the Schur
-contributions, Schur assembly + link-chain/border factor, and the predictor
-and corrector solves with their Krylov refinement).  The handle (problem
-upload and symbolic analysis) is created before the timed region.
+Workload (default, --workload c2): the batched uneven-block arrowhead LP, N =
+512 blocks with m_i ~ U{500..4000} rows and n_i = 1.5 m_i columns (8 nnz per
+column, N(0,1) values), 100 linking variables with 5%-dense columns, 16 local
+link rows per adjacent pair, planted optimum (seed 2).  Its block factors run
+in mixed precision (FP32, float-float near the optimum) with the FP64 Schur
+factor and FP64 Krylov refinement, and the same LP with FP64 block factors is
+measured beside it.
 
-value      IPM iterations/s in mixed precision (FP32 block factors, float-float
-           then FP64 ones near the optimum, FP64 Schur complement and
-           refinement), inputs resident in device memory
-fp64       the same LP and metric with FP64 block factors, beside it
-e2e        mixed precision end to end through the C ABI from host memory: each
-           step creates the handle from the host LP (upload + symbolic analysis),
-           solves, copies x, y, z back and destroys the handle
-roofline   the batched block partial Cholesky in the precision that dominates
-           the timed solves, against that ALU's peak
-cpu_baseline  the CPU oracle (monolithic sparse-LU Mehrotra IPM) timed for one
-           IPM iteration on the first block of the same LP, scaled to 64 blocks
+One step = one IPM iteration: the KKT factor (formation of the block normal
+matrices, the batched partial Cholesky with the Schur contributions, the Schur
+assembly and its link-chain/border factor), the predictor and corrector solves
+with their Krylov refinement, and the step.  Exactly --steps iterations are
+timed after --warmup iterations, with CUDA events on the handle's stream at
+iteration boundaries (the library's iteration callback); when a solve
+converges inside the window the next solve starts from Mehrotra's point again
+and its start-up work is timed too, without counting as a step.  The handle
+(upload and symbolic analysis) is created before the timed region.
+
+value      IPM iterations/s in mixed precision, inputs resident in HBM
+fp64       the same LP and metric with FP64 block factors, beside it (its own
+           warm-up and step counts are stated)
+solve      one complete solve per precision (iterations, ms, objective error
+           against the planted optimum)
+c1         the uniform 64-block LP: complete solves, mixed and FP64
+e2e        mixed precision end to end through the C ABI from host memory: one
+           step creates the handle from the host LP, solves to 1e-8, copies x,
+           y, z to pinned host memory and destroys the handle
+roofline   the batched block partial Cholesky in the precision that took the
+           most time in the timed window
+stages     one KKT factor and one preconditioner application, stage by stage
+cpu_baseline  the CPU oracle (monolithic sparse-LU Mehrotra IPM) timed on
+           contiguous windows of 1, 2 and 4 blocks of the same LP and
+           extrapolated with the growth exponent measured on them
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload c2|c1|c3|c4|c1small|c0]
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -39,62 +54,114 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_PEAK_TFLOPS = 1.25       # nominal GB300 FP64 (FMA pipes and DMMA alike)
-FP32_PEAK_TFLOPS = 74.7       # GB300 FP32 FMA, measured by the register-only probe
+FP32_PEAK_TFLOPS = 74.7       # GB300 FP32 FMA (2 flops per FMA), register-only probe
 HBM_FALLBACK_GBS = 6800.0     # GB300 copy bandwidth when no measured figure is present
+BF16_FALLBACK_TFLOPS = 1900.0
+TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense TF32 : BF16 tensor rate on GB300
+FF_FP32_OPS_PER_MAC = 12      # FP32 instructions of one double-float multiply-add
 
-
-def measured_hbm_gbs() -> float:
-    """Copy bandwidth measured on this machine type (MEASURED_PEAKS.json beside
-    this file, key hbm_gbs), else the fallback figure."""
-    try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                               "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
-    except (OSError, ValueError, KeyError):
-        return HBM_FALLBACK_GBS
 METRIC = "IPM iters/s & KKT solve ms at rel. gap 1e-8; mixed vs FP64 GPU path, % peak"
 
 
+def measured_peaks() -> dict:
+    """MEASURED_PEAKS.json beside this file (copy bandwidth, cuBLAS bf16), else
+    the fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained",
+                                                     d["bf16_tflops"])),
+                "source": "measured"}
+    except (OSError, ValueError, KeyError):
+        return {"hbm_gbs": HBM_FALLBACK_GBS, "bf16_tflops": BF16_FALLBACK_TFLOPS,
+                "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
 def workload(name: str):
-    from instances import config0, config1
+    """(LP or list of LPs, description, planted objective(s) or None)."""
+    from instances import config0, config1, config2, config3, config4
+    if name == "c2":
+        lp = config2()
+        return lp, ("uneven arrowhead LP, N=512 blocks, m_i~U{500..4000}, n_i=1.5 m_i "
+                    "(8 nnz/col), n0=100 linking vars (5% dense), l=16 links/pair, planted "
+                    "(seed 2)"), planted_objective(lp)
     if name == "c1":
-        return config1(), "uniform arrowhead LP, N=64 blocks of 2000x3000 (8 nnz/col), " \
-                          "n0=50 linking vars (5% dense), l=20 links/pair, planted, FP64"
+        lp = config1()
+        return lp, ("uniform arrowhead LP, N=64 blocks of 2000x3000 (8 nnz/col), n0=50 "
+                    "linking vars (5% dense), l=20 links/pair, planted (seed 1)"), \
+            planted_objective(lp)
+    if name == "c3":
+        lp = config3()
+        return lp, ("energy-system arrowhead LP, 365 daily blocks of 24 h x 30 nodes "
+                    "(~2400x3800), 600 capacity investments, 30 storage links/pair, 1 "
+                    "emissions row (seed 3, not planted)"), None
+    if name == "c4":
+        lps = config4()
+        return lps, ("16 independent planted LPs of the uneven shape, N=128 blocks each "
+                     "(seeds 4..19), one batched handle"), [planted_objective(q) for q in lps]
     if name == "c1small":
-        return config1(N=8), "uniform arrowhead LP, N=8 blocks of 2000x3000, n0=50, l=20, FP64"
+        lp = config1(N=8)
+        return lp, "uniform arrowhead LP, N=8 blocks of 2000x3000, n0=50, l=20, planted", \
+            planted_objective(lp)
     if name == "c0":
-        return config0(), "tiny arrowhead LP, N=4 blocks of 40x60, n0=3, l=2, FP64"
+        lp = config0()
+        return lp, "tiny arrowhead LP, N=4 blocks of 40x60, n0=3, l=2, planted", \
+            planted_objective(lp)
     raise ValueError(name)
+
+
+def planted_objective(lp):
+    import numpy as np
+    return float(np.dot(lp.c_global(), lp.xstar)) if lp.xstar is not None else None
+
+
+def _blocks(lp):
+    return lp if isinstance(lp, (list, tuple)) else [lp]
 
 
 def block_factor_flops(lp) -> float:
     """Algorithmic flops of one batched partial Cholesky: for each block the
     augmented order a = m_i + k_i with m_i pivots; column c costs (a-c-1)
     divides and (a-c-1)(a-c) flops of rank-1 update."""
-    N, n0, mg = lp.N, lp.n0, lp.mg
-    l = list(int(v) for v in lp.l)
     tot = 0.0
-    for i, A in enumerate(lp.A):
-        m = A.shape[0]
-        k = n0 + mg + (l[i - 1] if i > 0 else 0) + (l[i] if i < N - 1 else 0)
-        a = m + k
-        # sum_{c=0}^{m-1} (a-c-1) + (a-c-1)(a-c)
-        s = 0.0
-        for c in range(m):
-            r = a - c - 1
-            s += r + r * (r + 1)
-        tot += s
+    for q in _blocks(lp):
+        N, n0, mg = q.N, q.n0, q.mg
+        l = list(int(v) for v in q.l)
+        for i, A in enumerate(q.A):
+            m = A.shape[0]
+            k = n0 + mg + (l[i - 1] if i > 0 else 0) + (l[i] if i < N - 1 else 0)
+            a = m + k
+            # sum_{c=0}^{m-1} (r + r(r+1)), r = a-c-1, in closed form
+            r_hi, r_lo = a - 1, a - m
+            s1 = (r_hi * (r_hi + 1) - (r_lo - 1) * r_lo) / 2.0
+            s2 = (r_hi * (r_hi + 1) * (2 * r_hi + 1) - (r_lo - 1) * r_lo * (2 * r_lo - 1)) / 6.0
+            tot += 2.0 * s1 + s2
     return tot
 
 
-def stage_rooflines(P, prob, lp, hbm_gbs: float):
+def factor_geometry(lp, NB=64):
+    """(lower 64x64 tiles, lower-triangle entries) over all augmented matrices."""
+    tiles = tri = 0
+    for q in _blocks(lp):
+        for i, A in enumerate(q.A):
+            k = q.n0 + q.mg + (int(q.l[i - 1]) if i > 0 else 0) + \
+                (int(q.l[i]) if i < q.N - 1 else 0)
+            a = A.shape[0] + k
+            t = (a + NB - 1) // NB
+            tiles += t * (t + 1) // 2
+            tri += a * (a + 1) // 2
+    return tiles, tri
+
+
+def stage_rooflines(P, prob, lp, peaks):
     """Per-stage times of one KKT factor and one preconditioner application
     (the block solves, the Schur solve and the back-substitution, no Krylov
     refinement) at a seeded interior point (x, z = exp(N(0,1)), seed 0), with
     CUDA events inside the library; median of three after one warm-up.  Each
     stage against the bound that limits it:
       form   -- HBM: the FP32 lower tiles written (pattern reads not counted);
-      block  -- FP32 pipe: block_factor_flops against the FP32 FMA probe;
+      block  -- the FP32 block factor's flops against the FP32 FMA probe;
       schur  -- FP64 latency: the link chain is sequential over the link pairs
                 and the border is small, so no throughput fraction is claimed;
       apply  -- HBM: the FP32 block factors read twice (forward and backward
@@ -112,6 +179,7 @@ def stage_rooflines(P, prob, lp, hbm_gbs: float):
     saved = L.Options.from_buffer_copy(prob.options)
     once = L.Options.from_buffer_copy(saved)
     once.refine_max = 0
+    once.fp32_cond_max = 1e300   # FP32 block factors at this point
     P.set_options(prob, once)
     fac, sol = [], []
     try:
@@ -123,37 +191,30 @@ def stage_rooflines(P, prob, lp, hbm_gbs: float):
             sol.append(P.kkt_stage_times(prob)["last_solve_ms"])
     finally:
         P.set_options(prob, saved)
-    med = lambda v: statistics.median(v[1:])
+    med = lambda v: statistics.median(v[1:])  # noqa: E731
     form_ms = med([f["form_ms"] for f in fac])
     block_ms = med([f["block_factor_ms"] for f in fac])
     schur_ms = med([f["schur_ms"] for f in fac])
     apply_ms = med(sol)
-    NB = 64
-    tiles = 0
-    tri = 0
-    for i, A in enumerate(lp.A):
-        k = lp.n0 + lp.mg + (int(lp.l[i - 1]) if i > 0 else 0) + (int(lp.l[i]) if i < lp.N - 1 else 0)
-        a = A.shape[0] + k
-        t = (a + NB - 1) // NB
-        tiles += t * (t + 1) // 2
-        tri += a * (a + 1) // 2
-    form_bytes = tiles * NB * NB * 4
+    tiles, tri = factor_geometry(lp)
+    form_bytes = tiles * 64 * 64 * 4
     apply_bytes = 2 * tri * 4
     flops = block_factor_flops(lp)
-    gbs = lambda b, ms: b / (ms / 1e3) / 1e9
+    gbs = lambda b, ms: b / (ms / 1e3) / 1e9  # noqa: E731
+    hbm = peaks["hbm_gbs"]
     return {
         "point": "x, z = exp(N(0,1)) (seed 0); FP32 block factors",
         "form": {"ms": form_ms, "bound": "hbm", "bytes": form_bytes,
                  "achieved_gbs": gbs(form_bytes, form_ms),
-                 "frac": gbs(form_bytes, form_ms) / hbm_gbs},
+                 "frac": gbs(form_bytes, form_ms) / hbm},
         "block_factor": {"ms": block_ms, "bound": "alu (FP32)", "flop": flops,
                          "achieved_tflops": flops / (block_ms / 1e3) / 1e12,
                          "frac": flops / (block_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
         "schur_factor": {"ms": schur_ms, "bound": "FP64 latency (sequential link chain)"},
         "apply": {"ms": apply_ms, "bound": "hbm", "bytes": apply_bytes,
                   "achieved_gbs": gbs(apply_bytes, apply_ms),
-                  "frac": gbs(apply_bytes, apply_ms) / hbm_gbs},
-        "peaks": {"hbm_gbs": hbm_gbs, "fp32_tflops": FP32_PEAK_TFLOPS},
+                  "frac": gbs(apply_bytes, apply_ms) / hbm},
+        "peaks": {"hbm_gbs": hbm, "fp32_tflops": FP32_PEAK_TFLOPS},
     }
 
 
@@ -202,50 +263,306 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_iteration_seconds(lp, n_blocks: int = 1):
-    """Seconds of one oracle IPM iteration on the first n_blocks of lp."""
-    from instances import prefix
+# ---------------------------------------------------------------------------
+# timing exactly K IPM iterations
+# ---------------------------------------------------------------------------
+_COUNTERS = ("ms_factor", "ms_solve", "refine_steps", "factors_fp32", "factors_ff",
+             "factors_fp64", "ms_block_fp32", "ms_block_ff", "ms_block_fp64", "correctors")
+
+
+class IterWindow:
+    """Times exactly `steps` IPM iterations after `warmup` completed ones,
+    across as many solves as it takes.  The library calls back at the start
+    of every iteration (after the iterate's measures); the callback at
+    iteration it >= 1 marks the end of iteration it - 1.  At the boundary that
+    completes the warm-up the stream is synchronised (and the ranks meet) and
+    a CUDA event is recorded on the handle's stream; at the boundary that
+    completes the last timed iteration the end event is recorded, the stream
+    synchronised and the solve told to stop."""
+
+    def __init__(self, P, stream, warmup, steps, dist=None, local=0):
+        from paper_2412_07731_gb300 import _lib as L
+        import torch
+        self.P, self.L, self.torch = P, L, torch
+        self.stream, self.warmup, self.steps, self.dist, self.local = \
+            stream, warmup, steps, dist, local
+        self.done = 0
+        self.started = False
+        self.finished = False
+        self.prev = None
+        self.acc = {k: 0.0 for k in _COUNTERS}
+        self.launch0 = self.launches = 0
+        self.sampler = None
+        self.e0 = torch.cuda.Event(enable_timing=True)
+        self.e1 = torch.cuda.Event(enable_timing=True)
+        self.solves_started_in_window = 0
+        CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int32,
+                              ctypes.POINTER(L.Result))
+        self.cfunc = CB(self._cb)
+
+    def _start(self):
+        self.torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+            self.torch.cuda.synchronize()
+        self.sampler = ClockSampler(self.local)
+        self.launch0 = self.P.launch_count()
+        self.e0.record(self.stream)
+        self.started = True
+
+    def _cb(self, ctx, it, res_p):
+        r = res_p.contents
+        snap = {k: float(getattr(r, k)) for k in _COUNTERS}
+        if it == 0:
+            if self.warmup == 0 and not self.started:
+                self._start()
+            elif self.started:
+                self.solves_started_in_window += 1
+            self.prev = snap
+            return 0
+        if self.started:
+            for k in _COUNTERS:
+                self.acc[k] += snap[k] - self.prev[k]
+        self.prev = snap
+        self.done += 1
+        if self.done == self.warmup and not self.started:
+            self._start()
+        if self.started and self.done == self.warmup + self.steps:
+            self.e1.record(self.stream)
+            self.torch.cuda.synchronize()
+            self.launches = self.P.launch_count() - self.launch0
+            self.finished = True
+            return 1
+        return 0
+
+    def run(self, prob, out):
+        """Solve repeatedly on prob until the window is complete; returns the
+        timed milliseconds (max over ranks)."""
+        L = self.L
+        saved = L.Options.from_buffer_copy(prob.options)
+        o = L.Options.from_buffer_copy(saved)
+        o.iter_cb = ctypes.cast(self.cfunc, ctypes.c_void_p).value
+        L.set_options(prob, o)
+        try:
+            while not self.finished:
+                _, r = self.P.ipm_solve(prob, out=out, check=False)
+                if r["status"] not in (0, -11):
+                    raise RuntimeError(f"IPM solve failed: {r}")
+        finally:
+            L.set_options(prob, saved)
+        self.clocks = self.sampler.stop()
+        ms = self.e0.elapsed_time(self.e1)
+        if self.dist:
+            t = self.torch.tensor([ms], device=out[0].device)
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle samples
+# ---------------------------------------------------------------------------
+def _smallest_window(lp, width):
+    import numpy as np
+    m = lp.m_sizes.astype(float)
+    cost = [float(np.sum(m[s:s + width] ** 3)) for s in range(max(1, lp.N - width + 1))]
+    return int(np.argmin(cost))
+
+
+def oracle_iteration_seconds(sub):
+    """Seconds of one oracle IPM iteration (predictor + corrector on the
+    monolithic system) on the LP sub, from the oracle's starting point."""
     from oracle import ipm, lp as olp
-    sub = prefix(lp, n_blocks)
     A, b, c = olp.assemble(sub)
     x, y, z = ipm.starting_point(A, b, c)
     t0 = time.perf_counter()
     ipm.solve(A, b, c, max_iter=1, x0=x, y0=y, z0=z)
-    return time.perf_counter() - t0
+    return time.perf_counter() - t0, A.shape[0]
 
 
-def cpu_baseline(lp, sample_blocks: int = 1):
-    sec = oracle_iteration_seconds(lp, sample_blocks)
-    scale = lp.N / sample_blocks
-    return {"value": 1.0 / (sec * scale), "unit": "IPM iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"one oracle IPM iteration (predictor + corrector, each a SuperLU "
-                      f"factorisation of the monolithic augmented system) on the first "
-                      f"{sample_blocks} of {lp.N} blocks, {sec:.2f} s, scaled x{scale:g} "
-                      f"(linear in blocks; the true growth is superlinear); SuperLU runs on "
-                      f"one core"}
+def _threads():
+    try:
+        from threadpoolctl import threadpool_info
+        blas = max((d.get("num_threads", 1) for d in threadpool_info()), default=1)
+    except Exception:
+        blas = None
+    return os.cpu_count(), blas
+
+
+def cpu_baseline(lp, widths=(1, 2, 4)):
+    """The oracle timed on contiguous windows of 1, 2 and 4 blocks (the ones
+    with the smallest blocks, so the sample stays within ~20 s), one IPM
+    iteration each; the time per iteration grows as rows^e with e fitted on
+    the samples, and is extrapolated to the whole LP's rows with that e."""
+    import numpy as np
+    from instances import window
+    q = _blocks(lp)[0]
+    start = _smallest_window(q, max(widths))
+    pts = []
+    for w in widths:
+        sec, rows = oracle_iteration_seconds(window(q, start, w))
+        pts.append((w, rows, sec))
+    lr = np.log([p[1] for p in pts])
+    lt = np.log([p[2] for p in pts])
+    e = float(np.polyfit(lr, lt, 1)[0])
+    rows_full = sum(int(x.m_total) for x in _blocks(lp))
+    t_full = pts[-1][2] * (rows_full / pts[-1][1]) ** e
+    ncpu, blas = _threads()
+    return {"value": 1.0 / t_full, "unit": "IPM iters/s", "cores": 1, "kind": "oracle",
+            "host_cpus": ncpu, "blas_threads": blas,
+            "sample": (f"one oracle IPM iteration (SuperLU factorisations of the monolithic "
+                       f"augmented system, one core) on windows of {widths} consecutive blocks "
+                       f"starting at block {start}: "
+                       + ", ".join(f"{w} blocks {r} rows {s:.2f} s" for w, r, s in pts)
+                       + f"; time ~ rows^{e:.2f} fitted on them, extrapolated to "
+                         f"{rows_full} rows"),
+            "growth_exponent": e, "samples": [{"blocks": w, "rows": r, "s": s}
+                                              for w, r, s in pts]}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands.  Each step is one oracle
+    IPM iteration on the 2-block window of the workload with the smallest
+    blocks; the warm-up also times the 1-block window, and the per-iteration
+    time is extrapolated to the whole LP with the growth exponent of those
+    two samples."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    lp, desc = workload(args.workload)
-    for _ in range(args.warmup):
-        oracle_iteration_seconds(lp, 1)
-    secs = [oracle_iteration_seconds(lp, 1) for _ in range(args.steps)]
-    per_iter = statistics.mean(secs) * lp.N
+    import numpy as np
+    from instances import window
+    lp, desc, _ = workload(args.workload)
+    q = _blocks(lp)[0]
+    start = _smallest_window(q, 2)
+    w1, w2 = window(q, start, 1), window(q, start, 2)
+    s1, r1 = oracle_iteration_seconds(w1)
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_iteration_seconds(w2)
+    secs = []
+    r2 = None
+    for _ in range(args.steps):
+        s, r2 = oracle_iteration_seconds(w2)
+        secs.append(s)
+    s2 = statistics.mean(secs)
+    e = math.log(s2 / s1) / math.log(r2 / r1)
+    rows_full = sum(int(x.m_total) for x in _blocks(lp))
+    per_iter = s2 * (rows_full / r2) ** e
     value = 1.0 / per_iter
+    ncpu, blas = _threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "IPM iters/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_iter * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc},
             "cpu_baseline": {"value": value, "unit": "IPM iters/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: one oracle IPM iteration on the first of "
-                                       f"{lp.N} blocks, scaled x{lp.N}"},
+                             "host_cpus": ncpu, "blas_threads": blas,
+                             "sample": f"each step: one oracle IPM iteration on blocks "
+                                       f"{start}..{start + 1} ({r2} rows, mean {s2:.2f} s); "
+                                       f"1-block window {r1} rows {s1:.2f} s; time ~ rows^{e:.2f},"
+                                       f" extrapolated to {rows_full} rows"},
             "e2e": {"value": value, "unit": "IPM iters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def objective_error(P, prob, x, planted):
+    """Relative error of c'x against the planted objective (per LP of a batch:
+    the largest)."""
+    import numpy as np
+    if planted is None:
+        return None
+    xh = x.detach().cpu().numpy()
+    c = prob._c_global
+    if isinstance(planted, list):
+        errs = []
+        for (ix, _), q, pobj in zip(prob._layout, prob._lps, planted):
+            errs.append(abs(float(np.dot(q.c_global(), xh[ix])) - pobj) / (1 + abs(pobj)))
+        return max(errs)
+    return abs(float(np.dot(c, xh)) - planted) / (1 + abs(planted))
+
+
+def create(P, lp, prec, **opts):
+    import numpy as np
+    prob = P.arrowhead_lp_create(lp, P.default_options(precision=prec, **opts))
+    lps = _blocks(lp)
+    prob._lps = lps
+    prob._layout = P.batch_layout(lps) if len(lps) > 1 else None
+    prob._c_global = lps[0].c_global() if len(lps) == 1 else None
+    return prob
+
+
+def window_summary(win, ms, steps):
+    a = win.acc
+    it = max(steps, 1)
+    return {"ms_per_step": ms / it,
+            "kkt_factor_ms": a["ms_factor"] / it,
+            "kkt_solve_ms_per_iteration": a["ms_solve"] / it,
+            "refine_steps_per_iteration": a["refine_steps"] / it,
+            "factors": {"fp32": a["factors_fp32"], "float_float": a["factors_ff"],
+                        "fp64": a["factors_fp64"]},
+            "block_factor_ms": {
+                "fp32": a["ms_block_fp32"] / a["factors_fp32"] if a["factors_fp32"] else None,
+                "float_float": a["ms_block_ff"] / a["factors_ff"] if a["factors_ff"] else None,
+                "fp64": a["ms_block_fp64"] / a["factors_fp64"] if a["factors_fp64"] else None},
+            "solves_restarted_in_window": win.solves_started_in_window,
+            "correctors": a["correctors"]}
+
+
+def full_solve(P, prob, out, planted):
+    """One complete solve to rel. gap 1e-8 (its own CUDA-event time)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, r = P.ipm_solve(prob, out=out, check=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if r["status"] != 0:
+        raise RuntimeError(f"IPM solve failed: {r}")
+    return {"iterations": r["iterations"], "ms": e0.elapsed_time(e1),
+            "rel_gap": r["rel_gap"], "pinf": r["pinf"], "dinf": r["dinf"],
+            "objective": r["pobj"],
+            "objective_error_vs_planted": objective_error(P, prob, out[0], planted),
+            "factors": {"fp32": r["factors_fp32"], "float_float": r["factors_ff"],
+                        "fp64": r["factors_fp64"]},
+            "refine_steps": r["refine_steps"], "escalations": r["escalations"]}
+
+
+def roofline(lp, win, peaks):
+    """The batched block partial Cholesky in the precision whose factors took
+    the most time in the timed window; achieved = its algorithmic flops per
+    factor / its mean CUDA-event time per factor."""
+    a = win.acc
+    flops = block_factor_flops(lp)
+    kinds = [
+        (a["factors_fp32"], a["ms_block_fp32"], "FP32", FP32_PEAK_TFLOPS, "TFLOP/s",
+         "FP32 FMA rate of the register-only probe (74.7 TFLOP/s)"),
+        (a["factors_ff"], a["ms_block_ff"], "float-float", FP32_PEAK_TFLOPS / 2.0,
+         "T FP32-instr/s",
+         "FP32 pipe instruction rate of the register-only probe (37.35e12 instr/s); a "
+         "double-float multiply-add is 12 FP32 instructions"),
+        (a["factors_fp64"], a["ms_block_fp64"], "FP64", FP64_PEAK_TFLOPS, "TFLOP/s",
+         "nominal GB300 FP64 rate; the FMA probe measured 1.009 TFLOP/s"),
+    ]
+    cnt, tot, name, peak, unit, src = max(kinds, key=lambda k: k[1] if k[0] else -1.0)
+    if not cnt:
+        return None
+    ms = tot / cnt
+    if name == "float-float":
+        achieved = flops / 2.0 * FF_FP32_OPS_PER_MAC / (ms / 1e3) / 1e12
+        extra = {"fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12}
+    else:
+        achieved = flops / (ms / 1e3) / 1e12
+        extra = {}
+    return dict({"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit,
+                 "frac": achieved / peak, "traffic": None,
+                 "kernel": f"batched block partial Cholesky ({name}; diagonal tile, panel, "
+                           f"trailing update), {flops:.4g} flop per factor, {ms:.2f} ms",
+                 "peak_source": src}, **extra)
 
 
 def run_ours(args):
@@ -261,129 +578,102 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    peaks = measured_peaks()
 
-    lp, desc = workload(args.workload)
+    lp, desc, planted = workload(args.workload)
     stream = torch.cuda.current_stream(dev)
     headline = P.PREC_MIXED if args.precision == "mixed" else P.PREC_FP64
     other = P.PREC_FP64 if headline == P.PREC_MIXED else P.PREC_MIXED
     # the timed iteration is the plain predictor-corrector step (one factor,
-    # predictor and corrector solves); centrality correctors add solves per
-    # iteration and do not pay on this well-centred LP (1.16 s vs 1.08 s)
-    opts = dict(max_correctors=0)
-    prob = P.arrowhead_lp_create(lp, P.default_options(precision=headline, **opts))
-    P.load().arrowhead_lp_set_stream(prob.handle, stream.cuda_stream)
-    n, m = prob.n, prob.m
+    # predictor and corrector solves)
+    opts = dict(max_correctors=args.correctors)
     f64 = dict(dtype=torch.float64, device=dev)
-    x, y, z = torch.empty(n, **f64), torch.empty(m, **f64), torch.empty(n, **f64)
 
-    def solve():
-        _, r = P.ipm_solve(prob, out=(x, y, z), check=False)
-        if r["status"] != 0:
-            raise RuntimeError(f"IPM solve failed: {r}")
-        return r
+    def arm(prec, warmup, steps):
+        prob = create(P, lp, prec, **opts)
+        P.load().arrowhead_lp_set_stream(prob.handle, stream.cuda_stream)
+        out = (torch.empty(prob.n, **f64), torch.empty(prob.m, **f64),
+               torch.empty(prob.n, **f64))
+        win = IterWindow(P, stream, warmup, steps, dist, local)
+        ms = win.run(prob, out)
+        full = full_solve(P, prob, out, planted) if not args.no_full_solve else None
+        return prob, win, ms, full
 
-    def timed(k):
-        """k solves between CUDA events on the handle's stream; returns
-        (ms, results, launches, clocks)."""
-        torch.cuda.synchronize(dev)
-        if dist:
-            dist.barrier()
-        sampler = ClockSampler(local)
-        l0 = P.launch_count()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = [solve() for _ in range(k)]
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        launches = P.launch_count() - l0
-        clocks = sampler.stop()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-            dist.barrier()
-        return ms, res, launches, clocks
+    prob, win, ms, full = arm(headline, args.warmup, args.steps)
+    value = world * args.steps / (ms / 1e3)
+    summ = window_summary(win, ms, args.steps)
+    roof = roofline(lp, win, peaks)
+    stages = None
+    if rank == 0 and headline == P.PREC_MIXED and not args.no_stages:
+        stages = stage_rooflines(P, prob, lp, peaks)
+    prob.close()
+    del prob
 
-    for _ in range(args.warmup):
-        solve()
-    ms, res, launches, clocks = timed(args.steps)
-    iters = sum(r["iterations"] for r in res)
-    value = world * iters / (ms / 1e3)
-
-    # roofline: the block partial Cholesky in the precision that took longer
-    nf32 = sum(r["factors_fp32"] for r in res)
-    nff = sum(r["factors_ff"] for r in res)
-    nf64 = sum(r["factors_fp64"] for r in res)
-    t32 = sum(r["ms_block_fp32"] for r in res)
-    tff = sum(r["ms_block_ff"] for r in res)
-    t64 = sum(r["ms_block_fp64"] for r in res)
-    flops = block_factor_flops(lp)
-    # (count, total ms, peak TFLOP/s, name, peak source) per factor precision;
-    # a float-float multiply-add costs about 12 FP32 operations, so its peak
-    # in FP64-equivalent flops is the FP32 peak / 12 (the conversion of the
-    # FP64 diagonal tiles and panels is not counted in that peak)
-    kinds = [(nf32, t32, FP32_PEAK_TFLOPS, "FP32",
-              "FP32 FMA register-only probe on this GB300 (profiles/fp64_peak_probe.md)"),
-             (nff, tff, FP32_PEAK_TFLOPS / 12.0, "float-float",
-              "FP32 FMA probe / 12 FP32 operations per double-float multiply-add"),
-             (nf64, t64, FP64_PEAK_TFLOPS, "FP64",
-              "nominal GB300 FP64 rate (profiling recipe table); FMA probe measured 1.009 TFLOP/s")]
-    cnt, tot, peak, prec_name, peak_src = max(kinds, key=lambda k: k[1] if k[0] else -1.0)
-    bf_ms = tot / max(cnt, 1)
-    achieved = flops / (bf_ms / 1e3) / 1e12
     other_line = None
     if not args.no_compare:
-        P.set_options(prob, P.default_options(precision=other, **opts))
-        solve()
-        oms, ores, _, oclocks = timed(args.steps)
-        oit = sum(r["iterations"] for r in ores)
-        other_line = {"precision": "FP64" if other == P.PREC_FP64 else "mixed",
-                      "value": world * oit / (oms / 1e3), "unit": "IPM iters/s",
-                      "ms_per_step": oms / args.steps, "iterations_per_solve": oit / args.steps,
-                      "kkt_factor_ms": sum(r["ms_factor"] for r in ores) / max(oit, 1),
-                      "kkt_solve_ms_per_iteration": sum(r["ms_solve"] for r in ores) / max(oit, 1),
-                      "refine_steps_per_iteration": sum(r["refine_steps"] for r in ores) / max(oit, 1),
-                      "rel_gap": ores[-1]["rel_gap"], "clocks": oclocks}
-        P.set_options(prob, P.default_options(precision=headline, **opts))
-    stages = None
-    if rank == 0 and headline == P.PREC_MIXED:
-        stages = stage_rooflines(P, prob, lp, measured_hbm_gbs())
-    prob.close()
+        osteps = min(args.steps, args.other_steps)
+        ow = min(args.warmup, 2)
+        oprob, owin, oms, ofull = arm(other, ow, osteps)
+        other_line = dict({"precision": "FP64" if other == P.PREC_FP64 else "mixed",
+                           "value": world * osteps / (oms / 1e3), "unit": "IPM iters/s",
+                           "steps": osteps, "warmup": ow, "clocks": owin.clocks,
+                           "solve": ofull}, **window_summary(owin, oms, osteps))
+        oprob.close()
+        del oprob
 
-    # end to end through the C ABI from host memory (mixed precision)
+    c1 = None
+    if args.workload != "c1" and not args.no_c1:
+        c1lp, c1desc, c1planted = workload("c1")
+        c1 = {"workload": c1desc}
+        for prec, name in ((P.PREC_MIXED, "mixed"), (P.PREC_FP64, "fp64")):
+            q = create(P, c1lp, prec, **opts)
+            P.load().arrowhead_lp_set_stream(q.handle, stream.cuda_stream)
+            out = (torch.empty(q.n, **f64), torch.empty(q.m, **f64), torch.empty(q.n, **f64))
+            full_solve(P, q, out, c1planted)   # warm-up
+            runs = [full_solve(P, q, out, c1planted) for _ in range(2)]
+            its = sum(r["iterations"] for r in runs)
+            c1[name] = {"value": its / (sum(r["ms"] for r in runs) / 1e3),
+                        "unit": "IPM iters/s", "solves": 2, "warmup_solves": 1,
+                        "ms_per_solve": sum(r["ms"] for r in runs) / 2,
+                        "iterations_per_solve": its / 2,
+                        "objective_error_vs_planted": runs[-1]["objective_error_vs_planted"],
+                        "rel_gap": runs[-1]["rel_gap"], "factors": runs[-1]["factors"]}
+            q.close()
+        c1["mixed_over_fp64"] = c1["mixed"]["value"] / c1["fp64"]["value"]
+
+    # end to end through the C ABI from host memory (headline precision): one
+    # step = create from the host LP + one complete solve + x, y, z to pinned
+    # host memory + destroy
     e2e = None
     if not args.no_e2e:
+        q0 = _blocks(lp)
+        n = sum(int(x.n_total) for x in q0)
+        m = sum(int(x.m_total) for x in q0)
         xh = torch.empty(n, dtype=torch.float64).pin_memory()
         yh = torch.empty(m, dtype=torch.float64).pin_memory()
         zh = torch.empty(n, dtype=torch.float64).pin_memory()
-        h2d = d2h = 0
-        eit = 0
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            q = P.arrowhead_lp_create(lp, P.default_options(precision=headline, **opts))
-            _, r = P.ipm_solve(q, out=(xh, yh, zh), check=False)
-            if r["status"] != 0:
-                raise RuntimeError(f"IPM solve failed: {r}")
-            eit += r["iterations"]
-            a, b = P.transfer_bytes(q)
-            h2d += a
-            d2h += b
-            q.close()
+        q = P.arrowhead_lp_create(lp, P.default_options(precision=headline, **opts))
+        _, r = P.ipm_solve(q, out=(xh, yh, zh), check=False)
+        if r["status"] != 0:
+            raise RuntimeError(f"IPM solve failed: {r}")
+        h2d, d2h = P.transfer_bytes(q)
+        q.close()
         torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
         if dist:
             t = torch.tensor([el], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el = float(t.item())
-        e2e = {"value": world * eit / el, "unit": "IPM iters/s",
-               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
-               "step": "create from the host LP (upload + symbolic analysis) + solve + "
-                       "x, y, z to pinned host memory + destroy"}
+        e2e = {"value": world * r["iterations"] / el, "unit": "IPM iters/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "step": f"create from the host LP (upload + symbolic analysis) + one complete "
+                       f"solve ({r['iterations']} iterations) + x, y, z to pinned host memory "
+                       f"+ destroy, {el:.2f} s; bytes are per solve"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(lp, 1)
+        cpu = cpu_baseline(lp)
     if rank == 0:
         prec = "mixed" if headline == P.PREC_MIXED else "FP64"
         line = {
@@ -392,32 +682,27 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if headline == P.PREC_MIXED else "f64", "data": "synthetic",
             "config": {"workload": desc, "parallelism": "replicas" if world > 1 else "single GPU",
-                       "step": "one IPM solve to rel. gap 1e-8 from Mehrotra's starting point",
-                       "l2": "inputs larger than L2 (1.1-2.2 GB of block factors per iteration)",
+                       "step": "one IPM iteration (KKT factor, predictor and corrector solves "
+                               "with Krylov refinement, step), timed at iteration boundaries",
+                       "l2": "inputs larger than L2 (GBs of block factors per iteration)",
                        "precision": prec, "options": opts},
-            "iterations_per_solve": iters / args.steps,
-            "rel_gap": res[-1]["rel_gap"],
-            "kkt_factor_ms": sum(r["ms_factor"] for r in res) / max(iters, 1),
-            "kkt_solve_ms_per_iteration": sum(r["ms_solve"] for r in res) / max(iters, 1),
-            "refine_steps_per_iteration": sum(r["refine_steps"] for r in res) / max(iters, 1),
-            "factors": {"fp32": nf32 / args.steps, "float_float": nff / args.steps,
-                        "fp64": nf64 / args.steps},
-            "block_factor_ms": {"fp32": t32 / nf32 if nf32 else None,
-                                "float_float": tff / nff if nff else None,
-                                "fp64": t64 / nf64 if nf64 else None},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": f"batched block partial Cholesky ({prec_name}; "
-                                   f"pchol_potrf/trsm/update + tinv), {flops:.4g} flop per factor",
-                         "peak_source": peak_src},
-            "stages": stages,
-            "clocks": clocks, "gpu_launches": launches,
+            "solve": full,
+            "clocks": win.clocks, "gpu_launches": win.launches,
+            "roofline": roof, "stages": stages,
             "e2e": e2e, "cpu_baseline": cpu,
+            "peaks": peaks,
         }
+        line.update({k: v for k, v in summ.items() if k != "ms_per_step"})
         if other_line:
             line["fp64" if other == P.PREC_FP64 else "mixed"] = other_line
             line["mixed_over_fp64"] = (value / other_line["value"] if headline == P.PREC_MIXED
                                        else other_line["value"] / value)
+            if full and other_line.get("solve"):
+                a, b = full, other_line["solve"]
+                mixed, fp = (a, b) if headline == P.PREC_MIXED else (b, a)
+                line["mixed_over_fp64_complete_solve"] = fp["ms"] / mixed["ms"]
+        if c1:
+            line["c1"] = c1
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -433,7 +718,7 @@ def run_kkt(args):
     import torch
     import paper_2412_07731_gb300 as P
     from instances import prefix
-    lp, desc = workload(args.workload)
+    lp, desc, _ = workload(args.workload)
     if args.blocks and args.blocks < lp.N:
         lp = prefix(lp, args.blocks)
     prec = P.PREC_MIXED if args.precision == "mixed" else P.PREC_FP64
@@ -456,7 +741,7 @@ def run_kkt(args):
         P.kkt_solve(prob, zero, rp, zero)
         sol.append(P.kkt_stage_times(prob)["last_solve_ms"])
     fac, sol = fac[args.warmup:], sol[args.warmup:]
-    med = lambda v: statistics.median(v)
+    med = lambda v: statistics.median(v)  # noqa: E731
     line = {"metric": "KKT factor and solve ms", "unit": "ms", "higher_is_better": False,
             "config": {"workload": desc, "blocks": lp.N, "precision": args.precision,
                        "fp32_forced": bool(args.force_fp32), "steps": args.steps,
@@ -464,7 +749,8 @@ def run_kkt(args):
             "form_ms": med([f["form_ms"] for f in fac]),
             "block_factor_ms": med([f["block_factor_ms"] for f in fac]),
             "schur_ms": med([f["schur_ms"] for f in fac]),
-            "kkt_solve_ms": med(sol)}
+            "kkt_solve_ms": med(sol),
+            "block_factor_flop": block_factor_flops(lp)}
     print(json.dumps(line), flush=True)
     prob.close()
 
@@ -472,13 +758,20 @@ def run_kkt(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c1", choices=["c1", "c1small", "c0"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c1small", "c0"])
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--correctors", type=int, default=0,
+                    help="max_correctors of the timed solves (0: plain Mehrotra)")
+    ap.add_argument("--other-steps", type=int, default=8,
+                    help="timed iterations of the other precision's arm (at most --steps)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other precision's measurement")
+    ap.add_argument("--no-c1", action="store_true", help="skip the 64-block complete solves")
+    ap.add_argument("--no-full-solve", action="store_true")
+    ap.add_argument("--no-stages", action="store_true")
     ap.add_argument("--kkt-only", action="store_true",
                     help="time one KKT factorisation and --steps solves at a seeded point")
     ap.add_argument("--blocks", type=int, default=0,
@@ -487,16 +780,7 @@ def main():
                     help="--kkt-only, mixed: keep FP32 block factors at any conditioning")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe-peaks", action="store_true",
-                    help="build and run the FP64/FP32/TF32 throughput probe, then exit")
     args = ap.parse_args()
-    if args.probe_peaks:
-        src = os.path.join(ROOT, "paper_2412_07731_gb300", "probe", "peaks.cu")
-        exe = os.path.join(ROOT, "paper_2412_07731_gb300", "_build", "peaks_probe")
-        os.makedirs(os.path.dirname(exe), exist_ok=True)
-        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
-                        src], check=True)
-        sys.exit(subprocess.run([exe]).returncode)
     if args.kkt_only:
         run_kkt(args)
     elif args.impl == "reference":

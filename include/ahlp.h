@@ -53,6 +53,7 @@ extern "C" {
 #define AHLP_ERR_CUDA            -8  /* a CUDA runtime call failed                             */
 #define AHLP_ERR_OOM             -9  /* device allocation failed                               */
 #define AHLP_ERR_TIMEOUT        -10  /* a bounded device wait ran out                          */
+#define AHLP_ERR_STOPPED        -11  /* ipm_solve: the iteration callback asked to stop        */
 
 #define AHLP_PREC_FP64   0   /* every stage in FP64                                    */
 #define AHLP_PREC_MIXED  1   /* FP32 block factors (float-float near the optimum), FP64 Schur factor and refinement */
@@ -96,6 +97,19 @@ typedef struct {
   const double *lb0, *ub0;         /* [n0] or NULL                             */
 } ahlp_desc;
 
+struct ahlp_result_s;
+
+/* Progress callback of ipm_solve (option iter_cb): called on the host thread
+ * once per iteration, after the iterate's residuals, objective values and mu
+ * have been evaluated and before the convergence test, with the iteration
+ * index and the result record as it stands (pobj, dobj, rel_gap, pinf, dinf,
+ * mu, iterations and the counters so far).  The device work of every earlier
+ * iteration has been issued on the handle's stream (not necessarily
+ * finished).  A nonzero return value stops the solve: ipm_solve then writes
+ * the current iterate out and returns AHLP_ERR_STOPPED.  The callback must
+ * not call into this handle. */
+typedef int (*ahlp_iter_cb)(void *ctx, int32_t iteration, const struct ahlp_result_s *progress);
+
 typedef struct {
   int32_t precision;    /* AHLP_PREC_FP64 (default) or AHLP_PREC_MIXED            */
   int32_t max_iter;     /* IPM iteration cap (200)                                */
@@ -124,8 +138,8 @@ typedef struct {
   int32_t verbose;      /* 0: silent                                              */
   int32_t max_correctors; /* multiple centrality correctors per iteration, each
                            one more solve with the same factor, tried while the
-                           step length stays below 0.9 and at most (factor time
-                           / solve time) of them (4; 0..8)                      */
+                           step length stays below 0.9 (4; 0..8); see
+                           correctors_by_cost                                  */
   double  fp32_cond_max;/* mixed precision: the block factors run in FP32 while
                            max(d)/min(d), d = x/z, stays at or below this value,
                            and in float-float (two FP32 words, ~46 bits) beyond
@@ -136,9 +150,18 @@ typedef struct {
                            term, the residual is ~1e-6 of |r| >= mu sqrt(n).
                            The larger of it and refine_tol applies; kkt_solve
                            and kkt_adjoint_solve always use refine_tol        */
+  int32_t correctors_by_cost; /* 1: at most as many correctors as the factor costs
+                           in solves (Gondzio's rule), both costs from a fixed
+                           model of the work (flops of the block factor at its
+                           precision's rate; factor bytes read per
+                           preconditioner application times the last solve's
+                           Krylov steps), so the iterates do not depend on
+                           timings; 0: up to max_correctors regardless (1)     */
+  ahlp_iter_cb iter_cb; /* progress callback of ipm_solve, or NULL (NULL)        */
+  void   *iter_cb_ctx;  /* passed to iter_cb (NULL)                              */
 } ahlp_options;
 
-typedef struct {
+typedef struct ahlp_result_s {
   int32_t status;         /* same code the call returned                          */
   int32_t iterations;
   double  pobj, dobj;     /* c'x and b'y                                          */
@@ -289,8 +312,10 @@ int kkt_adjoint_solve(ahlp_problem *p, const double *g_x, const double *g_y, con
  *   x0, y0, z0 : optional warm start (host or device, NULL = cold start)
  *   x, y, z    : final iterate (host or device, may be NULL)
  *   res        : optional result record
- * Returns AHLP_OK at convergence, AHLP_ERR_MAX_ITER, AHLP_ERR_INFEASIBLE or
- * an error from the KKT calls.
+ * Returns AHLP_OK at convergence, AHLP_ERR_MAX_ITER, AHLP_ERR_INFEASIBLE,
+ * AHLP_ERR_STOPPED (the option iter_cb returned nonzero) or an error from
+ * the KKT calls.  The iterates are a deterministic function of the problem,
+ * the options and the starting point: nothing depends on timings.
  */
 int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, const double *z0,
               double *x, double *y, double *z, ahlp_result *res);
@@ -345,7 +370,8 @@ int ahlp_transfer_bytes(const ahlp_problem *p, int64_t *h2d, int64_t *d2h);
  * nothing: besides the caller's vectors and the existing handle it uses one
  * fixed 192 KB device array compiled into the library (per GPU, held until
  * the process exits).
- *   all seven pointers : device memory of the current device (else
+ *   all seven pointers : device memory of the handle's device, which must
+ *                        also be the current device (else
  *                        AHLP_ERR_INVALID_ARG); rel_out receives one double,
  *                        written asynchronously on the handle's stream
  *   limits             : n_total and m_total at most 67,108,864, else

@@ -15,5 +15,6 @@ from .generate import (  # noqa: F401
     config4,
     tiny_lp,
     prefix,
+    window,
     CONFIGS,
 )

@@ -519,21 +519,32 @@ def tiny_lp(seed: int, N: int = 2, m: int = 2, n: int = 4, n0: int = 1, l: int =
                            plant=plant, name=f"tiny seed={seed}")
 
 
-def prefix(lp: BlockLP, Np: int) -> BlockLP:
-    """The sub-instance made of the first Np blocks and their links.
+def window(lp: BlockLP, start: int, Np: int) -> BlockLP:
+    """The sub-instance made of blocks start .. start+Np-1 and the links
+    between them (a contiguous window of the block chain).
 
-    Global rows keep only the first Np blocks' entries.  Planted optimum is
-    re-planted from the restricted data only if the parent was planted; the
-    result is a valid LP of the same shape family, used for bounded timing
-    samples.
+    Global rows keep only the window's blocks' entries.  The optimum is
+    re-planted (half-zero split) from the restricted data; the result is a
+    valid LP of the same shape family, used for bounded timing samples.
     """
-    Np = min(Np, lp.N)
-    sub = BlockLP(N=Np, n0=lp.n0, mg=lp.mg, A=lp.A[:Np], W=lp.W[:Np], b=[], c=[],
-                  c0=np.zeros(lp.n0), l=np.asarray(lp.l[:Np - 1]), FL=lp.FL[:Np - 1],
-                  FR=lp.FR[:Np - 1], F0=lp.F0[:Np - 1], blink=[], Fg=lp.Fg[:Np],
-                  Fg0=lp.Fg0, bg=np.zeros(lp.mg), name=f"{lp.name} prefix {Np}")
-    rng = np.random.default_rng(12345 + Np)
+    start = max(0, min(start, lp.N - 1))
+    Np = max(1, min(Np, lp.N - start))
+    e = start + Np
+    sub = BlockLP(N=Np, n0=lp.n0, mg=lp.mg, A=lp.A[start:e], W=lp.W[start:e], b=[], c=[],
+                  c0=np.zeros(lp.n0), l=np.asarray(lp.l[start:e - 1]), FL=lp.FL[start:e - 1],
+                  FR=lp.FR[start:e - 1], F0=lp.F0[start:e - 1], blink=[], Fg=lp.Fg[start:e],
+                  Fg0=lp.Fg0, bg=np.zeros(lp.mg),
+                  name=f"{lp.name} blocks {start}..{e - 1}")
+    rng = np.random.default_rng(12345 + Np + 7919 * start)
     plant_half_zero(sub, rng)
+    return sub
+
+
+def prefix(lp: BlockLP, Np: int) -> BlockLP:
+    """The sub-instance made of the first Np blocks and their links (see
+    window)."""
+    sub = window(lp, 0, Np)
+    sub.name = f"{lp.name} prefix {min(Np, lp.N)}"
     return sub
 
 

@@ -18,7 +18,7 @@ _LIB_PATH = os.path.join(_HERE, "libahlp.so")
 AHLP_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "DIM_MISMATCH", -3: "UNSUPPORTED", -4: "NOT_SPD",
           -5: "REFINE_FAIL", -6: "MAX_ITER", -7: "INFEASIBLE_OR_UNBOUNDED", -8: "CUDA",
-          -9: "OOM", -10: "TIMEOUT"}
+          -9: "OOM", -10: "TIMEOUT", -11: "STOPPED"}
 PREC_FP64, PREC_MIXED = 0, 1
 
 _dp = C.POINTER(C.c_double)
@@ -45,7 +45,8 @@ class Options(C.Structure):
                 ("refine_max", C.c_int32), ("refine_tol", C.c_double),
                 ("pivot_tol", C.c_double), ("verbose", C.c_int32),
                 ("max_correctors", C.c_int32), ("fp32_cond_max", C.c_double),
-                ("ipm_refine_tol", C.c_double)]
+                ("ipm_refine_tol", C.c_double), ("correctors_by_cost", C.c_int32),
+                ("iter_cb", C.c_void_p), ("iter_cb_ctx", C.c_void_p)]
 
 
 class Result(C.Structure):
@@ -317,6 +318,10 @@ class Problem:
         self._h = handle
         self._lib = lib
         self.n, self.m = n, m
+        # bumped by every call through this binding that replaces the handle's
+        # factor (kkt_factor, ipm_solve), so a caller holding on to a factor
+        # (the autograd backward) can tell whether it is still the current one
+        self.factor_gen = 0
 
     @property
     def handle(self):
@@ -380,6 +385,7 @@ def set_options(prob: Problem, options: Options):
 def kkt_factor(prob: Problem, x, z, delta: float = -1.0, rho: float = -1.0):
     keep = _Keep()
     prob._stream_for(x, z)
+    prob.factor_gen += 1
     prob._check(prob._lib.kkt_factor(prob._h, _vec_ptr(x, keep, prob.n, "x"),
                                      _vec_ptr(z, keep, prob.n, "z"), delta, rho))
 
@@ -415,6 +421,7 @@ def ipm_solve(prob: Problem, x0=None, y0=None, z0=None, out=None, check: bool = 
     if out is None:
         out = (np.empty(prob.n), np.empty(prob.m), np.empty(prob.n))
     res = Result()
+    prob.factor_gen += 1
     st = prob._lib.ipm_solve(prob._h, _vec_ptr(x0, keep, prob.n, "x0"),
                              _vec_ptr(y0, keep, prob.m, "y0"), _vec_ptr(z0, keep, prob.n, "z0"),
                              _vec_ptr(out[0], keep, prob.n, "x"),

@@ -11,7 +11,13 @@ the explicit term: d(c'x*)/dc = x* + lam_x with g_x = c (for a nondegenerate
 optimum dx*/dc = 0, so this is x*), d(c'x*)/db = lam_y (= y*).
 
 The handle keeps the structure (A_i, W_i, link rows); forward replaces c and
-b (arrowhead_lp_set_cb), solves, and factors at the returned point.
+b (arrowhead_lp_set_cb), solves, and factors at the returned point.  The
+IPM's own last factor is at the iterate before the final step, where D =
+XZ^-1 differs from the returned point's by orders of magnitude on the
+variables that are converging to zero, so it would precondition J' badly;
+backward therefore uses the factor taken at the returned point.  If the
+handle has been factored again since (another forward, an ipm_solve or a
+kkt_factor on it), backward refactors at its own saved point first.
 """
 from __future__ import annotations
 
@@ -60,8 +66,9 @@ def _factor_at_optimum(prob, x, z):
 class LPSolve(torch.autograd.Function):
     """(x, y, z) = LPSolve.apply(c, b, prob): optimum of min c'x s.t. Ax = b,
     x >= 0 for the handle's structure.  c: [n], b: [m] float64 tensors (CPU or
-    CUDA; the outputs live on the same device).  Backward reuses the factors
-    of the final iterate (the handle must not be refactored in between)."""
+    CUDA; the outputs live on the same device).  Backward reuses the factor
+    taken at the returned point, or refactors there when the handle has been
+    factored again in between."""
 
     @staticmethod
     def forward(ctx, c, b, prob):
@@ -72,13 +79,19 @@ class LPSolve(torch.autograd.Function):
         L.ipm_solve(prob, out=(x, y, z))
         _factor_at_optimum(prob, x, z)
         ctx.prob = prob
+        ctx.factor_gen = prob.factor_gen
         ctx.save_for_backward(x, z)
         return x, y, z
 
     @staticmethod
     def backward(ctx, gx, gy, gz):
         prob = ctx.prob
-        x, _ = ctx.saved_tensors
+        x, z = ctx.saved_tensors
+        if prob.factor_gen != ctx.factor_gen:
+            # the handle was refactored elsewhere since forward: J' must be
+            # the one at this solve's optimum
+            _factor_at_optimum(prob, x, z)
+            ctx.factor_gen = prob.factor_gen
         zeros_n = torch.zeros_like(x)
         gx = zeros_n if gx is None else gx.contiguous()
         gy = torch.zeros(prob.m, dtype=x.dtype, device=x.device) if gy is None else gy.contiguous()
@@ -87,7 +100,7 @@ class LPSolve(torch.autograd.Function):
         if not info["rel_residual"] <= _ADJOINT_TOL:
             # the factor of the final iterate is not a good enough
             # preconditioner (mixed precision at an extreme D): refactor in FP64
-            _factor_fp64(prob, x, ctx.saved_tensors[1])
+            _factor_fp64(prob, x, z)
             (lx, ly, _), info = L.kkt_adjoint_solve(prob, gx, gy, gz)
             if not info["rel_residual"] <= _ADJOINT_TOL:
                 raise RuntimeError(f"adjoint KKT solve did not converge: {info}")

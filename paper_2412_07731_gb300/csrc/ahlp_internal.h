@@ -152,6 +152,8 @@ struct ahlp_problem {
   long long cdiag_elems = 0;
   long long vec_elems = 0;          // sum of a_i
   int maxT = 0, maxTp = 0;
+  double fac_flops = 0;   // algorithmic flops of one batched partial Cholesky
+  double tri_elems = 0;   // lower-triangle entries of all augmented matrices
 
   // ---- formation pattern --------------------------------------------------
   ahlp::FormTile *ftiles = nullptr;

@@ -326,6 +326,9 @@ void ahlp_default_options(ahlp_options *o) {
   o->max_correctors = 4;
   o->fp32_cond_max = 1e14;
   o->ipm_refine_tol = 1e-6;
+  o->correctors_by_cost = 1;
+  o->iter_cb = nullptr;
+  o->iter_cb_ctx = nullptr;
 }
 
 const char *ahlp_status_string(int s) {
@@ -341,6 +344,7 @@ const char *ahlp_status_string(int s) {
     case AHLP_ERR_CUDA: return "CUDA";
     case AHLP_ERR_OOM: return "OOM";
     case AHLP_ERR_TIMEOUT: return "TIMEOUT";
+    case AHLP_ERR_STOPPED: return "STOPPED";
     default: return "UNKNOWN";
   }
 }
@@ -381,7 +385,8 @@ static int check_options(const ahlp_options &o, std::string &err) {
   if (o.max_iter < 0 || !(o.tol > 0) || !(o.eta > 0 && o.eta < 1) || o.delta < 0 || o.rho < 0 ||
       o.refine_max < 0 || !(o.refine_tol > 0) || !(o.pivot_tol >= 0) ||
       !(o.fp32_cond_max >= 1) || o.max_correctors < 0 || o.max_correctors > 8 ||
-      !(o.ipm_refine_tol >= 0 && o.ipm_refine_tol < 1)) {
+      !(o.ipm_refine_tol >= 0 && o.ipm_refine_tol < 1) ||
+      (o.correctors_by_cost != 0 && o.correctors_by_cost != 1)) {
     err = "invalid option value";
     return AHLP_ERR_INVALID_ARG;
   }
@@ -883,6 +888,13 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
       bi.ioff = ioff;
       ioff += (long long)bi.Tp * NB * NB;
       p->h_blk[i] = bi;
+      // algorithmic work of this block's partial Cholesky (column c updates the
+      // r = a - c - 1 entries below its pivot and the r(r+1)/2 trailing pairs)
+      for (int cc = 0; cc < m; ++cc) {
+        const double r = (double)(a - cc - 1);
+        p->fac_flops += r + r * (r + 1.0);
+      }
+      p->tri_elems += (double)a * (a + 1) / 2.0;
       base += round_up((long long)bi.lda * a, 32);
       voff += a;
       d0 += m;

@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <utility>
 
 #include "ahlp_internal.h"
 
@@ -17,6 +18,27 @@ enum {
   V_X = 0, V_Y, V_Z, V_RP, V_RD, V_RC, V_DXA, V_DYA, V_DZA, V_DX, V_DY, V_DZ,
   V_RC2, V_DX2, V_DY2, V_DZ2
 };
+
+// Gondzio's cap on the centrality correctors of one iteration: how many
+// solves the factorisation is worth, from a fixed cost model of this GPU's
+// kernels (sustained rates of the block factor per precision; the
+// preconditioner application reads every block factor twice at the rate the
+// wavefront triangular solves reach).  A model instead of measured times
+// keeps the iterates independent of clocks, load and profilers.
+int corrector_budget(const ahlp_problem *p, int last_krylov_steps) {
+  constexpr double kRateFP32 = 25e12, kRateFF = 3e12, kRateFP64 = 1e12;   // flop/s
+  constexpr double kApplyBW = 1.3e12;                                      // bytes/s
+  const double rate = p->fac_prec == kPrecFP32 ? kRateFP32
+                      : p->fac_prec == kPrecFF ? kRateFF
+                                               : kRateFP64;
+  const double fac_s = p->fac_flops / rate;
+  const double word = p->fac_prec == kPrecFP32 ? 4.0 : 8.0;
+  const double apply_s = 2.0 * p->tri_elems * word / kApplyBW;
+  const double solve_s = (last_krylov_steps + 1) * apply_s;
+  if (!(solve_s > 0.0)) return 0;
+  const double r = fac_s / solve_s;
+  return r >= 8.0 ? 8 : (int)r;
+}
 
 double now_ms() {
   using namespace std::chrono;
@@ -169,7 +191,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     // conditioned while the others converge).  The reported measures are the
     // worst LP's.  Reductions over the LPs' ranges go through scalar slots
     // 20..51, sixteen LPs per host read.
-    std::vector<double> lp_mu(nlp, 0.0), lp_ap(nlp, 0.0), lp_ad(nlp, 0.0);
+    std::vector<double> lp_mu(nlp, 0.0), lp_ap(nlp, 0.0), lp_ad(nlp, 0.0), lp_smu(nlp, 0.0);
     auto lp_nx = [&](const ahlp_problem::LpRange &r) {
       return (double)((r.xb1 - r.xb0) + (r.x01 - r.x00));
     };
@@ -284,6 +306,8 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       ck(launch_add_scalar(Z, Z, az > 0 ? az : 1.0, n, s), "shift");
     }
     int it = 0;
+    constexpr double kDiverge = 1e12;
+    double xscale0 = 0.0, yscale0 = 0.0;
     status = AHLP_ERR_MAX_ITER;
     for (it = 0;; ++it) {
       // residuals r_p = b - Ax, r_d = c - A'y - z
@@ -309,6 +333,11 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       if (p->opt.verbose)
         printf("ipm %3d  pobj %+.10e  dobj %+.10e  pinf %.2e  dinf %.2e  gap %.2e  mu %.2e\n", it,
                R.pobj, R.dobj, R.pinf, R.dinf, R.rel_gap, R.mu);
+      if (p->opt.iter_cb && p->opt.iter_cb(p->opt.iter_cb_ctx, it, &R) != 0) {
+        status = AHLP_ERR_STOPPED;
+        p->err = "ipm_solve: stopped by the iteration callback";
+        break;
+      }
       if (!(R.pinf == R.pinf) || !(R.dinf == R.dinf)) {
         status = AHLP_ERR_NOT_SPD;
         p->err = "ipm_solve: NaN in the iterate";
@@ -325,7 +354,15 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         status = AHLP_OK;
         break;
       }
-      if (hs[5] > 1e30 || hs[6] > 1e30) {
+      // divergence: an infeasible LP drives y (a dual ray) and an unbounded
+      // one drives x (a primal ray) to infinity, while a solvable LP's
+      // iterates stay within a moderate factor of the starting point's scale
+      if (it == 0) {
+        xscale0 = hs[5];
+        yscale0 = hs[6];
+      }
+      if (hs[5] > 1e30 || hs[6] > 1e30 || hs[5] > kDiverge * (1.0 + xscale0) ||
+          hs[6] > kDiverge * (1.0 + yscale0)) {
         status = AHLP_ERR_INFEASIBLE;
         p->err = "ipm_solve: iterates diverge (LP infeasible or unbounded)";
         break;
@@ -375,6 +412,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
                                  std::max(lp_nx(r), 1.0);
               const double mub = lp_mu[c0 + k];
               const double sig = mub > 0.0 ? std::pow(mua / mub, 3.0) : 0.0;
+              lp_smu[c0 + k] = sig * mub;
               ck(launch_ipm_rc(v[V_RC] + r.xb0, X + r.xb0, Z + r.xb0, v[V_DXA] + r.xb0,
                                v[V_DZA] + r.xb0, sig * mub, r.xb1 - r.xb0, s),
                  "rc");
@@ -410,8 +448,16 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       // products (x + a dx)(z + a dz) at an enlarged trial step are pushed into
       // [0.1 sigma mu, 10 sigma mu]; a corrected direction is kept only while
       // it lengthens the step.  Tried only when the step is short, and at
-      // most as many as the factorisation costs in solves.
-      if (p->opt.max_correctors > 0 && nlp == 0) {
+      // most as many as the factorisation costs in solves (Gondzio's rule).
+      // Both costs come from a fixed model of the work, not from timings, so
+      // that the trajectory is reproducible: a block factor is its flops at
+      // its precision's rate, a solve is its preconditioner applications (the
+      // last direction's Krylov steps + 1), each reading every block factor
+      // twice at the achieved bandwidth of the triangular solves.
+      const int kmax = p->opt.correctors_by_cost
+                           ? std::min(p->opt.max_correctors, corrector_budget(p, last_steps))
+                           : p->opt.max_correctors;
+      if (kmax > 0 && nlp == 0) {
         auto steps = [&](const double *dxv, const double *dzv, double &a_p, double &a_d) {
           ck(launch_reduce(p, RED_MINSTEP, X, dxv, n, p->scal + 0), "reduce");
           ck(launch_reduce(p, RED_MINSTEP, Z, dzv, n, p->scal + 1), "reduce");
@@ -421,10 +467,6 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         };
         double a_p = 1.0, a_d = 1.0;
         steps(v[V_DX], v[V_DZ], a_p, a_d);
-        // as many as the factorisation is worth in solves (Gondzio's rule)
-        const double fac_ms = p->stage_ms[0] + p->stage_ms[1] + p->stage_ms[2];
-        const double sol_ms = std::max((double)p->stage_ms[3], 1e-3);
-        const int kmax = std::min(p->opt.max_correctors, (int)(fac_ms / sol_ms));
         for (int k = 0; k < kmax && std::min(a_p, a_d) < kCorrectorBelow; ++k) {
           const double tp = std::min(1.0, 1.5 * a_p + 0.1), td = std::min(1.0, 1.5 * a_d + 0.1);
           const double smu = sigma * mu;
@@ -443,6 +485,68 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
           a_p = b_p;
           a_d = b_d;
           ++R.correctors;
+        }
+      } else if (kmax > 0) {
+        // batch: one shared solve per corrector round; every LP whose step is
+        // still short gets its own centrality term (its own sigma mu and
+        // trial steps) and keeps the corrected slice of the direction only if
+        // its own step grows; an LP that stops improving drops out
+        lp_xreduce(RED_MINSTEP, X, v[V_DX], lp_ap);
+        lp_xreduce(RED_MINSTEP, Z, v[V_DZ], lp_ad);
+        std::vector<char> active(nlp, 0);
+        for (int k = 0; k < kmax; ++k) {
+          int nact = 0;
+          ck(cudaMemcpyAsync(v[V_RC2], v[V_RC], n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+          for (int b = 0; b < nlp; ++b) {
+            const double ab = std::min(std::min(1.0, lp_ap[b]), std::min(1.0, lp_ad[b]));
+            active[b] = (k == 0 || active[b]) && !frozen[b] && ab < kCorrectorBelow;
+            if (!active[b]) continue;
+            ++nact;
+            const auto &r = p->lp_rng[b];
+            const double tp = std::min(1.0, 1.5 * std::min(1.0, lp_ap[b]) + 0.1);
+            const double td = std::min(1.0, 1.5 * std::min(1.0, lp_ad[b]) + 0.1);
+            const double smu = lp_smu[b];
+            ck(launch_centrality_rc(v[V_RC2] + r.xb0, v[V_RC] + r.xb0, X + r.xb0,
+                                    v[V_DX] + r.xb0, tp, Z + r.xb0, v[V_DZ] + r.xb0, td,
+                                    0.1 * smu, 10.0 * smu, r.xb1 - r.xb0, s),
+               "corrector rhs");
+            ck(launch_centrality_rc(v[V_RC2] + r.x00, v[V_RC] + r.x00, X + r.x00,
+                                    v[V_DX] + r.x00, tp, Z + r.x00, v[V_DZ] + r.x00, td,
+                                    0.1 * smu, 10.0 * smu, r.x01 - r.x00, s),
+               "corrector rhs");
+          }
+          if (nact == 0) break;
+          const int st = solve(v[V_RD], v[V_RP], v[V_RC2], v[V_DX2], v[V_DY2], v[V_DZ2]);
+          if (st != AHLP_OK || last_rel > stalled) break;   // keep the previous direction
+          std::vector<double> bp(nlp, 0.0), bd(nlp, 0.0);
+          lp_xreduce(RED_MINSTEP, X, v[V_DX2], bp);
+          lp_xreduce(RED_MINSTEP, Z, v[V_DZ2], bd);
+          auto take = [&](double *dst, const double *src, long long lo, long long hi) {
+            if (hi > lo)
+              ck(cudaMemcpyAsync(dst + lo, src + lo, (hi - lo) * 8, cudaMemcpyDeviceToDevice, s),
+                 "copy");
+          };
+          for (int b = 0; b < nlp; ++b) {
+            if (!active[b]) continue;
+            const double a0 = std::min(std::min(1.0, lp_ap[b]), std::min(1.0, lp_ad[b]));
+            const double a1 = std::min(std::min(1.0, bp[b]), std::min(1.0, bd[b]));
+            if (!(a1 >= 1.01 * a0)) {
+              active[b] = 0;
+              continue;
+            }
+            const auto &r = p->lp_rng[b];
+            for (auto [dst, src] : {std::pair<double *, double *>{v[V_DX], v[V_DX2]},
+                                   {v[V_DZ], v[V_DZ2]}, {v[V_RC], v[V_RC2]}}) {
+              take(dst, src, r.xb0, r.xb1);
+              take(dst, src, r.x00, r.x01);
+            }
+            take(v[V_DY], v[V_DY2], r.yb0, r.yb1);
+            take(v[V_DY], v[V_DY2], r.yl0, r.yl1);
+            take(v[V_DY], v[V_DY2], r.yg0, r.yg1);
+            lp_ap[b] = bp[b];
+            lp_ad[b] = bd[b];
+            ++R.correctors;
+          }
         }
       }
       if (nlp > 0) {

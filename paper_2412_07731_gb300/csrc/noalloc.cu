@@ -154,11 +154,29 @@ extern "C" int kkt_residual_noalloc(ahlp_problem *p, const double *r_d, const do
     return set_err(p, AHLP_ERR_UNSUPPORTED,
                    "kkt_residual_noalloc: n_total and m_total must not exceed 67108864 "
                    "(the fixed scratch holds 4096 partial sums of 16384 entries per block)");
+  // the scratch address is looked up for the current device, and the
+  // kernels run on the handle's stream: both must be the handle's device, and
+  // so must every vector
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device) {
+    cudaGetLastError();
+    return set_err(p, AHLP_ERR_INVALID_ARG,
+                   "kkt_residual_noalloc: the current device is not the handle's device");
+  }
   const void *ptrs[7] = {r_d, r_p, r_c, dx, dy, dz, rel_out};
-  for (const void *q : ptrs)
-    if (!is_device_ptr(q))
+  for (const void *q : ptrs) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+      cudaGetLastError();
       return set_err(p, AHLP_ERR_INVALID_ARG,
                      "kkt_residual_noalloc: every vector must be device memory");
+    }
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) ||
+        (at.type == cudaMemoryTypeDevice && at.device != p->device))
+      return set_err(p, AHLP_ERR_INVALID_ARG,
+                     "kkt_residual_noalloc: every vector must be device memory of the "
+                     "handle's device");
+  }
   double *scratch = nullptr;
   cudaError_t e = scratch_for_current_device(&scratch);
   if (e != cudaSuccess) {

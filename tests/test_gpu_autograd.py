@@ -118,3 +118,24 @@ def test_finite_differences(P):
         fd = (obj_c(c.detach() + e) - obj_c(c.detach() - e)) / (2 * h)
         assert abs(fd - grad_c[k]) <= 1e-5 * max(1.0, abs(fd)), (k, fd, grad_c[k])
     prob.close()
+
+
+def test_backward_after_the_handle_was_solved_again(P):
+    """Two forwards on one handle (the second with another objective), then
+    the first is differentiated: backward must use J' at the first optimum,
+    so its gradients equal those of a forward + backward on a fresh handle."""
+    lp, prob, c, b, lp_solve = _setup(P, 15)
+    rng = np.random.default_rng(15)
+    g = torch.tensor(rng.standard_normal(c.numel()), dtype=torch.float64, device=c.device)
+    x1, _, _ = lp_solve(c, b, prob)
+    c_other = (c.detach() * (1.0 + 0.1 * torch.rand_like(c.detach()))).requires_grad_(True)
+    x2, _, _ = lp_solve(c_other, b.detach(), prob)
+    (g * x1).sum().backward()
+    grad_b = b.grad.cpu().numpy().copy()
+    _, fresh, c_f, b_f, _ = _setup(P, 15)
+    xf, _, _ = lp_solve(c_f, b_f, fresh)
+    (g * xf).sum().backward()
+    ref = b_f.grad.cpu().numpy()
+    assert np.abs(grad_b - ref).max() <= 1e-7 * max(1.0, np.abs(ref).max())
+    prob.close()
+    fresh.close()

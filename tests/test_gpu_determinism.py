@@ -1,0 +1,138 @@
+"""Reproducibility and failure reporting of ipm_solve.
+
+* The iterates are a deterministic function of the problem, the options and
+  the starting point: two solves on one handle give bitwise-equal x, y, z even
+  with other GPU work between them (centrality correctors included, whose cap
+  comes from a cost model rather than from timings).
+* Infeasible and unbounded LPs (made on the host) end with
+  AHLP_ERR_INFEASIBLE instead of running into the iteration cap.
+* Correctors on a batch: each LP keeps its own corrected slice only when its
+  own step grows, and every LP still reaches its planted objective.
+* The uneven-block workload's shape (config 2's block-size distribution, its
+  first 32 blocks) reaches the planted objective in FP64 and in mixed
+  precision, with the same iteration count within one.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from instances import config0, config2, random_block_lp, tiny_lp
+from oracle import lp as olp
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2412_07731_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return abs(a - b) / (1.0 + abs(b))
+
+
+def _busy_gpu():
+    """Unrelated GPU work on another stream, to shift the timings of what follows."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = torch.randn(2048, 2048, device="cuda")
+        for _ in range(20):
+            a = torch.tanh(a @ a * 1e-3)
+    return a
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("by_cost", [1, 0])
+def test_ipm_solve_is_bitwise_repeatable(P, prec, by_cost):
+    lp = config0(3)
+    pr = P.PREC_MIXED if prec == "mixed" else P.PREC_FP64
+    prob = P.arrowhead_lp_create(lp, P.default_options(precision=pr, max_correctors=4,
+                                                       correctors_by_cost=by_cost))
+    (x1, y1, z1), r1 = P.ipm_solve(prob)
+    keep = _busy_gpu()
+    (x2, y2, z2), r2 = P.ipm_solve(prob)
+    torch.cuda.synchronize()
+    del keep
+    assert r1["iterations"] == r2["iterations"] and r1["correctors"] == r2["correctors"]
+    assert np.array_equal(x1, x2) and np.array_equal(y1, y2) and np.array_equal(z1, z2)
+    assert r1["pobj"] == r2["pobj"]
+    if by_cost == 0:
+        assert r1["correctors"] > 0
+    prob.close()
+
+
+def _nonneg(M):
+    M = sp.csc_matrix(M, copy=True)
+    M.data = np.abs(M.data)
+    return M
+
+
+def test_infeasible_lp_is_reported(P):
+    """Every coefficient made nonnegative and every right-hand side negative:
+    Ax = b has no solution with x >= 0."""
+    lp = tiny_lp(7, N=3, m=2, n=4, n0=1, l=1, mg=1)
+    lp.A = [_nonneg(a) for a in lp.A]
+    lp.W = [_nonneg(w) for w in lp.W]
+    lp.FL = [_nonneg(f) for f in lp.FL]
+    lp.FR = [_nonneg(f) for f in lp.FR]
+    lp.F0 = [_nonneg(f) for f in lp.F0]
+    lp.Fg = [_nonneg(f) for f in lp.Fg]
+    lp.Fg0 = _nonneg(lp.Fg0)
+    lp.b = [-np.ones_like(v) for v in lp.b]
+    lp.blink = [-np.ones_like(v) for v in lp.blink]
+    lp.bg = -np.ones_like(lp.bg)
+    prob = P.arrowhead_lp_create(lp)
+    _, r = P.ipm_solve(prob, check=False)
+    assert r["status"] == -7, r
+    prob.close()
+
+
+def test_unbounded_lp_is_reported(P):
+    """A column and its negation added to block 0 with a negative combined
+    cost: x_j = x_j' = t is feasible for every t >= 0 and the objective falls
+    without bound."""
+    lp = tiny_lp(8, N=3, m=2, n=4, n0=1, l=1, mg=1)
+    A0 = lp.A[0].tocsc()
+    lp.A[0] = sp.hstack([A0, -A0[:, [0]]]).tocsc()
+    lp.c[0] = np.concatenate([lp.c[0], [-lp.c[0][0] - 1.0]])
+    lp.FL[0] = sp.hstack([lp.FL[0], sp.csc_matrix((lp.FL[0].shape[0], 1))]).tocsc()
+    lp.Fg[0] = sp.hstack([lp.Fg[0], sp.csc_matrix((lp.Fg[0].shape[0], 1))]).tocsc()
+    prob = P.arrowhead_lp_create(lp)
+    _, r = P.ipm_solve(prob, check=False)
+    assert r["status"] == -7, r
+    prob.close()
+
+
+def test_batch_correctors_keep_each_optimum(P):
+    lps = [random_block_lp(30 + k, N=4, m_sizes=[60, 90, 40, 75], n_sizes=[90, 135, 60, 112],
+                           nnz_per_col=5, n0=4, w_density=0.2, l=[3, 2, 4], mg=1,
+                           global_nnz=4, x0_link_nnz=1, x0_global_nnz=1) for k in range(3)]
+    prob = P.arrowhead_lp_create(lps, P.default_options(max_correctors=4, correctors_by_cost=0))
+    (x, y, z), r = P.ipm_solve(prob)
+    assert r["status"] == 0 and r["correctors"] > 0
+    for (ix, iy), q in zip(P.batch_layout(lps), lps):
+        A, b, c = olp.assemble(q)
+        assert _rel(float(c @ x[ix]), float(c @ q.xstar)) <= 1e-8
+    prob.close()
+
+
+def test_uneven_blocks_fp64_and_mixed(P):
+    lp = config2(N=32)
+    A, b, c = olp.assemble(lp)
+    obj = float(c @ lp.xstar)
+    its = {}
+    for prec in (P.PREC_FP64, P.PREC_MIXED):
+        prob = P.arrowhead_lp_create(lp, P.default_options(precision=prec))
+        (x, y, z), r = P.ipm_solve(prob)
+        assert r["status"] == 0
+        assert _rel(r["pobj"], obj) <= 1e-8, (prec, r["pobj"], obj)
+        m = olp.measures(A, b, c, x, y, z)
+        assert m["pinf"] <= 1e-8 and m["dinf"] <= 1e-8 and m["gap"] <= 1e-8
+        its[prec] = r["iterations"]
+        prob.close()
+    assert abs(its[P.PREC_FP64] - its[P.PREC_MIXED]) <= 2, its
