@@ -722,9 +722,11 @@ def run_kkt(args):
     if args.blocks and args.blocks < lp.N:
         lp = prefix(lp, args.blocks)
     prec = P.PREC_MIXED if args.precision == "mixed" else P.PREC_FP64
-    opts = dict(refine_max=0)
+    opts = dict(refine_max=0, fp32_update=args.fp32_update)
     if args.force_fp32:
         opts["fp32_cond_max"] = 1e300
+    if args.force_ff:
+        opts["fp32_cond_max"] = 1.0
     prob = P.arrowhead_lp_create(lp, P.default_options(precision=prec, **opts))
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(0)
@@ -744,7 +746,8 @@ def run_kkt(args):
     med = lambda v: statistics.median(v)  # noqa: E731
     line = {"metric": "KKT factor and solve ms", "unit": "ms", "higher_is_better": False,
             "config": {"workload": desc, "blocks": lp.N, "precision": args.precision,
-                       "fp32_forced": bool(args.force_fp32), "steps": args.steps,
+                       "fp32_forced": bool(args.force_fp32), "ff_forced": bool(args.force_ff),
+                       "fp32_update": args.fp32_update, "steps": args.steps,
                        "warmup": args.warmup},
             "form_ms": med([f["form_ms"] for f in fac]),
             "block_factor_ms": med([f["block_factor_ms"] for f in fac]),
@@ -778,6 +781,11 @@ def main():
                     help="--kkt-only: use the first BLOCKS blocks of the workload")
     ap.add_argument("--force-fp32", action="store_true",
                     help="--kkt-only, mixed: keep FP32 block factors at any conditioning")
+    ap.add_argument("--force-ff", action="store_true",
+                    help="--kkt-only, mixed: float-float block factors at any conditioning")
+    ap.add_argument("--fp32-update", type=int, default=0, choices=[0, 1, 2],
+                    help="--kkt-only: trailing update of FP32 factors (0 auto, 1 FP32 pipe, "
+                         "2 tensor cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

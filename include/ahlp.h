@@ -157,6 +157,11 @@ typedef struct {
                            preconditioner application times the last solve's
                            Krylov steps), so the iterates do not depend on
                            timings; 0: up to max_correctors regardless (1)     */
+  int32_t fp32_update;  /* trailing updates of FP32 block factors: 0 = tensor
+                           cores when available (tcgen05, TF32 hi/lo split
+                           operands, FP32 accumulation), 1 = FP32 pipe,
+                           2 = tensor cores (AHLP_ERR_UNSUPPORTED when the
+                           driver cannot encode tensor maps) (0)               */
   ahlp_iter_cb iter_cb; /* progress callback of ipm_solve, or NULL (NULL)        */
   void   *iter_cb_ctx;  /* passed to iter_cb (NULL)                              */
 } ahlp_options;

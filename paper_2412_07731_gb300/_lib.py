@@ -46,7 +46,8 @@ class Options(C.Structure):
                 ("pivot_tol", C.c_double), ("verbose", C.c_int32),
                 ("max_correctors", C.c_int32), ("fp32_cond_max", C.c_double),
                 ("ipm_refine_tol", C.c_double), ("correctors_by_cost", C.c_int32),
-                ("iter_cb", C.c_void_p), ("iter_cb_ctx", C.c_void_p)]
+                ("fp32_update", C.c_int32), ("iter_cb", C.c_void_p),
+                ("iter_cb_ctx", C.c_void_p)]
 
 
 class Result(C.Structure):

@@ -49,6 +49,7 @@ struct BlkInfo {
   int tag;           // added to the problem index in pivot reports (kTag*)
   long long cdoff;   // offset of the corner (non-pivot) diagonal in cdiag0
   long long ioff;    // offset of its Tp inverted diagonal tiles (block solves)
+  long long soff;    // first staging slot of its panel tiles (tensor-core update)
 };
 constexpr int kTagBorderX = 1 << 20;   // pivot reports of the border x_0 factor
 constexpr int kTagBorderG = 2 << 20;   // pivot reports of the border y_g factor
@@ -152,6 +153,18 @@ struct ahlp_problem {
   long long cdiag_elems = 0;
   long long vec_elems = 0;          // sum of a_i
   int maxT = 0, maxTp = 0;
+  // tensor-core trailing update of FP32 factors (k_tc.cu): each panel tile
+  // of the current step staged as TF32 hi / lo words in the MMA operand
+  // layout (one 8192-word slot per tile of every block), the update jobs of
+  // every step as prefix offsets over the blocks, and one tensor map per
+  // block over its FP32 augmented matrix
+  float *pstage = nullptr;
+  long long stage_slots = 0;
+  int *tc_joff = nullptr;            // [maxTp][N + 1]
+  std::vector<long long> tc_jobs;    // [maxTp]
+  void *tc_tmap = nullptr;           // [N] CUtensorMap
+  bool tc_ready = false;
+  int fp32_update = 0;               // trailing update of FP32 factors: 1 SIMT, 2 tensor cores
   double fac_flops = 0;   // algorithmic flops of one batched partial Cholesky
   double tri_elems = 0;   // lower-triangle entries of all augmented matrices
 
@@ -253,10 +266,12 @@ cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<Blk
 cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
                             const BlkInfo *info, const std::vector<BlkInfo> &h,
                             const double *diag0, double tol, int *status, cudaStream_t s);
-// FP32: also writes the inverted diagonal tiles into tinv (see launch_tinv)
+// FP32: also writes the inverted diagonal tiles into tinv (see launch_tinv);
+// with tc (a handle set up by tc_setup) the trailing updates run on the
+// tensor cores (k_tc.cu), else on the FP32 pipe
 cudaError_t launch_pchol_f32(float *buf, float *tinv, const BlkInfo *info,
                              const std::vector<BlkInfo> &h, const double *diag0, double tol,
-                             int *status, cudaStream_t s);
+                             int *status, cudaStream_t s, ahlp_problem *tc = nullptr);
 // forward / backward solves with one partial factor per CTA (the border
 // factors; vectors FP64, held in shared memory)
 cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,
@@ -315,7 +330,16 @@ cudaError_t launch_step_dot(const double *x, const double *dx, double ap, const 
                             const double *dz, double ad, long long n, double *part,
                             double *out, cudaStream_t s);  // (x+ap dx)'(z+ad dz)
 
+// ---- tensor-core trailing update (k_tc.cu) -----------------------------------
+// staging, job offsets and tensor maps for the FP32 factors (needs aug32);
+// false when the driver has no tensor-map encoder
+bool tc_setup(ahlp_problem *p);
+cudaError_t launch_update_tc(ahlp_problem *p, int k, cudaStream_t s);
+
 // ---- host runtime helpers (api.cpp) -------------------------------------------
+// device allocations owned by the handle (freed at destroy); throw Fail
+void *dalloc_bytes(ahlp_problem *p, size_t bytes);
+void *dupload_bytes(ahlp_problem *p, const void *h, size_t bytes);
 bool is_device_ptr(const void *ptr);
 const double *stage_in(ahlp_problem *p, const double *v, long long n, double *staging);
 int set_err(ahlp_problem *p, int code, const std::string &msg);

@@ -327,6 +327,7 @@ void ahlp_default_options(ahlp_options *o) {
   o->fp32_cond_max = 1e14;
   o->ipm_refine_tol = 1e-6;
   o->correctors_by_cost = 1;
+  o->fp32_update = 0;
   o->iter_cb = nullptr;
   o->iter_cb_ctx = nullptr;
 }
@@ -386,7 +387,8 @@ static int check_options(const ahlp_options &o, std::string &err) {
       o.refine_max < 0 || !(o.refine_tol > 0) || !(o.pivot_tol >= 0) ||
       !(o.fp32_cond_max >= 1) || o.max_correctors < 0 || o.max_correctors > 8 ||
       !(o.ipm_refine_tol >= 0 && o.ipm_refine_tol < 1) ||
-      (o.correctors_by_cost != 0 && o.correctors_by_cost != 1)) {
+      (o.correctors_by_cost != 0 && o.correctors_by_cost != 1) || o.fp32_update < 0 ||
+      o.fp32_update > 2) {
     err = "invalid option value";
     return AHLP_ERR_INVALID_ARG;
   }
@@ -887,6 +889,8 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
       bi.Tp = (m + NB - 1) / NB;
       bi.ioff = ioff;
       ioff += (long long)bi.Tp * NB * NB;
+      bi.soff = p->stage_slots;
+      p->stage_slots += bi.T;
       p->h_blk[i] = bi;
       // algorithmic work of this block's partial Cholesky (column c updates the
       // r = a - c - 1 entries below its pivot and the r(r+1)/2 trailing pairs)
@@ -1224,6 +1228,20 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
 // ===========================================================================
 namespace ahlp {
 
+void *dalloc_bytes(ahlp_problem *p, size_t bytes) {
+  return dalloc<unsigned char>(p, (long long)std::max<size_t>(bytes, 1));
+}
+
+void *dupload_bytes(ahlp_problem *p, const void *h, size_t bytes) {
+  void *d = dalloc_bytes(p, bytes);
+  if (bytes) {
+    cudaError_t e = cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice);
+    p->bytes_h2d += (long long)bytes;
+    if (e != cudaSuccess) fail(AHLP_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+  }
+  return d;
+}
+
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
@@ -1317,10 +1335,22 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol, boo
   }
   ck(launch_form(p, delta), "form");
   ck(cudaEventRecord(p->ev[1], s), "event");
-  if (p->fac_prec == kPrecFP32)
+  if (p->fac_prec == kPrecFP32) {
+    // trailing updates on the tensor cores unless the FP32 pipe is asked for
+    ahlp_problem *tc = nullptr;
+    if (p->opt.fp32_update != 1) {
+      if (tc_setup(p))
+        tc = p;
+      else if (p->opt.fp32_update == 2)
+        return set_err(p, AHLP_ERR_UNSUPPORTED,
+                       "kkt_factor: tensor-core update requested, but the driver cannot "
+                       "encode tensor maps");
+    }
+    p->fp32_update = tc ? 2 : 1;
     ck(launch_pchol_f32(p->aug32, p->tinv32, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol,
-                        p->status, s),
+                        p->status, s, tc),
        "pchol");
+  }
   else if (p->fac_prec == kPrecFF)
     ck(launch_pchol_ff(p->aug32, p->aug_lo, p->aug, p->aug_elems, p->blk, p->h_blk, p->diag0,
                        p->fac_pivot_tol, p->status, s),
@@ -1341,6 +1371,9 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol, boo
   cudaEventElapsedTime(&p->stage_ms[1], p->ev[1], p->ev[2]);
   cudaEventElapsedTime(&p->stage_ms[2], p->ev[2], p->ev[3]);
   p->tiny_pivots = st[1];
+  if (st[4] != 0)
+    return set_err(p, AHLP_ERR_TIMEOUT,
+                   "kkt_factor: a bounded wait of the tensor-core update ran out");
   if (st[0] > 0) {
     char buf[160];
     if (st[2] >= kTagBorderG)

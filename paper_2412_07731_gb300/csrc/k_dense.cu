@@ -357,9 +357,26 @@ __global__ void __launch_bounds__(kPotrf32Threads) pchol_potrf_f32_kernel(
 // Panel tile (I, k) below the diagonal: X = A_Ik L_kk^-T on the pivot columns
 // (a 64x64x64 product with the stored inverse), then the non-pivot columns of
 // a block's last pivot tile: A_Is -= X L_sk'.
+// TF32 rounding (round to nearest, ties away), the value with its low 13
+// mantissa bits zero
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+
+// With pstage (FP32 factors, tensor-core update) the finished panel tile is
+// also written to its staging slot as two TF32 words, hi = tf32(x) and
+// lo = tf32(x - hi), in the K-major operand layout of tcgen05.mma without
+// swizzling: 8-row x 4-column core matrices of 16-byte rows, the 16 core
+// matrices of an 8-row group along the pivot columns, then the next group
+// (entry (r, c) at (r/8)*512 + (c/4)*32 + (r%8)*4 + c%4; hi in words
+// 0..4095, lo in 4096..8191).  Rows past the matrix and columns past the
+// pivots are zero.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pchol_trsm_inv_kernel(T *buf, const T *tinv,
-                                                                  const BlkInfo *blk, int k) {
+                                                                  const BlkInfo *blk, int k,
+                                                                  float *pstage) {
   const BlkInfo bi = blk[blockIdx.y];
   if (k >= bi.Tp) return;
   const int I = k + 1 + blockIdx.x;
@@ -419,6 +436,18 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_inv_kernel(T *buf, const 
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
     if (r < nri && c < nr) gx[(long long)c * bi.lda + r] = A[r][c];
+  }
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (pstage) {
+      float *st = pstage + (bi.soff + I) * 8192LL;
+      for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = (e >> 9) * 8 + ((e >> 2) & 7), c = ((e >> 5) & 15) * 4 + (e & 3);
+        const float v = (r < nri && c < npiv) ? (float)A[r][c] : 0.0f;
+        const float h = tf32_round(v);
+        st[e] = h;
+        st[NB * NB + e] = tf32_round(v - h);
+      }
+    }
   }
 }
 
@@ -1340,7 +1369,8 @@ constexpr size_t tinv_smem() {
 
 template <typename T>
 cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkInfo> &h,
-                    const double *diag0, double tol, int *status, cudaStream_t s) {
+                    const double *diag0, double tol, int *status, cudaStream_t s,
+                    ahlp_problem *tc = nullptr) {
   int nblk = (int)h.size();
   if (nblk == 0) return cudaSuccess;
   int maxTp = 0;
@@ -1358,7 +1388,8 @@ cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkI
                                                                  (float)tol, status);
       if (maxPanel > 0)
         count_launch(), pchol_trsm_inv_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads,
-                                                   trsm_smem<T>(), s>>>(buf, tinv, info, k);
+                                                   trsm_smem<T>(), s>>>(
+                            buf, tinv, info, k, tc ? tc->pstage : nullptr);
     } else {
       count_launch(), pchol_potrf_kernel<T><<<nblk, kThreads, 0, s>>>(buf, info, k, diag0, tol,
                                                                       status);
@@ -1367,10 +1398,15 @@ cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkI
                                                trsm_smem<T>(), s>>>(buf, info, k);
     }
     if (maxTrail > 0) {
-      if constexpr (sizeof(T) == sizeof(float))
-        count_launch(), pchol_update_f32_kernel<<<dim3((unsigned)maxTrail, nblk), kUpdF32Threads, 0,
-                                                  s>>>(buf, info, k);
-      else
+      if constexpr (sizeof(T) == sizeof(float)) {
+        if (tc) {
+          cudaError_t e = launch_update_tc(tc, k, s);
+          if (e != cudaSuccess) return e;
+        } else {
+          count_launch(), pchol_update_f32_kernel<<<dim3((unsigned)maxTrail, nblk),
+                                                    kUpdF32Threads, 0, s>>>(buf, info, k);
+        }
+      } else
         count_launch(), pchol_update_kernel<T><<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(
                             buf, info, k);
     }
@@ -1446,8 +1482,8 @@ cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<Blk
 
 cudaError_t launch_pchol_f32(float *buf, float *tinv, const BlkInfo *info,
                              const std::vector<BlkInfo> &h, const double *diag0, double tol,
-                             int *status, cudaStream_t s) {
-  return pchol_t<float>(buf, tinv, info, h, diag0, tol, status, s);
+                             int *status, cudaStream_t s, ahlp_problem *tc) {
+  return pchol_t<float>(buf, tinv, info, h, diag0, tol, status, s, tc);
 }
 
 cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,

@@ -93,15 +93,16 @@ def test_infeasible_lp_is_reported(P):
 
 
 def test_unbounded_lp_is_reported(P):
-    """A column and its negation added to block 0 with a negative combined
-    cost: x_j = x_j' = t is feasible for every t >= 0 and the objective falls
+    """The negation of block 0's first column (in its block rows, link rows and
+    global rows) added as a new column with a negative combined cost:
+    x_0 = x_new = t is feasible for every t >= 0 and the objective falls
     without bound."""
     lp = tiny_lp(8, N=3, m=2, n=4, n0=1, l=1, mg=1)
-    A0 = lp.A[0].tocsc()
-    lp.A[0] = sp.hstack([A0, -A0[:, [0]]]).tocsc()
+    neg = lambda M: -sp.csc_matrix(M)[:, [0]]  # noqa: E731
+    lp.A[0] = sp.hstack([lp.A[0], neg(lp.A[0])]).tocsc()
+    lp.FL[0] = sp.hstack([lp.FL[0], neg(lp.FL[0])]).tocsc()
+    lp.Fg[0] = sp.hstack([lp.Fg[0], neg(lp.Fg[0])]).tocsc()
     lp.c[0] = np.concatenate([lp.c[0], [-lp.c[0][0] - 1.0]])
-    lp.FL[0] = sp.hstack([lp.FL[0], sp.csc_matrix((lp.FL[0].shape[0], 1))]).tocsc()
-    lp.Fg[0] = sp.hstack([lp.Fg[0], sp.csc_matrix((lp.Fg[0].shape[0], 1))]).tocsc()
     prob = P.arrowhead_lp_create(lp)
     _, r = P.ipm_solve(prob, check=False)
     assert r["status"] == -7, r
