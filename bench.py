@@ -532,6 +532,91 @@ def full_solve(P, prob, out, planted):
             "refine_steps": r["refine_steps"], "escalations": r["escalations"]}
 
 
+def update_geometry(lp, NB=64):
+    """(lower-triangle entries the trailing updates read and write, summed over
+    the steps; their flops) of one batched partial Cholesky: at step k a block
+    with T tiles and Tp pivot tiles updates the lower triangle of its trailing
+    (a - 64(k+1))-order matrix with the 64 pivot columns of step k (fewer at
+    a ragged last pivot tile)."""
+    elems = flops = 0.0
+    for q in _blocks(lp):
+        for i, A in enumerate(q.A):
+            kk = q.n0 + q.mg + (int(q.l[i - 1]) if i > 0 else 0) + \
+                (int(q.l[i]) if i < q.N - 1 else 0)
+            m = A.shape[0]
+            a = m + kk
+            for k in range((m + NB - 1) // NB):
+                t = a - NB * (k + 1)
+                if t <= 0:
+                    break
+                piv = min(NB, m - NB * k)
+                e = t * (t + 1) / 2.0
+                elems += e
+                flops += 2.0 * piv * e
+    return elems, flops
+
+
+# DRAM bytes per algorithmic byte of the trailing-update kernels, from the ncu
+# captures summarised in profiles/ (uniform 8-block workload, FP32 and
+# float-float factors); the live bench scales them by the bytes of its own
+# launches to fill roofline.traffic
+UPDATE_TRAFFIC_PER_BYTE = {"FP32": None, "float-float": None}
+
+
+def kernel_roofline(P, prob, lp, x, z, prec_name, peaks):
+    """The trailing-update kernel of the block factor in precision prec_name at
+    the iterate (x, z) where the timed window ended: CUDA events around its
+    launches (option profile_kernels), median of three factors after one
+    warm-up.  Its algorithmic bytes are the lower-triangle entries it reads
+    and writes (4 bytes each way for FP32, 8 for float-float's two words,
+    8 for FP64); for FP64 the bound is the FP64 pipe instead."""
+    from paper_2412_07731_gb300 import _lib as L
+    saved = L.Options.from_buffer_copy(prob.options)
+    o = L.Options.from_buffer_copy(saved)
+    o.profile_kernels = 1
+    o.refine_max = 0
+    if prec_name == "FP32":
+        o.precision, o.fp32_cond_max = P.PREC_MIXED, 1e300
+    elif prec_name == "float-float":
+        o.precision, o.fp32_cond_max = P.PREC_MIXED, 1.0
+    else:
+        o.precision = P.PREC_FP64
+    P.set_options(prob, o)
+    times = []
+    try:
+        for _ in range(4):
+            P.kkt_factor(prob, x, z)
+            times.append(P.kkt_factor_kernel_times(prob))
+    finally:
+        P.set_options(prob, saved)
+    med = lambda key: statistics.median([t[key] for t in times[1:]])  # noqa: E731
+    upd_ms, launches = med("update_ms"), med("update_launches")
+    elems, flops = update_geometry(lp)
+    out = {"kernel": f"trailing update of the {prec_name} block factor", "launches": launches,
+           "ms_per_factor": upd_ms, "diag_ms": med("diag_ms"), "panel_ms": med("panel_ms")}
+    if prec_name == "FP64":
+        ach = flops / (upd_ms / 1e3) / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "flop_per_launch": flops / launches,
+                    "peak_source": "nominal GB300 FP64 rate"})
+        return out
+    word = 4 if prec_name == "FP32" else 8
+    bytes_ = 2.0 * word * elems
+    gbs = bytes_ / (upd_ms / 1e3) / 1e9
+    ratio = UPDATE_TRAFFIC_PER_BYTE.get(prec_name)
+    out.update({"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"],
+                "traffic": ratio * bytes_ / launches if ratio else None,
+                "bytes_per_launch": bytes_ / launches,
+                "peak_source": f"{peaks['source']} copy bandwidth (MEASURED_PEAKS.json)",
+                "tensor": {"flop_per_factor": flops,
+                           "achieved_tflops": flops / (upd_ms / 1e3) / 1e12,
+                           "note": "FP32: 3 TF32 MMAs per product (hi*hi, hi*lo, lo*hi); "
+                                   "float-float: 21 FP16 digit MMAs per product"}})
+    return out
+
+
 def roofline(lp, win, peaks):
     """The batched block partial Cholesky in the precision whose factors took
     the most time in the timed window; achieved = its algorithmic flops per
@@ -596,13 +681,21 @@ def run_ours(args):
                torch.empty(prob.n, **f64))
         win = IterWindow(P, stream, warmup, steps, dist, local)
         ms = win.run(prob, out)
+        win.last_out = tuple(t.clone() for t in out)
         full = full_solve(P, prob, out, planted) if not args.no_full_solve else None
         return prob, win, ms, full
 
     prob, win, ms, full = arm(headline, args.warmup, args.steps)
     value = world * args.steps / (ms / 1e3)
     summ = window_summary(win, ms, args.steps)
-    roof = roofline(lp, win, peaks)
+    factor_roof = roofline(lp, win, peaks)
+    roof = None
+    if factor_roof is not None and rank == 0:
+        # the dominant kernel: the trailing update of the block factor in the
+        # precision that took the most time, at the window's last iterate
+        name = factor_roof["kernel"].split("(")[1].split(";")[0]
+        xw, _, zw = win.last_out
+        roof = kernel_roofline(P, prob, lp, xw, zw, name, peaks)
     stages = None
     if rank == 0 and headline == P.PREC_MIXED and not args.no_stages:
         stages = stage_rooflines(P, prob, lp, peaks)
@@ -688,7 +781,7 @@ def run_ours(args):
                        "precision": prec, "options": opts},
             "solve": full,
             "clocks": win.clocks, "gpu_launches": win.launches,
-            "roofline": roof, "stages": stages,
+            "roofline": roof, "block_factor": factor_roof, "stages": stages,
             "e2e": e2e, "cpu_baseline": cpu,
             "peaks": peaks,
         }

@@ -162,6 +162,18 @@ typedef struct {
                            operands, FP32 accumulation), 1 = FP32 pipe,
                            2 = tensor cores (AHLP_ERR_UNSUPPORTED when the
                            driver cannot encode tensor maps) (0)               */
+  int32_t ff_update;    /* trailing updates of float-float block factors: 0 or 2 =
+                           tensor cores (each panel entry as six FP16 integer
+                           digits under a per-row exponent, the digit products
+                           accumulated exactly in FP32, 49 bits in all),
+                           1 = double-float arithmetic on the FP32 pipe (0)     */
+  int32_t schur_chain;  /* factor and solves of the block-tridiagonal link chain
+                           of the Schur complement: 0 = block cyclic reduction
+                           (log2 of the chain length sequential levels),
+                           1 = sequential block Cholesky along the chain (0)   */
+  int32_t profile_kernels; /* 1: kkt_factor records CUDA events around each group
+                           of block-factor launches (diagonal tiles, panels,
+                           trailing updates) for kkt_factor_kernel_times (0) */
   ahlp_iter_cb iter_cb; /* progress callback of ipm_solve, or NULL (NULL)        */
   void   *iter_cb_ctx;  /* passed to iter_cb (NULL)                              */
 } ahlp_options;
@@ -358,6 +370,14 @@ int kkt_stage_times(ahlp_problem *p, double *out4);
  * process so far (all handles).  The difference of two readings is the
  * launch count of the calls made in between. */
 int64_t ahlp_launch_count(void);
+
+/* Diagnostic: device times (ms, CUDA events on the handle's stream) of the
+ * block partial Cholesky of the last kkt_factor, by kernel class: ms3[0]
+ * diagonal tiles, ms3[1] panels, ms3[2] trailing updates (the block
+ * factorisation and Schur-contribution steps of Alg. 2); launches3 (may be
+ * NULL) the number of launch groups of each class.  Zero unless the option
+ * profile_kernels was set for that factor. */
+int kkt_factor_kernel_times(const ahlp_problem *p, double *ms3, int64_t *launches3);
 
 /* Diagnostic: bytes this handle has copied host -> device and device -> host
  * since arrowhead_lp_create (the problem upload included; scalars read back

@@ -17,6 +17,7 @@ from ._lib import (  # noqa: F401
     ipm_solve,
     kkt_adjoint_solve,
     kkt_factor,
+    kkt_factor_kernel_times,
     kkt_schur_dense,
     kkt_solve,
     kkt_stage_times,

@@ -46,7 +46,9 @@ class Options(C.Structure):
                 ("pivot_tol", C.c_double), ("verbose", C.c_int32),
                 ("max_correctors", C.c_int32), ("fp32_cond_max", C.c_double),
                 ("ipm_refine_tol", C.c_double), ("correctors_by_cost", C.c_int32),
-                ("fp32_update", C.c_int32), ("iter_cb", C.c_void_p),
+                ("fp32_update", C.c_int32), ("ff_update", C.c_int32),
+                ("schur_chain", C.c_int32), ("profile_kernels", C.c_int32),
+                ("iter_cb", C.c_void_p),
                 ("iter_cb_ctx", C.c_void_p)]
 
 
@@ -75,7 +77,7 @@ EXPORTS = ["ahlp_default_options", "ahlp_status_string", "arrowhead_lp_create",
            "arrowhead_lp_set_stream", "arrowhead_lp_set_options", "kkt_factor", "kkt_solve",
            "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense", "kkt_stage_times",
            "ahlp_launch_count", "kkt_residual_noalloc", "kkt_block_factor_dense",
-           "ahlp_transfer_bytes", "arrowhead_lp_set_cb"]
+           "ahlp_transfer_bytes", "arrowhead_lp_set_cb", "kkt_factor_kernel_times"]
 
 
 def kkt_block_factor_dense(prob, block: int):
@@ -127,6 +129,16 @@ def set_cb(prob, c=None, b=None):
     prob._stream_for(c, b)
     prob._check(prob._lib.arrowhead_lp_set_cb(prob._h, _vec_ptr(c, keep, prob.n, "c"),
                                               _vec_ptr(b, keep, prob.m, "b")))
+
+
+def kkt_factor_kernel_times(prob):
+    """Device ms and launch groups of the last factor's diagonal tiles, panels
+    and trailing updates (option profile_kernels)."""
+    ms = (C.c_double * 3)()
+    n = (C.c_int64 * 3)()
+    prob._check(prob._lib.kkt_factor_kernel_times(prob._h, ms, n))
+    return {"diag_ms": ms[0], "panel_ms": ms[1], "update_ms": ms[2],
+            "diag_launches": n[0], "panel_launches": n[1], "update_launches": n[2]}
 
 
 def transfer_bytes(prob) -> tuple[int, int]:
@@ -181,6 +193,8 @@ def load(path: str | None = None):
     L.kkt_block_factor_dense.restype = C.c_int
     L.ahlp_transfer_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.ahlp_transfer_bytes.restype = C.c_int
+    L.kkt_factor_kernel_times.argtypes = [vp, _dp, C.POINTER(C.c_int64)]
+    L.kkt_factor_kernel_times.restype = C.c_int
     L.arrowhead_lp_set_cb.argtypes = [vp, vp, vp]
     L.arrowhead_lp_set_cb.restype = C.c_int
     for name in ("arrowhead_lp_sizes", "arrowhead_lp_set_stream", "arrowhead_lp_set_options",

@@ -1,6 +1,7 @@
 // Internal declarations shared by the host runtime and the kernels.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -164,6 +165,13 @@ struct ahlp_problem {
   std::vector<long long> tc_jobs;    // [maxTp]
   void *tc_tmap = nullptr;           // [N] CUtensorMap
   bool tc_ready = false;
+  // float-float factors on the tensor cores: each panel tile as six FP16
+  // digit planes (6 x 4096 halves per slot) and one exponent per row
+  __half *dstage = nullptr;
+  int *dexp = nullptr;
+  bool oz_ready = false;
+  void *oz_tmap = nullptr;           // [2N] CUtensorMap: each block's hi, then lo matrix
+  int ff_update = 0;                 // trailing update of float-float factors: 1 FP32 pipe, 2 tensor cores
   int fp32_update = 0;               // trailing update of FP32 factors: 1 SIMT, 2 tensor cores
   double fac_flops = 0;   // algorithmic flops of one batched partial Cholesky
   double tri_elems = 0;   // lower-triangle entries of all augmented matrices
@@ -194,6 +202,14 @@ struct ahlp_problem {
   int *chain_seg = nullptr;          // [2 nchain_seg] pair ranges with link rows throughout
   int nchain_seg = 0;
   int *zlo = nullptr, *zhi = nullptr;   // [B] link rows a border column of Z can touch
+  // cyclic reduction of the link chain (k_bcr.cu): pairs in level order,
+  // per pair (level, segment first pair, segment end, -), the level offsets
+  // into the order, and per pair its couplings GL_j, GR_j (lmax^2 each)
+  int *bcr_order = nullptr, *bcr_info = nullptr;
+  std::vector<int> bcr_loff;
+  int bcr_lmax = 0;
+  double *bcr_GL = nullptr, *bcr_GR = nullptr;
+  bool fac_bcr = false;   // the current Schur factor's chain is the cyclic-reduction one
   long long *yoff_d = nullptr;       // [N] start of y_i
   long long *kmap_off_d = nullptr;   // [N]
   std::vector<long long> kmap_off;
@@ -242,6 +258,10 @@ struct ahlp_problem {
 
   // ---- timing -------------------------------------------------------------
   cudaEvent_t ev[8] = {};
+  std::vector<cudaEvent_t> kt_pool;     // kernel-class timer: events, and per
+  std::vector<int> kt_cls;              // recorded event the class it opens
+  double kt_ms[3] = {0, 0, 0};          // last factor: diagonal tiles, panels, updates
+  long long kt_n[3] = {0, 0, 0};        // and their launch groups
   float stage_ms[4] = {0, 0, 0, 0};
 
   std::vector<ahlp::DeviceBuf> allocs;
@@ -258,20 +278,27 @@ long long launch_count();
 // All wrappers enqueue on p->stream and return the cudaError_t of the launch.
 cudaError_t launch_dscale(ahlp_problem *p);   // dscale = x / (z + fac_rho_x x)
 cudaError_t launch_form(ahlp_problem *p, double delta);
+// prof (nullable): a handle whose kernel-class timer records the launches
+// (kt_mark); classes 0 diagonal tiles, 1 panels, 2 trailing updates
 cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
-                         const double *diag0, double tol, int *status, cudaStream_t s);
+                         const double *diag0, double tol, int *status, cudaStream_t s,
+                         ahlp_problem *prof = nullptr);
 // float-float (hi = aug32, lo): diagonal tiles and panels in FP64 arithmetic,
 // trailing updates in double-float; then hi + lo is expanded into out (the
 // FP64 factor buffer, elems entries), which the Schur assembly and the solves use
+// with oz (a handle set up by oz_setup) the trailing updates run on the
+// tensor cores as exact FP16 digit products (k_tc.cu)
 cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
                             const BlkInfo *info, const std::vector<BlkInfo> &h,
-                            const double *diag0, double tol, int *status, cudaStream_t s);
+                            const double *diag0, double tol, int *status, cudaStream_t s,
+                            ahlp_problem *oz = nullptr, ahlp_problem *prof = nullptr);
 // FP32: also writes the inverted diagonal tiles into tinv (see launch_tinv);
 // with tc (a handle set up by tc_setup) the trailing updates run on the
 // tensor cores (k_tc.cu), else on the FP32 pipe
 cudaError_t launch_pchol_f32(float *buf, float *tinv, const BlkInfo *info,
                              const std::vector<BlkInfo> &h, const double *diag0, double tol,
-                             int *status, cudaStream_t s, ahlp_problem *tc = nullptr);
+                             int *status, cudaStream_t s, ahlp_problem *tc = nullptr,
+                             ahlp_problem *prof = nullptr);
 // forward / backward solves with one partial factor per CTA (the border
 // factors; vectors FP64, held in shared memory)
 cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,
@@ -283,6 +310,10 @@ cudaError_t launch_tinv(ahlp_problem *p);
 cudaError_t launch_trsv(ahlp_problem *p, bool forward);
 cudaError_t launch_schur_assemble(ahlp_problem *p, double delta, double rho);
 cudaError_t launch_schur_factor(ahlp_problem *p);
+// cyclic reduction of the link chain: factor (T_j, Linv_j, GL_j, GR_j, and Z
+// into Et) and the forward / backward solves in place on the link part of u
+cudaError_t launch_bcr_factor(ahlp_problem *p);
+cudaError_t launch_bcr_solve(ahlp_problem *p, double *u, bool forward);
 cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
                          const double *r_c, double *dx, double *dy, double *dz, bool adjoint);
 cudaError_t launch_residual(ahlp_problem *p, const double *r_d, const double *r_p,
@@ -335,6 +366,17 @@ cudaError_t launch_step_dot(const double *x, const double *dx, double ap, const 
 // false when the driver has no tensor-map encoder
 bool tc_setup(ahlp_problem *p);
 cudaError_t launch_update_tc(ahlp_problem *p, int k, cudaStream_t s);
+// the same for float-float factors: FP16 digit staging and job offsets
+bool oz_setup(ahlp_problem *p);
+cudaError_t launch_update_oz(ahlp_problem *p, int k, cudaStream_t s);
+
+// ---- kernel-class timer (option profile_kernels) -----------------------------
+// kt_mark records an event on s that ends the previous mark's interval and
+// opens one of class cls (0 diagonal tiles, 1 panels, 2 trailing updates,
+// 3 closes without opening); kt_collect, after the stream has synchronised,
+// sums the intervals per class into kt_ms and their counts into kt_n
+void kt_mark(ahlp_problem *p, int cls, cudaStream_t s);
+void kt_collect(ahlp_problem *p);
 
 // ---- host runtime helpers (api.cpp) -------------------------------------------
 // device allocations owned by the handle (freed at destroy); throw Fail

@@ -23,6 +23,7 @@ using namespace ahlp;
 namespace ahlp {
 cudaError_t set_dense_smem_limits(int bytes);
 cudaError_t set_schur_smem_limits(int bytes);
+cudaError_t set_bcr_smem_limits(int lmax);
 }
 
 static std::string g_create_err;
@@ -328,6 +329,9 @@ void ahlp_default_options(ahlp_options *o) {
   o->ipm_refine_tol = 1e-6;
   o->correctors_by_cost = 1;
   o->fp32_update = 0;
+  o->ff_update = 0;
+  o->schur_chain = 0;
+  o->profile_kernels = 0;
   o->iter_cb = nullptr;
   o->iter_cb_ctx = nullptr;
 }
@@ -356,6 +360,7 @@ const char *ahlp_last_error(const ahlp_problem *p) {
 
 void arrowhead_lp_destroy(ahlp_problem *p) {
   if (!p) return;
+  for (auto e : p->kt_pool) cudaEventDestroy(e);
   for (auto &b : p->allocs) cudaFree(b.ptr);
   if (p->gm_V) cudaFree(p->gm_V);
   if (p->gm_Z) cudaFree(p->gm_Z);
@@ -388,7 +393,8 @@ static int check_options(const ahlp_options &o, std::string &err) {
       !(o.fp32_cond_max >= 1) || o.max_correctors < 0 || o.max_correctors > 8 ||
       !(o.ipm_refine_tol >= 0 && o.ipm_refine_tol < 1) ||
       (o.correctors_by_cost != 0 && o.correctors_by_cost != 1) || o.fp32_update < 0 ||
-      o.fp32_update > 2) {
+      o.fp32_update > 2 || o.ff_update < 0 || o.ff_update > 2 || o.schur_chain < 0 ||
+      o.schur_chain > 1 || o.profile_kernels < 0 || o.profile_kernels > 1) {
     err = "invalid option value";
     return AHLP_ERR_INVALID_ARG;
   }
@@ -1146,6 +1152,42 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
       }
       p->nchain_seg = (int)seg.size() / 2;
       if (!seg.empty()) p->chain_seg = dupload(p, seg);
+      // cyclic-reduction schedule: in a segment of n pairs position i is
+      // eliminated at level ctz(i + 1); per level the list of its pairs, per
+      // pair its level and its segment
+      {
+        std::vector<int> info((size_t)4 * std::max(N - 1, 1), 0), lvl(std::max(N - 1, 1), -1);
+        int nlev = 0;
+        for (size_t sgi = 0; sgi < seg.size(); sgi += 2) {
+          const int jb = seg[sgi], je = seg[sgi + 1];
+          for (int j = jb; j < je; ++j) {
+            int v = 0;
+            while (((j - jb + 1) >> v & 1) == 0) ++v;
+            lvl[j] = v;
+            info[4 * j] = v;
+            info[4 * j + 1] = jb;
+            info[4 * j + 2] = je;
+            nlev = std::max(nlev, v + 1);
+          }
+        }
+        std::vector<int> order;
+        p->bcr_loff.assign(1, 0);
+        for (int v = 0; v < nlev; ++v) {
+          for (int j = 0; j + 1 < N; ++j)
+            if (lvl[j] == v) order.push_back(j);
+          p->bcr_loff.push_back((int)order.size());
+        }
+        int lm = 0;
+        for (int v : l) lm = std::max(lm, v);
+        p->bcr_lmax = lm;
+        if (!order.empty()) {
+          p->bcr_order = dupload(p, order);
+          p->bcr_info = dupload(p, info);
+          p->bcr_GL = dalloc<double>(p, (long long)(N - 1) * lm * lm);
+          p->bcr_GR = dalloc<double>(p, (long long)(N - 1) * lm * lm);
+          ck(set_bcr_smem_limits(lm), "smem limit");
+        }
+      }
       // link-row range of each border column of Z = L_T^-1 E': all links for one
       // LP; in a batch, the links of the LP that owns the linking variable or
       // global row
@@ -1285,6 +1327,34 @@ void read_scalars(ahlp_problem *p, int k) {
   ck(cudaStreamSynchronize(p->stream), "stream sync");
 }
 
+void kt_mark(ahlp_problem *p, int cls, cudaStream_t s) {
+  const size_t i = p->kt_cls.size();
+  if (i == p->kt_pool.size()) {
+    cudaEvent_t e;
+    ck(cudaEventCreate(&e), "event");
+    p->kt_pool.push_back(e);
+  }
+  ck(cudaEventRecord(p->kt_pool[i], s), "event");
+  p->kt_cls.push_back(cls);
+}
+
+void kt_collect(ahlp_problem *p) {
+  for (int c = 0; c < 3; ++c) {
+    p->kt_ms[c] = 0.0;
+    p->kt_n[c] = 0;
+  }
+  for (size_t i = 0; i + 1 < p->kt_cls.size(); ++i) {
+    const int c = p->kt_cls[i];
+    if (c < 0 || c > 2) continue;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p->kt_pool[i], p->kt_pool[i + 1]) == cudaSuccess) {
+      p->kt_ms[c] += ms;
+      ++p->kt_n[c];
+    }
+  }
+  p->kt_cls.clear();
+}
+
 int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol, bool ff_nan_up) {
   // an FP32 pivot that lost six digits, a float-float one that lost eleven,
   // is rounding noise
@@ -1335,6 +1405,8 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol, boo
   }
   ck(launch_form(p, delta), "form");
   ck(cudaEventRecord(p->ev[1], s), "event");
+  ahlp_problem *prof = p->opt.profile_kernels ? p : nullptr;
+  p->kt_cls.clear();
   if (p->fac_prec == kPrecFP32) {
     // trailing updates on the tensor cores unless the FP32 pipe is asked for
     ahlp_problem *tc = nullptr;
@@ -1348,15 +1420,19 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol, boo
     }
     p->fp32_update = tc ? 2 : 1;
     ck(launch_pchol_f32(p->aug32, p->tinv32, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol,
-                        p->status, s, tc),
+                        p->status, s, tc, prof),
        "pchol");
   }
-  else if (p->fac_prec == kPrecFF)
+  else if (p->fac_prec == kPrecFF) {
+    ahlp_problem *oz = (p->opt.ff_update != 1 && oz_setup(p)) ? p : nullptr;
+    p->ff_update = oz ? 2 : 1;
     ck(launch_pchol_ff(p->aug32, p->aug_lo, p->aug, p->aug_elems, p->blk, p->h_blk, p->diag0,
-                       p->fac_pivot_tol, p->status, s),
+                       p->fac_pivot_tol, p->status, s, oz, prof),
        "pchol");
+  }
   else
-    ck(launch_pchol(p->aug, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s), "pchol");
+    ck(launch_pchol(p->aug, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s, prof),
+       "pchol");
   ck(launch_tinv(p), "diagonal tile inverses");
   ck(cudaEventRecord(p->ev[2], s), "event");
   ck(launch_schur_assemble(p, delta, rho), "schur assemble");
@@ -1370,6 +1446,7 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol, boo
   cudaEventElapsedTime(&p->stage_ms[0], p->ev[0], p->ev[1]);
   cudaEventElapsedTime(&p->stage_ms[1], p->ev[1], p->ev[2]);
   cudaEventElapsedTime(&p->stage_ms[2], p->ev[2], p->ev[3]);
+  if (prof) kt_collect(p);
   p->tiny_pivots = st[1];
   if (st[4] != 0)
     return set_err(p, AHLP_ERR_TIMEOUT,
@@ -1639,6 +1716,15 @@ int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld) {
 }
 
 int64_t ahlp_launch_count(void) { return ahlp::launch_count(); }
+
+int kkt_factor_kernel_times(const ahlp_problem *p, double *ms3, int64_t *launches3) {
+  if (!p || !ms3) return AHLP_ERR_INVALID_ARG;
+  for (int c = 0; c < 3; ++c) {
+    ms3[c] = p->kt_ms[c];
+    if (launches3) launches3[c] = p->kt_n[c];
+  }
+  return AHLP_OK;
+}
 
 int ahlp_transfer_bytes(const ahlp_problem *p, int64_t *h2d, int64_t *d2h) {
   if (!p) return AHLP_ERR_INVALID_ARG;

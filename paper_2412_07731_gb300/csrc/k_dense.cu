@@ -14,6 +14,7 @@
 // FP64 and FP32 are templated on the storage type; the FP32 and float-float
 // trailing updates and the FP32 diagonal tile have their own kernels.
 // Entries are always formed in FP64 and rounded once.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "ahlp_internal.h"
@@ -540,8 +541,46 @@ __global__ void __launch_bounds__(kThreads) pchol_potrf_ff_kernel(float *hi, flo
   }
 }
 
+// With dstage (the tensor-core float-float update, k_tc.cu) the finished
+// panel tile is also written as exact integer digits: per row r, E_r is the
+// exponent with max_c |x_rc| < 2^E_r, and x = 2^E_r sum_s d_s 2^(-9-8s),
+// s = 0..5, with |d_0| <= 512 and |d_s| <= 128 (s > 0), each digit an FP16
+// integer (49 bits in all).  The digits are taken from the stored pair
+// (hi, lo), scaled by a power of two and peeled off in FP32 with every
+// remainder kept exactly (a two-word remainder, renormalised by two-sum).
+// Digit plane s of the tile is a 64 x 64 FP16 K-major operand without
+// swizzling: entry (r, c) at (r/8)*512 + (c/8)*64 + (r%8)*8 + c%8; the six
+// planes follow each other (4096 entries each).  Rows past the matrix and
+// columns past the pivots are zero.
+constexpr int kOzDigits = 6;
+
+__device__ __forceinline__ void two_sum_f(float &a, float &b) {   // (a, b) <- fl(a+b), error
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  a = s;
+  b = err;
+}
+
+__device__ __forceinline__ void oz_digits(float h, float l, int e, float (&d)[kOzDigits]) {
+  h = ldexpf(h, 9 - e);
+  l = ldexpf(l, 9 - e);
+#pragma unroll
+  for (int s = 0; s < kOzDigits; ++s) {
+    if (s > 0) {
+      h = __fmul_rn(h, 256.0f);
+      l = __fmul_rn(l, 256.0f);
+    }
+    const float q = rintf(h);
+    d[s] = q;
+    h = __fsub_rn(h, q);   // exact: q is the integer nearest to h
+    two_sum_f(h, l);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, float *lo,
-                                                                 const BlkInfo *blk, int k) {
+                                                                 const BlkInfo *blk, int k,
+                                                                 __half *dstage, int *dexp) {
   const BlkInfo bi = blk[blockIdx.y];
   if (k >= bi.Tp) return;
   const int I = k + 1 + blockIdx.x;
@@ -576,6 +615,36 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, floa
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
     if (r < nri && c < nr) ff_put(hi, lo, gx + (long long)c * bi.lda + r, X[r][c]);
+  }
+  if (dstage) {
+    __shared__ int s_exp[NB];
+    const long long slot = bi.soff + I;
+    if (threadIdx.x < NB) {
+      const int r = threadIdx.x;
+      float mx = 0.0f;
+      if (r < nri)
+        for (int c = 0; c < npiv; ++c) mx = fmaxf(mx, fabsf((float)X[r][c]));
+      int e = 0;
+      if (mx > 0.0f) frexpf(mx, &e);   // mx = f 2^e, f in [0.5, 1)
+      s_exp[r] = e;
+      dexp[slot * NB + r] = e;
+    }
+    __syncthreads();
+    __half *st = dstage + slot * (kOzDigits * NB * NB);
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+      const int r = (e >> 9) * 8 + ((e >> 3) & 7), c = ((e >> 6) & 7) * 8 + (e & 7);
+      float d[kOzDigits];
+      if (r < nri && c < npiv) {
+        const double v = X[r][c];
+        const float h = (float)v;
+        oz_digits(h, (float)(v - (double)h), s_exp[r], d);
+      } else {
+#pragma unroll
+        for (int q = 0; q < kOzDigits; ++q) d[q] = 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < kOzDigits; ++q) st[q * NB * NB + e] = __float2half_rn(d[q]);
+    }
   }
 }
 
@@ -1370,7 +1439,7 @@ constexpr size_t tinv_smem() {
 template <typename T>
 cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkInfo> &h,
                     const double *diag0, double tol, int *status, cudaStream_t s,
-                    ahlp_problem *tc = nullptr) {
+                    ahlp_problem *tc = nullptr, ahlp_problem *prof = nullptr) {
   int nblk = (int)h.size();
   if (nblk == 0) return cudaSuccess;
   int maxTp = 0;
@@ -1384,19 +1453,24 @@ cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkI
       if (t * (t + 1) / 2 > maxTrail) maxTrail = t * (t + 1) / 2;
     }
     if constexpr (sizeof(T) == sizeof(float)) {
+      if (prof) kt_mark(prof, 0, s);
       count_launch(), pchol_potrf_f32_kernel<<<nblk, kPotrf32Threads, 0, s>>>(buf, tinv, info, k, diag0,
                                                                  (float)tol, status);
+      if (prof) kt_mark(prof, 1, s);
       if (maxPanel > 0)
         count_launch(), pchol_trsm_inv_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads,
                                                    trsm_smem<T>(), s>>>(
                             buf, tinv, info, k, tc ? tc->pstage : nullptr);
     } else {
+      if (prof) kt_mark(prof, 0, s);
       count_launch(), pchol_potrf_kernel<T><<<nblk, kThreads, 0, s>>>(buf, info, k, diag0, tol,
                                                                       status);
+      if (prof) kt_mark(prof, 1, s);
       if (maxPanel > 0)
         count_launch(), pchol_trsm_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads,
                                                trsm_smem<T>(), s>>>(buf, info, k);
     }
+    if (prof) kt_mark(prof, 2, s);
     if (maxTrail > 0) {
       if constexpr (sizeof(T) == sizeof(float)) {
         if (tc) {
@@ -1410,6 +1484,7 @@ cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkI
         count_launch(), pchol_update_kernel<T><<<dim3((unsigned)maxTrail, nblk), kThreads, 0, s>>>(
                             buf, info, k);
     }
+    if (prof) kt_mark(prof, 3, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1446,7 +1521,8 @@ cudaError_t launch_form(ahlp_problem *p, double delta) {
 
 cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
                             const BlkInfo *info, const std::vector<BlkInfo> &h,
-                            const double *diag0, double tol, int *status, cudaStream_t s) {
+                            const double *diag0, double tol, int *status, cudaStream_t s,
+                            ahlp_problem *oz, ahlp_problem *prof) {
   int nblk = (int)h.size();
   if (nblk == 0) return cudaSuccess;
   int maxTp = 0;
@@ -1459,14 +1535,25 @@ cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
       if (t > maxPanel) maxPanel = t;
       if (t * (t + 1) / 2 > maxTrail) maxTrail = t * (t + 1) / 2;
     }
+    if (prof) kt_mark(prof, 0, s);
     count_launch(), pchol_potrf_ff_kernel<<<nblk, kThreads, 0, s>>>(hi, lo, info, k, diag0, tol,
                                                                     status);
+    if (prof) kt_mark(prof, 1, s);
     if (maxPanel > 0)
       count_launch(), pchol_trsm_ff_kernel<<<dim3((unsigned)maxPanel, nblk), kThreads,
-                                             trsm_smem<double>(), s>>>(hi, lo, info, k);
-    if (maxTrail > 0)
-      count_launch(), pchol_update_ff8_kernel<<<dim3((unsigned)maxTrail, nblk), kUpdFFThreads,
-                                                kUpdFFSmem, s>>>(hi, lo, info, k);
+                                             trsm_smem<double>(), s>>>(
+                          hi, lo, info, k, oz ? oz->dstage : nullptr, oz ? oz->dexp : nullptr);
+    if (prof) kt_mark(prof, 2, s);
+    if (maxTrail > 0) {
+      if (oz) {
+        cudaError_t e = launch_update_oz(oz, k, s);
+        if (e != cudaSuccess) return e;
+      } else {
+        count_launch(), pchol_update_ff8_kernel<<<dim3((unsigned)maxTrail, nblk), kUpdFFThreads,
+                                                  kUpdFFSmem, s>>>(hi, lo, info, k);
+      }
+    }
+    if (prof) kt_mark(prof, 3, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1476,14 +1563,16 @@ cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
 }
 
 cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
-                         const double *diag0, double tol, int *status, cudaStream_t s) {
-  return pchol_t<double>(buf, nullptr, info, h, diag0, tol, status, s);
+                         const double *diag0, double tol, int *status, cudaStream_t s,
+                         ahlp_problem *prof) {
+  return pchol_t<double>(buf, nullptr, info, h, diag0, tol, status, s, nullptr, prof);
 }
 
 cudaError_t launch_pchol_f32(float *buf, float *tinv, const BlkInfo *info,
                              const std::vector<BlkInfo> &h, const double *diag0, double tol,
-                             int *status, cudaStream_t s, ahlp_problem *tc) {
-  return pchol_t<float>(buf, tinv, info, h, diag0, tol, status, s, tc);
+                             int *status, cudaStream_t s, ahlp_problem *tc,
+                             ahlp_problem *prof) {
+  return pchol_t<float>(buf, tinv, info, h, diag0, tol, status, s, tc, prof);
 }
 
 cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,

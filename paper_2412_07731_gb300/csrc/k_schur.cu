@@ -932,8 +932,13 @@ cudaError_t launch_schur_factor(ahlp_problem *p) {
   cudaStream_t s = p->stream;
   int lmax = 0;
   for (int j = 0; j + 1 < p->N; ++j) lmax = std::max(lmax, (int)(p->link_off[j + 1] - p->link_off[j]));
+  // the solves must use the factor that was built: remember which one
+  p->fac_bcr = p->opt.schur_chain == 0 && p->bcr_order != nullptr;
   if (p->N > 1 && lmax > 0) {
-    if (p->nchain_seg > 0 && lmax <= kChainRegL) {
+    if (p->fac_bcr) {
+      cudaError_t e = launch_bcr_factor(p);
+      if (e != cudaSuccess) return e;
+    } else if (p->nchain_seg > 0 && lmax <= kChainRegL) {
       const CArgs A = cargs(p);
       count_launch(), chain_critical_kernel<<<p->nchain_seg, 256, (size_t)lmax * lmax * 8, s>>>(A);
       count_launch(), chain_ops_kernel<<<p->N - 1, 128, (size_t)2 * lmax * lmax * 8, s>>>(A);
@@ -995,9 +1000,15 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
                                (long long)kChainSmem /
                                    std::max(1LL, 8LL * ((long long)lmax * lmax + lmax))));
     const size_t csm = (size_t)stages * ((size_t)lmax * lmax + lmax) * sizeof(double);
-    if (p->nl > 0 && lmax > 0 && p->nchain_seg > 0)
-      count_launch(), chain_solve_kernel<<<p->nchain_seg, kChainSolveThreads, csm, s>>>(
-          C, p->svec, 0, stages, lmax);
+    if (p->nl > 0 && lmax > 0 && p->nchain_seg > 0) {
+      if (p->fac_bcr) {
+        e = launch_bcr_solve(p, p->svec, true);
+        if (e != cudaSuccess) return e;
+      } else {
+        count_launch(), chain_solve_kernel<<<p->nchain_seg, kChainSolveThreads, csm, s>>>(
+            C, p->svec, 0, stages, lmax);
+      }
+    }
     if (p->B > 0) {
       if (p->nl > 0) count_launch(), border_rhs_kernel<<<nb((long long)p->B * 32, 256), 256, 0, s>>>(p->Et, p->B, p->nl, p->svec);
       double *sb = p->svec + p->nl;
@@ -1018,9 +1029,15 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
       }
       if (p->nl > 0) count_launch(), link_back_kernel<<<nb(p->nl, 128), 128, 0, s>>>(p->Et, p->B, p->nl, p->svec);
     }
-    if (p->nl > 0 && lmax > 0 && p->nchain_seg > 0)
-      count_launch(), chain_solve_kernel<<<p->nchain_seg, kChainSolveThreads, csm, s>>>(
-          C, p->svec, 1, stages, lmax);
+    if (p->nl > 0 && lmax > 0 && p->nchain_seg > 0) {
+      if (p->fac_bcr) {
+        e = launch_bcr_solve(p, p->svec, false);
+        if (e != cudaSuccess) return e;
+      } else {
+        count_launch(), chain_solve_kernel<<<p->nchain_seg, kChainSolveThreads, csm, s>>>(
+            C, p->svec, 1, stages, lmax);
+      }
+    }
     int kmax = 0;
     for (int k : p->ki) kmax = std::max(kmax, k);
     if (kmax > 0)

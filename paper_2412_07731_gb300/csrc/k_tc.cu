@@ -28,6 +28,7 @@
 // the failure in the factor's status word, waits (bounded again) for its own
 // operations in flight, frees its tensor memory and returns.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -163,6 +164,37 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// One update job of step k: block b, the row tile pair (I0, I0 + 1) (the
+// second one only when has_i1) and the column tile J.  The jobs of a step are
+// numbered block after block (joff: prefix over the blocks); inside a block
+// with t trailing tiles, row pair R holds min(2R + 2, t) jobs, so the jobs
+// before it number R(R + 1).
+struct Job {
+  int b, I0, J;
+  bool has_i1;
+};
+
+__device__ __forceinline__ Job decode_job(const int *joff, int nblk, int k, const BlkInfo *blk) {
+  const int q = blockIdx.x;
+  int lo = 0, hi = nblk;   // joff[lo] <= q < joff[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (joff[mid] <= q) lo = mid;
+    else hi = mid;
+  }
+  const int t = blk[lo].T - k - 1;
+  const long long local = q - joff[lo];
+  long long R = (long long)((sqrt(4.0 * (double)local + 1.0) - 1.0) * 0.5);
+  while (R * (R + 1) > local) --R;
+  while ((R + 1) * (R + 2) <= local) ++R;
+  Job j;
+  j.b = lo;
+  j.I0 = k + 1 + 2 * (int)R;
+  j.J = k + 1 + (int)(local - R * (R + 1));
+  j.has_i1 = 2 * R + 1 < t;
+  return j;
+}
+
 struct TcArgs {
   const float *stage;      // staged panel tiles: per slot 4096 hi then 4096 lo words
   const int *joff;         // [nblk + 1] job prefix of this step over the blocks
@@ -186,24 +218,10 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_tc_kernel(const TcArg
   float *b_lo = reinterpret_cast<float *>(base + 2 * kSmemA + kSmemB);
 
   // ---- which block and tiles ------------------------------------------------
-  const int q = blockIdx.x;
-  int lo = 0, hi = args.nblk;   // joff[lo] <= q < joff[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (args.joff[mid] <= q) lo = mid;
-    else hi = mid;
-  }
-  const int b = lo;
+  const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk);
+  const int b = jb.b, I0 = jb.I0, J = jb.J;
+  const bool has_i1 = jb.has_i1;
   const BlkInfo bi = args.blk[b];
-  const int k = args.k;
-  const int t = bi.T - k - 1;
-  const long long local = q - args.joff[b];
-  long long R = (long long)((sqrt(4.0 * (double)local + 1.0) - 1.0) * 0.5);
-  while (R * (R + 1) > local) --R;
-  while ((R + 1) * (R + 2) <= local) ++R;
-  const int jj = (int)(local - R * (R + 1));
-  const int I0 = k + 1 + 2 * (int)R, J = k + 1 + jj;
-  const bool has_i1 = 2 * R + 1 < t;
   const float *st0 = args.stage + (bi.soff + I0) * 8192LL;
   const float *st1 = args.stage + (bi.soff + I0 + 1) * 8192LL;
   const float *stJ = args.stage + (bi.soff + J) * 8192LL;
@@ -314,6 +332,242 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_tc_kernel(const TcArg
                  : "memory");
 }
 
+
+// --------------------------------------------------------------------------
+// Float-float trailing update on the tensor cores.  The panel kernel leaves
+// every panel tile as six planes of FP16 integer digits with one exponent per
+// row, x = 2^E_r sum_s d_s 2^(-9-8s) (|d_0| <= 512, |d_s| <= 128).  Then
+//     sum_k x_rk y_ck = 2^(E_r + E_c - 18) sum_q 2^(-8q) D_q,
+//     D_q = sum_{s+t=q} sum_k d_s(r,k) d_t(c,k),
+// and every D_q (q <= 5) is an integer below 2^24 in magnitude over the 64
+// pivot columns (|D_0| <= 64 * 512^2, the others below 1.5 * 2^23), so the
+// tensor core's FP32 accumulation of FP16 products computes each one exactly.
+// The 21 digit products with s + t <= 5 run as kind::f16 MMAs (M = 128,
+// N = 64, K = 16) into six TMEM accumulators; the epilogue sums
+// 2^(-8q) D_q as a float-float pair (each term exact, two-sum), scales it by
+// the row and column exponents and subtracts it from C's hi/lo pair.  The
+// truncated digits and the dropped products (s + t >= 6) sit near 2^-47 of
+// sum_k |x_rk| |y_ck|, the accuracy of the double-float FP32-pipe kernel.
+// --------------------------------------------------------------------------
+constexpr int kOzQ = 6;                                   // digits per entry
+constexpr uint32_t kOzPlaneA = 2 * NB * NB * 2;           // 128 rows x 64 k FP16
+constexpr uint32_t kOzPlaneB = NB * NB * 2;               // 64 rows x 64 k FP16
+constexpr uint32_t kOzCTile = kTcM * kTcN * 4;           // one word of the 128 x 64 C tile
+constexpr uint32_t kOzSmem = kOzQ * kOzPlaneA + kOzQ * kOzPlaneB + 2 * kOzCTile + 1024;
+constexpr uint32_t kOzCols = 512;                         // TMEM: 6 accumulators of 64 columns
+
+// kind::f16 instruction descriptor: FP32 accumulator, FP16 A and B, both
+// K-major, M = 128, N = 64
+constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) |
+                               ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdescF16), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void two_sum(float &a, float &b) {   // (a, b) <- fl(a+b), error
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  a = s;
+  b = err;
+}
+
+struct OzArgs {
+  const __half *dstage;    // digit planes: per slot 6 x 4096 halves
+  const int *dexp;         // per slot 64 row exponents
+  const int *joff;
+  const BlkInfo *blk;
+  const CUtensorMap *tmap; // [2 nblk]: each block's hi matrix, then its lo matrix
+  int nblk, k;
+  int *status;
+};
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(dst),
+      "l"(tm), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *tm, int x, int y, uint32_t src) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(tm),
+      "r"(x), "r"(y), "r"(src)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads) pchol_update_oz_kernel(const OzArgs args) {
+  extern __shared__ __align__(1024) unsigned char oz_raw[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  __shared__ int eA[kTcM], eB[kTcN];
+  unsigned char *base = oz_raw + ((1024 - (smem_u32(oz_raw) & 1023)) & 1023);
+  const uint32_t sA = smem_u32(base), sB = sA + kOzQ * kOzPlaneA;
+  // the C tile (hi, then lo), [64 columns][128 rows], the tensor maps' box order
+  float *c_hi = reinterpret_cast<float *>(base + kOzQ * kOzPlaneA + kOzQ * kOzPlaneB);
+  float *c_lo = c_hi + kTcM * kTcN;
+
+  const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk);
+  const int b = jb.b, I0 = jb.I0, J = jb.J;
+  const bool has_i1 = jb.has_i1;
+  const BlkInfo bi = args.blk[b];
+  const long long slot0 = bi.soff + I0, slotJ = bi.soff + J;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t bar_ld = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+
+  {
+    const int r = threadIdx.x;   // 128 threads: the A rows, then the B columns
+    eA[r] = (r < NB || has_i1) ? args.dexp[slot0 * NB + r] : 0;
+    if (r < kTcN) eB[r] = args.dexp[slotJ * NB + r];
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(kOzCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    mbar_init(bar_ld, 1);
+    mbar_init(bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (threadIdx.x == 0) {
+    const __half *st0 = args.dstage + slot0 * (kOzQ * NB * NB);
+    const __half *stJ = args.dstage + slotJ * (kOzQ * NB * NB);
+    const uint32_t plane = NB * NB * 2;   // bytes of one 64-row plane
+    const CUtensorMap *tmh = args.tmap + b, *tml = args.tmap + args.nblk + b;
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmh) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tml) : "memory");
+    // the whole box counts, rows past the matrix included (zero-filled)
+    mbar_expect_tx(bar_ld, (has_i1 ? 3u : 2u) * kOzQ * plane + 2 * kOzCTile);
+    tma_load_2d(smem_u32(c_hi), tmh, I0 * NB, J * NB, bar_ld);
+    tma_load_2d(smem_u32(c_lo), tml, I0 * NB, J * NB, bar_ld);
+#pragma unroll
+    for (int q = 0; q < kOzQ; ++q) {
+      bulk_g2s(sA + q * kOzPlaneA, st0 + q * NB * NB, plane, bar_ld);
+      if (has_i1) bulk_g2s(sA + q * kOzPlaneA + plane, st0 + (kOzQ + q) * NB * NB, plane, bar_ld);
+      bulk_g2s(sB + q * kOzPlaneB, stJ + q * NB * NB, plane, bar_ld);
+    }
+    bool ok = mbar_wait(bar_ld, 0);
+    if (ok) {
+      tc_fence_after();
+#pragma unroll
+      for (int q = 0; q < kOzQ; ++q)
+#pragma unroll
+        for (int sd = 0; sd <= q; ++sd)
+#pragma unroll
+          for (int ks = 0; ks < NB / 16; ++ks) {
+            // K step ks: two 16-byte core-matrix columns, 2 x 128 bytes further
+            const uint64_t da = smem_desc(sA + sd * kOzPlaneA + ks * 256, 128, 1024);
+            const uint64_t db = smem_desc(sB + (q - sd) * kOzPlaneB + ks * 256, 128, 1024);
+            mma_f16(tmem + q * kTcN, da, db, (sd | ks) != 0);
+          }
+      mma_commit(bar_mma);
+      ok = mbar_wait(bar_mma, 0);
+      if (!ok) s_fail = 2;
+    } else {
+      s_fail = 1;
+    }
+  }
+  __syncthreads();
+  tc_fence_after();
+  const int fail = s_fail;
+  if (fail) {
+    if (threadIdx.x == 0) {
+      atomicExch(&args.status[4], 1);
+      if (fail == 1) mbar_wait(bar_ld, 0);
+      else mbar_wait(bar_mma, 0);
+    }
+    __syncthreads();
+  } else {
+    const int r = warp * 32 + lane;
+    const int grow = I0 * NB + r;
+    const int er = eA[r];
+#pragma unroll 1
+    for (int ch = 0; ch < kTcN / 16; ++ch) {
+      float D[kOzQ][16];
+#pragma unroll
+      for (int q = 0; q < kOzQ; ++q)
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kTcN + ch * 16), D[q]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = ch * 16 + j, gcol = J * NB + c;
+        // entries above the diagonal keep their value (the tile goes back
+        // whole); rows and columns past the matrix are clipped by the store
+        if (gcol > grow) continue;
+        float sh = D[0][j], sl = 0.0f;
+#pragma unroll
+        for (int q = 1; q < kOzQ; ++q) {
+          float t = ldexpf(D[q][j], -8 * q);   // exact
+          two_sum(sh, t);
+          sl = __fadd_rn(sl, t);
+        }
+        two_sum(sh, sl);
+        const int sc = er + eB[c] - 18;
+        sh = ldexpf(sh, sc);
+        sl = ldexpf(sl, sc);
+        // (ch + cl) - (sh + sl): two-sum of the high parts, low parts added
+        const int e = c * kTcM + r;
+        const float chv = c_hi[e], clv = c_lo[e];
+        const float tt = __fsub_rn(chv, sh);
+        const float bv = __fsub_rn(tt, chv);
+        const float err = __fadd_rn(__fsub_rn(chv, __fsub_rn(tt, bv)), __fsub_rn(-sh, bv));
+        const float el = __fadd_rn(err, __fsub_rn(clv, sl));
+        const float h = __fadd_rn(tt, el);
+        c_hi[e] = h;
+        c_lo[e] = __fsub_rn(el, __fsub_rn(h, tt));
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tma_store_2d(args.tmap + b, I0 * NB, J * NB, smem_u32(c_hi));
+      tma_store_2d(args.tmap + args.nblk + b, I0 * NB, J * NB, smem_u32(c_lo));
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kOzCols)
+                 : "memory");
+}
+
 // the number of update jobs of a block with t trailing tiles: row pairs R
 // cover tiles (2R, 2R+1) and the columns up to their last tile
 long long tc_jobs_of(int t) {
@@ -328,6 +582,26 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// job offsets per step, over the blocks (shared by both tensor-core updates)
+void jobs_setup(ahlp_problem *p) {
+  if (p->tc_joff) return;
+  const int N = (int)p->h_blk.size();
+  const int maxTp = p->maxTp;
+  std::vector<int> joff((size_t)std::max(maxTp, 1) * (N + 1), 0);
+  p->tc_jobs.assign(maxTp, 0);
+  for (int k = 0; k < maxTp; ++k) {
+    long long acc = 0;
+    for (int b = 0; b < N; ++b) {
+      joff[(size_t)k * (N + 1) + b] = (int)acc;
+      const BlkInfo &bi = p->h_blk[b];
+      if (k < bi.Tp) acc += tc_jobs_of(bi.T - k - 1);
+    }
+    joff[(size_t)k * (N + 1) + N] = (int)acc;
+    p->tc_jobs[k] = acc;
+  }
+  p->tc_joff = static_cast<int *>(dupload_bytes(p, joff.data(), joff.size() * sizeof(int)));
+}
 
 }  // namespace
 
@@ -359,22 +633,8 @@ bool tc_setup(ahlp_problem *p) {
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
   }
-  // job offsets per step, over the blocks
-  const int maxTp = p->maxTp;
-  std::vector<int> joff((size_t)maxTp * (N + 1));
-  p->tc_jobs.assign(maxTp, 0);
-  for (int k = 0; k < maxTp; ++k) {
-    long long acc = 0;
-    for (int b = 0; b < N; ++b) {
-      joff[(size_t)k * (N + 1) + b] = (int)acc;
-      const BlkInfo &bi = p->h_blk[b];
-      if (k < bi.Tp) acc += tc_jobs_of(bi.T - k - 1);
-    }
-    joff[(size_t)k * (N + 1) + N] = (int)acc;
-    p->tc_jobs[k] = acc;
-  }
+  jobs_setup(p);
   p->tc_tmap = dupload_bytes(p, maps.data(), sizeof(CUtensorMap) * maps.size());
-  p->tc_joff = static_cast<int *>(dupload_bytes(p, joff.data(), joff.size() * sizeof(int)));
   p->pstage = static_cast<float *>(
       dalloc_bytes(p, (size_t)std::max(p->stage_slots, 1LL) * 8192 * sizeof(float)));
   ck(cudaFuncSetAttribute(pchol_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -391,6 +651,56 @@ cudaError_t launch_update_tc(ahlp_problem *p, int k, cudaStream_t s) {
            reinterpret_cast<const CUtensorMap *>(p->tc_tmap), (int)p->h_blk.size(), k,
            p->status};
   count_launch(), pchol_update_tc_kernel<<<(unsigned)jobs, kTcThreads, kSmemBytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+// FP16 digit staging and job offsets of the float-float tensor-core update
+bool oz_setup(ahlp_problem *p) {
+  if (p->oz_ready) return true;
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  auto encode = reinterpret_cast<EncodeTiledFn>(fn);
+  const int N = (int)p->h_blk.size();
+  std::vector<CUtensorMap> maps(std::max(2 * N, 1));
+  for (int w = 0; w < 2; ++w)
+    for (int b = 0; b < N; ++b) {
+      const BlkInfo &bi = p->h_blk[b];
+      const cuuint64_t dims[2] = {(cuuint64_t)bi.a, (cuuint64_t)bi.a};
+      const cuuint64_t strides[1] = {(cuuint64_t)bi.lda * sizeof(float)};
+      const cuuint32_t box[2] = {(cuuint32_t)kTcM, (cuuint32_t)kTcN};
+      const cuuint32_t estr[2] = {1, 1};
+      CUresult r = encode(&maps[(size_t)w * N + b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                          (w == 0 ? p->aug32 : p->aug_lo) + bi.base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return false;
+    }
+  jobs_setup(p);
+  p->oz_tmap = dupload_bytes(p, maps.data(), sizeof(CUtensorMap) * maps.size());
+  p->dstage = static_cast<__half *>(
+      dalloc_bytes(p, (size_t)std::max(p->stage_slots, 1LL) * kOzQ * NB * NB * sizeof(__half)));
+  p->dexp = static_cast<int *>(
+      dalloc_bytes(p, (size_t)std::max(p->stage_slots, 1LL) * NB * sizeof(int)));
+  ck(cudaFuncSetAttribute(pchol_update_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)kOzSmem),
+     "float-float tensor-core update shared memory");
+  p->oz_ready = true;
+  return true;
+}
+
+cudaError_t launch_update_oz(ahlp_problem *p, int k, cudaStream_t s) {
+  const long long jobs = p->tc_jobs[k];
+  if (jobs <= 0) return cudaSuccess;
+  OzArgs a{p->dstage, p->dexp, p->tc_joff + (size_t)k * (p->h_blk.size() + 1), p->blk,
+           reinterpret_cast<const CUtensorMap *>(p->oz_tmap), (int)p->h_blk.size(), k,
+           p->status};
+  count_launch(), pchol_update_oz_kernel<<<(unsigned)jobs, kTcThreads, kOzSmem, s>>>(a);
   return cudaGetLastError();
 }
 

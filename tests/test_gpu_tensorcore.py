@@ -105,3 +105,70 @@ def test_tensor_core_ipm_reaches_oracle_optimum(P):
     assert r["status"] == 0 and r["factors_fp32"] > 0
     assert abs(r["pobj"] - ref["pobj"]) / (1 + abs(ref["pobj"])) <= 1e-8
     prob.close()
+
+
+# ---------------------------------------------------------------------------
+# float-float factors: exact FP16 digit products on the tensor cores
+# ---------------------------------------------------------------------------
+def _ff(P, update, **kw):
+    return P.default_options(precision=P.PREC_MIXED, fp32_cond_max=1.0, ff_update=update, **kw)
+
+
+@pytest.mark.parametrize("name", sorted(SHAPES))
+def test_digit_float_float_factor_matches_double_float(P, name):
+    """At a point where D spans ~1e10, block by block, the float-float factor
+    of the digit-product update is nearly as close to the FP64 factor as the
+    double-float FP32-pipe update's is (within 10x, and below 1e-8 of the
+    block's scale: the per-row digit scaling keeps 49 bits relative to the
+    row's largest entry, not to each entry), and both give the oracle's Schur complement to 1e-10 of
+    its scale (FP32 factors reach only ~1e-5)."""
+    from paper_2412_07731_gb300._lib import kkt_block_factor_dense
+    lp = random_block_lp(10, **SHAPES[name])
+    A, x, z, *_ = _point(lp, 5, 3.0)
+    poz = P.arrowhead_lp_create(lp, _ff(P, 2))
+    pdf = P.arrowhead_lp_create(lp, _ff(P, 1))
+    p64 = P.arrowhead_lp_create(lp)
+    for prob in (poz, pdf, p64):
+        P.kkt_factor(prob, x, z, 0.0, 0.0)
+    for i in range(lp.N):
+        F64 = kkt_block_factor_dense(p64, i)
+        scale = np.abs(F64).max()
+        e_oz = np.abs(kkt_block_factor_dense(poz, i) - F64).max() / scale
+        e_dd = np.abs(kkt_block_factor_dense(pdf, i) - F64).max() / scale
+        assert e_oz <= max(10.0 * e_dd, 1e-12) and e_oz <= 1e-8, (i, e_oz, e_dd)
+    S_ref = oschur.schur_reduced(lp, x, z)
+    for prob in (poz, pdf):
+        S = P.kkt_schur_dense(prob)
+        assert np.abs(S - S_ref).max() <= 1e-10 * np.abs(S_ref).max()
+    for prob in (poz, pdf, p64):
+        prob.close()
+
+
+@pytest.mark.parametrize("name", sorted(SHAPES))
+def test_digit_float_float_direction_matches_oracle(P, name):
+    lp = random_block_lp(11, **SHAPES[name])
+    A, x, z, rd, rp, rc = _point(lp, 6, 2.0)
+    prob = P.arrowhead_lp_create(lp, _ff(P, 2))
+    P.kkt_factor(prob, x, z)
+    (dx, dy, dz), info = P.kkt_solve(prob, rd, rp, rc)
+    res = onewton.relative_residual(A, x, z, dx, dy, dz, rd, rp, rc)
+    assert res < 1e-10, (res, info)
+    assert info["refine_steps"] <= 3, info   # the factor is nearly exact
+    ex, ey, ez = onewton.direction_dense(A, x, z, rd, rp, rc)
+    got = np.concatenate([dx, dy, dz])
+    ref = np.concatenate([ex, ey, ez])
+    J = onewton.newton_matrix_dense(A, x, z)
+    bound = max(1e-9, 1e-13 * np.linalg.cond(J))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < bound
+    prob.close()
+
+
+def test_digit_float_float_ipm_reaches_oracle_optimum(P):
+    lp = random_block_lp(12, **SHAPES["ragged_multi"])
+    A, b, c = olp.assemble(lp)
+    ref = oipm.solve(A, b, c)
+    prob = P.arrowhead_lp_create(lp, _ff(P, 2))
+    (x, y, z), r = P.ipm_solve(prob)
+    assert r["status"] == 0 and r["factors_ff"] > 0
+    assert abs(r["pobj"] - ref["pobj"]) / (1 + abs(ref["pobj"])) <= 1e-8
+    prob.close()
