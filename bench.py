@@ -674,9 +674,15 @@ def run_ours(args):
     opts = dict(max_correctors=args.correctors)
     f64 = dict(dtype=torch.float64, device=dev)
 
+    tuned = {}
+
     def arm(prec, warmup, steps):
         prob = create(P, lp, prec, **opts)
         P.load().arrowhead_lp_set_stream(prob.handle, stream.cuda_stream)
+        if prec == P.PREC_MIXED and not args.no_autotune:
+            # the project's autotuner picks the trailing-update kernels of the
+            # FP32 and float-float factors on this LP's blocks (before timing)
+            tuned.update(P.autotune(prob))
         out = (torch.empty(prob.n, **f64), torch.empty(prob.m, **f64),
                torch.empty(prob.n, **f64))
         win = IterWindow(P, stream, warmup, steps, dist, local)
@@ -782,6 +788,7 @@ def run_ours(args):
             "solve": full,
             "clocks": win.clocks, "gpu_launches": win.launches,
             "roofline": roof, "block_factor": factor_roof, "stages": stages,
+            "autotune": tuned or None,
             "e2e": e2e, "cpu_baseline": cpu,
             "peaks": peaks,
         }
@@ -868,6 +875,8 @@ def main():
     ap.add_argument("--no-c1", action="store_true", help="skip the 64-block complete solves")
     ap.add_argument("--no-full-solve", action="store_true")
     ap.add_argument("--no-stages", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default trailing-update kernels (no autotuning)")
     ap.add_argument("--kkt-only", action="store_true",
                     help="time one KKT factorisation and --steps solves at a seeded point")
     ap.add_argument("--blocks", type=int, default=0,

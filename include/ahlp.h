@@ -45,7 +45,7 @@ extern "C" {
 #define AHLP_OK                   0
 #define AHLP_ERR_INVALID_ARG     -1  /* NaN/Inf, negative size, bad index, NULL where required */
 #define AHLP_ERR_DIM_MISMATCH    -2  /* block sizes disagree with each other                 */
-#define AHLP_ERR_UNSUPPORTED     -3  /* finite upper bounds, lower bounds != 0, size limits  */
+#define AHLP_ERR_UNSUPPORTED     -3  /* a size limit or a feature not available            */
 #define AHLP_ERR_NOT_SPD         -4  /* a pivot became NaN / negative beyond repair            */
 #define AHLP_ERR_REFINE_FAIL     -5  /* refinement did not reach refine_tol                    */
 #define AHLP_ERR_MAX_ITER        -6  /* ipm_solve hit max_iter                                 */
@@ -73,8 +73,16 @@ typedef struct {
 
 /* The arrowhead LP (Sec. 3.2/3.3).  Arrays of per-block items have N
  * entries, per-pair items N-1.  lb/ub: NULL means x >= 0, no upper bound;
- * otherwise every lb must be 0 and every ub +inf (other bounds return
- * AHLP_ERR_UNSUPPORTED). */
+ * otherwise any bounds -inf <= lb <= ub <= +inf (free, fixed, one- and
+ * two-sided variables).  With bounds or inequality rows the LP is in the
+ * full statement of Sec. 3.2; arrowhead_lp_create reduces it to the
+ * equality form with x >= 0 that the solver works on (an inequality row gets
+ * a bounded slack variable in its block -- the left block for a local link
+ * row, the last block for a global row; a variable bounded below is shifted,
+ * one bounded above negated and shifted, a free one split into two, a boxed
+ * one given a new row in its block (a global row for a linking variable)
+ * and a new column).  Every entry point after create then works on that
+ * form; arrowhead_lp_recover maps its x back to the original variables. */
 typedef struct {
   int32_t N;                       /* number of blocks (>= 1)                  */
   int32_t n0;                      /* linking variables x_0 (>= 0)             */
@@ -95,6 +103,24 @@ typedef struct {
   const double *const *lb;         /* [N] -> [n_i] or NULL                     */
   const double *const *ub;         /* [N] -> [n_i] or NULL                     */
   const double *lb0, *ub0;         /* [n0] or NULL                             */
+  /* Inequality rows of the full statement (Sec. 3.2), d <= (row) x <= f with
+   * entries of d possibly -inf and of f +inf.  Every pointer may be NULL (no
+   * rows of that kind; then the counts must be 0 or NULL too). */
+  const int32_t *mD;               /* [N]  inequality rows of block i          */
+  const ahlp_csc *D;               /* [N]  mD_i x n_i  (the paper's D_i)      */
+  const ahlp_csc *C;               /* [N]  mD_i x n0   (the paper's C_i)      */
+  const double *const *dlo;        /* [N] -> [mD_i]                            */
+  const double *const *dhi;        /* [N] -> [mD_i]                            */
+  const int32_t *lG;               /* [N-1] local link inequality rows of pair j */
+  const ahlp_csc *GL;              /* [N-1] lG_j x n_j                         */
+  const ahlp_csc *GR;              /* [N-1] lG_j x n_{j+1}                     */
+  const ahlp_csc *G0;              /* [N-1] lG_j x n0                          */
+  const double *const *glo;        /* [N-1] -> [lG_j]                          */
+  const double *const *ghi;        /* [N-1] -> [lG_j]                          */
+  int32_t mgG;                     /* global linking inequality rows           */
+  const ahlp_csc *Gg;              /* [N]  mgG x n_i                           */
+  const ahlp_csc *Gg0;             /* mgG x n0                                 */
+  const double *gglo, *gghi;       /* [mgG]                                    */
 } ahlp_desc;
 
 struct ahlp_result_s;
@@ -243,6 +269,35 @@ void arrowhead_lp_destroy(ahlp_problem *p);
 /* Text of the last error on this handle (or of the last failed create when
  * p is NULL).  Valid until the next call on the handle. */
 const char *ahlp_last_error(const ahlp_problem *p);
+
+/*
+ * arrowhead_lp_recover -- the original variables of an LP given in the full
+ * statement (bounds or inequality rows, Sec. 3.2) from a point x of the
+ * equality form the handle works on.  x [n_total] (host or device); x_orig
+ * [n_orig] (host or device) ordered like x for a batch: the original block
+ * variables of every LP in block order, then every LP's original linking
+ * variables; obj_offset (may be NULL) receives the constant the reduction
+ * took out of the objective (summed over the LPs of a batch): the original
+ * objective is c'x + obj_offset.  n_orig is returned by
+ * arrowhead_lp_original_size.  LPs already in equality form map unchanged.
+ */
+int arrowhead_lp_recover(ahlp_problem *p, const double *x, double *x_orig, double *obj_offset);
+int arrowhead_lp_original_size(const ahlp_problem *p, int64_t *n_orig);
+
+/*
+ * arrowhead_lp_autotune -- pick the trailing-update kernel of the FP32 and of
+ * the float-float block factors for this handle's block sizes: each
+ * candidate (FP32: tensor cores on 128 x 64 output tiles, or the FP32 pipe
+ * on 64 x 64 tiles; float-float: FP16 digit products on the tensor cores,
+ * or double-float arithmetic on the FP32 pipe) factors the blocks at the
+ * point (x, z) (NULL: x = z = 1), timed with CUDA events on the handle's
+ * stream (best of two after one warm-up), and the faster one is written into
+ * the handle's options (fp32_update, ff_update).  Later calls do not time
+ * anything, so results stay reproducible once the choice is made.
+ *   ms4 (may be NULL) : receives the four block-factor times [FP32 tensor,
+ *                       FP32 pipe, float-float tensor, float-float pipe]
+ */
+int arrowhead_lp_autotune(ahlp_problem *p, const double *x, const double *z, double *ms4);
 
 /* Sizes of the global vectors. */
 int arrowhead_lp_sizes(const ahlp_problem *p, int64_t *n_total, int64_t *m_total);

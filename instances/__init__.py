@@ -16,5 +16,6 @@ from .generate import (  # noqa: F401
     tiny_lp,
     prefix,
     window,
+    general_block_lp,
     CONFIGS,
 )

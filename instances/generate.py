@@ -57,6 +57,27 @@ class BlockLP:
     zstar: Optional[np.ndarray] = None
     basis: Optional[np.ndarray] = None   # planted basis (nondegenerate plant only)
     meta: dict = field(default_factory=dict)
+    # the full statement of Sec. 3.2 (all optional): bounds lb <= x <= ub per
+    # block and for x_0, and inequality rows d <= row x <= f of three kinds --
+    # block rows D_i x_i + C_i x_0, local link rows GL_j x_j + GR_j x_{j+1}
+    # + G0_j x_0 and global rows sum_i Gg_i x_i + Gg0 x_0
+    lb: Optional[List[np.ndarray]] = None
+    ub: Optional[List[np.ndarray]] = None
+    lb0: Optional[np.ndarray] = None
+    ub0: Optional[np.ndarray] = None
+    D: Optional[List[sp.csc_matrix]] = None
+    C: Optional[List[sp.csc_matrix]] = None
+    dlo: Optional[List[np.ndarray]] = None
+    dhi: Optional[List[np.ndarray]] = None
+    GL: Optional[List[sp.csc_matrix]] = None
+    GR: Optional[List[sp.csc_matrix]] = None
+    G0: Optional[List[sp.csc_matrix]] = None
+    glo: Optional[List[np.ndarray]] = None
+    ghi: Optional[List[np.ndarray]] = None
+    Gg: Optional[List[sp.csc_matrix]] = None
+    Gg0: Optional[sp.csc_matrix] = None
+    gglo: Optional[np.ndarray] = None
+    gghi: Optional[np.ndarray] = None
 
     # ---- sizes ---------------------------------------------------------
     @property
@@ -538,6 +559,81 @@ def window(lp: BlockLP, start: int, Np: int) -> BlockLP:
     rng = np.random.default_rng(12345 + Np + 7919 * start)
     plant_half_zero(sub, rng)
     return sub
+
+
+def general_block_lp(seed: int, N: int = 4, m: int = 20, n: int = 30, n0: int = 3, l: int = 2,
+                     mg: int = 1, mD: int = 4, lG: int = 2, mgG: int = 1) -> BlockLP:
+    """An arrowhead LP in the full statement of Sec. 3.2: the equality rows of
+    random_block_lp plus block, local-link and global inequality rows, and
+    every kind of bound (lower, upper, box, free, fixed) on block and linking
+    variables.  A point x~ inside the bounds is drawn first; the equality
+    right-hand sides are A x~ and every inequality row holds x~ strictly, so
+    the LP is feasible; the objective is a random vector."""
+    lp = random_block_lp(seed, N=N, m_sizes=[m] * N, n_sizes=[n] * N, nnz_per_col=3, n0=n0,
+                         w_density=0.3, l=l, link_nnz=(2, 2), mg=mg, global_nnz=4,
+                         x0_link_nnz=1 if n0 else 0, x0_global_nnz=1 if (n0 and mg) else 0,
+                         plant=None, name=f"general seed={seed}")
+    rng = np.random.default_rng(seed + 7777)
+
+    def bounds(k):
+        x = rng.uniform(-1.0, 1.0, k)
+        kind = rng.integers(0, 5, k)   # 0 lower, 1 upper, 2 box, 3 free, 4 lower (often)
+        lo = np.where((kind == 0) | (kind == 2) | (kind == 4), x - rng.uniform(0.2, 1, k), -np.inf)
+        hi = np.where((kind == 1) | (kind == 2), x + rng.uniform(0.2, 1, k), np.inf)
+        fixed = rng.random(k) < 0.05
+        lo = np.where(fixed, x, lo)
+        hi = np.where(fixed, x, hi)
+        return x, lo, hi
+
+    xs, lp.lb, lp.ub = [], [], []
+    for _ in range(N):
+        x, lo, hi = bounds(n)
+        xs.append(x)
+        lp.lb.append(lo)
+        lp.ub.append(hi)
+    x0, lp.lb0, lp.ub0 = bounds(n0)
+
+    def rows(M, k_lo, width):
+        """two-sided / one-sided bounds around M x~ for k_lo rows"""
+        v = np.asarray(M).ravel()
+        kind = rng.integers(0, 3, k_lo)
+        lo = np.where(kind >= 1, v - rng.uniform(0.1, width, k_lo), -np.inf)
+        hi = np.where(kind != 1, v + rng.uniform(0.1, width, k_lo), np.inf)
+        return lo, hi
+
+    lp.D = [_csc(_random_csc(rng, mD, n, 2)) for _ in range(N)]
+    lp.C = [_csc(sp.random(mD, n0, density=0.3, random_state=rng,
+                           data_rvs=rng.standard_normal)) for _ in range(N)]
+    lp.dlo, lp.dhi = [], []
+    for i in range(N):
+        lo, hi = rows(lp.D[i] @ xs[i] + lp.C[i] @ x0, mD, 1.0)
+        lp.dlo.append(lo)
+        lp.dhi.append(hi)
+    lp.GL = [_csc(sp.random(lG, n, density=0.1, random_state=rng,
+                            data_rvs=rng.standard_normal)) for _ in range(N - 1)]
+    lp.GR = [_csc(sp.random(lG, n, density=0.1, random_state=rng,
+                            data_rvs=rng.standard_normal)) for _ in range(N - 1)]
+    lp.G0 = [_csc(sp.random(lG, n0, density=0.3, random_state=rng,
+                            data_rvs=rng.standard_normal)) for _ in range(N - 1)]
+    lp.glo, lp.ghi = [], []
+    for j in range(N - 1):
+        lo, hi = rows(lp.GL[j] @ xs[j] + lp.GR[j] @ xs[j + 1] + lp.G0[j] @ x0, lG, 1.0)
+        lp.glo.append(lo)
+        lp.ghi.append(hi)
+    lp.Gg = [_csc(sp.random(mgG, n, density=0.1, random_state=rng,
+                            data_rvs=rng.standard_normal)) for _ in range(N)]
+    lp.Gg0 = _csc(sp.random(mgG, n0, density=0.5, random_state=rng, data_rvs=rng.standard_normal))
+    gx = sum(lp.Gg[i] @ xs[i] for i in range(N)) + lp.Gg0 @ x0
+    lp.gglo, lp.gghi = rows(gx, mgG, 2.0)
+    # equality right-hand sides through x~, a random objective
+    xg = np.concatenate(xs + [x0])
+    lp.b = [lp.A[i] @ xs[i] + lp.W[i] @ x0 for i in range(N)]
+    lp.blink = [lp.FL[j] @ xs[j] + lp.FR[j] @ xs[j + 1] + lp.F0[j] @ x0 for j in range(N - 1)]
+    lp.bg = sum(lp.Fg[i] @ xs[i] for i in range(N)) + lp.Fg0 @ x0 if mg else np.zeros(0)
+    lp.c = [rng.standard_normal(n) for _ in range(N)]
+    lp.c0 = rng.standard_normal(n0)
+    lp.meta.update(x_interior=xg)
+    return lp
 
 
 def prefix(lp: BlockLP, Np: int) -> BlockLP:

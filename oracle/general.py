@@ -110,3 +110,62 @@ def solve_general(c, A, b, C, d, f, lo, hi, tol: float = 1e-9, max_iter: int = 2
     x, s = back(r["x"])
     return {"x": x, "s": s, "objective": float(np.dot(c, x)), "status": r["status"],
             "iterations": r["iterations"], "standard_objective": r["pobj"] + const}
+
+
+def assemble_general(lp):
+    """(c, A, b, C, d, f, lo, hi) of an arrowhead LP in the full statement of
+    Sec. 3.2, in the global orderings: columns [x_1 .. x_N | x_0], equality rows
+    as lp.assemble, inequality rows [block rows of blocks 1..N | local link
+    rows of pairs 1..N-1 | global rows].  Missing parts are empty; missing
+    bounds are x >= 0."""
+    from . import lp as lpm
+    A, b, c = lpm.assemble(lp)
+    N, n0 = lp.N, lp.n0
+    ns = [a.shape[1] for a in lp.A]
+    col0 = np.concatenate([[0], np.cumsum(ns)]).astype(int)
+    n = int(col0[N]) + n0
+    blocks, dl, dh = [], [], []
+
+    def place(parts, nrows):
+        R, Cc, V = [], [], []
+        for M, c_ in parts:
+            if M is None:
+                continue
+            Mc = sp.coo_matrix(M)
+            R.append(Mc.row)
+            Cc.append(Mc.col + c_)
+            V.append(Mc.data)
+        if not R:
+            return sp.csr_matrix((nrows, n))
+        return sp.csr_matrix((np.concatenate(V), (np.concatenate(R), np.concatenate(Cc))),
+                             shape=(nrows, n))
+
+    if getattr(lp, "D", None) is not None:
+        for i in range(N):
+            blocks.append(place([(lp.D[i], col0[i]),
+                                 (lp.C[i] if getattr(lp, "C", None) is not None else None,
+                                  col0[N])], lp.D[i].shape[0]))
+            dl.append(lp.dlo[i])
+            dh.append(lp.dhi[i])
+    if getattr(lp, "GL", None) is not None:
+        for j in range(N - 1):
+            blocks.append(place([(lp.GL[j], col0[j]), (lp.GR[j], col0[j + 1]),
+                                 (lp.G0[j] if getattr(lp, "G0", None) is not None else None,
+                                  col0[N])], lp.GL[j].shape[0]))
+            dl.append(lp.glo[j])
+            dh.append(lp.ghi[j])
+    if getattr(lp, "Gg", None) is not None and getattr(lp, "gglo", None) is not None:
+        mgG = len(lp.gglo)
+        blocks.append(place([(lp.Gg[i], col0[i]) for i in range(N)] + [(lp.Gg0, col0[N])], mgG))
+        dl.append(lp.gglo)
+        dh.append(lp.gghi)
+    C = sp.vstack(blocks).tocsr() if blocks else sp.csr_matrix((0, n))
+    d = np.concatenate(dl) if dl else np.zeros(0)
+    f = np.concatenate(dh) if dh else np.zeros(0)
+    lo = np.concatenate([(lp.lb[i] if getattr(lp, "lb", None) is not None else np.zeros(ns[i]))
+                         for i in range(N)] +
+                        [lp.lb0 if getattr(lp, "lb0", None) is not None else np.zeros(n0)])
+    hi = np.concatenate([(lp.ub[i] if getattr(lp, "ub", None) is not None
+                          else np.full(ns[i], np.inf)) for i in range(N)] +
+                        [lp.ub0 if getattr(lp, "ub0", None) is not None else np.full(n0, np.inf)])
+    return c, A, b, C, d, f, lo, hi

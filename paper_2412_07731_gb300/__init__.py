@@ -12,6 +12,7 @@ from ._lib import (  # noqa: F401
     Problem,
     STATUS,
     arrowhead_lp_create,
+    autotune,
     batch_layout,
     default_options,
     ipm_solve,
@@ -25,6 +26,7 @@ from ._lib import (  # noqa: F401
     transfer_bytes,
     lib_path,
     load,
+    recover,
     set_cb,
     set_options,
 )

@@ -36,7 +36,13 @@ class Desc(C.Structure):
                 ("c", C.POINTER(_dp)), ("l", _ip), ("FL", C.POINTER(CSC)),
                 ("FR", C.POINTER(CSC)), ("F0", C.POINTER(CSC)), ("blink", C.POINTER(_dp)),
                 ("Fg", C.POINTER(CSC)), ("Fg0", C.POINTER(CSC)), ("bg", _dp),
-                ("lb", C.POINTER(_dp)), ("ub", C.POINTER(_dp)), ("lb0", _dp), ("ub0", _dp)]
+                ("lb", C.POINTER(_dp)), ("ub", C.POINTER(_dp)), ("lb0", _dp), ("ub0", _dp),
+                ("mD", _ip), ("D", C.POINTER(CSC)), ("C", C.POINTER(CSC)),
+                ("dlo", C.POINTER(_dp)), ("dhi", C.POINTER(_dp)),
+                ("lG", _ip), ("GL", C.POINTER(CSC)), ("GR", C.POINTER(CSC)),
+                ("G0", C.POINTER(CSC)), ("glo", C.POINTER(_dp)), ("ghi", C.POINTER(_dp)),
+                ("mgG", C.c_int32), ("Gg", C.POINTER(CSC)), ("Gg0", C.POINTER(CSC)),
+                ("gglo", _dp), ("gghi", _dp)]
 
 
 class Options(C.Structure):
@@ -77,7 +83,8 @@ EXPORTS = ["ahlp_default_options", "ahlp_status_string", "arrowhead_lp_create",
            "arrowhead_lp_set_stream", "arrowhead_lp_set_options", "kkt_factor", "kkt_solve",
            "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense", "kkt_stage_times",
            "ahlp_launch_count", "kkt_residual_noalloc", "kkt_block_factor_dense",
-           "ahlp_transfer_bytes", "arrowhead_lp_set_cb", "kkt_factor_kernel_times"]
+           "ahlp_transfer_bytes", "arrowhead_lp_set_cb", "kkt_factor_kernel_times",
+           "arrowhead_lp_recover", "arrowhead_lp_original_size", "arrowhead_lp_autotune"]
 
 
 def kkt_block_factor_dense(prob, block: int):
@@ -129,6 +136,39 @@ def set_cb(prob, c=None, b=None):
     prob._stream_for(c, b)
     prob._check(prob._lib.arrowhead_lp_set_cb(prob._h, _vec_ptr(c, keep, prob.n, "c"),
                                               _vec_ptr(b, keep, prob.m, "b")))
+
+
+def autotune(prob, x=None, z=None):
+    """Choose the faster trailing-update kernels (FP32 and float-float block
+    factors) for this handle at (x, z) (default x = z = 1); the choice goes
+    into the handle's options.  Returns the four block-factor times (ms)."""
+    keep = _Keep()
+    prob._stream_for(x, z)
+    ms = (C.c_double * 4)()
+    prob._check(prob._lib.arrowhead_lp_autotune(
+        prob._h, _vec_ptr(x, keep, prob.n, "x") if x is not None else None,
+        _vec_ptr(z, keep, prob.n, "z") if z is not None else None, ms))
+    # mirror the handle's new choice in the Python-side copy of its options
+    prob.options.fp32_update = 2 if ms[0] <= ms[1] else 1
+    prob.options.ff_update = 2 if ms[2] <= ms[3] else 1
+    return {"fp32_tensor_ms": ms[0], "fp32_pipe_ms": ms[1], "ff_tensor_ms": ms[2],
+            "ff_pipe_ms": ms[3], "fp32_update": prob.options.fp32_update,
+            "ff_update": prob.options.ff_update}
+
+
+def recover(prob, x):
+    """(x_orig, obj_offset): the original variables of an LP given with bounds
+    or inequality rows, from a point x of the equality form the handle works
+    on; the original objective is c'x + obj_offset."""
+    keep = _Keep()
+    n = C.c_int64(0)
+    prob._check(prob._lib.arrowhead_lp_original_size(prob._h, C.byref(n)))
+    out = _out_like(x, n.value)
+    off = C.c_double(0.0)
+    prob._check(prob._lib.arrowhead_lp_recover(prob._h, _vec_ptr(x, keep, prob.n, "x"),
+                                               _vec_ptr(out, keep, n.value, "x_orig"),
+                                               C.byref(off)))
+    return out, off.value
 
 
 def kkt_factor_kernel_times(prob):
@@ -193,6 +233,12 @@ def load(path: str | None = None):
     L.kkt_block_factor_dense.restype = C.c_int
     L.ahlp_transfer_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.ahlp_transfer_bytes.restype = C.c_int
+    L.arrowhead_lp_autotune.argtypes = [vp, vp, vp, _dp]
+    L.arrowhead_lp_autotune.restype = C.c_int
+    L.arrowhead_lp_recover.argtypes = [vp, vp, vp, _dp]
+    L.arrowhead_lp_recover.restype = C.c_int
+    L.arrowhead_lp_original_size.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.arrowhead_lp_original_size.restype = C.c_int
     L.kkt_factor_kernel_times.argtypes = [vp, _dp, C.POINTER(C.c_int64)]
     L.kkt_factor_kernel_times.restype = C.c_int
     L.arrowhead_lp_set_cb.argtypes = [vp, vp, vp]
@@ -300,6 +346,43 @@ def make_desc(lp, keep: _Keep) -> Desc:
     keep.refs.append(fg0)
     d.Fg0 = fg0
     d.bg = keep.f64(lp.bg if mg else np.zeros(1))
+    # the full statement of Sec. 3.2: bounds and inequality rows (optional)
+    g = lambda name: getattr(lp, name, None)  # noqa: E731
+    if g("lb") is not None:
+        d.lb = keep.ptr_array(lp.lb)
+    if g("ub") is not None:
+        d.ub = keep.ptr_array(lp.ub)
+    if g("lb0") is not None and n0:
+        d.lb0 = keep.f64(lp.lb0)
+    if g("ub0") is not None and n0:
+        d.ub0 = keep.f64(lp.ub0)
+    if g("D") is not None:
+        mD = [int(M.shape[0]) for M in lp.D]
+        d.mD = keep.i32(mD)
+        d.D = keep.csc_array(lp.D, [(mD[i], ns[i]) for i in range(N)])
+        d.C = keep.csc_array(lp.C if g("C") is not None else [None] * N,
+                             [(mD[i], n0) for i in range(N)])
+        d.dlo = keep.ptr_array([v if len(v) else np.zeros(1) for v in lp.dlo])
+        d.dhi = keep.ptr_array([v if len(v) else np.zeros(1) for v in lp.dhi])
+    if g("GL") is not None and N > 1:
+        lG = [int(M.shape[0]) for M in lp.GL]
+        d.lG = keep.i32(lG)
+        d.GL = keep.csc_array(lp.GL, [(lG[j], ns[j]) for j in range(N - 1)])
+        d.GR = keep.csc_array(lp.GR, [(lG[j], ns[j + 1]) for j in range(N - 1)])
+        d.G0 = keep.csc_array(lp.G0 if g("G0") is not None else [None] * (N - 1),
+                              [(lG[j], n0) for j in range(N - 1)])
+        d.glo = keep.ptr_array([v if len(v) else np.zeros(1) for v in lp.glo])
+        d.ghi = keep.ptr_array([v if len(v) else np.zeros(1) for v in lp.ghi])
+    if g("Gg") is not None and g("gglo") is not None and len(lp.gglo):
+        mgG = len(lp.gglo)
+        d.mgG = mgG
+        d.Gg = keep.csc_array(lp.Gg, [(mgG, nn) for nn in ns])
+        gg0 = (CSC * 1)()
+        gg0[0] = keep.csc(g("Gg0"), (mgG, n0))
+        keep.refs.append(gg0)
+        d.Gg0 = gg0
+        d.gglo = keep.f64(lp.gglo)
+        d.gghi = keep.f64(lp.gghi)
     return d
 
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ahlp.h"
@@ -93,6 +94,62 @@ struct SchurBlk {
   int glo, gn;     // its LP's ones in a batch) and of the global rows
 };
 
+// A sparse matrix assembled column by column (host), and the equality-form
+// description of an LP given in the full statement (general.cpp), with the
+// map back to its original variables.
+struct StdCsc {
+  using Entry = std::pair<int, double>;   // (row, value)
+  using Col = std::vector<Entry>;
+  int m = 0;
+  std::vector<int32_t> cp{0}, ri;
+  std::vector<double> v;
+  void push(const Col &c) {
+    for (auto &e : c) {
+      ri.push_back(e.first);
+      v.push_back(e.second);
+    }
+    cp.push_back((int32_t)ri.size());
+  }
+  int n() const { return (int)cp.size() - 1; }
+  ahlp_csc csc() const {
+    return ahlp_csc{m, n(), cp.data(), ri.empty() ? nullptr : ri.data(),
+                    v.empty() ? nullptr : v.data()};
+  }
+};
+
+struct StdDesc {
+  // original variable `orig` of block blk (-1: of x_0) = shift + sign x'_k
+  // (- x'_k2 when k2 >= 0), k and k2 indices among its block's (x_0's)
+  // standard-form columns
+  struct Recov {
+    int blk, orig;
+    double shift;
+    int k;
+    double sign;
+    int k2;
+  };
+  int N = 0;
+  std::vector<StdCsc> A, W, Fg, FL, FR, F0;
+  StdCsc Fg0;
+  std::vector<std::vector<double>> b, c, blink;
+  std::vector<double> bg, c0;
+  std::vector<int32_t> l;
+  std::vector<ahlp_csc> Ac, Wc, Fgc, FLc, FRc, F0c;
+  ahlp_csc Fg0c{};
+  std::vector<const double *> bp, cp, blp;
+  ahlp_desc d{};
+  std::vector<Recov> recov;
+  double const_obj = 0.0;
+  std::vector<int> n_orig;
+  int n0_orig = 0;
+};
+
+// true when the description uses bounds or inequality rows
+bool desc_is_general(const ahlp_desc &d);
+// the equality form with x >= 0 of a description in the full statement
+// (throws Fail on invalid input)
+void standardize(const ahlp_desc &d, StdDesc &S);
+
 struct DeviceBuf {
   void *ptr = nullptr;
   size_t bytes = 0;
@@ -113,6 +170,15 @@ struct ahlp_problem {
     double bnorm, cnorm;                      // its ||b||_inf and ||c||_inf
   };
   std::vector<LpRange> lp_rng;
+  // LPs given in the full statement: per LP its map back to the original
+  // variables (empty: the LP was already in equality form with x >= 0)
+  struct LpRecov {
+    std::vector<ahlp::StdDesc::Recov> recov;
+    std::vector<int> n_orig;
+    int n0_orig = 0;
+    double const_obj = 0.0;
+  };
+  std::vector<LpRecov> lp_recov;
   long long n = 0, m = 0, msum = 0;   // n_total, m_total, sum of m_i
   std::vector<int> mi, ni, ki, lprev, lnext;
   std::vector<long long> xoff, yoff, link_off;   // link_off has N entries (pairs + 1)

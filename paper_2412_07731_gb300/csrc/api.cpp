@@ -611,6 +611,43 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     g_create_err = "batch must be >= 1";
     return AHLP_ERR_INVALID_ARG;
   }
+  // LPs in the full statement (bounds, inequality rows): their equality form
+  std::deque<StdDesc> stds;
+  std::vector<ahlp_desc> eqform;
+  std::vector<ahlp_problem::LpRecov> recov(batch);
+  try {
+    bool any = false;
+    for (int b = 0; b < batch; ++b) {
+      any = any || desc_is_general(descs[b]);
+      // original sizes (for the map back) of an LP already in equality form
+      if (descs[b].A && descs[b].N > 0 && !desc_is_general(descs[b])) {
+        for (int i = 0; i < descs[b].N; ++i) recov[b].n_orig.push_back(descs[b].A[i].n);
+        recov[b].n0_orig = descs[b].n0;
+      }
+    }
+    if (any) {
+      for (int b = 0; b < batch; ++b) {
+        if (desc_is_general(descs[b])) {
+          stds.emplace_back();
+          standardize(descs[b], stds.back());
+          eqform.push_back(stds.back().d);
+          recov[b].recov = stds.back().recov;
+          recov[b].n_orig = stds.back().n_orig;
+          recov[b].n0_orig = stds.back().n0_orig;
+          recov[b].const_obj = stds.back().const_obj;
+        } else {
+          eqform.push_back(descs[b]);
+        }
+      }
+      descs = eqform.data();
+    }
+  } catch (const Fail &f) {
+    g_create_err = f.msg;
+    return f.code;
+  } catch (const std::bad_alloc &) {
+    g_create_err = "host memory exhausted while reducing the LP to equality form";
+    return AHLP_ERR_OOM;
+  }
   BatchDesc composed;
   if (batch > 1) {
     try {
@@ -623,6 +660,7 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
   }
   ahlp_problem *p = new ahlp_problem();
   p->batch = batch;
+  p->lp_recov = std::move(recov);
   if (batch > 1) {
     p->lp_blk0 = composed.blk0;
     p->lp_x0off = composed.x0off;
@@ -1716,6 +1754,127 @@ int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld) {
 }
 
 int64_t ahlp_launch_count(void) { return ahlp::launch_count(); }
+
+int arrowhead_lp_autotune(ahlp_problem *p, const double *x, const double *z, double *ms4) {
+  if (!p) return AHLP_ERR_INVALID_ARG;
+  const ahlp_options saved = p->opt;
+  const int saved_prec = p->fac_prec;
+  double best[4] = {0, 0, 0, 0};
+  try {
+    const double *xx = x ? stage_in(p, x, p->n, p->stg[0]) : nullptr;
+    const double *zz = z ? stage_in(p, z, p->n, p->stg[1]) : nullptr;
+    if (!xx || !zz) {
+      ck(launch_fill(p->stg[0], 1.0, p->n, p->stream), "fill");
+      xx = zz = p->stg[0];
+    }
+    ck(cudaMemcpyAsync(p->x, xx, p->n * 8, cudaMemcpyDeviceToDevice, p->stream), "copy");
+    ck(cudaMemcpyAsync(p->z, zz, p->n * 8, cudaMemcpyDeviceToDevice, p->stream), "copy");
+    // (precision, update option, value) of the four candidates
+    const int prec[4] = {kPrecFP32, kPrecFP32, kPrecFF, kPrecFF};
+    const int val[4] = {2, 1, 2, 1};
+    for (int c = 0; c < 4; ++c) {
+      p->opt = saved;
+      p->opt.precision = AHLP_PREC_MIXED;
+      p->opt.fp32_cond_max = prec[c] == kPrecFP32 ? 1e300 : 1.0;
+      if (prec[c] == kPrecFP32) p->opt.fp32_update = val[c];
+      else p->opt.ff_update = val[c];
+      double t = 1e300;
+      for (int rep = 0; rep < 3; ++rep) {
+        p->fac_prec = prec[c];
+        const int st = factor_impl(p, p->opt.delta, p->opt.rho, p->opt.pivot_tol);
+        if (st != AHLP_OK) throw Fail{st, p->err};
+        if (rep > 0) t = std::min(t, (double)p->stage_ms[1]);
+      }
+      best[c] = t;
+    }
+    p->opt = saved;
+    p->opt.fp32_update = best[0] <= best[1] ? 2 : 1;
+    p->opt.ff_update = best[2] <= best[3] ? 2 : 1;
+    p->fac_prec = saved_prec;
+    p->factored = false;
+    if (ms4)
+      for (int c = 0; c < 4; ++c) ms4[c] = best[c];
+    return AHLP_OK;
+  } catch (const Fail &f) {
+    p->opt = saved;
+    p->fac_prec = saved_prec;
+    p->factored = false;
+    return set_err(p, f.code, f.msg);
+  }
+}
+
+int arrowhead_lp_original_size(const ahlp_problem *p, int64_t *n_orig) {
+  if (!p || !n_orig) return AHLP_ERR_INVALID_ARG;
+  long long n = 0;
+  for (auto &r : p->lp_recov) {
+    for (int v : r.n_orig) n += v;
+    n += r.n0_orig;
+  }
+  *n_orig = n;
+  return AHLP_OK;
+}
+
+int arrowhead_lp_recover(ahlp_problem *p, const double *x, double *x_orig, double *obj_offset) {
+  if (!p || !x || !x_orig) return AHLP_ERR_INVALID_ARG;
+  try {
+    std::vector<double> xs(p->n);
+    if (p->n > 0) {
+      const bool dev = is_device_ptr(x);
+      ck(cudaMemcpyAsync(xs.data(), x, p->n * 8, dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                         p->stream),
+         "copy");
+      ck(cudaStreamSynchronize(p->stream), "sync");
+    }
+    // standard-form offsets of every LP's blocks and linking variables
+    long long norig = 0, n0orig_total = 0;
+    for (auto &r : p->lp_recov) {
+      for (int v : r.n_orig) norig += v;
+      n0orig_total += r.n0_orig;
+    }
+    std::vector<double> xo(norig + n0orig_total, 0.0);
+    long long blk = 0, ob = 0, o0 = norig, x0s = 0;
+    double off = 0.0;
+    const long long x0base = p->xoff[p->N];
+    for (size_t b = 0; b < p->lp_recov.size(); ++b) {
+      const auto &r = p->lp_recov[b];
+      const int Nb = (int)r.n_orig.size();
+      std::vector<long long> obase(Nb);
+      for (int i = 0; i < Nb; ++i) {
+        obase[i] = ob;
+        ob += r.n_orig[i];
+      }
+      const long long n0std = b + 1 < p->lp_recov.size()
+                                  ? (p->batch > 1 ? p->lp_x0off[b + 1] : p->n0) - x0s
+                                  : p->n0 - x0s;
+      if (r.recov.empty()) {   // already in equality form: copied as it is
+        for (int i = 0; i < Nb; ++i)
+          for (int t = 0; t < r.n_orig[i]; ++t) xo[obase[i] + t] = xs[p->xoff[blk + i] + t];
+        for (int t = 0; t < r.n0_orig; ++t) xo[o0 + t] = xs[x0base + x0s + t];
+      } else {
+        for (const auto &q : r.recov) {
+          const long long base = q.blk >= 0 ? p->xoff[blk + q.blk] : x0base + x0s;
+          double v = q.shift + q.sign * xs[base + q.k];
+          if (q.k2 >= 0) v -= xs[base + q.k2];
+          if (q.blk >= 0) xo[obase[q.blk] + q.orig] = v;
+          else xo[o0 + q.orig] = v;
+        }
+        off += r.const_obj;
+      }
+      blk += Nb;
+      o0 += r.n0_orig;
+      x0s += n0std;
+    }
+    const bool dev = is_device_ptr(x_orig);
+    ck(cudaMemcpyAsync(x_orig, xo.data(), xo.size() * 8,
+                       dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, p->stream),
+       "copy");
+    ck(cudaStreamSynchronize(p->stream), "sync");
+    if (obj_offset) *obj_offset = off;
+    return AHLP_OK;
+  } catch (const Fail &f) {
+    return set_err(p, f.code, f.msg);
+  }
+}
 
 int kkt_factor_kernel_times(const ahlp_problem *p, double *ms3, int64_t *launches3) {
   if (!p || !ms3) return AHLP_ERR_INVALID_ARG;

@@ -84,8 +84,9 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     constexpr double kMinRhoX = 1e-10, kMaxRhoX = 1e-6;
     // a float-float factor that breaks down (its FP32 exponent range is
     // exceeded behind clamped pivots) first gets more regularisation, up to
-    // kFFMaxDelta, before the blocks move to FP64 at ~3x its cost
-    constexpr double kFFMaxDelta = 1e-6;
+    // kFFMaxDelta, before the blocks move to FP64 at ~6x its cost
+    constexpr double kFFMaxDelta = 1e-4;
+    constexpr double kStallAccept = 1e-1;
     // inexact Newton: the IPM's directions are solved to a relative residual
     // of ipm_refine_tol, not the refine_tol of kkt_solve
     const double ipm_tol = std::max(p->opt.refine_tol, p->opt.ipm_refine_tol);
@@ -162,6 +163,22 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     static const char *kPrecName[] = {"FP64", "FP32", "float-float"};
     // next safeguard; false when none is left (allow_delta: NaN recovery only)
     auto escalate = [&](bool allow_delta, const char *why) {
+      // A stalled direction (Krylov budget spent above `stalled`) whose
+      // residual is still at most kStallAccept is an acceptable inexact
+      // Newton step once the remaining safeguards are an FP64 refactor or a
+      // coarser pivot threshold: in the degenerate end game the factors of
+      // every precision stop being good preconditioners (FP64 ones too), so
+      // a refactor costs several float-float factors and buys no accuracy.
+      // (Not for a batch: its residual is measured over all LPs together, so
+      // a moderate total can hide a useless slice for an LP whose own
+      // right-hand side is small.)
+      if (!allow_delta && nlp == 0 && last_rel <= kStallAccept &&
+          (p->fac_prec == kPrecFF || p->fac_prec == kPrecFP64)) {
+        if (p->opt.verbose)
+          printf("       %s accepted (%s factor, residual %.2e)\n", why,
+                 kPrecName[p->fac_prec], last_rel);
+        return false;
+      }
       if (p->opt.verbose)
         printf("       safeguard after %s (%s factor, residual %.2e)\n", why,
                kPrecName[p->fac_prec], last_rel);

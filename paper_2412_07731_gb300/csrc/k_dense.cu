@@ -578,6 +578,32 @@ __device__ __forceinline__ void oz_digits(float h, float l, int e, float (&d)[kO
   }
 }
 
+// The panel in double-float arithmetic on the FP32 pipe (FP64 runs at 1/74
+// of the FP32 rate on this part): column c of X = A_Ik L_kk^-T is scaled by
+// the pivot's reciprocal (taken in FP64 and split into two words), then
+// removed from the columns right of it, every product an FMA-based exact
+// product and every difference an error-free two-sum.
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph,
+                                       float &pl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  ph = __fadd_rn(p, e);
+  pl = __fsub_rn(e, __fsub_rn(ph, p));
+}
+
+__device__ __forceinline__ void df_sub(float &xh, float &xl, float ph, float pl) {
+  const float s = __fsub_rn(xh, ph);
+  const float bv = __fsub_rn(s, xh);
+  const float err = __fadd_rn(__fsub_rn(xh, __fsub_rn(s, bv)), __fsub_rn(-ph, bv));
+  const float el = __fadd_rn(err, __fsub_rn(xl, pl));
+  xh = __fadd_rn(s, el);
+  xl = __fsub_rn(el, __fsub_rn(xh, s));
+}
+
+constexpr size_t kTrsmFFSmem = 4 * NB * (NB + 1) * sizeof(float);
+
 __global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, float *lo,
                                                                  const BlkInfo *blk, int k,
                                                                  __half *dstage, int *dexp) {
@@ -585,9 +611,12 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, floa
   if (k >= bi.Tp) return;
   const int I = k + 1 + blockIdx.x;
   if (I >= bi.T) return;
-  extern __shared__ __align__(16) unsigned char trsm_raw[];   // two (NB x NB+1) FP64 tiles
-  double(*L)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(trsm_raw);
-  double(*X)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(trsm_raw + sizeof(double) * NB * (NB + 1));
+  extern __shared__ __align__(16) float trsm_f[];   // L hi, L lo, X hi, X lo: (NB x NB+1) each
+  float(*Lh)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(trsm_f);
+  float(*Ll)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(trsm_f + NB * (NB + 1));
+  float(*Xh)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(trsm_f + 2 * NB * (NB + 1));
+  float(*Xl)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(trsm_f + 3 * NB * (NB + 1));
+  __shared__ float s_ih, s_il;
   const int r0 = k * NB;
   const int nr = min(NB, bi.a - r0);
   const int npiv = min(NB, bi.p - r0);
@@ -597,24 +626,40 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, floa
   const long long gx = bi.base + (long long)r0 * bi.lda + ri;
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
-    L[r][c] = (r < nr && c < nr && r >= c) ? ff_get(hi, lo, gl + (long long)c * bi.lda + r) : 0.0;
-    X[r][c] = (r < nri && c < nr) ? ff_get(hi, lo, gx + (long long)c * bi.lda + r) : 0.0;
+    const bool lin = r < nr && c < nr && r >= c, xin = r < nri && c < nr;
+    const long long el = gl + (long long)c * bi.lda + r, ex = gx + (long long)c * bi.lda + r;
+    Lh[r][c] = lin ? hi[el] : 0.0f;
+    Ll[r][c] = lin ? lo[el] : 0.0f;
+    Xh[r][c] = xin ? hi[ex] : 0.0f;
+    Xl[r][c] = xin ? lo[ex] : 0.0f;
   }
   __syncthreads();
   for (int c = 0; c < npiv; ++c) {
-    const double inv = 1.0 / L[c][c];
-    for (int r = threadIdx.x; r < nri; r += blockDim.x) X[r][c] *= inv;
+    if (threadIdx.x == 0) {
+      const double inv = 1.0 / ((double)Lh[c][c] + (double)Ll[c][c]);
+      s_ih = (float)inv;
+      s_il = (float)(inv - (double)s_ih);
+    }
+    __syncthreads();
+    const float ih = s_ih, il = s_il;
+    for (int r = threadIdx.x; r < nri; r += blockDim.x)
+      df_mul(Xh[r][c], Xl[r][c], ih, il, Xh[r][c], Xl[r][c]);
     __syncthreads();
     const int ns = nr - c - 1;
     for (int idx = threadIdx.x; idx < nri * ns; idx += blockDim.x) {
       const int r = idx % nri, sc = c + 1 + idx / nri;
-      X[r][sc] -= X[r][c] * L[sc][c];
+      float ph, pl;
+      df_mul(Xh[r][c], Xl[r][c], Lh[sc][c], Ll[sc][c], ph, pl);
+      df_sub(Xh[r][sc], Xl[r][sc], ph, pl);
     }
     __syncthreads();
   }
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
     const int r = i % NB, c = i / NB;
-    if (r < nri && c < nr) ff_put(hi, lo, gx + (long long)c * bi.lda + r, X[r][c]);
+    if (r < nri && c < nr) {
+      hi[gx + (long long)c * bi.lda + r] = Xh[r][c];
+      lo[gx + (long long)c * bi.lda + r] = Xl[r][c];
+    }
   }
   if (dstage) {
     __shared__ int s_exp[NB];
@@ -623,7 +668,7 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, floa
       const int r = threadIdx.x;
       float mx = 0.0f;
       if (r < nri)
-        for (int c = 0; c < npiv; ++c) mx = fmaxf(mx, fabsf((float)X[r][c]));
+        for (int c = 0; c < npiv; ++c) mx = fmaxf(mx, fabsf(Xh[r][c]));
       int e = 0;
       if (mx > 0.0f) frexpf(mx, &e);   // mx = f 2^e, f in [0.5, 1)
       s_exp[r] = e;
@@ -635,9 +680,7 @@ __global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, floa
       const int r = (e >> 9) * 8 + ((e >> 3) & 7), c = ((e >> 6) & 7) * 8 + (e & 7);
       float d[kOzDigits];
       if (r < nri && c < npiv) {
-        const double v = X[r][c];
-        const float h = (float)v;
-        oz_digits(h, (float)(v - (double)h), s_exp[r], d);
+        oz_digits(Xh[r][c], Xl[r][c], s_exp[r], d);
       } else {
 #pragma unroll
         for (int q = 0; q < kOzDigits; ++q) d[q] = 0.0f;
@@ -1541,7 +1584,7 @@ cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
     if (prof) kt_mark(prof, 1, s);
     if (maxPanel > 0)
       count_launch(), pchol_trsm_ff_kernel<<<dim3((unsigned)maxPanel, nblk), kThreads,
-                                             trsm_smem<double>(), s>>>(
+                                             kTrsmFFSmem, s>>>(
                           hi, lo, info, k, oz ? oz->dstage : nullptr, oz ? oz->dexp : nullptr);
     if (prof) kt_mark(prof, 2, s);
     if (maxTrail > 0) {
@@ -1635,7 +1678,7 @@ cudaError_t set_dense_smem_limits(int bytes) {
                            (int)kUpdFFSmem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(pchol_trsm_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)trsm_smem<double>());
+                           (int)kTrsmFFSmem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(pchol_trsm_kernel<double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
