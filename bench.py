@@ -53,8 +53,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FP64_PEAK_TFLOPS = 1.25       # nominal GB300 FP64 (FMA pipes and DMMA alike)
-FP32_PEAK_TFLOPS = 74.7       # GB300 FP32 FMA (2 flops per FMA), register-only probe
+FP64_PEAK_TFLOPS = 1.25       # nominal GB300 FP64 rate (profiling recipe's table)
+# FP32 FMA rate from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops
+# x 2.07 GHz (the maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0     # GB300 copy bandwidth when no measured figure is present
 BF16_FALLBACK_TFLOPS = 1900.0
 TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense TF32 : BF16 tensor rate on GB300
@@ -161,7 +163,7 @@ def stage_rooflines(P, prob, lp, peaks):
     CUDA events inside the library; median of three after one warm-up.  Each
     stage against the bound that limits it:
       form   -- HBM: the FP32 lower tiles written (pattern reads not counted);
-      block  -- the FP32 block factor's flops against the FP32 FMA probe;
+      block  -- the FP32 block factor's flops against the FP32 FMA rate;
       schur  -- FP64 latency: the link chain is sequential over the link pairs
                 and the border is small, so no throughput fraction is claimed;
       apply  -- HBM: the FP32 block factors read twice (forward and backward
@@ -557,10 +559,11 @@ def update_geometry(lp, NB=64):
 
 
 # DRAM bytes per algorithmic byte of the trailing-update kernels, from the ncu
-# captures summarised in profiles/ (uniform 8-block workload, FP32 and
-# float-float factors); the live bench scales them by the bytes of its own
+# captures of profiles/pchol_update_tc_c1small.md and
+# profiles/pchol_update_oz_c1small.md (uniform 8-block workload, whose trailing
+# matrices partly fit L2); the live bench scales them by the bytes of its own
 # launches to fill roofline.traffic
-UPDATE_TRAFFIC_PER_BYTE = {"FP32": None, "float-float": None}
+UPDATE_TRAFFIC_PER_BYTE = {"FP32": 0.68, "float-float": 0.89}
 
 
 def kernel_roofline(P, prob, lp, x, z, prec_name, peaks):
@@ -625,13 +628,13 @@ def roofline(lp, win, peaks):
     flops = block_factor_flops(lp)
     kinds = [
         (a["factors_fp32"], a["ms_block_fp32"], "FP32", FP32_PEAK_TFLOPS, "TFLOP/s",
-         "FP32 FMA rate of the register-only probe (74.7 TFLOP/s)"),
+         "FP32 FMA rate from unit counts and the maximum SM clock (80.5 TFLOP/s)"),
         (a["factors_ff"], a["ms_block_ff"], "float-float", FP32_PEAK_TFLOPS / 2.0,
          "T FP32-instr/s",
-         "FP32 pipe instruction rate of the register-only probe (37.35e12 instr/s); a "
+         "FP32 pipe instruction rate from unit counts and clock (40.3e12 instr/s); a "
          "double-float multiply-add is 12 FP32 instructions"),
         (a["factors_fp64"], a["ms_block_fp64"], "FP64", FP64_PEAK_TFLOPS, "TFLOP/s",
-         "nominal GB300 FP64 rate; the FMA probe measured 1.009 TFLOP/s"),
+         "nominal GB300 FP64 rate"),
     ]
     cnt, tot, name, peak, unit, src = max(kinds, key=lambda k: k[1] if k[0] else -1.0)
     if not cnt:

@@ -296,7 +296,7 @@ struct ahlp_problem {
   double *stg[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // staging for host I/O
   double *res[3] = {nullptr, nullptr, nullptr};            // refinement residual
   double *cor[3] = {nullptr, nullptr, nullptr};            // refinement correction
-  double *ipmv[16] = {};      // IPM work vectors
+  double *ipmv[19] = {};      // IPM work vectors (the last three: a batch's balanced rhs)
   double *red_part = nullptr; // reduction partials
   double *mdot_part = nullptr;  // multi-dot partials [kMaxKrylov+1][304]
   double *gm_V = nullptr, *gm_Z = nullptr;   // Krylov bases, allocated on first use

@@ -16,7 +16,7 @@ namespace {
 
 enum {
   V_X = 0, V_Y, V_Z, V_RP, V_RD, V_RC, V_DXA, V_DYA, V_DZA, V_DX, V_DY, V_DZ,
-  V_RC2, V_DX2, V_DY2, V_DZ2
+  V_RC2, V_DX2, V_DY2, V_DZ2, V_SD, V_SP, V_SC
 };
 
 // Gondzio's cap on the centrality correctors of one iteration: how many
@@ -149,10 +149,91 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       }
       return st;
     };
+    // Batch: the Newton matrix is the direct sum of the LPs' ones, so every
+    // LP's slice of the right-hand side can be scaled by its own factor and its
+    // slice of the solution scaled back.  Each LP's slice is brought to unit
+    // norm before the Krylov solve, so that the relative residual it is
+    // stopped on bounds every LP's own relative residual, not a total that an
+    // LP with a large right-hand side dominates.
+    std::vector<double> lp_scale;
+    auto balance = [&](const double *rd, const double *rp, const double *rc) {
+      lp_scale.assign(nlp, 1.0);
+      std::vector<double> nd(nlp);   // squared norm of each LP's slice
+      for (int c0 = 0; c0 < nlp; c0 += 6) {
+        const int cn = std::min(6, nlp - c0);
+        for (int k = 0; k < cn; ++k) {
+          const auto &r = p->lp_rng[c0 + k];
+          double *sc = p->scal + 20 + 5 * k;
+          ck(launch_reduce(p, RED_DOT, rd + r.xb0, rd + r.xb0, r.xb1 - r.xb0, sc + 0), "reduce");
+          ck(launch_reduce(p, RED_DOT, rd + r.x00, rd + r.x00, r.x01 - r.x00, sc + 1), "reduce");
+          ck(launch_reduce(p, RED_DOT, rc + r.xb0, rc + r.xb0, r.xb1 - r.xb0, sc + 2), "reduce");
+          ck(launch_reduce(p, RED_DOT, rc + r.x00, rc + r.x00, r.x01 - r.x00, sc + 3), "reduce");
+          ck(launch_reduce(p, RED_DOT, rp + r.yb0, rp + r.yb0, r.yb1 - r.yb0, sc + 4), "reduce");
+        }
+        read_scalars(p, 20 + 5 * cn);
+        for (int k = 0; k < cn; ++k) {
+          const double *h = p->h_scal + 20 + 5 * k;
+          nd[c0 + k] = h[0] + h[1] + h[2] + h[3] + h[4];
+        }
+        // the link and global rows of each LP
+        for (int k = 0; k < cn; ++k) {
+          const auto &r = p->lp_rng[c0 + k];
+          double *sc = p->scal + 20 + 2 * k;
+          ck(launch_reduce(p, RED_DOT, rp + r.yl0, rp + r.yl0, r.yl1 - r.yl0, sc + 0), "reduce");
+          ck(launch_reduce(p, RED_DOT, rp + r.yg0, rp + r.yg0, r.yg1 - r.yg0, sc + 1), "reduce");
+        }
+        read_scalars(p, 20 + 2 * cn);
+        for (int k = 0; k < cn; ++k) nd[c0 + k] += p->h_scal[20 + 2 * k] + p->h_scal[21 + 2 * k];
+      }
+      const long long n = p->n, m = p->m;
+      ck(cudaMemcpyAsync(v[V_SD], rd, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+      ck(cudaMemcpyAsync(v[V_SP], rp, m * 8, cudaMemcpyDeviceToDevice, s), "copy");
+      ck(cudaMemcpyAsync(v[V_SC], rc, n * 8, cudaMemcpyDeviceToDevice, s), "copy");
+      auto scale = [&](double *vec, long long lo, long long hi, double f) {
+        if (hi > lo) ck(launch_axpby(vec + lo, vec + lo, f - 1.0, 1.0, hi - lo, s), "scale");
+      };
+      for (int b = 0; b < nlp; ++b) {
+        const double nrm = std::sqrt(nd[b]);
+        if (!(nrm > 0.0) || !std::isfinite(nrm)) continue;   // a frozen LP: zero stays zero
+        lp_scale[b] = nrm;
+        const auto &r = p->lp_rng[b];
+        const double f = 1.0 / nrm;
+        scale(v[V_SD], r.xb0, r.xb1, f);
+        scale(v[V_SD], r.x00, r.x01, f);
+        scale(v[V_SC], r.xb0, r.xb1, f);
+        scale(v[V_SC], r.x00, r.x01, f);
+        scale(v[V_SP], r.yb0, r.yb1, f);
+        scale(v[V_SP], r.yl0, r.yl1, f);
+        scale(v[V_SP], r.yg0, r.yg1, f);
+      }
+    };
+    auto unbalance = [&](double *dx, double *dy, double *dz) {
+      auto scale = [&](double *vec, long long lo, long long hi, double f) {
+        if (hi > lo && f != 1.0) ck(launch_axpby(vec + lo, vec + lo, f - 1.0, 1.0, hi - lo, s), "scale");
+      };
+      for (int b = 0; b < nlp; ++b) {
+        const auto &r = p->lp_rng[b];
+        const double f = lp_scale[b];
+        scale(dx, r.xb0, r.xb1, f);
+        scale(dx, r.x00, r.x01, f);
+        scale(dz, r.xb0, r.xb1, f);
+        scale(dz, r.x00, r.x01, f);
+        scale(dy, r.yb0, r.yb1, f);
+        scale(dy, r.yl0, r.yl1, f);
+        scale(dy, r.yg0, r.yg1, f);
+      }
+    };
     auto solve = [&](const double *rd, const double *rp, const double *rc, double *dx, double *dy,
                      double *dz) {
       ahlp_solve_info info{};
+      if (nlp > 0) {
+        balance(rd, rp, rc);
+        rd = v[V_SD];
+        rp = v[V_SP];
+        rc = v[V_SC];
+      }
       int st = solve_impl(p, rd, rp, rc, dx, dy, dz, false, &info, ipm_tol);
+      if (nlp > 0 && st == AHLP_OK) unbalance(dx, dy, dz);
       R.ms_solve += p->stage_ms[3];
       R.refine_steps += info.refine_steps;
       R.kkt_residual = std::max(R.kkt_residual, info.rel_residual);
