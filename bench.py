@@ -531,7 +531,8 @@ def full_solve(P, prob, out, planted):
             "objective_error_vs_planted": objective_error(P, prob, out[0], planted),
             "factors": {"fp32": r["factors_fp32"], "float_float": r["factors_ff"],
                         "fp64": r["factors_fp64"]},
-            "refine_steps": r["refine_steps"], "escalations": r["escalations"]}
+            "refine_steps": r["refine_steps"], "escalations": r["escalations"],
+            "ms_factor": r["ms_factor"], "ms_solve": r["ms_solve"]}
 
 
 def update_geometry(lp, NB=64):
@@ -730,6 +731,7 @@ def run_ours(args):
         for prec, name in ((P.PREC_MIXED, "mixed"), (P.PREC_FP64, "fp64")):
             q = create(P, c1lp, prec, **opts)
             P.load().arrowhead_lp_set_stream(q.handle, stream.cuda_stream)
+            tuned1 = P.autotune(q) if prec == P.PREC_MIXED and not args.no_autotune else None
             out = (torch.empty(q.n, **f64), torch.empty(q.m, **f64), torch.empty(q.n, **f64))
             full_solve(P, q, out, c1planted)   # warm-up
             runs = [full_solve(P, q, out, c1planted) for _ in range(2)]
@@ -739,7 +741,12 @@ def run_ours(args):
                         "ms_per_solve": sum(r["ms"] for r in runs) / 2,
                         "iterations_per_solve": its / 2,
                         "objective_error_vs_planted": runs[-1]["objective_error_vs_planted"],
-                        "rel_gap": runs[-1]["rel_gap"], "factors": runs[-1]["factors"]}
+                        "rel_gap": runs[-1]["rel_gap"], "factors": runs[-1]["factors"],
+                        "ms_factor_per_solve": runs[-1]["ms_factor"],
+                        "ms_solve_per_solve": runs[-1]["ms_solve"],
+                        "refine_steps": runs[-1]["refine_steps"]}
+            if tuned1:
+                c1[name]["autotune"] = tuned1
             q.close()
         c1["mixed_over_fp64"] = c1["mixed"]["value"] / c1["fp64"]["value"]
 
@@ -825,7 +832,7 @@ def run_kkt(args):
     if args.blocks and args.blocks < lp.N:
         lp = prefix(lp, args.blocks)
     prec = P.PREC_MIXED if args.precision == "mixed" else P.PREC_FP64
-    opts = dict(refine_max=0, fp32_update=args.fp32_update)
+    opts = dict(refine_max=0, fp32_update=args.fp32_update, ff_update=args.ff_update)
     if args.force_fp32:
         opts["fp32_cond_max"] = 1e300
     if args.force_ff:
@@ -850,7 +857,8 @@ def run_kkt(args):
     line = {"metric": "KKT factor and solve ms", "unit": "ms", "higher_is_better": False,
             "config": {"workload": desc, "blocks": lp.N, "precision": args.precision,
                        "fp32_forced": bool(args.force_fp32), "ff_forced": bool(args.force_ff),
-                       "fp32_update": args.fp32_update, "steps": args.steps,
+                       "fp32_update": args.fp32_update, "ff_update": args.ff_update,
+                       "steps": args.steps,
                        "warmup": args.warmup},
             "form_ms": med([f["form_ms"] for f in fac]),
             "block_factor_ms": med([f["block_factor_ms"] for f in fac]),
@@ -888,9 +896,12 @@ def main():
                     help="--kkt-only, mixed: keep FP32 block factors at any conditioning")
     ap.add_argument("--force-ff", action="store_true",
                     help="--kkt-only, mixed: float-float block factors at any conditioning")
-    ap.add_argument("--fp32-update", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--fp32-update", type=int, default=0, choices=[0, 1, 2, 3],
                     help="--kkt-only: trailing update of FP32 factors (0 auto, 1 FP32 pipe, "
-                         "2 tensor cores)")
+                         "2 tensor cores per tile, 3 tensor cores persistent)")
+    ap.add_argument("--ff-update", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="--kkt-only: trailing update of float-float factors (0 auto, 1 FP32 "
+                         "pipe, 2 tensor-core digits per tile, 3 persistent)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -186,13 +186,21 @@ typedef struct {
   int32_t fp32_update;  /* trailing updates of FP32 block factors: 0 = tensor
                            cores when available (tcgen05, TF32 hi/lo split
                            operands, FP32 accumulation), 1 = FP32 pipe,
-                           2 = tensor cores (AHLP_ERR_UNSUPPORTED when the
-                           driver cannot encode tensor maps) (0)               */
+                           2 = tensor cores, one CTA per 128 x 64 output tile,
+                           3 = tensor cores, one persistent CTA per SM that
+                           overlaps the copies, products and reduce of
+                           consecutive tiles (2 and 3: AHLP_ERR_UNSUPPORTED
+                           when the driver cannot encode tensor maps) (0)      */
   int32_t ff_update;    /* trailing updates of float-float block factors: 0 or 2 =
                            tensor cores (each panel entry as six FP16 integer
                            digits under a per-row exponent, the digit products
-                           accumulated exactly in FP32, 49 bits in all),
-                           1 = double-float arithmetic on the FP32 pipe (0)     */
+                           accumulated exactly in FP32, 49 bits in all), one
+                           CTA per 128 x 64 output tile; 3 = the same products
+                           in one persistent CTA per SM that overlaps the
+                           copies, products and C-tile update of consecutive
+                           tiles (bitwise the same factor); 1 = double-float
+                           arithmetic on the FP32 pipe.  0, 2 and 3 fall back
+                           to 1 when the driver cannot encode tensor maps (0) */
   int32_t schur_chain;  /* factor and solves of the block-tridiagonal link chain
                            of the Schur complement: 0 = block cyclic reduction
                            (log2 of the chain length sequential levels),
@@ -287,17 +295,21 @@ int arrowhead_lp_original_size(const ahlp_problem *p, int64_t *n_orig);
 /*
  * arrowhead_lp_autotune -- pick the trailing-update kernel of the FP32 and of
  * the float-float block factors for this handle's block sizes: each
- * candidate (FP32: tensor cores on 128 x 64 output tiles, or the FP32 pipe
- * on 64 x 64 tiles; float-float: FP16 digit products on the tensor cores,
- * or double-float arithmetic on the FP32 pipe) factors the blocks at the
- * point (x, z) (NULL: x = z = 1), timed with CUDA events on the handle's
- * stream (best of two after one warm-up), and the faster one is written into
- * the handle's options (fp32_update, ff_update).  Later calls do not time
- * anything, so results stay reproducible once the choice is made.
- *   ms4 (may be NULL) : receives the four block-factor times [FP32 tensor,
- *                       FP32 pipe, float-float tensor, float-float pipe]
+ * candidate (FP32: tensor cores with one CTA per 128 x 64 output tile, the
+ * persistent pipelined tensor-core kernel, or the FP32 pipe on 64 x 64
+ * tiles; float-float: FP16 digit products on the tensor cores per tile or
+ * persistent, or double-float arithmetic on the FP32 pipe) factors the
+ * blocks at the point (x, z) (NULL: x = z = 1), timed with CUDA events on
+ * the handle's stream (best of two after one warm-up), and the fastest is
+ * written into the handle's options (fp32_update, ff_update).  Later calls
+ * do not time anything, so results stay reproducible once the choice is
+ * made.
+ *   ms6 (may be NULL) : receives the six block-factor times [FP32 tensor
+ *                       per tile, FP32 pipe, float-float tensor per tile,
+ *                       float-float pipe, FP32 tensor persistent,
+ *                       float-float tensor persistent]
  */
-int arrowhead_lp_autotune(ahlp_problem *p, const double *x, const double *z, double *ms4);
+int arrowhead_lp_autotune(ahlp_problem *p, const double *x, const double *z, double *ms6);
 
 /* Sizes of the global vectors. */
 int arrowhead_lp_sizes(const ahlp_problem *p, int64_t *n_total, int64_t *m_total);

@@ -144,16 +144,18 @@ def autotune(prob, x=None, z=None):
     into the handle's options.  Returns the four block-factor times (ms)."""
     keep = _Keep()
     prob._stream_for(x, z)
-    ms = (C.c_double * 4)()
+    ms = (C.c_double * 6)()
     prob._check(prob._lib.arrowhead_lp_autotune(
         prob._h, _vec_ptr(x, keep, prob.n, "x") if x is not None else None,
         _vec_ptr(z, keep, prob.n, "z") if z is not None else None, ms))
     # mirror the handle's new choice in the Python-side copy of its options
-    prob.options.fp32_update = 2 if ms[0] <= ms[1] else 1
-    prob.options.ff_update = 2 if ms[2] <= ms[3] else 1
+    prob.options.fp32_update = (3 if ms[4] <= min(ms[0], ms[1]) else
+                                2 if ms[0] <= ms[1] else 1)
+    prob.options.ff_update = 3 if ms[5] <= min(ms[2], ms[3]) else 2 if ms[2] <= ms[3] else 1
     return {"fp32_tensor_ms": ms[0], "fp32_pipe_ms": ms[1], "ff_tensor_ms": ms[2],
-            "ff_pipe_ms": ms[3], "fp32_update": prob.options.fp32_update,
-            "ff_update": prob.options.ff_update}
+            "ff_pipe_ms": ms[3], "fp32_tensor_persistent_ms": ms[4],
+            "ff_tensor_persistent_ms": ms[5],
+            "fp32_update": prob.options.fp32_update, "ff_update": prob.options.ff_update}
 
 
 def recover(prob, x):

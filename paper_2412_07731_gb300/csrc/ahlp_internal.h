@@ -238,7 +238,10 @@ struct ahlp_problem {
   bool oz_ready = false;
   void *oz_tmap = nullptr;           // [2N] CUtensorMap: each block's hi, then lo matrix
   int ff_update = 0;                 // trailing update of float-float factors: 1 FP32 pipe, 2 tensor cores
-  int fp32_update = 0;               // trailing update of FP32 factors: 1 SIMT, 2 tensor cores
+  int fp32_update = 0;               // trailing update of FP32 factors: 1 SIMT, 2 tensor
+                                     // cores (one CTA per job), 3 tensor cores (persistent
+                                     // warp-specialised pipeline)
+  int num_sms = 1;
   double fac_flops = 0;   // algorithmic flops of one batched partial Cholesky
   double tri_elems = 0;   // lower-triangle entries of all augmented matrices
 

@@ -393,7 +393,7 @@ static int check_options(const ahlp_options &o, std::string &err) {
       !(o.fp32_cond_max >= 1) || o.max_correctors < 0 || o.max_correctors > 8 ||
       !(o.ipm_refine_tol >= 0 && o.ipm_refine_tol < 1) ||
       (o.correctors_by_cost != 0 && o.correctors_by_cost != 1) || o.fp32_update < 0 ||
-      o.fp32_update > 2 || o.ff_update < 0 || o.ff_update > 2 || o.schur_chain < 0 ||
+      o.fp32_update > 3 || o.ff_update < 0 || o.ff_update > 3 || o.schur_chain < 0 ||
       o.schur_chain > 1 || o.profile_kernels < 0 || o.profile_kernels > 1) {
     err = "invalid option value";
     return AHLP_ERR_INVALID_ARG;
@@ -1451,19 +1451,19 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol, boo
     if (p->opt.fp32_update != 1) {
       if (tc_setup(p))
         tc = p;
-      else if (p->opt.fp32_update == 2)
+      else if (p->opt.fp32_update >= 2)
         return set_err(p, AHLP_ERR_UNSUPPORTED,
                        "kkt_factor: tensor-core update requested, but the driver cannot "
                        "encode tensor maps");
     }
-    p->fp32_update = tc ? 2 : 1;
+    p->fp32_update = tc ? (p->opt.fp32_update == 3 ? 3 : 2) : 1;
     ck(launch_pchol_f32(p->aug32, p->tinv32, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol,
                         p->status, s, tc, prof),
        "pchol");
   }
   else if (p->fac_prec == kPrecFF) {
     ahlp_problem *oz = (p->opt.ff_update != 1 && oz_setup(p)) ? p : nullptr;
-    p->ff_update = oz ? 2 : 1;
+    p->ff_update = oz ? (p->opt.ff_update == 3 ? 3 : 2) : 1;
     ck(launch_pchol_ff(p->aug32, p->aug_lo, p->aug, p->aug_elems, p->blk, p->h_blk, p->diag0,
                        p->fac_pivot_tol, p->status, s, oz, prof),
        "pchol");
@@ -1755,11 +1755,11 @@ int kkt_schur_dense(ahlp_problem *p, double *S, int64_t ld) {
 
 int64_t ahlp_launch_count(void) { return ahlp::launch_count(); }
 
-int arrowhead_lp_autotune(ahlp_problem *p, const double *x, const double *z, double *ms4) {
+int arrowhead_lp_autotune(ahlp_problem *p, const double *x, const double *z, double *ms6) {
   if (!p) return AHLP_ERR_INVALID_ARG;
   const ahlp_options saved = p->opt;
   const int saved_prec = p->fac_prec;
-  double best[4] = {0, 0, 0, 0};
+  double best[6] = {0, 0, 0, 0, 0, 0};
   try {
     const double *xx = x ? stage_in(p, x, p->n, p->stg[0]) : nullptr;
     const double *zz = z ? stage_in(p, z, p->n, p->stg[1]) : nullptr;
@@ -1769,10 +1769,10 @@ int arrowhead_lp_autotune(ahlp_problem *p, const double *x, const double *z, dou
     }
     ck(cudaMemcpyAsync(p->x, xx, p->n * 8, cudaMemcpyDeviceToDevice, p->stream), "copy");
     ck(cudaMemcpyAsync(p->z, zz, p->n * 8, cudaMemcpyDeviceToDevice, p->stream), "copy");
-    // (precision, update option, value) of the four candidates
-    const int prec[4] = {kPrecFP32, kPrecFP32, kPrecFF, kPrecFF};
-    const int val[4] = {2, 1, 2, 1};
-    for (int c = 0; c < 4; ++c) {
+    // (precision, update option value) of the six candidates
+    const int prec[6] = {kPrecFP32, kPrecFP32, kPrecFF, kPrecFF, kPrecFP32, kPrecFF};
+    const int val[6] = {2, 1, 2, 1, 3, 3};
+    for (int c = 0; c < 6; ++c) {
       p->opt = saved;
       p->opt.precision = AHLP_PREC_MIXED;
       p->opt.fp32_cond_max = prec[c] == kPrecFP32 ? 1e300 : 1.0;
@@ -1788,12 +1788,12 @@ int arrowhead_lp_autotune(ahlp_problem *p, const double *x, const double *z, dou
       best[c] = t;
     }
     p->opt = saved;
-    p->opt.fp32_update = best[0] <= best[1] ? 2 : 1;
-    p->opt.ff_update = best[2] <= best[3] ? 2 : 1;
+    p->opt.fp32_update = best[4] <= std::min(best[0], best[1]) ? 3 : best[0] <= best[1] ? 2 : 1;
+    p->opt.ff_update = best[5] <= std::min(best[2], best[3]) ? 3 : best[2] <= best[3] ? 2 : 1;
     p->fac_prec = saved_prec;
     p->factored = false;
-    if (ms4)
-      for (int c = 0; c < 4; ++c) ms4[c] = best[c];
+    if (ms6)
+      for (int c = 0; c < 6; ++c) ms6[c] = best[c];
     return AHLP_OK;
   } catch (const Fail &f) {
     p->opt = saved;

@@ -156,8 +156,10 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
     // stopped on bounds every LP's own relative residual, not a total that an
     // LP with a large right-hand side dominates.
     std::vector<double> lp_scale;
+    int n_active = 0;   // LPs whose slice was brought to unit norm
     auto balance = [&](const double *rd, const double *rp, const double *rc) {
       lp_scale.assign(nlp, 1.0);
+      n_active = 0;
       std::vector<double> nd(nlp);   // squared norm of each LP's slice
       for (int c0 = 0; c0 < nlp; c0 += 6) {
         const int cn = std::min(6, nlp - c0);
@@ -196,6 +198,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
         const double nrm = std::sqrt(nd[b]);
         if (!(nrm > 0.0) || !std::isfinite(nrm)) continue;   // a frozen LP: zero stays zero
         lp_scale[b] = nrm;
+        ++n_active;
         const auto &r = p->lp_rng[b];
         const double f = 1.0 / nrm;
         scale(v[V_SD], r.xb0, r.xb1, f);
@@ -250,10 +253,13 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       // coarser pivot threshold: in the degenerate end game the factors of
       // every precision stop being good preconditioners (FP64 ones too), so
       // a refactor costs several float-float factors and buys no accuracy.
-      // (Not for a batch: its residual is measured over all LPs together, so
-      // a moderate total can hide a useless slice for an LP whose own
-      // right-hand side is small.)
-      if (!allow_delta && nlp == 0 && last_rel <= kStallAccept &&
+      // In a batch every active LP's slice of the right-hand side has unit
+      // norm (balance), so the total relative residual times sqrt(active
+      // LPs) bounds each LP's own relative residual, and that bound is what
+      // is tested.
+      const double per_lp =
+          nlp > 0 ? last_rel * std::sqrt((double)std::max(n_active, 1)) : last_rel;
+      if (!allow_delta && per_lp <= kStallAccept &&
           (p->fac_prec == kPrecFF || p->fac_prec == kPrecFP64)) {
         if (p->opt.verbose)
           printf("       %s accepted (%s factor, residual %.2e)\n", why,

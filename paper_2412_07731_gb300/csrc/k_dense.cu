@@ -549,9 +549,10 @@ __global__ void __launch_bounds__(kThreads) pchol_potrf_ff_kernel(float *hi, flo
 // (hi, lo), scaled by a power of two and peeled off in FP32 with every
 // remainder kept exactly (a two-word remainder, renormalised by two-sum).
 // Digit plane s of the tile is a 64 x 64 FP16 K-major operand without
-// swizzling: entry (r, c) at (r/8)*512 + (c/8)*64 + (r%8)*8 + c%8; the six
-// planes follow each other (4096 entries each).  Rows past the matrix and
-// columns past the pivots are zero.
+// swizzling, split into two K halves so that either half is one contiguous
+// 4 KB run: entry (r, c) at (c/32)*2048 + (r/8)*256 + ((c%32)/8)*64 +
+// (r%8)*8 + c%8; the six planes follow each other (4096 entries each).  Rows
+// past the matrix and columns past the pivots are zero.
 constexpr int kOzDigits = 6;
 
 __device__ __forceinline__ void two_sum_f(float &a, float &b) {   // (a, b) <- fl(a+b), error
@@ -602,91 +603,144 @@ __device__ __forceinline__ void df_sub(float &xh, float &xl, float ph, float pl)
   xl = __fsub_rn(el, __fsub_rn(xh, s));
 }
 
-constexpr size_t kTrsmFFSmem = 4 * NB * (NB + 1) * sizeof(float);
+// Rows of X are independent (X_r = A_r L^-T), so one thread solves one row
+// and no step waits for another thread.  A row is taken in chunks of 16
+// columns held in registers: first every finished column left of the chunk
+// (kept in shared memory) is removed from it, then the chunk's own triangle
+// is solved.  Every entry so receives the same operations in the same order
+// as in column-by-column substitution (the subtractions of columns
+// 0, 1, ..., c - 1, then the scaling), and the same rounding.  Two tiles of
+// the same block and step per CTA share the pivot tile.
+constexpr int kFFRowTiles = 2;
+constexpr int kFFRowThreads = kFFRowTiles * NB;
+constexpr int kFFChunk = 16;
+constexpr size_t kTrsmFFSmem =
+    (2 * NB * NB + 2 * kFFRowTiles * NB * NB + 2 * NB) * sizeof(float);
 
-__global__ void __launch_bounds__(kThreads) pchol_trsm_ff_kernel(float *hi, float *lo,
-                                                                 const BlkInfo *blk, int k,
-                                                                 __half *dstage, int *dexp) {
+__global__ void __launch_bounds__(kFFRowThreads) pchol_trsm_ff_kernel(float *hi, float *lo,
+                                                                     const BlkInfo *blk, int k,
+                                                                     __half *dstage, int *dexp) {
   const BlkInfo bi = blk[blockIdx.y];
   if (k >= bi.Tp) return;
-  const int I = k + 1 + blockIdx.x;
-  if (I >= bi.T) return;
-  extern __shared__ __align__(16) float trsm_f[];   // L hi, L lo, X hi, X lo: (NB x NB+1) each
-  float(*Lh)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(trsm_f);
-  float(*Ll)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(trsm_f + NB * (NB + 1));
-  float(*Xh)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(trsm_f + 2 * NB * (NB + 1));
-  float(*Xl)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(trsm_f + 3 * NB * (NB + 1));
-  __shared__ float s_ih, s_il;
+  const int I0 = k + 1 + kFFRowTiles * blockIdx.x;
+  if (I0 >= bi.T) return;
+  extern __shared__ __align__(16) float trsm_f[];
+  float *Lth = trsm_f;                     // [c][sc] = L_kk(sc, c): pivot column c contiguous
+  float *Ltl = Lth + NB * NB;
+  float *Xsh = Ltl + NB * NB;              // [tile][c][r]: finished columns of the rows
+  float *Xsl = Xsh + kFFRowTiles * NB * NB;
+  float *s_ih = Xsl + kFFRowTiles * NB * NB;   // pivot reciprocals, split in two words
+  float *s_il = s_ih + NB;
   const int r0 = k * NB;
   const int nr = min(NB, bi.a - r0);
   const int npiv = min(NB, bi.p - r0);
-  const int ri = I * NB;
-  const int nri = min(NB, bi.a - ri);
   const long long gl = bi.base + (long long)r0 * bi.lda + r0;
-  const long long gx = bi.base + (long long)r0 * bi.lda + ri;
   for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
-    const int r = i % NB, c = i / NB;
-    const bool lin = r < nr && c < nr && r >= c, xin = r < nri && c < nr;
-    const long long el = gl + (long long)c * bi.lda + r, ex = gx + (long long)c * bi.lda + r;
-    Lh[r][c] = lin ? hi[el] : 0.0f;
-    Ll[r][c] = lin ? lo[el] : 0.0f;
-    Xh[r][c] = xin ? hi[ex] : 0.0f;
-    Xl[r][c] = xin ? lo[ex] : 0.0f;
+    const int sc = i % NB, c = i / NB;
+    const bool lin = sc < nr && c < nr && sc >= c;
+    const long long el = gl + (long long)c * bi.lda + sc;
+    Lth[c * NB + sc] = lin ? hi[el] : 0.0f;
+    Ltl[c * NB + sc] = lin ? lo[el] : 0.0f;
   }
   __syncthreads();
-  for (int c = 0; c < npiv; ++c) {
-    if (threadIdx.x == 0) {
-      const double inv = 1.0 / ((double)Lh[c][c] + (double)Ll[c][c]);
-      s_ih = (float)inv;
-      s_il = (float)(inv - (double)s_ih);
-    }
-    __syncthreads();
-    const float ih = s_ih, il = s_il;
-    for (int r = threadIdx.x; r < nri; r += blockDim.x)
-      df_mul(Xh[r][c], Xl[r][c], ih, il, Xh[r][c], Xl[r][c]);
-    __syncthreads();
-    const int ns = nr - c - 1;
-    for (int idx = threadIdx.x; idx < nri * ns; idx += blockDim.x) {
-      const int r = idx % nri, sc = c + 1 + idx / nri;
-      float ph, pl;
-      df_mul(Xh[r][c], Xl[r][c], Lh[sc][c], Ll[sc][c], ph, pl);
-      df_sub(Xh[r][sc], Xl[r][sc], ph, pl);
-    }
-    __syncthreads();
+  if (threadIdx.x < npiv) {
+    const int c = threadIdx.x;
+    const double inv = 1.0 / ((double)Lth[c * NB + c] + (double)Ltl[c * NB + c]);
+    s_ih[c] = (float)inv;
+    s_il[c] = (float)(inv - (double)s_ih[c]);
   }
-  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) {
-    const int r = i % NB, c = i / NB;
-    if (r < nri && c < nr) {
-      hi[gx + (long long)c * bi.lda + r] = Xh[r][c];
-      lo[gx + (long long)c * bi.lda + r] = Xl[r][c];
-    }
-  }
-  if (dstage) {
-    __shared__ int s_exp[NB];
-    const long long slot = bi.soff + I;
-    if (threadIdx.x < NB) {
-      const int r = threadIdx.x;
-      float mx = 0.0f;
-      if (r < nri)
-        for (int c = 0; c < npiv; ++c) mx = fmaxf(mx, fabsf(Xh[r][c]));
-      int e = 0;
-      if (mx > 0.0f) frexpf(mx, &e);   // mx = f 2^e, f in [0.5, 1)
-      s_exp[r] = e;
-      dexp[slot * NB + r] = e;
-    }
-    __syncthreads();
-    __half *st = dstage + slot * (kOzDigits * NB * NB);
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-      const int r = (e >> 9) * 8 + ((e >> 3) & 7), c = ((e >> 6) & 7) * 8 + (e & 7);
-      float d[kOzDigits];
-      if (r < nri && c < npiv) {
-        oz_digits(Xh[r][c], Xl[r][c], s_exp[r], d);
-      } else {
+  __syncthreads();
+
+  const int t = threadIdx.x / NB, r = threadIdx.x % NB;
+  const int I = I0 + t;
+  const bool tile_ok = I < bi.T;
+  const int ri = I * NB;
+  const int nri = tile_ok ? min(NB, bi.a - ri) : 0;
+  const bool row_ok = r < nri;
+  const long long gx = bi.base + (long long)r0 * bi.lda + ri;
+  float *xsh = Xsh + t * NB * NB + r, *xsl = Xsl + t * NB * NB + r;   // column c at [c * NB]
+  for (int c0 = 0; c0 < nr; c0 += kFFChunk) {
+    float xh[kFFChunk], xl[kFFChunk];
 #pragma unroll
-        for (int q = 0; q < kOzDigits; ++q) d[q] = 0.0f;
+    for (int j = 0; j < kFFChunk; ++j) {
+      const int c = c0 + j;
+      const bool in = row_ok && c < nr;
+      xh[j] = in ? hi[gx + (long long)c * bi.lda + r] : 0.0f;
+      xl[j] = in ? lo[gx + (long long)c * bi.lda + r] : 0.0f;
+    }
+    // the finished pivot columns left of the chunk
+    const int cend = min(c0, npiv);
+    for (int c = 0; c < cend; ++c) {
+      const float ah = xsh[c * NB], al = xsl[c * NB];
+      const float4 *Lh4 = reinterpret_cast<const float4 *>(Lth + c * NB + c0);
+      const float4 *Ll4 = reinterpret_cast<const float4 *>(Ltl + c * NB + c0);
+#pragma unroll
+      for (int q = 0; q < kFFChunk / 4; ++q) {
+        const float4 bh = Lh4[q], bl = Ll4[q];
+        const float bhv[4] = {bh.x, bh.y, bh.z, bh.w}, blv[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float ph, pl;
+          df_mul(ah, al, bhv[u], blv[u], ph, pl);
+          df_sub(xh[4 * q + u], xl[4 * q + u], ph, pl);
+        }
       }
+    }
+    // the chunk's own triangle
 #pragma unroll
-      for (int q = 0; q < kOzDigits; ++q) st[q * NB * NB + e] = __float2half_rn(d[q]);
+    for (int j = 0; j < kFFChunk; ++j) {
+      const int c = c0 + j;
+      if (c < npiv) {
+        df_mul(xh[j], xl[j], s_ih[c], s_il[c], xh[j], xl[j]);
+#pragma unroll
+        for (int jj = j + 1; jj < kFFChunk; ++jj) {
+          float ph, pl;
+          df_mul(xh[j], xl[j], Lth[c * NB + c0 + jj], Ltl[c * NB + c0 + jj], ph, pl);
+          df_sub(xh[jj], xl[jj], ph, pl);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kFFChunk; ++j) {
+      const int c = c0 + j;
+      xsh[c * NB] = xh[j];
+      xsl[c * NB] = xl[j];
+      if (row_ok && c < nr) {
+        hi[gx + (long long)c * bi.lda + r] = xh[j];
+        lo[gx + (long long)c * bi.lda + r] = xl[j];
+      }
+    }
+  }
+  if (dstage && tile_ok) {
+    const long long slot = bi.soff + I;
+    float mx = 0.0f;
+    if (row_ok)
+      for (int c = 0; c < npiv; ++c) mx = fmaxf(mx, fabsf(xsh[c * NB]));
+    int e = 0;
+    if (mx > 0.0f) frexpf(mx, &e);   // mx = f 2^e, f in [0.5, 1)
+    dexp[slot * NB + r] = e;
+    __half *st = dstage + slot * (kOzDigits * NB * NB) + (r >> 3) * 256 + (r & 7) * 8;
+#pragma unroll 1
+    for (int cg = 0; cg < NB / 8; ++cg) {   // 8 consecutive columns: one 16-byte run per plane
+      __align__(16) __half dv[kOzDigits][8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = cg * 8 + u;
+        float d[kOzDigits];
+        if (row_ok && c < npiv) {
+          oz_digits(xsh[c * NB], xsl[c * NB], e, d);
+        } else {
+#pragma unroll
+          for (int q = 0; q < kOzDigits; ++q) d[q] = 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < kOzDigits; ++q) dv[q][u] = __float2half_rn(d[q]);
+      }
+      const int off = (cg >> 2) * 2048 + (cg & 3) * 64;
+#pragma unroll
+      for (int q = 0; q < kOzDigits; ++q)
+        *reinterpret_cast<uint4 *>(st + q * NB * NB + off) =
+            *reinterpret_cast<const uint4 *>(dv[q]);
     }
   }
 }
@@ -1583,8 +1637,10 @@ cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
                                                                     status);
     if (prof) kt_mark(prof, 1, s);
     if (maxPanel > 0)
-      count_launch(), pchol_trsm_ff_kernel<<<dim3((unsigned)maxPanel, nblk), kThreads,
-                                             kTrsmFFSmem, s>>>(
+      count_launch(), pchol_trsm_ff_kernel<<<dim3((unsigned)((maxPanel + kFFRowTiles - 1) /
+                                                             kFFRowTiles),
+                                                  nblk),
+                                             kFFRowThreads, kTrsmFFSmem, s>>>(
                           hi, lo, info, k, oz ? oz->dstage : nullptr, oz ? oz->dexp : nullptr);
     if (prof) kt_mark(prof, 2, s);
     if (maxTrail > 0) {

@@ -174,8 +174,8 @@ struct Job {
   bool has_i1;
 };
 
-__device__ __forceinline__ Job decode_job(const int *joff, int nblk, int k, const BlkInfo *blk) {
-  const int q = blockIdx.x;
+__device__ __forceinline__ Job decode_job(const int *joff, int nblk, int k, const BlkInfo *blk,
+                                          int q) {
   int lo = 0, hi = nblk;   // joff[lo] <= q < joff[hi]
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_tc_kernel(const TcArg
   float *b_lo = reinterpret_cast<float *>(base + 2 * kSmemA + kSmemB);
 
   // ---- which block and tiles ------------------------------------------------
-  const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk);
+  const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk, blockIdx.x);
   const int b = jb.b, I0 = jb.I0, J = jb.J;
   const bool has_i1 = jb.has_i1;
   const BlkInfo bi = args.blk[b];
@@ -333,6 +333,191 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_tc_kernel(const TcArg
 }
 
 
+
+// --------------------------------------------------------------------------
+// The same FP32 update as a persistent, warp-specialised pipeline: one CTA
+// per SM walks the step's jobs (job blockIdx.x, + gridDim.x, ...), and its
+// warps overlap consecutive jobs --
+//   warp 0  producer: bulk copies of job j's operands into smem stage j % 2,
+//           once the MMAs of job j - 2 have released that stage;
+//   warp 1  MMA issuer: the 24 MMAs of job j into TMEM accumulator j % 2, once
+//           its operands have landed and the epilogue has drained job j - 2
+//           from that accumulator; its commits release the stage and hand the
+//           accumulator to the epilogue;
+//   warps 2-5  epilogue: accumulator -> -P in a staging tile -> one tensor
+//           reduce-add into the block's matrix, while the next job's copies
+//           and MMAs run.
+// mbarrier phases alternate per use of a stage / accumulator; every wait is
+// bounded as in the kernel above.
+// --------------------------------------------------------------------------
+constexpr int kTc2Threads = 192;
+constexpr uint32_t kTc2Stage = 2 * kSmemA + 2 * kSmemB;             // 96 KB of operands
+constexpr uint32_t kTc2Smem = 2 * kTc2Stage + kTcM * kTcN * 4 + 1024;  // 2 stages + staging
+
+__global__ void __launch_bounds__(kTc2Threads, 1) pchol_update_tc2_kernel(const TcArgs args,
+                                                                         int njobs) {
+  extern __shared__ __align__(1024) unsigned char tc2_raw[];
+  __shared__ __align__(8) uint64_t full[2], empty[2], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail, s_epi_fail;
+  unsigned char *base = tc2_raw + ((1024 - (smem_u32(tc2_raw) & 1023)) & 1023);
+  float *stage_out = reinterpret_cast<float *>(base + 2 * kTc2Stage);   // [64 cols][128 rows]
+  volatile int *vfail = &s_fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int myjobs = (int)blockIdx.x < njobs ? (njobs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
+                                             : 0;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(2u * kTcN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_epi_fail = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&empty[i]), 1);
+      mbar_init(smem_u32(&tfull[i]), 1);
+      mbar_init(smem_u32(&tempty[i]), kTcM);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // ---- producer: operands of job j into stage j % 2 -----------------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int j = 0; j < myjobs && !*vfail; ++j) {
+        const int st = j & 1;
+        if (!mbar_wait(smem_u32(&empty[st]), ((j >> 1) & 1) ^ 1)) {
+          atomicExch(&s_fail, 1);
+          break;
+        }
+        const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk,
+                                  (int)blockIdx.x + j * (int)gridDim.x);
+        const BlkInfo bi = args.blk[jb.b];
+        const float *st0 = args.stage + (bi.soff + jb.I0) * 8192LL;
+        const float *stJ = args.stage + (bi.soff + jb.J) * 8192LL;
+        const uint32_t sa = smem_u32(base + st * kTc2Stage);
+        const uint32_t bar = smem_u32(&full[st]);
+        mbar_expect_tx(bar, (jb.has_i1 ? 6u : 4u) * kTileBytes);
+        bulk_g2s(sa, st0, kTileBytes, bar);                                 // A hi, rows 0..63
+        bulk_g2s(sa + kSmemA, st0 + 4096, kTileBytes, bar);                 // A lo
+        if (jb.has_i1) {                                                    // rows 64..127
+          bulk_g2s(sa + kTileBytes, st0 + 8192, kTileBytes, bar);
+          bulk_g2s(sa + kSmemA + kTileBytes, st0 + 8192 + 4096, kTileBytes, bar);
+        }
+        bulk_g2s(sa + 2 * kSmemA, stJ, kTileBytes, bar);                    // B hi
+        bulk_g2s(sa + 2 * kSmemA + kSmemB, stJ + 4096, kTileBytes, bar);    // B lo
+        issued = j + 1;
+      }
+      if (*vfail)   // copies still in flight (the last two jobs) land before exit
+        for (int j = issued >= 2 ? issued - 2 : 0; j < issued; ++j)
+          mbar_wait(smem_u32(&full[j & 1]), (j >> 1) & 1);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: job j into accumulator j % 2 ---------------------------
+    if (lane == 0) {
+      int committed = 0;
+      for (int j = 0; j < myjobs && !*vfail; ++j) {
+        const int st = j & 1;
+        if (!mbar_wait(smem_u32(&full[st]), (j >> 1) & 1) ||
+            !mbar_wait(smem_u32(&tempty[st]), ((j >> 1) & 1) ^ 1)) {
+          atomicExch(&s_fail, 2);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(base + st * kTc2Stage);
+        const uint32_t ah = sa, al = sa + kSmemA, bh = sa + 2 * kSmemA, bl = bh + kSmemB;
+        const uint32_t pa[3] = {al, ah, ah}, pb[3] = {bh, bl, bh};
+        const uint32_t d = tmem + (uint32_t)(st * kTcN);
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+          for (int ks = 0; ks < NB / 8; ++ks)
+            mma_tf32(d, smem_desc(pa[pass] + ks * 256, 128, 2048),
+                     smem_desc(pb[pass] + ks * 256, 128, 2048), (pass | ks) != 0);
+        mma_commit(smem_u32(&empty[st]));   // operands read: stage free
+        mma_commit(smem_u32(&tfull[st]));   // product complete: epilogue may read it
+        committed = j + 1;
+      }
+      if (*vfail && committed > 0) {   // MMAs in flight finish before TMEM is freed
+        const int j = committed - 1;
+        mbar_wait(smem_u32(&tfull[j & 1]), (j >> 1) & 1);
+      }
+    }
+  } else {
+    // ---- epilogue: warps 2..5 read TMEM lane quarters 2, 3, 0, 1 -------------
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;   // row of the 128-row block
+    const bool leader = threadIdx.x == 64;
+    for (int j = 0; j < myjobs; ++j) {
+      const int acc = j & 1;
+      // one lane waits, the warp follows its verdict (tcgen05.ld is warp-wide)
+      int ok = 0;
+      if (lane == 0) ok = mbar_wait(smem_u32(&tfull[acc]), (j >> 1) & 1) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      float v[2][32];
+      if (ok) {
+        tc_fence_after();
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * kTcN), v[0]);
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * kTcN + 32), v[1]);
+        tc_fence_before();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[acc]))
+                     : "memory");
+      } else if (lane == 0) {
+        s_epi_fail = 1;
+      }
+      // the previous job's reduce has finished reading the staging tile
+      if (leader) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (s_epi_fail) {   // the same verdict in all four warps
+        if (leader) atomicExch(&s_fail, 3);
+        break;
+      }
+      const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk,
+                                (int)blockIdx.x + j * (int)gridDim.x);
+      const int grow = jb.I0 * NB + r;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int col = h * 32 + c;
+          stage_out[col * kTcM + r] = grow >= jb.J * NB + col ? -v[h][c] : 0.0f;
+        }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (leader) {
+        const CUtensorMap *tm = args.tmap + jb.b;
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm) : "memory");
+        asm volatile(
+            "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, "
+            "%2}], [%3];" ::"l"(tm),
+            "r"(jb.I0 * NB), "r"(jb.J * NB), "r"(smem_u32(stage_out))
+            : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+    }
+    if (leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && *vfail) atomicExch(&args.status[4], 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2u * kTcN)
+                 : "memory");
+}
+
 // --------------------------------------------------------------------------
 // Float-float trailing update on the tensor cores.  The panel kernel leaves
 // every panel tile as six planes of FP16 integer digits with one exponent per
@@ -430,7 +615,7 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_oz_kernel(const OzArg
   float *c_hi = reinterpret_cast<float *>(base + kOzQ * kOzPlaneA + kOzQ * kOzPlaneB);
   float *c_lo = c_hi + kTcM * kTcN;
 
-  const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk);
+  const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk, blockIdx.x);
   const int b = jb.b, I0 = jb.I0, J = jb.J;
   const bool has_i1 = jb.has_i1;
   const BlkInfo bi = args.blk[b];
@@ -473,10 +658,18 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_oz_kernel(const OzArg
     mbar_expect_tx(bar_ld, (has_i1 ? 3u : 2u) * kOzQ * plane + 2 * kOzCTile);
     tma_load_2d(smem_u32(c_hi), tmh, I0 * NB, J * NB, bar_ld);
     tma_load_2d(smem_u32(c_lo), tml, I0 * NB, J * NB, bar_ld);
+    // A plane q: K half h holds rows 0..63 (tile I0) then rows 64..127 (tile
+    // I0 + 1), 4 KB each; a B plane is the staged plane as it is
 #pragma unroll
     for (int q = 0; q < kOzQ; ++q) {
-      bulk_g2s(sA + q * kOzPlaneA, st0 + q * NB * NB, plane, bar_ld);
-      if (has_i1) bulk_g2s(sA + q * kOzPlaneA + plane, st0 + (kOzQ + q) * NB * NB, plane, bar_ld);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        bulk_g2s(sA + q * kOzPlaneA + h * plane, st0 + q * NB * NB + h * (NB * NB / 2),
+                 plane / 2, bar_ld);
+        if (has_i1)
+          bulk_g2s(sA + q * kOzPlaneA + h * plane + plane / 2,
+                   st0 + (kOzQ + q) * NB * NB + h * (NB * NB / 2), plane / 2, bar_ld);
+      }
       bulk_g2s(sB + q * kOzPlaneB, stJ + q * NB * NB, plane, bar_ld);
     }
     bool ok = mbar_wait(bar_ld, 0);
@@ -488,9 +681,12 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_oz_kernel(const OzArg
         for (int sd = 0; sd <= q; ++sd)
 #pragma unroll
           for (int ks = 0; ks < NB / 16; ++ks) {
-            // K step ks: two 16-byte core-matrix columns, 2 x 128 bytes further
-            const uint64_t da = smem_desc(sA + sd * kOzPlaneA + ks * 256, 128, 1024);
-            const uint64_t db = smem_desc(sB + (q - sd) * kOzPlaneB + ks * 256, 128, 1024);
+            // K step ks: K half ks / 2, two 16-byte core-matrix columns into it
+            // (an A half is 128 rows = 8 KB, a B half 64 rows = 4 KB)
+            const uint32_t kin = (ks & 1) * 256;
+            const uint64_t da = smem_desc(sA + sd * kOzPlaneA + (ks >> 1) * plane + kin, 128, 512);
+            const uint64_t db =
+                smem_desc(sB + (q - sd) * kOzPlaneB + (ks >> 1) * (plane / 2) + kin, 128, 512);
             mma_f16(tmem + q * kTcN, da, db, (sd | ks) != 0);
           }
       mma_commit(bar_mma);
@@ -568,6 +764,285 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_oz_kernel(const OzArg
                  : "memory");
 }
 
+// --------------------------------------------------------------------------
+// The float-float digit update as a persistent, warp-specialised pipeline:
+// one CTA per SM walks the step's jobs (job blockIdx.x, + gridDim.x, ...).
+// A job's operands come in two units, one per K half (all six A and B
+// digit planes over 32 pivot columns, 72 KB), each with its own shared-
+// memory stage, so the next job's first half loads while this job's
+// second half multiplies --
+//   warp 0  producer: bulk copies of unit (j, h) into stage h once the MMAs
+//           of job j - 1 have released it, and an L2 prefetch of job j's C
+//           tile;
+//   warp 1  MMA issuer: the 2 x 42 MMAs of job j into the six TMEM
+//           accumulators, once both halves have landed and the epilogue has
+//           read job j - 1 out of tensor memory;
+//   warps 2-9  epilogue: two warps per TMEM lane quarter, 32 columns each;
+//           the accumulators go to registers as float-float values (which
+//           frees tensor memory for the next job's MMAs), the C tile (hi,
+//           lo), loaded by tensor copy after the previous job's store has
+//           read it, is updated in shared memory and stored back.
+// The D_q are exact integers whatever the order of their products, so the
+// factor equals the one-CTA-per-job kernel's bit for bit.  Every wait is
+// bounded as above.
+// --------------------------------------------------------------------------
+constexpr int kOz2Threads = 320;
+constexpr uint32_t kOz2HalfA = kTcM * (NB / 2) * 2;             // one K half of an A plane: 8 KB
+constexpr uint32_t kOz2HalfB = kTcN * (NB / 2) * 2;             // 4 KB
+constexpr uint32_t kOz2Stage = kOzQ * (kOz2HalfA + kOz2HalfB);  // 72 KB
+constexpr uint32_t kOz2Smem = 2 * kOz2Stage + 2 * kOzCTile + 1024;
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *tm, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(tm),
+               "r"(x), "r"(y)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const OzArgs args,
+                                                                         int njobs) {
+  extern __shared__ __align__(1024) unsigned char oz2_raw[];
+  __shared__ __align__(8) uint64_t full[2], empty[2], tfull, tempty, cfull;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail, s_epi_fail;
+  unsigned char *base = oz2_raw + ((1024 - (smem_u32(oz2_raw) & 1023)) & 1023);
+  float *c_hi = reinterpret_cast<float *>(base + 2 * kOz2Stage);   // [64 cols][128 rows]
+  float *c_lo = c_hi + kTcM * kTcN;
+  volatile int *vfail = &s_fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int myjobs = (int)blockIdx.x < njobs ? (njobs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
+                                             : 0;
+  const CUtensorMap *tmh0 = args.tmap, *tml0 = args.tmap + args.nblk;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(kOzCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_epi_fail = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&full[i]), 1);
+      mbar_init(smem_u32(&empty[i]), 1);
+    }
+    mbar_init(smem_u32(&tfull), 1);
+    mbar_init(smem_u32(&tempty), 8 * 32);
+    mbar_init(smem_u32(&cfull), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // ---- producer: unit (j, h) = K half h of job j into stage h -----------------
+    if (lane == 0) {
+      int issued = 0;   // units
+      Job jb{};
+      for (int u = 0; u < 2 * myjobs && !*vfail; ++u) {
+        const int j = u >> 1, h = u & 1;
+        if (!mbar_wait(smem_u32(&empty[h]), (j & 1) ^ 1)) {
+          atomicExch(&s_fail, 1);
+          break;
+        }
+        if (h == 0) {   // next job: its C tile towards L2 ahead of the epilogue's load
+          jb = decode_job(args.joff, args.nblk, args.k, args.blk,
+                          (int)blockIdx.x + j * (int)gridDim.x);
+          const CUtensorMap *th = tmh0 + jb.b, *tl = tml0 + jb.b;
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(th) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tl) : "memory");
+          tma_prefetch_2d(th, jb.I0 * NB, jb.J * NB);
+          tma_prefetch_2d(tl, jb.I0 * NB, jb.J * NB);
+        }
+        const BlkInfo bi = args.blk[jb.b];
+        const __half *st0 = args.dstage + (bi.soff + jb.I0) * (kOzQ * NB * NB) + h * (NB * NB / 2);
+        const __half *stJ = args.dstage + (bi.soff + jb.J) * (kOzQ * NB * NB) + h * (NB * NB / 2);
+        const uint32_t sa = smem_u32(base + h * kOz2Stage), sb = sa + kOzQ * kOz2HalfA;
+        const uint32_t bar = smem_u32(&full[h]);
+        const uint32_t q4 = NB * NB;   // halves of one 64-row K half = 4 KB
+        mbar_expect_tx(bar, (jb.has_i1 ? 3u : 2u) * kOzQ * q4);
+#pragma unroll
+        for (int q = 0; q < kOzQ; ++q) {
+          bulk_g2s(sa + q * kOz2HalfA, st0 + q * NB * NB, q4, bar);                 // rows 0..63
+          if (jb.has_i1)
+            bulk_g2s(sa + q * kOz2HalfA + q4, st0 + (kOzQ + q) * NB * NB, q4, bar);  // 64..127
+          bulk_g2s(sb + q * kOz2HalfB, stJ + q * NB * NB, q4, bar);
+        }
+        issued = u + 1;
+      }
+      if (*vfail)   // copies still in flight (the last two units) land before exit
+        for (int u = issued >= 2 ? issued - 2 : 0; u < issued; ++u)
+          mbar_wait(smem_u32(&full[u & 1]), (u >> 1) & 1);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ----------------------------------------------------------------
+    if (lane == 0) {
+      int last = -1;   // last unit whose MMAs were committed
+      for (int j = 0; j < myjobs && !*vfail; ++j) {
+        if (!mbar_wait(smem_u32(&tempty), (j & 1) ^ 1)) {
+          atomicExch(&s_fail, 2);
+          break;
+        }
+        bool ok = true;
+        for (int h = 0; h < 2; ++h) {
+          if (!mbar_wait(smem_u32(&full[h]), j & 1)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(base + h * kOz2Stage), sb = sa + kOzQ * kOz2HalfA;
+#pragma unroll
+          for (int q = 0; q < kOzQ; ++q)
+#pragma unroll
+            for (int sd = 0; sd <= q; ++sd)
+#pragma unroll
+              for (int ks = 0; ks < 2; ++ks)
+                mma_f16(tmem + q * kTcN, smem_desc(sa + sd * kOz2HalfA + ks * 256, 128, 512),
+                        smem_desc(sb + (q - sd) * kOz2HalfB + ks * 256, 128, 512),
+                        (h | sd | ks) != 0);
+          mma_commit(smem_u32(&empty[h]));   // stage h free once these MMAs complete
+          last = 2 * j + h;
+        }
+        if (!ok) {
+          atomicExch(&s_fail, 2);
+          break;
+        }
+        mma_commit(smem_u32(&tfull));   // all 84 products of job j complete
+      }
+      if (*vfail && last >= 0)   // MMAs in flight finish before tensor memory is freed
+        mbar_wait(smem_u32(&empty[last & 1]), (last >> 1) & 1);
+    }
+  } else {
+    // ---- epilogue ------------------------------------------------------------------
+    const int ew = warp - 2;
+    const int quarter = warp & 3;           // TMEM lanes 32 quarter .. + 31
+    const int cbase = (ew >> 2) * 32;       // this warp's 32 columns of the tile
+    const int r = quarter * 32 + lane;      // row of the 128-row tile
+    const bool leader = threadIdx.x == 64;  // warp 2, lane 0
+    int c_issued = -1;                      // last job whose C tile load was issued
+    auto load_c = [&](int j) {
+      const Job jn = decode_job(args.joff, args.nblk, args.k, args.blk,
+                                (int)blockIdx.x + j * (int)gridDim.x);
+      const CUtensorMap *th = tmh0 + jn.b, *tl = tml0 + jn.b;
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(th) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tl) : "memory");
+      // the whole box counts, rows past the matrix included (zero-filled)
+      mbar_expect_tx(smem_u32(&cfull), 2 * kOzCTile);
+      tma_load_2d(smem_u32(c_hi), th, jn.I0 * NB, jn.J * NB, smem_u32(&cfull));
+      tma_load_2d(smem_u32(c_lo), tl, jn.I0 * NB, jn.J * NB, smem_u32(&cfull));
+      c_issued = j;
+    };
+    if (leader && myjobs > 0) load_c(0);
+    for (int j = 0; j < myjobs; ++j) {
+      const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk,
+                                (int)blockIdx.x + j * (int)gridDim.x);
+      const BlkInfo bi = args.blk[jb.b];
+      const long long slot0 = bi.soff + jb.I0, slotJ = bi.soff + jb.J;
+      const int er = (r < NB || jb.has_i1) ? args.dexp[slot0 * NB + r] : 0;
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(smem_u32(&tfull), j & 1) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      // the six accumulators -> sum_q 2^(-8q) D_q as a float-float pair
+      float sh[32], sl[32];
+      if (ok) {
+        tc_fence_after();
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          float D[kOzQ][8];
+#pragma unroll
+          for (int q = 0; q < kOzQ; ++q)
+            tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) +
+                         (uint32_t)(q * kTcN + cbase + ch * 8),
+                     D[q]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            float h = D[0][u], l = 0.0f;
+#pragma unroll
+            for (int q = 1; q < kOzQ; ++q) {
+              float t = ldexpf(D[q][u], -8 * q);   // exact
+              two_sum(h, t);
+              l = __fadd_rn(l, t);
+            }
+            two_sum(h, l);
+            sh[ch * 8 + u] = h;
+            sl[ch * 8 + u] = l;
+          }
+        }
+        tc_fence_before();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty))
+                     : "memory");
+        if (lane == 0 && !mbar_wait(smem_u32(&cfull), j & 1)) s_epi_fail = 1;
+      } else if (lane == 0) {
+        s_epi_fail = 1;
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (s_epi_fail) {   // the same verdict in all eight warps
+        if (leader) atomicExch(&s_fail, 3);
+        break;
+      }
+      const int grow = jb.I0 * NB + r;
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        const int c = cbase + u, gcol = jb.J * NB + c;
+        // entries above the diagonal keep their value (the tile goes back
+        // whole); rows and columns past the matrix are clipped by the store
+        if (gcol > grow) continue;
+        const int sc = er + args.dexp[slotJ * NB + c] - 18;
+        const float ph = ldexpf(sh[u], sc), pl = ldexpf(sl[u], sc);
+        // (ch + cl) - (ph + pl): two-sum of the high parts, low parts added
+        const int e = c * kTcM + r;
+        const float chv = c_hi[e], clv = c_lo[e];
+        const float tt = __fsub_rn(chv, ph);
+        const float bv = __fsub_rn(tt, chv);
+        const float err = __fadd_rn(__fsub_rn(chv, __fsub_rn(tt, bv)), __fsub_rn(-ph, bv));
+        const float el = __fadd_rn(err, __fsub_rn(clv, pl));
+        const float hh = __fadd_rn(tt, el);
+        c_hi[e] = hh;
+        c_lo[e] = __fsub_rn(el, __fsub_rn(hh, tt));
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (leader) {
+        tma_store_2d(tmh0 + jb.b, jb.I0 * NB, jb.J * NB, smem_u32(c_hi));
+        tma_store_2d(tml0 + jb.b, jb.I0 * NB, jb.J * NB, smem_u32(c_lo));
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        // the next tile may overwrite shared memory once the store has read it
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        if (j + 1 < myjobs) load_c(j + 1);
+      }
+    }
+    if (leader) {
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+      if (*vfail && c_issued >= 0)   // a C tile load still in flight lands before exit
+        mbar_wait(smem_u32(&cfull), c_issued & 1);
+    }
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && *vfail) atomicExch(&args.status[4], 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kOzCols)
+                 : "memory");
+}
+
 // the number of update jobs of a block with t trailing tiles: row pairs R
 // cover tiles (2R, 2R+1) and the columns up to their last tile
 long long tc_jobs_of(int t) {
@@ -640,6 +1115,15 @@ bool tc_setup(ahlp_problem *p) {
   ck(cudaFuncSetAttribute(pchol_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)kSmemBytes),
      "tensor-core update shared memory");
+  ck(cudaFuncSetAttribute(pchol_update_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)kTc2Smem),
+     "tensor-core update shared memory");
+  {
+    int dev = 0, sms = 0;
+    ck(cudaGetDevice(&dev), "device");
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    p->num_sms = std::max(sms, 1);
+  }
   p->tc_ready = true;
   return true;
 }
@@ -650,7 +1134,12 @@ cudaError_t launch_update_tc(ahlp_problem *p, int k, cudaStream_t s) {
   TcArgs a{p->pstage, p->tc_joff + (size_t)k * (p->h_blk.size() + 1), p->blk,
            reinterpret_cast<const CUtensorMap *>(p->tc_tmap), (int)p->h_blk.size(), k,
            p->status};
-  count_launch(), pchol_update_tc_kernel<<<(unsigned)jobs, kTcThreads, kSmemBytes, s>>>(a);
+  if (p->fp32_update == 3) {   // persistent pipeline: one CTA per SM
+    const int grid = (int)std::min<long long>(jobs, p->num_sms);
+    count_launch(), pchol_update_tc2_kernel<<<grid, kTc2Threads, kTc2Smem, s>>>(a, (int)jobs);
+  } else {
+    count_launch(), pchol_update_tc_kernel<<<(unsigned)jobs, kTcThreads, kSmemBytes, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -690,6 +1179,15 @@ bool oz_setup(ahlp_problem *p) {
   ck(cudaFuncSetAttribute(pchol_update_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)kOzSmem),
      "float-float tensor-core update shared memory");
+  ck(cudaFuncSetAttribute(pchol_update_oz2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)kOz2Smem),
+     "float-float tensor-core update shared memory");
+  {
+    int dev = 0, sms = 0;
+    ck(cudaGetDevice(&dev), "device");
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    p->num_sms = std::max(sms, 1);
+  }
   p->oz_ready = true;
   return true;
 }
@@ -700,7 +1198,12 @@ cudaError_t launch_update_oz(ahlp_problem *p, int k, cudaStream_t s) {
   OzArgs a{p->dstage, p->dexp, p->tc_joff + (size_t)k * (p->h_blk.size() + 1), p->blk,
            reinterpret_cast<const CUtensorMap *>(p->oz_tmap), (int)p->h_blk.size(), k,
            p->status};
-  count_launch(), pchol_update_oz_kernel<<<(unsigned)jobs, kTcThreads, kOzSmem, s>>>(a);
+  if (p->ff_update == 3) {   // persistent pipeline: one CTA per SM
+    const int grid = (int)std::min<long long>(jobs, p->num_sms);
+    count_launch(), pchol_update_oz2_kernel<<<grid, kOz2Threads, kOz2Smem, s>>>(a, (int)jobs);
+  } else {
+    count_launch(), pchol_update_oz_kernel<<<(unsigned)jobs, kTcThreads, kOzSmem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -107,11 +107,82 @@ def test_tensor_core_ipm_reaches_oracle_optimum(P):
     prob.close()
 
 
+def test_persistent_update_matches_per_tile_update(P):
+    """The persistent pipelined kernel (one CTA per SM walking the step's
+    output tiles, two operand stages and two TMEM accumulators in flight)
+    issues the same products in the same order as the one-CTA-per-tile
+    kernel, and each output tile is reduced into C by exactly one job per
+    step, so the two factors agree bit for bit.  40 blocks of about nine
+    tiles give several hundred jobs per step: each CTA runs several, so both
+    stages and both accumulators are reused across mbarrier phases."""
+    from paper_2412_07731_gb300._lib import kkt_block_factor_dense
+    N = 40
+    rng = np.random.default_rng(5)
+    m = [int(v) for v in rng.integers(420, 560, N)]
+    n = [int(1.4 * v) for v in m]
+    lp = random_block_lp(11, N=N, m_sizes=m, n_sizes=n, nnz_per_col=5, n0=4, w_density=0.2,
+                         l=[4] * (N - 1), mg=2, global_nnz=4)
+    A, x, z, *_ = _point(lp, 6, 0.5)
+    probs = {u: P.arrowhead_lp_create(lp, _fp32(P, u)) for u in (1, 2, 3)}
+    for prob in probs.values():
+        P.kkt_factor(prob, x, z, 0.0, 0.0)
+    for i in range(N):
+        F2 = kkt_block_factor_dense(probs[2], i)
+        F3 = kkt_block_factor_dense(probs[3], i)
+        assert np.array_equal(F2, F3), i
+        Fc = kkt_block_factor_dense(probs[1], i)
+        assert np.abs(F3 - Fc).max() <= 2e-5 * np.abs(Fc).max(), i
+    S_ref = oschur.schur_reduced(lp, x, z)
+    S = P.kkt_schur_dense(probs[3])
+    assert np.abs(S - S_ref).max() <= 1e-4 * np.abs(S_ref).max()
+    for prob in probs.values():
+        prob.close()
+
+
+def test_persistent_update_ipm_reaches_oracle_optimum(P):
+    lp = random_block_lp(9, **SHAPES["ragged_multi"])
+    A, b, c = olp.assemble(lp)
+    ref = oipm.solve(A, b, c)
+    prob = P.arrowhead_lp_create(lp, P.default_options(precision=P.PREC_MIXED, fp32_update=3))
+    (x, y, z), r = P.ipm_solve(prob)
+    assert r["status"] == 0 and r["factors_fp32"] > 0
+    assert abs(r["pobj"] - ref["pobj"]) / (1 + abs(ref["pobj"])) <= 1e-8
+    prob.close()
+
+
 # ---------------------------------------------------------------------------
 # float-float factors: exact FP16 digit products on the tensor cores
 # ---------------------------------------------------------------------------
 def _ff(P, update, **kw):
     return P.default_options(precision=P.PREC_MIXED, fp32_cond_max=1.0, ff_update=update, **kw)
+
+
+def test_persistent_digit_update_matches_per_tile_update(P):
+    """The persistent digit-product kernel (two K-half operand stages, the
+    C tile reloaded after each store) sums the same exact integer products
+    D_q, only in another order, so its float-float factor equals the
+    one-CTA-per-tile kernel's bit for bit; several hundred jobs per step
+    give each CTA several jobs.  Both stay near the FP64 factor."""
+    from paper_2412_07731_gb300._lib import kkt_block_factor_dense
+    N = 40
+    rng = np.random.default_rng(6)
+    m = [int(v) for v in rng.integers(420, 560, N)]
+    n = [int(1.4 * v) for v in m]
+    lp = random_block_lp(12, N=N, m_sizes=m, n_sizes=n, nnz_per_col=5, n0=4, w_density=0.2,
+                         l=[4] * (N - 1), mg=2, global_nnz=4)
+    A, x, z, *_ = _point(lp, 7, 2.0)
+    probs = {u: P.arrowhead_lp_create(lp, _ff(P, u)) for u in (2, 3)}
+    p64 = P.arrowhead_lp_create(lp)
+    for prob in list(probs.values()) + [p64]:
+        P.kkt_factor(prob, x, z, 0.0, 0.0)
+    for i in range(N):
+        F2 = kkt_block_factor_dense(probs[2], i)
+        F3 = kkt_block_factor_dense(probs[3], i)
+        assert np.array_equal(F2, F3), i
+        F64 = kkt_block_factor_dense(p64, i)
+        assert np.abs(F3 - F64).max() <= 1e-8 * np.abs(F64).max(), i
+    for prob in list(probs.values()) + [p64]:
+        prob.close()
 
 
 @pytest.mark.parametrize("name", sorted(SHAPES))
@@ -183,8 +254,9 @@ def test_autotune_picks_a_kernel_and_solves(P):
     A, b, c = olp.assemble(lp)
     prob = P.arrowhead_lp_create(lp, P.default_options(precision=P.PREC_MIXED))
     t = P.autotune(prob)
-    assert all(t[k] > 0 for k in ("fp32_tensor_ms", "fp32_pipe_ms", "ff_tensor_ms", "ff_pipe_ms"))
-    assert t["fp32_update"] in (1, 2) and t["ff_update"] in (1, 2)
+    assert all(t[k] > 0 for k in ("fp32_tensor_ms", "fp32_pipe_ms", "ff_tensor_ms", "ff_pipe_ms",
+                                  "fp32_tensor_persistent_ms", "ff_tensor_persistent_ms"))
+    assert t["fp32_update"] in (1, 2, 3) and t["ff_update"] in (1, 2, 3)
     (x, y, z), r = P.ipm_solve(prob)
     ref = oipm.solve(A, b, c)
     assert r["status"] == 0
