@@ -559,12 +559,22 @@ def update_geometry(lp, NB=64):
     return elems, flops
 
 
-# DRAM bytes per algorithmic byte of the trailing-update kernels, from the ncu
-# captures of profiles/pchol_update_tc_c1small.md and
-# profiles/pchol_update_oz_c1small.md (uniform 8-block workload, whose trailing
-# matrices partly fit L2); the live bench scales them by the bytes of its own
-# launches to fill roofline.traffic
-UPDATE_TRAFFIC_PER_BYTE = {"FP32": 0.68, "float-float": 0.89}
+# DRAM bytes per algorithmic byte of the trailing-update kernels, keyed by
+# (precision, update option), from the ncu captures in profiles/ (uniform
+# 8-block workload, whose trailing matrices partly fit L2):
+# pchol_update_tc_c1small.md (per-tile TF32), pchol_update_tc2_c1small.md
+# (persistent TF32), pchol_update_oz_c1small.md (per-tile digits),
+# pchol_update_oz2_c1small.md (persistent digits).  The live bench scales them
+# by the bytes of its own launches to fill roofline.traffic; a kernel without
+# a capture of its current code reports null.
+UPDATE_TRAFFIC_PER_BYTE = {("FP32", 2): 0.68, ("FP32", 3): 0.70, ("float-float", 2): 0.89,
+                           ("float-float", 3): None}
+UPDATE_KERNEL = {("FP32", 1): "pchol_update_f32_kernel (FP32 pipe)",
+                 ("FP32", 2): "pchol_update_tc_kernel (tcgen05, one CTA per tile)",
+                 ("FP32", 3): "pchol_update_tc2_kernel (tcgen05, persistent)",
+                 ("float-float", 1): "pchol_update_ff8_kernel (double-float, FP32 pipe)",
+                 ("float-float", 2): "pchol_update_oz_kernel (tcgen05 digits, one CTA per tile)",
+                 ("float-float", 3): "pchol_update_oz2_kernel (tcgen05 digits, persistent)"}
 
 
 def kernel_roofline(P, prob, lp, x, z, prec_name, peaks):
@@ -596,7 +606,10 @@ def kernel_roofline(P, prob, lp, x, z, prec_name, peaks):
     med = lambda key: statistics.median([t[key] for t in times[1:]])  # noqa: E731
     upd_ms, launches = med("update_ms"), med("update_launches")
     elems, flops = update_geometry(lp)
-    out = {"kernel": f"trailing update of the {prec_name} block factor", "launches": launches,
+    variant = (saved.fp32_update if prec_name == "FP32" else saved.ff_update) or 2
+    out = {"kernel": f"trailing update of the {prec_name} block factor: "
+                     f"{UPDATE_KERNEL.get((prec_name, variant), 'FP64 pipe')}",
+           "launches": launches,
            "ms_per_factor": upd_ms, "diag_ms": med("diag_ms"), "panel_ms": med("panel_ms")}
     if prec_name == "FP64":
         ach = flops / (upd_ms / 1e3) / 1e12
@@ -608,7 +621,7 @@ def kernel_roofline(P, prob, lp, x, z, prec_name, peaks):
     word = 4 if prec_name == "FP32" else 8
     bytes_ = 2.0 * word * elems
     gbs = bytes_ / (upd_ms / 1e3) / 1e9
-    ratio = UPDATE_TRAFFIC_PER_BYTE.get(prec_name)
+    ratio = UPDATE_TRAFFIC_PER_BYTE.get((prec_name, variant))
     out.update({"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / peaks["hbm_gbs"],
                 "traffic": ratio * bytes_ / launches if ratio else None,

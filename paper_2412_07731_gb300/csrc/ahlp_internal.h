@@ -23,6 +23,11 @@ constexpr int kPrecFP32 = 1;
 constexpr int kPrecFF = 2;
 constexpr double kFp32PivotTol = 1e-6;    // smallest clamp threshold for FP32 pivots
 constexpr double kFFPivotTol = 1e-12;     // smallest clamp threshold for float-float pivots
+// pivot_mode 1: a failing pivot becomes scale * max(its starting diagonal, 1),
+// capped so that its square root and reciprocal stay normal in the factor's
+// storage words
+constexpr double kDropFP64 = 1e32, kDropFF = 1e16, kDropFP32 = 1e16;
+constexpr double kDropCapFF = 1e60, kDropCapFP32 = 1e30;
 constexpr long long kSmemVecBytes = 160 * 1024;   // dynamic smem of the border solves
 constexpr int kThreads = 256;     // threads per CTA of the dense kernels
 
@@ -59,22 +64,28 @@ constexpr int kTagBorderG = 2 << 20;   // pivot reports of the border y_g factor
 #ifdef __CUDACC__
 // Pivot safeguard shared by every Cholesky in the library.  A pivot that is
 // not above tol * (the diagonal entry it started from) has lost all its
-// significant digits to cancellation; it is clamped to that threshold, which
+// significant digits to cancellation.  It is clamped to that threshold, which
 // keeps the factor nonsingular (the Krylov refinement of kkt_solve then
-// corrects the solve against the exact Newton matrix).  NaN pivots are
-// counted in status[0] with the first location, clamped pivots in status[1].
+// corrects the solve against the exact Newton matrix); or, with drop > 0, it
+// becomes drop * max(orig, 1) (at most cap), which leaves the row out of the
+// factor: its column below the pivot and its solution entry come out ~0, the
+// treatment of nearly dependent rows of A D A' in interior-point codes.  NaN
+// pivots are counted in status[0] with the first location, failing pivots in
+// status[1].
 __device__ __forceinline__ void pivot_fix(double &piv, double orig, double tol, int *status,
-                                          int where, int row) {
+                                          int where, int row, double drop = 0.0,
+                                          double cap = 1e300) {
   const double floor_v = tol * orig > 0.0 ? tol * orig : 1.0;
+  const double repl = drop > 0.0 ? fmin(drop * fmax(orig, 1.0), cap) : floor_v;
   if (!(piv == piv)) {
     if (atomicAdd(&status[0], 1) == 0) {
       status[2] = where;
       status[3] = row;
     }
-    piv = floor_v;
+    piv = repl;
   } else if (!(piv > tol * orig) || !(piv > 0.0)) {
     atomicAdd(&status[1], 1);
-    piv = floor_v;
+    piv = repl;
   }
 }
 #endif
@@ -292,6 +303,7 @@ struct ahlp_problem {
 
   // ---- vectors ------------------------------------------------------------
   double *x = nullptr, *z = nullptr, *dscale = nullptr;   // current point, d = x/z
+  double *xinv = nullptr, *wfin = nullptr;   // 1 / x, 1 / (1 / d + rho on x_0)
   double *vec = nullptr;      // block solve segments [sum a_i]
   float *vec32 = nullptr;     // FP32 copy of the forward solution (FP32 factors)
   double *svec = nullptr;     // Schur vector [nS]
@@ -351,7 +363,7 @@ cudaError_t launch_form(ahlp_problem *p, double delta);
 // (kt_mark); classes 0 diagonal tiles, 1 panels, 2 trailing updates
 cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
                          const double *diag0, double tol, int *status, cudaStream_t s,
-                         ahlp_problem *prof = nullptr);
+                         ahlp_problem *prof = nullptr, double drop = 0.0);
 // float-float (hi = aug32, lo): diagonal tiles and panels in FP64 arithmetic,
 // trailing updates in double-float; then hi + lo is expanded into out (the
 // FP64 factor buffer, elems entries), which the Schur assembly and the solves use
@@ -360,14 +372,15 @@ cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<Blk
 cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
                             const BlkInfo *info, const std::vector<BlkInfo> &h,
                             const double *diag0, double tol, int *status, cudaStream_t s,
-                            ahlp_problem *oz = nullptr, ahlp_problem *prof = nullptr);
+                            ahlp_problem *oz = nullptr, ahlp_problem *prof = nullptr,
+                            double drop = 0.0);
 // FP32: also writes the inverted diagonal tiles into tinv (see launch_tinv);
 // with tc (a handle set up by tc_setup) the trailing updates run on the
 // tensor cores (k_tc.cu), else on the FP32 pipe
 cudaError_t launch_pchol_f32(float *buf, float *tinv, const BlkInfo *info,
                              const std::vector<BlkInfo> &h, const double *diag0, double tol,
                              int *status, cudaStream_t s, ahlp_problem *tc = nullptr,
-                             ahlp_problem *prof = nullptr);
+                             ahlp_problem *prof = nullptr, double drop = 0.0);
 // forward / backward solves with one partial factor per CTA (the border
 // factors; vectors FP64, held in shared memory)
 cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,

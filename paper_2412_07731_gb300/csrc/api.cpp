@@ -334,6 +334,7 @@ void ahlp_default_options(ahlp_options *o) {
   o->profile_kernels = 0;
   o->iter_cb = nullptr;
   o->iter_cb_ctx = nullptr;
+  o->pivot_mode = 0;
 }
 
 const char *ahlp_status_string(int s) {
@@ -394,7 +395,8 @@ static int check_options(const ahlp_options &o, std::string &err) {
       !(o.ipm_refine_tol >= 0 && o.ipm_refine_tol < 1) ||
       (o.correctors_by_cost != 0 && o.correctors_by_cost != 1) || o.fp32_update < 0 ||
       o.fp32_update > 3 || o.ff_update < 0 || o.ff_update > 3 || o.schur_chain < 0 ||
-      o.schur_chain > 1 || o.profile_kernels < 0 || o.profile_kernels > 1) {
+      o.schur_chain > 1 || o.profile_kernels < 0 || o.profile_kernels > 1 ||
+      o.pivot_mode < 0 || o.pivot_mode > 1) {
     err = "invalid option value";
     return AHLP_ERR_INVALID_ARG;
   }
@@ -1263,6 +1265,8 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->x = dalloc<double>(p, p->n);
     p->z = dalloc<double>(p, p->n);
     p->dscale = dalloc<double>(p, p->n);
+    p->xinv = dalloc<double>(p, p->n);
+    p->wfin = dalloc<double>(p, p->n);
     p->vec = dalloc<double>(p, p->vec_elems);
     p->svec = dalloc<double>(p, p->nS);
     p->f = dalloc<double>(p, p->n);
@@ -1444,6 +1448,7 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol, boo
   ck(launch_form(p, delta), "form");
   ck(cudaEventRecord(p->ev[1], s), "event");
   ahlp_problem *prof = p->opt.profile_kernels ? p : nullptr;
+  const bool drop = p->opt.pivot_mode == 1;
   p->kt_cls.clear();
   if (p->fac_prec == kPrecFP32) {
     // trailing updates on the tensor cores unless the FP32 pipe is asked for
@@ -1458,18 +1463,19 @@ int factor_impl(ahlp_problem *p, double delta, double rho, double pivot_tol, boo
     }
     p->fp32_update = tc ? (p->opt.fp32_update == 3 ? 3 : 2) : 1;
     ck(launch_pchol_f32(p->aug32, p->tinv32, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol,
-                        p->status, s, tc, prof),
+                        p->status, s, tc, prof, drop ? kDropFP32 : 0.0),
        "pchol");
   }
   else if (p->fac_prec == kPrecFF) {
     ahlp_problem *oz = (p->opt.ff_update != 1 && oz_setup(p)) ? p : nullptr;
     p->ff_update = oz ? (p->opt.ff_update == 3 ? 3 : 2) : 1;
     ck(launch_pchol_ff(p->aug32, p->aug_lo, p->aug, p->aug_elems, p->blk, p->h_blk, p->diag0,
-                       p->fac_pivot_tol, p->status, s, oz, prof),
+                       p->fac_pivot_tol, p->status, s, oz, prof, drop ? kDropFF : 0.0),
        "pchol");
   }
   else
-    ck(launch_pchol(p->aug, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s, prof),
+    ck(launch_pchol(p->aug, p->blk, p->h_blk, p->diag0, p->fac_pivot_tol, p->status, s, prof,
+                    drop ? kDropFP64 : 0.0),
        "pchol");
   ck(launch_tinv(p), "diagonal tile inverses");
   ck(cudaEventRecord(p->ev[2], s), "event");

@@ -89,11 +89,19 @@ __global__ void __launch_bounds__(kThreads) form_aug_kernel(FormArgs<T> A) {
 
 // d = x / z; on the block variables x / (z + rho_x x) with the factor's primal
 // regularisation, i.e. D^-1 + rho_x (caps d at 1 / rho_x).  The linking
-// variables get theirs in the Schur border (-D_0^-1 - rho).
-__global__ void dscale_kernel(const double *x, const double *z, double *d, long long n,
-                              double rho_x, const unsigned char *is_x0) {
+// variables get theirs in the Schur border (-D_0^-1 - rho).  With them, the
+// two per-variable quotients every solve at this point needs (FP64 division
+// is a long instruction sequence on this part): xinv = 1 / x and
+// w = 1 / (1 / d + rho on the linking variables).
+__global__ void dscale_kernel(const double *x, const double *z, double *d, double *xinv,
+                              double *w, long long n, double rho_x, double rho,
+                              const unsigned char *is_x0) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) d[i] = (rho_x > 0.0 && !is_x0[i]) ? x[i] / (z[i] + rho_x * x[i]) : x[i] / z[i];
+  if (i >= n) return;
+  const double di = (rho_x > 0.0 && !is_x0[i]) ? x[i] / (z[i] + rho_x * x[i]) : x[i] / z[i];
+  d[i] = di;
+  xinv[i] = 1.0 / x[i];
+  w[i] = 1.0 / (1.0 / di + (is_x0[i] ? rho : 0.0));
 }
 
 // --------------------------------------------------------------------------
@@ -102,7 +110,7 @@ __global__ void dscale_kernel(const double *x, const double *z, double *d, long 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pchol_potrf_kernel(T *buf, const BlkInfo *blk, int k,
                                                                const double *diag0, double tol,
-                                                               int *status) {
+                                                               int *status, double drop) {
   const BlkInfo bi = blk[blockIdx.x];
   if (k >= bi.Tp) return;
   __shared__ T t[NB][NB + 1];
@@ -119,7 +127,8 @@ __global__ void __launch_bounds__(kThreads) pchol_potrf_kernel(T *buf, const Blk
   for (int c = 0; c < npiv; ++c) {
     if (threadIdx.x == 0) {
       double piv = (double)t[c][c];
-      pivot_fix(piv, diag0[bi.d0off + r0 + c], tol, status, bi.tag + (int)blockIdx.x, r0 + c);
+      pivot_fix(piv, diag0[bi.d0off + r0 + c], tol, status, bi.tag + (int)blockIdx.x, r0 + c,
+                drop, sizeof(T) == 4 ? kDropCapFP32 : 1e300);
       const T l = (T)sqrt(piv);
       t[c][c] = l;
       s_inv = T(1) / l;
@@ -205,7 +214,7 @@ constexpr int kPW = 16;   // panel width
 
 __global__ void __launch_bounds__(kPotrf32Threads) pchol_potrf_f32_kernel(
     float *buf, float *tinv, const BlkInfo *blk, int k, const double *diag0, float tol,
-    int *status) {
+    int *status, float drop) {
   const BlkInfo bi = blk[blockIdx.x];
   if (k >= bi.Tp) return;
   __shared__ float t[NB][NB + 1];
@@ -242,17 +251,21 @@ __global__ void __launch_bounds__(kPotrf32Threads) pchol_potrf_f32_kernel(
           const float va = ra[u], vb = rb[u];
           const bool hi = c >= 32;
           float piv = __shfl_sync(0xffffffffu, hi ? vb : va, c & 31);
-          const float lim = tol * __shfl_sync(0xffffffffu, hi ? dref_b : dref_a, c & 31);
-          const float floor_v = lim > 0.0f ? lim : 1.0f;
+          const float dref = __shfl_sync(0xffffffffu, hi ? dref_b : dref_a, c & 31);
+          const float lim = tol * dref;
+          // the same safeguard as pivot_fix, in FP32
+          const float repl = drop > 0.0f ? fminf(drop * fmaxf(dref, 1.0f), (float)kDropCapFP32)
+                             : lim > 0.0f ? lim
+                                          : 1.0f;
           if (!(piv == piv)) {
             if (lane == 0 && atomicAdd(&status[0], 1) == 0) {
               status[2] = bi.tag + (int)blockIdx.x;
               status[3] = r0 + c;
             }
-            piv = floor_v;
+            piv = repl;
           } else if (!(piv > lim) || !(piv > 0.0f)) {
             if (lane == 0) atomicAdd(&status[1], 1);
-            piv = floor_v;
+            piv = repl;
           }
           const float lcc = sqrtf(piv), inv = 1.0f / lcc;
           const float la = lane == c ? lcc : va * inv;
@@ -502,7 +515,7 @@ __global__ void ff_expand_kernel(const float *__restrict__ hi, const float *__re
 __global__ void __launch_bounds__(kThreads) pchol_potrf_ff_kernel(float *hi, float *lo,
                                                                   const BlkInfo *blk, int k,
                                                                   const double *diag0, double tol,
-                                                                  int *status) {
+                                                                  int *status, double drop) {
   const BlkInfo bi = blk[blockIdx.x];
   if (k >= bi.Tp) return;
   __shared__ double t[NB][NB + 1];
@@ -519,7 +532,8 @@ __global__ void __launch_bounds__(kThreads) pchol_potrf_ff_kernel(float *hi, flo
   for (int c = 0; c < npiv; ++c) {
     if (threadIdx.x == 0) {
       double piv = t[c][c];
-      pivot_fix(piv, diag0[bi.d0off + r0 + c], tol, status, bi.tag + (int)blockIdx.x, r0 + c);
+      pivot_fix(piv, diag0[bi.d0off + r0 + c], tol, status, bi.tag + (int)blockIdx.x, r0 + c,
+                drop, kDropCapFF);
       const double l = sqrt(piv);
       t[c][c] = l;
       s_inv = 1.0 / l;
@@ -1206,7 +1220,6 @@ __global__ void __launch_bounds__(kSolveThreads) ptri_bwd_kernel(const T *__rest
 // forward : v <- [L11 0; L21 I]^-1 v     (all a rows; pivot tiles publish)
 // backward: v_top <- L11^-T (v_top - L21' v_bottom), v_bottom unchanged
 // --------------------------------------------------------------------------
-constexpr int kTrsvThreads = 512;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -1286,11 +1299,6 @@ __global__ void __launch_bounds__(NB) tinv_kernel(const T *__restrict__ buf, T *
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void stage_tile(const T *__restrict__ src, T *dst) {
-  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) dst[i] = src[i];
-}
-
 // Called by all threads when the next needed tile k may not be published.
 // Warp 0 scans up to 32 flags fl[k + dir*i] in one round (tiles publish in
 // order, so the set flags form a run starting at k), waits (bounded) when
@@ -1318,19 +1326,68 @@ __device__ __forceinline__ int published_run(const int *fl, int k, int dir, int 
 }
 
 // thread = (row rho of a 64-row tile or chunk, column lane q); lane q owns the
-// columns q, q + kQL, ... of a 64-column tile.  The next tile's factor entries
-// are loaded into registers while the current one is used, so every CTA keeps
-// two tiles of the factor in flight.
-constexpr int kQL = kTrsvThreads / NB;   // column lanes
-constexpr int kJC = NB / kQL;            // columns per thread
+// columns q, q + kQL, ... of a 64-column tile.  The factor tiles a CTA reads
+// are streamed into a ring of shared-memory stages by cp.async (16 bytes per
+// copy, rows past the matrix zero-filled), kTrsvStages - 1 tiles ahead of
+// the one in use, so each SM keeps several tiles of the factor in flight
+// without holding them in registers; the inverse of the diagonal tile comes
+// in with the first stage.
+
+// FP64 factors go through the ring (two 32 KB stages, 512 threads, two CTAs
+// per SM); FP32 factors hold the next tile in registers instead, which
+// measured faster for their 16 KB tiles than a ring with a barrier per tile:
+// the forward sweep with 256 threads (sixteen entries each, three CTAs per
+// SM), the backward one, which also keeps sixteen accumulators per thread at
+// that width, with 512 threads (eight entries each, two CTAs per SM).
+template <typename T, bool Bwd>
+struct TrsvCfg {
+  static constexpr bool narrow = sizeof(T) == 4 && !Bwd;
+  static constexpr int threads = narrow ? 256 : 512;
+  static constexpr int min_ctas = narrow ? 3 : 2;   // per SM
+  static constexpr int stages = sizeof(T) == 4 ? 0 : 2;
+  static constexpr int ql = threads / NB;   // column lanes
+  static constexpr int jc = NB / ql;        // columns per thread
+};
+template <typename T>
+constexpr size_t trsv_smem() {
+  return (size_t)TrsvCfg<T, false>::stages * NB * NB * sizeof(T);
+}
+
+// One 64 x 64 tile of a column-major factor into dst ([c][row], 64 entries per
+// column): columns [0, ncols) of the tile starting at src, rows below
+// `rows` are zero, so are the other columns.  Every copy reads only entries
+// of the matrix.
+template <typename T>
+__device__ __forceinline__ void stage_factor_tile(T *dst, const T *src, long long lda, int ncols,
+                                                  int rows) {
+  constexpr int EPC = 16 / sizeof(T);   // entries per 16-byte copy
+  constexpr int CPC = NB / EPC;         // copies per column
+  for (int ch = threadIdx.x; ch < NB * CPC; ch += blockDim.x) {
+    const int c = ch / CPC, rr = (ch % CPC) * EPC;
+    const int valid = c < ncols ? max(0, min(EPC, rows - rr)) : 0;
+    const T *g = valid ? src + (long long)c * lda + rr : src;
+    cp_async16(dst + c * NB + rr, g, valid * (int)sizeof(T));
+  }
+}
+
+// n contiguous entries (a multiple of 16 bytes)
+template <typename T>
+__device__ __forceinline__ void stage_contiguous(T *dst, const T *src, int n) {
+  constexpr int EPC = 16 / sizeof(T);
+  for (int i = threadIdx.x * EPC; i < n; i += blockDim.x * EPC) cp_async16(dst + i, src + i, 16);
+}
 
 template <typename T>
-__global__ void __launch_bounds__(kTrsvThreads, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(TrsvCfg<T, false>::threads, TrsvCfg<T, false>::min_ctas)
     trsv_fwd_kernel(const T *__restrict__ buf, const T *__restrict__ tinv,
                     const BlkInfo *__restrict__ blk, const int *__restrict__ sched,
                     const int *__restrict__ flag_off, int *flags, int *ticket, int *err,
                     double *vec, T *vecT) {
-  __shared__ T Xs[NB * NB];   // column-major, Xs[c * NB + r]
+  constexpr int S = TrsvCfg<T, false>::stages;
+  constexpr int kQL = TrsvCfg<T, false>::ql, kJC = TrsvCfg<T, false>::jc;
+  extern __shared__ __align__(16) unsigned char trsv_raw[];
+  T *ring = reinterpret_cast<T *>(trsv_raw);   // S tiles, [c][row]
+  __shared__ __align__(16) T Xs[NB * NB];      // column-major, Xs[c * NB + r]
   __shared__ T red[kQL][NB];
   __shared__ T u[NB];
   __shared__ T xs[NB];
@@ -1347,41 +1404,77 @@ __global__ void __launch_bounds__(kTrsvThreads, sizeof(T) == 4 ? 2 : 1)
   const int r0 = r * NB, nr = min(NB, bi.a - r0);
   const bool pivtile = r < bi.Tp;
   const int npiv = pivtile ? min(NB, bi.p - r0) : 0;
-  if (pivtile) stage_tile(tinv + bi.ioff + (long long)r * NB * NB, Xs);
   const int rho = threadIdx.x & (NB - 1), q = threadIdx.x / NB;
-  const bool rok = rho < nr;
-  const T *__restrict__ Lr = L + r0 + rho;
   const int nct = min(r, bi.Tp);   // pivot column tiles left of this tile
-  T l[kJC], ln[kJC];
-  auto load_tile = [&](int k, T(&dst)[kJC]) {
-    const int c0 = k * NB, nc = min(NB, bi.p - c0);
-#pragma unroll
-    for (int j = 0; j < kJC; ++j) {
-      const int c = q + kQL * j;
-      dst[j] = (rok && c < nc) ? Lr[(long long)(c0 + c) * lda] : T(0);
-    }
-  };
-  if (nct > 0) load_tile(0, l);
+  if (pivtile) stage_contiguous(Xs, tinv + bi.ioff + (long long)r * NB * NB, NB * NB);
+  cp_async_commit();
   T acc0 = T(0), acc1 = T(0);
   int ready = 0;   // column tiles [0, ready) are published
-  for (int k = 0; k < nct; ++k) {
-    const int c0 = k * NB, nc = min(NB, bi.p - c0);
-    if (k + 1 < nct) load_tile(k + 1, ln);
-    if (k >= ready) ready = k + published_run(fl, k, 1, nct, err);
+  if constexpr (S > 0) {
+    auto issue = [&](int k) {
+      const int c0 = k * NB;
+      stage_factor_tile(ring + (k % S) * NB * NB, L + (long long)c0 * lda + r0, lda,
+                        min(NB, bi.p - c0), nr);
+    };
 #pragma unroll
-    for (int j = 0; j < kJC; ++j) {
-      const int c = q + kQL * j;
-      if (c < nc) {
-        const T xv = __ldcg(gvT + c0 + c);
-        if (j & 1)
-          acc1 = fma(l[j], xv, acc1);
-        else
-          acc0 = fma(l[j], xv, acc0);
+    for (int s = 0; s < S - 1; ++s) {
+      if (s < nct) issue(s);
+      cp_async_commit();
+    }
+    for (int k = 0; k < nct; ++k) {
+      const int c0 = k * NB, nc = min(NB, bi.p - c0);
+      cp_async_wait<S - 2>();   // tile k has landed (this thread's copies) ...
+      __syncthreads();          // ... everyone's, and stage (k - 1) % S is free
+      if (k + S - 1 < nct) issue(k + S - 1);
+      cp_async_commit();
+      if (k >= ready) ready = k + published_run(fl, k, 1, nct, err);
+      const T *t = ring + (k % S) * NB * NB;
+#pragma unroll
+      for (int j = 0; j < kJC; ++j) {
+        const int c = q + kQL * j;
+        if (c < nc) {
+          const T xv = __ldcg(gvT + c0 + c);
+          if (j & 1)
+            acc1 = fma(t[c * NB + rho], xv, acc1);
+          else
+            acc0 = fma(t[c * NB + rho], xv, acc0);
+        }
       }
     }
+  } else {
+    // the next tile's entries are loaded into registers while this one is used
+    const bool rok = rho < nr;
+    const T *__restrict__ Lr = L + r0 + rho;
+    T l[kJC], ln[kJC];
+    auto load_tile = [&](int k, T(&dst)[kJC]) {
+      const int c0 = k * NB, nc = min(NB, bi.p - c0);
 #pragma unroll
-    for (int j = 0; j < kJC; ++j) l[j] = ln[j];
+      for (int j = 0; j < kJC; ++j) {
+        const int c = q + kQL * j;
+        dst[j] = (rok && c < nc) ? Lr[(long long)(c0 + c) * lda] : T(0);
+      }
+    };
+    if (nct > 0) load_tile(0, l);
+    for (int k = 0; k < nct; ++k) {
+      const int c0 = k * NB, nc = min(NB, bi.p - c0);
+      if (k + 1 < nct) load_tile(k + 1, ln);
+      if (k >= ready) ready = k + published_run(fl, k, 1, nct, err);
+#pragma unroll
+      for (int j = 0; j < kJC; ++j) {
+        const int c = q + kQL * j;
+        if (c < nc) {
+          const T xv = __ldcg(gvT + c0 + c);
+          if (j & 1)
+            acc1 = fma(l[j], xv, acc1);
+          else
+            acc0 = fma(l[j], xv, acc0);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kJC; ++j) l[j] = ln[j];
+    }
   }
+  cp_async_wait<0>();
   auto sum_lanes = [&](int t) {
     T s = T(0);
 #pragma unroll
@@ -1409,7 +1502,7 @@ __global__ void __launch_bounds__(kTrsvThreads, sizeof(T) == 4 ? 2 : 1)
     if (npiv < nr) {
       // non-pivot rows of the last pivot tile: u -= L(rows, pivots) x
       T s2 = T(0);
-      if (rho >= npiv && rok) {
+      if (rho >= npiv && rho < nr) {
 #pragma unroll
         for (int j = 0; j < kJC; ++j) {
           const int c = q + kQL * j;
@@ -1437,13 +1530,17 @@ __global__ void __launch_bounds__(kTrsvThreads, sizeof(T) == 4 ? 2 : 1)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTrsvThreads, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(TrsvCfg<T, true>::threads, TrsvCfg<T, true>::min_ctas)
     trsv_bwd_kernel(const T *__restrict__ buf, const T *__restrict__ tinv,
                     const BlkInfo *__restrict__ blk, const int *__restrict__ sched,
                     const int *__restrict__ flag_off, int *flags, int *ticket, int *err,
                     double *vec) {
-  __shared__ T Xs[NB * NB];   // column-major, Xs[c * NB + r]
-  __shared__ T red[kTrsvThreads / 32][kJC];
+  constexpr int S = TrsvCfg<T, true>::stages;
+  constexpr int kQL = TrsvCfg<T, true>::ql, kJC = TrsvCfg<T, true>::jc;
+  extern __shared__ __align__(16) unsigned char trsv_raw[];
+  T *ring = reinterpret_cast<T *>(trsv_raw);   // S chunks of 64 rows, [c][row]
+  __shared__ __align__(16) T Xs[NB * NB];      // column-major, Xs[c * NB + r]
+  __shared__ T red[TrsvCfg<T, true>::threads / 32][kJC];
   __shared__ T u[NB];
   __shared__ int s_job;
   if (threadIdx.x == 0) s_job = atomicAdd(ticket, 1);
@@ -1455,7 +1552,6 @@ __global__ void __launch_bounds__(kTrsvThreads, sizeof(T) == 4 ? 2 : 1)
   double *gv = vec + bi.voff;
   int *fl = flags + flag_off[b];
   const int r0 = r * NB, nr = min(NB, bi.a - r0), npiv = min(NB, bi.p - r0);
-  stage_tile(tinv + bi.ioff + (long long)r * NB * NB, Xs);
   // lane q dots the tile's columns q, q + kQL, ... with the rows of each chunk
   const int rho = threadIdx.x & (NB - 1), q = threadIdx.x / NB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1464,32 +1560,70 @@ __global__ void __launch_bounds__(kTrsvThreads, sizeof(T) == 4 ? 2 : 1)
   // pivot tiles publish upwards.  Chunk r itself holds the non-pivot rows of
   // the last pivot tile (if any).
   const int kend = npiv < nr ? r : r + 1;
-  T l[kJC], ln[kJC], acc[kJC];
-  auto load_chunk = [&](int k, T(&dst)[kJC]) {
-    const int row = k * NB + rho;
-    const bool ok = row < bi.a && (k > r || rho >= npiv);
-#pragma unroll
-    for (int j = 0; j < kJC; ++j) {
-      const int c = q + kQL * j;
-      dst[j] = (ok && c < npiv) ? Lc[(long long)c * lda + row] : T(0);
-    }
-  };
+  const int nch = bi.T - kend;   // chunks, taken k = T - 1, T - 2, ..., kend
+  stage_contiguous(Xs, tinv + bi.ioff + (long long)r * NB * NB, NB * NB);
+  cp_async_commit();
+  T acc[kJC];
 #pragma unroll
   for (int j = 0; j < kJC; ++j) acc[j] = T(0);
-  if (bi.T - 1 >= kend) load_chunk(bi.T - 1, l);
   int ready_from = bi.Tp;   // chunks k >= ready_from are final
-  for (int k = bi.T - 1; k >= kend; --k) {
-    if (k - 1 >= kend) load_chunk(k - 1, ln);
-    // tiles publish in decreasing order
-    if (k > r && k < ready_from) ready_from = k + 1 - published_run(fl, k, -1, r, err);
-    const int row = k * NB + rho;
-    const bool ok = row < bi.a && (k > r || rho >= npiv);
-    const T xv = ok ? (T)__ldcg(gv + row) : T(0);
+  if constexpr (S > 0) {
+    auto issue = [&](int i) {      // i-th chunk taken: k = T - 1 - i
+      const int k = bi.T - 1 - i;
+      stage_factor_tile(ring + (i % S) * NB * NB, Lc + (long long)k * NB, lda, npiv,
+                        bi.a - k * NB);
+    };
 #pragma unroll
-    for (int j = 0; j < kJC; ++j) acc[j] = fma(l[j], xv, acc[j]);
+    for (int s = 0; s < S - 1; ++s) {
+      if (s < nch) issue(s);
+      cp_async_commit();
+    }
+    for (int i = 0; i < nch; ++i) {
+      const int k = bi.T - 1 - i;
+      cp_async_wait<S - 2>();
+      __syncthreads();
+      if (i + S - 1 < nch) issue(i + S - 1);
+      cp_async_commit();
+      // tiles publish in decreasing order
+      if (k > r && k < ready_from) ready_from = k + 1 - published_run(fl, k, -1, r, err);
+      const int row = k * NB + rho;
+      // rows past the matrix are zero in the stage; the pivot rows of chunk r
+      // (entries of L_rr) take no part
+      if (row < bi.a && (k > r || rho >= npiv)) {
+        const T xv = (T)__ldcg(gv + row);
+        const T *t = ring + (i % S) * NB * NB;
 #pragma unroll
-    for (int j = 0; j < kJC; ++j) l[j] = ln[j];
+        for (int j = 0; j < kJC; ++j) acc[j] = fma(t[(q + kQL * j) * NB + rho], xv, acc[j]);
+      }
+    }
+  } else {
+    // the next chunk's entries are loaded into registers while this one is used
+    T l[kJC], ln[kJC];
+    auto load_chunk = [&](int k, T(&dst)[kJC]) {
+      const int row = k * NB + rho;
+      const bool ok = row < bi.a && (k > r || rho >= npiv);
+#pragma unroll
+      for (int j = 0; j < kJC; ++j) {
+        const int c = q + kQL * j;
+        dst[j] = (ok && c < npiv) ? Lc[(long long)c * lda + row] : T(0);
+      }
+    };
+    if (nch > 0) load_chunk(bi.T - 1, l);
+    for (int k = bi.T - 1; k >= kend; --k) {
+      if (k - 1 >= kend) load_chunk(k - 1, ln);
+      // tiles publish in decreasing order
+      if (k > r && k < ready_from) ready_from = k + 1 - published_run(fl, k, -1, r, err);
+      const int row = k * NB + rho;
+      const bool ok = row < bi.a && (k > r || rho >= npiv);
+      const T xv = ok ? (T)__ldcg(gv + row) : T(0);
+#pragma unroll
+      for (int j = 0; j < kJC; ++j) acc[j] = fma(l[j], xv, acc[j]);
+#pragma unroll
+      for (int j = 0; j < kJC; ++j) l[j] = ln[j];
+    }
   }
+  cp_async_wait<0>();
+  __syncthreads();
   // column c = q + kQL j is summed over the two warps of lane q
   auto col_sum = [&](int c) {
     const int cq = c % kQL, cj = c / kQL;
@@ -1536,7 +1670,8 @@ constexpr size_t tinv_smem() {
 template <typename T>
 cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkInfo> &h,
                     const double *diag0, double tol, int *status, cudaStream_t s,
-                    ahlp_problem *tc = nullptr, ahlp_problem *prof = nullptr) {
+                    ahlp_problem *tc = nullptr, ahlp_problem *prof = nullptr,
+                    double drop = 0.0) {
   int nblk = (int)h.size();
   if (nblk == 0) return cudaSuccess;
   int maxTp = 0;
@@ -1551,8 +1686,8 @@ cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkI
     }
     if constexpr (sizeof(T) == sizeof(float)) {
       if (prof) kt_mark(prof, 0, s);
-      count_launch(), pchol_potrf_f32_kernel<<<nblk, kPotrf32Threads, 0, s>>>(buf, tinv, info, k, diag0,
-                                                                 (float)tol, status);
+      count_launch(), pchol_potrf_f32_kernel<<<nblk, kPotrf32Threads, 0, s>>>(
+                          buf, tinv, info, k, diag0, (float)tol, status, (float)drop);
       if (prof) kt_mark(prof, 1, s);
       if (maxPanel > 0)
         count_launch(), pchol_trsm_inv_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads,
@@ -1561,7 +1696,7 @@ cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkI
     } else {
       if (prof) kt_mark(prof, 0, s);
       count_launch(), pchol_potrf_kernel<T><<<nblk, kThreads, 0, s>>>(buf, info, k, diag0, tol,
-                                                                      status);
+                                                                      status, drop);
       if (prof) kt_mark(prof, 1, s);
       if (maxPanel > 0)
         count_launch(), pchol_trsm_kernel<T><<<dim3((unsigned)maxPanel, nblk), kThreads,
@@ -1594,7 +1729,7 @@ cudaError_t pchol_t(T *buf, T *tinv, const BlkInfo *info, const std::vector<BlkI
 cudaError_t launch_dscale(ahlp_problem *p) {
   if (p->n <= 0) return cudaSuccess;
   count_launch(), dscale_kernel<<<(unsigned)((p->n + 255) / 256), 256, 0, p->stream>>>(
-      p->x, p->z, p->dscale, p->n, p->fac_rho_x, p->is_x0);
+      p->x, p->z, p->dscale, p->xinv, p->wfin, p->n, p->fac_rho_x, p->fac_rho, p->is_x0);
   return cudaGetLastError();
 }
 
@@ -1619,7 +1754,7 @@ cudaError_t launch_form(ahlp_problem *p, double delta) {
 cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
                             const BlkInfo *info, const std::vector<BlkInfo> &h,
                             const double *diag0, double tol, int *status, cudaStream_t s,
-                            ahlp_problem *oz, ahlp_problem *prof) {
+                            ahlp_problem *oz, ahlp_problem *prof, double drop) {
   int nblk = (int)h.size();
   if (nblk == 0) return cudaSuccess;
   int maxTp = 0;
@@ -1634,7 +1769,7 @@ cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
     }
     if (prof) kt_mark(prof, 0, s);
     count_launch(), pchol_potrf_ff_kernel<<<nblk, kThreads, 0, s>>>(hi, lo, info, k, diag0, tol,
-                                                                    status);
+                                                                    status, drop);
     if (prof) kt_mark(prof, 1, s);
     if (maxPanel > 0)
       count_launch(), pchol_trsm_ff_kernel<<<dim3((unsigned)((maxPanel + kFFRowTiles - 1) /
@@ -1663,15 +1798,15 @@ cudaError_t launch_pchol_ff(float *hi, float *lo, double *out, long long elems,
 
 cudaError_t launch_pchol(double *buf, const BlkInfo *info, const std::vector<BlkInfo> &h,
                          const double *diag0, double tol, int *status, cudaStream_t s,
-                         ahlp_problem *prof) {
-  return pchol_t<double>(buf, nullptr, info, h, diag0, tol, status, s, nullptr, prof);
+                         ahlp_problem *prof, double drop) {
+  return pchol_t<double>(buf, nullptr, info, h, diag0, tol, status, s, nullptr, prof, drop);
 }
 
 cudaError_t launch_pchol_f32(float *buf, float *tinv, const BlkInfo *info,
                              const std::vector<BlkInfo> &h, const double *diag0, double tol,
                              int *status, cudaStream_t s, ahlp_problem *tc,
-                             ahlp_problem *prof) {
-  return pchol_t<float>(buf, tinv, info, h, diag0, tol, status, s, tc, prof);
+                             ahlp_problem *prof, double drop) {
+  return pchol_t<float>(buf, tinv, info, h, diag0, tol, status, s, tc, prof, drop);
 }
 
 cudaError_t launch_ptri(const double *buf, const BlkInfo *info, int nblk, int amax, double *vec,
@@ -1696,20 +1831,20 @@ cudaError_t launch_trsv(ahlp_problem *p, bool forward) {
   const int *sched = forward ? p->trsv_fsched : p->trsv_bsched;
   if (p->fac_prec == kPrecFP32) {
     if (forward)
-      count_launch(), trsv_fwd_kernel<float><<<njobs, kTrsvThreads, 0, s>>>(
+      count_launch(), trsv_fwd_kernel<float><<<njobs, TrsvCfg<float, false>::threads, trsv_smem<float>(), s>>>(
           p->aug32, p->tinv32, p->blk, sched, p->trsv_flag_off, p->trsv_flags, ticket,
           p->trsv_err, p->vec, p->vec32);
     else
-      count_launch(), trsv_bwd_kernel<float><<<njobs, kTrsvThreads, 0, s>>>(
+      count_launch(), trsv_bwd_kernel<float><<<njobs, TrsvCfg<float, true>::threads, trsv_smem<float>(), s>>>(
           p->aug32, p->tinv32, p->blk, sched, p->trsv_flag_off, p->trsv_flags, ticket,
           p->trsv_err, p->vec);
   } else {
     if (forward)
-      count_launch(), trsv_fwd_kernel<double><<<njobs, kTrsvThreads, 0, s>>>(
+      count_launch(), trsv_fwd_kernel<double><<<njobs, TrsvCfg<double, false>::threads, trsv_smem<double>(), s>>>(
           p->aug, p->tinv, p->blk, sched, p->trsv_flag_off, p->trsv_flags, ticket, p->trsv_err,
           p->vec, p->vec);
     else
-      count_launch(), trsv_bwd_kernel<double><<<njobs, kTrsvThreads, 0, s>>>(
+      count_launch(), trsv_bwd_kernel<double><<<njobs, TrsvCfg<double, true>::threads, trsv_smem<double>(), s>>>(
           p->aug, p->tinv, p->blk, sched, p->trsv_flag_off, p->trsv_flags, ticket, p->trsv_err,
           p->vec);
   }
@@ -1729,6 +1864,18 @@ cudaError_t set_dense_smem_limits(int bytes) {
   cudaError_t e = cudaFuncSetAttribute(tinv_kernel<double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tinv_smem<double>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(trsv_fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trsv_smem<float>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(trsv_bwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trsv_smem<float>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(trsv_fwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trsv_smem<double>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(trsv_bwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trsv_smem<double>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(pchol_update_ff8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kUpdFFSmem);

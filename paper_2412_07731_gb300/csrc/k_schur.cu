@@ -644,11 +644,11 @@ __global__ void negate_corner_kernel(double *bd, int ld, int n0, int mg, double 
 // --------------------------------------------------------------------------
 // f = r_d - X^-1 r_c (forward) or g_x - Z X^-1 g_z (adjoint); g = D f on block columns
 __global__ void prep_f_kernel(double *f, double *g, const double *rd, const double *rc,
-                              const double *x, const double *z, const double *d,
+                              const double *xinv, const double *z, const double *d,
                               const unsigned char *is_x0, long long n, int adjoint) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double fi = adjoint ? rd[i] - z[i] * rc[i] / x[i] : rd[i] - rc[i] / x[i];
+  const double fi = adjoint ? rd[i] - z[i] * rc[i] * xinv[i] : rd[i] - rc[i] * xinv[i];
   f[i] = fi;
   g[i] = is_x0[i] ? 0.0 : d[i] * fi;
 }
@@ -672,28 +672,38 @@ struct RArgs {
   double *svec;
 };
 
-// Schur right-hand side: base rows plus every block's -L21 w_i, fixed order
-__global__ void schur_rhs_kernel(RArgs A) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= A.nl + A.B) return;
-  double v;
-  if (q < A.nl) {
+// Schur right-hand side: base rows plus every block's -L21 w_i, fixed order.
+// A link row touches two blocks (one thread each); a border row touches every
+// block, so one warp takes it: lane i sums blocks i, i + 32, ... in order, then
+// a fixed shuffle tree adds the lanes.  Launch: link_ctas CTAs of 256 threads
+// for the link rows, then ceil(B / 8) CTAs for the border rows.
+__global__ void schur_rhs_kernel(RArgs A, int link_ctas) {
+  if ((int)blockIdx.x < link_ctas) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= A.nl) return;
     const int j = A.link_pair[q];
     const SchurBlk s0 = A.sb[j], s1 = A.sb[j + 1];
     const int r = q - s0.link_next_off;
-    v = A.rhat[A.msum + q];
+    double v = A.rhat[A.msum + q];
     v += A.vec[A.blk[j].voff + s0.m + s0.x0n + s0.lprev + r];
     v += A.vec[A.blk[j + 1].voff + s1.m + s1.x0n + r];
-  } else {
-    const int rb = q - A.nl;
-    v = (rb < A.n0) ? A.f[A.x0off + rb] : A.rhat[A.msum + A.nl + (rb - A.n0)];
-    for (int i = 0; i < A.N; ++i) {
-      const SchurBlk s = A.sb[i];
-      const int t = border_local(s, A.n0, rb);
-      if (t >= 0) v += A.vec[A.blk[i].voff + s.m + t];
-    }
+    A.svec[q] = v;
+    return;
   }
-  A.svec[q] = v;
+  const int lane = threadIdx.x & 31;
+  const int rb = ((int)blockIdx.x - link_ctas) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (rb >= A.B) return;
+  double v = 0.0;
+  for (int i = lane; i < A.N; i += 32) {
+    const SchurBlk s = A.sb[i];
+    const int t = border_local(s, A.n0, rb);
+    if (t >= 0) v += A.vec[A.blk[i].voff + s.m + t];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0)
+    A.svec[A.nl + rb] =
+        ((rb < A.n0) ? A.f[A.x0off + rb] : A.rhat[A.msum + A.nl + (rb - A.n0)]) + v;
 }
 
 // forward (dir = 0) or backward (dir = 1) solve with the block-bidiagonal L_T,
@@ -859,14 +869,16 @@ __global__ void schur_dy_kernel(const double *svec, int nl, int n0, int mg, long
 }
 
 // dx = (A'dy - f) / (1/d + rho[x0]);  dz = X^-1 (r_c - Z dx)  or  X^-1 (g_z - dx)
+// dx = (A'dy - f) / (D^-1 + rho on the linking variables), dz from dx; w and
+// xinv are those quotients' reciprocals, taken once per factor point
 __global__ void finish_kernel(double *dx, double *dz, const double *aty, const double *f,
-                              const double *d, const double *x, const double *z, const double *rc,
-                              const unsigned char *is_x0, double rho, long long n, int adjoint) {
+                              const double *w, const double *xinv, const double *z,
+                              const double *rc, long long n, int adjoint) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double dxi = (aty[i] - f[i]) / (1.0 / d[i] + (is_x0[i] ? rho : 0.0));
+  const double dxi = (aty[i] - f[i]) * w[i];
   dx[i] = dxi;
-  dz[i] = adjoint ? (rc[i] - dxi) / x[i] : (rc[i] - z[i] * dxi) / x[i];
+  dz[i] = adjoint ? (rc[i] - dxi) * xinv[i] : (rc[i] - z[i] * dxi) * xinv[i];
 }
 
 // residual blocks of J d = r (forward) or J' d = r (adjoint)
@@ -976,7 +988,7 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
   cudaStream_t s = p->stream;
   const long long n = p->n;
   cudaError_t e;
-  count_launch(), prep_f_kernel<<<nb(n, 256), 256, 0, s>>>(p->f, p->g, r_d, r_c, p->x, p->z, p->dscale, p->is_x0,
+  count_launch(), prep_f_kernel<<<nb(n, 256), 256, 0, s>>>(p->f, p->g, r_d, r_c, p->xinv, p->z, p->dscale, p->is_x0,
                                           n, adjoint ? 1 : 0);
   e = launch_spmv(p->Amat, p->g, p->rhat, 1.0, r_p, s);
   if (e != cudaSuccess) return e;
@@ -991,7 +1003,10 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
     RArgs R{p->N, p->n0, p->mg, p->B, p->nl, p->blk, p->sblk,
             p->link_pair_d, p->vec, p->rhat, p->f, p->msum,
             p->xoff[p->N], p->svec};
-    count_launch(), schur_rhs_kernel<<<nb(p->nS, 256), 256, 0, s>>>(R);
+    {
+      const int link_ctas = (int)nb(p->nl, 256);
+      count_launch(), schur_rhs_kernel<<<link_ctas + (int)nb(p->B, 8), 256, 0, s>>>(R, link_ctas);
+    }
     CArgs C = cargs(p);
     // one stage = one operator (<= lmax^2) plus one pair's rows (<= lmax); the
     // last meta slot is reserved
@@ -1056,8 +1071,8 @@ cudaError_t launch_solve(ahlp_problem *p, const double *r_d, const double *r_p,
   // dx, dz
   e = launch_spmv(p->ATmat, dy, p->g, 1.0, nullptr, s);
   if (e != cudaSuccess) return e;
-  count_launch(), finish_kernel<<<nb(n, 256), 256, 0, s>>>(dx, dz, p->g, p->f, p->dscale, p->x, p->z, r_c,
-                                          p->is_x0, p->fac_rho, n, adjoint ? 1 : 0);
+  count_launch(), finish_kernel<<<nb(n, 256), 256, 0, s>>>(dx, dz, p->g, p->f, p->wfin, p->xinv,
+                                                            p->z, r_c, n, adjoint ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -529,8 +529,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) pchol_update_tc2_kernel(const 
 // tensor core's FP32 accumulation of FP16 products computes each one exactly.
 // The 21 digit products with s + t <= 5 run as kind::f16 MMAs (M = 128,
 // N = 64, K = 16) into six TMEM accumulators; the epilogue sums
-// 2^(-8q) D_q as a float-float pair (each term exact, two-sum), scales it by
-// the row and column exponents and subtracts it from C's hi/lo pair.  The
+// 2^(-8q) D_q as a float-float pair (oz_combine), scales it by the row and
+// column exponents and subtracts it from C's hi/lo pair.  The
 // truncated digits and the dropped products (s + t >= 6) sit near 2^-47 of
 // sum_k |x_rk| |y_ck|, the accuracy of the double-float FP32-pipe kernel.
 // --------------------------------------------------------------------------
@@ -577,6 +577,21 @@ __device__ __forceinline__ void two_sum(float &a, float &b) {   // (a, b) <- fl(
   b = err;
 }
 
+// sum_q 2^(-8q) D_q (q = 0..5) as a float-float pair (h, l): each term is
+// exact (a power-of-two scaling of an integer below 2^24), added to the high
+// word by an error-free two-sum whose error goes to the low word.
+__device__ __forceinline__ void oz_combine(const float (&D)[kOzQ], float &h, float &l) {
+  h = D[0];
+  l = 0.0f;
+#pragma unroll
+  for (int q = 1; q < kOzQ; ++q) {
+    float t = ldexpf(D[q], -8 * q);   // exact
+    two_sum(h, t);
+    l = __fadd_rn(l, t);
+  }
+  two_sum(h, l);
+}
+
 struct OzArgs {
   const __half *dstage;    // digit planes: per slot 6 x 4096 halves
   const int *dexp;         // per slot 64 row exponents
@@ -585,6 +600,7 @@ struct OzArgs {
   const CUtensorMap *tmap; // [2 nblk]: each block's hi matrix, then its lo matrix
   int nblk, k;
   int *status;
+  float *hi, *lo;          // the augmented matrices' words (persistent kernel)
 };
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, int x, int y,
@@ -723,14 +739,10 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_oz_kernel(const OzArg
         // entries above the diagonal keep their value (the tile goes back
         // whole); rows and columns past the matrix are clipped by the store
         if (gcol > grow) continue;
-        float sh = D[0][j], sl = 0.0f;
+        float Dq[kOzQ], sh, sl;
 #pragma unroll
-        for (int q = 1; q < kOzQ; ++q) {
-          float t = ldexpf(D[q][j], -8 * q);   // exact
-          two_sum(sh, t);
-          sl = __fadd_rn(sl, t);
-        }
-        two_sum(sh, sl);
+        for (int q = 0; q < kOzQ; ++q) Dq[q] = D[q][j];
+        oz_combine(Dq, sh, sl);
         const int sc = er + eB[c] - 18;
         sh = ldexpf(sh, sc);
         sl = ldexpf(sl, sc);
@@ -767,40 +779,45 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_oz_kernel(const OzArg
 // --------------------------------------------------------------------------
 // The float-float digit update as a persistent, warp-specialised pipeline:
 // one CTA per SM walks the step's jobs (job blockIdx.x, + gridDim.x, ...).
-// A job's operands come in two units, one per K half (all six A and B
-// digit planes over 32 pivot columns, 72 KB), each with its own shared-
-// memory stage, so the next job's first half loads while this job's
-// second half multiplies --
-//   warp 0  producer: bulk copies of unit (j, h) into stage h once the MMAs
-//           of job j - 1 have released it, and an L2 prefetch of job j's C
-//           tile;
+// A job's operands come in two units, one per K half (all six A and B digit
+// planes over 32 pivot columns, 72 KB), through a ring of three shared-memory
+// stages, so the producer runs one and a half jobs ahead --
+//   warp 0  producer: bulk copies of unit u into stage u % 3 once the MMAs of
+//           unit u - 3 have released it, and an L2 prefetch of each job's C
+//           tile (hi and lo) when its first unit goes out;
 //   warp 1  MMA issuer: the 2 x 42 MMAs of job j into the six TMEM
-//           accumulators, once both halves have landed and the epilogue has
+//           accumulators, once both units have landed and the epilogue has
 //           read job j - 1 out of tensor memory;
-//   warps 2-9  epilogue: two warps per TMEM lane quarter, 32 columns each;
-//           the accumulators go to registers as float-float values (which
-//           frees tensor memory for the next job's MMAs), the C tile (hi,
-//           lo), loaded by tensor copy after the previous job's store has
-//           read it, is updated in shared memory and stored back.
-// The D_q are exact integers whatever the order of their products, so the
-// factor equals the one-CTA-per-job kernel's bit for bit.  Every wait is
-// bounded as above.
+//   warps 2-9  epilogue: two warps per TMEM lane quarter, each owning a
+//           32-row x 32-column quarter of the output tile.  A warp loads its
+//           part of C (hi, lo; coalesced, one column per instruction) into
+//           registers before the job's products are ready, takes the
+//           accumulators out of tensor memory as float-float values (freeing
+//           it for the next job's MMAs), and writes C - P back directly.
+// Warps of the epilogue never wait for each other.  The D_q are exact
+// integers whatever the order of their products, so the factor equals the
+// one-CTA-per-job kernel's bit for bit.  Every wait is bounded as above.
 // --------------------------------------------------------------------------
 constexpr int kOz2Threads = 320;
+constexpr int kOz2Stages = 2;
 constexpr uint32_t kOz2HalfA = kTcM * (NB / 2) * 2;             // one K half of an A plane: 8 KB
 constexpr uint32_t kOz2HalfB = kTcN * (NB / 2) * 2;             // 4 KB
 constexpr uint32_t kOz2Stage = kOzQ * (kOz2HalfA + kOz2HalfB);  // 72 KB
-constexpr uint32_t kOz2Smem = 2 * kOz2Stage + 2 * kOzCTile + 1024;
+constexpr uint32_t kOz2Smem = kOz2Stages * kOz2Stage + 8 * 8192 + 1024;   // + C quarters
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
 #pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void cp_async16_oz(float *dst, const float *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
 }
 
 __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *tm, int x, int y) {
@@ -812,17 +829,14 @@ __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *tm, int x, in
 __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const OzArgs args,
                                                                          int njobs) {
   extern __shared__ __align__(1024) unsigned char oz2_raw[];
-  __shared__ __align__(8) uint64_t full[2], empty[2], tfull, tempty, cfull;
+  __shared__ __align__(8) uint64_t full[kOz2Stages], empty[kOz2Stages], tfull, tempty;
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_fail, s_epi_fail;
+  __shared__ int s_fail;
   unsigned char *base = oz2_raw + ((1024 - (smem_u32(oz2_raw) & 1023)) & 1023);
-  float *c_hi = reinterpret_cast<float *>(base + 2 * kOz2Stage);   // [64 cols][128 rows]
-  float *c_lo = c_hi + kTcM * kTcN;
   volatile int *vfail = &s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int myjobs = (int)blockIdx.x < njobs ? (njobs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
                                              : 0;
-  const CUtensorMap *tmh0 = args.tmap, *tml0 = args.tmap + args.nblk;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
@@ -832,14 +846,12 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
   }
   if (threadIdx.x == 0) {
     s_fail = 0;
-    s_epi_fail = 0;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kOz2Stages; ++i) {
       mbar_init(smem_u32(&full[i]), 1);
       mbar_init(smem_u32(&empty[i]), 1);
     }
     mbar_init(smem_u32(&tfull), 1);
     mbar_init(smem_u32(&tempty), 8 * 32);
-    mbar_init(smem_u32(&cfull), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -849,20 +861,20 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0) {
-    // ---- producer: unit (j, h) = K half h of job j into stage h -----------------
+    // ---- producer: unit u = (job u / 2, K half u % 2) into stage u % 3 ----------
     if (lane == 0) {
       int issued = 0;   // units
       Job jb{};
       for (int u = 0; u < 2 * myjobs && !*vfail; ++u) {
-        const int j = u >> 1, h = u & 1;
-        if (!mbar_wait(smem_u32(&empty[h]), (j & 1) ^ 1)) {
+        const int j = u >> 1, h = u & 1, st = u % kOz2Stages, use = u / kOz2Stages;
+        if (!mbar_wait(smem_u32(&empty[st]), (use & 1) ^ 1)) {
           atomicExch(&s_fail, 1);
           break;
         }
-        if (h == 0) {   // next job: its C tile towards L2 ahead of the epilogue's load
+        if (h == 0) {   // next job: its C tile towards L2 ahead of the epilogue's loads
           jb = decode_job(args.joff, args.nblk, args.k, args.blk,
                           (int)blockIdx.x + j * (int)gridDim.x);
-          const CUtensorMap *th = tmh0 + jb.b, *tl = tml0 + jb.b;
+          const CUtensorMap *th = args.tmap + jb.b, *tl = args.tmap + args.nblk + jb.b;
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(th) : "memory");
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tl) : "memory");
           tma_prefetch_2d(th, jb.I0 * NB, jb.J * NB);
@@ -871,9 +883,9 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
         const BlkInfo bi = args.blk[jb.b];
         const __half *st0 = args.dstage + (bi.soff + jb.I0) * (kOzQ * NB * NB) + h * (NB * NB / 2);
         const __half *stJ = args.dstage + (bi.soff + jb.J) * (kOzQ * NB * NB) + h * (NB * NB / 2);
-        const uint32_t sa = smem_u32(base + h * kOz2Stage), sb = sa + kOzQ * kOz2HalfA;
-        const uint32_t bar = smem_u32(&full[h]);
-        const uint32_t q4 = NB * NB;   // halves of one 64-row K half = 4 KB
+        const uint32_t sa = smem_u32(base + st * kOz2Stage), sb = sa + kOzQ * kOz2HalfA;
+        const uint32_t bar = smem_u32(&full[st]);
+        const uint32_t q4 = NB * NB;   // bytes of one 64-row K half = 4 KB
         mbar_expect_tx(bar, (jb.has_i1 ? 3u : 2u) * kOzQ * q4);
 #pragma unroll
         for (int q = 0; q < kOzQ; ++q) {
@@ -884,9 +896,9 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
         }
         issued = u + 1;
       }
-      if (*vfail)   // copies still in flight (the last two units) land before exit
-        for (int u = issued >= 2 ? issued - 2 : 0; u < issued; ++u)
-          mbar_wait(smem_u32(&full[u & 1]), (u >> 1) & 1);
+      if (*vfail)   // copies still in flight (the last three units) land before exit
+        for (int u = issued >= kOz2Stages ? issued - kOz2Stages : 0; u < issued; ++u)
+          mbar_wait(smem_u32(&full[u % kOz2Stages]), (u / kOz2Stages) & 1);
     }
   } else if (warp == 1) {
     // ---- MMA issuer ----------------------------------------------------------------
@@ -899,12 +911,13 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
         }
         bool ok = true;
         for (int h = 0; h < 2; ++h) {
-          if (!mbar_wait(smem_u32(&full[h]), j & 1)) {
+          const int u = 2 * j + h, st = u % kOz2Stages;
+          if (!mbar_wait(smem_u32(&full[st]), (u / kOz2Stages) & 1)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(base + h * kOz2Stage), sb = sa + kOzQ * kOz2HalfA;
+          const uint32_t sa = smem_u32(base + st * kOz2Stage), sb = sa + kOzQ * kOz2HalfA;
 #pragma unroll
           for (int q = 0; q < kOzQ; ++q)
 #pragma unroll
@@ -914,8 +927,8 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
                 mma_f16(tmem + q * kTcN, smem_desc(sa + sd * kOz2HalfA + ks * 256, 128, 512),
                         smem_desc(sb + (q - sd) * kOz2HalfB + ks * 256, 128, 512),
                         (h | sd | ks) != 0);
-          mma_commit(smem_u32(&empty[h]));   // stage h free once these MMAs complete
-          last = 2 * j + h;
+          mma_commit(smem_u32(&empty[st]));   // stage free once these MMAs complete
+          last = u;
         }
         if (!ok) {
           atomicExch(&s_fail, 2);
@@ -924,112 +937,90 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
         mma_commit(smem_u32(&tfull));   // all 84 products of job j complete
       }
       if (*vfail && last >= 0)   // MMAs in flight finish before tensor memory is freed
-        mbar_wait(smem_u32(&empty[last & 1]), (last >> 1) & 1);
+        mbar_wait(smem_u32(&empty[last % kOz2Stages]), (last / kOz2Stages) & 1);
     }
   } else {
     // ---- epilogue ------------------------------------------------------------------
-    const int ew = warp - 2;
-    const int quarter = warp & 3;           // TMEM lanes 32 quarter .. + 31
-    const int cbase = (ew >> 2) * 32;       // this warp's 32 columns of the tile
-    const int r = quarter * 32 + lane;      // row of the 128-row tile
-    const bool leader = threadIdx.x == 64;  // warp 2, lane 0
-    int c_issued = -1;                      // last job whose C tile load was issued
-    auto load_c = [&](int j) {
-      const Job jn = decode_job(args.joff, args.nblk, args.k, args.blk,
-                                (int)blockIdx.x + j * (int)gridDim.x);
-      const CUtensorMap *th = tmh0 + jn.b, *tl = tml0 + jn.b;
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(th) : "memory");
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tl) : "memory");
-      // the whole box counts, rows past the matrix included (zero-filled)
-      mbar_expect_tx(smem_u32(&cfull), 2 * kOzCTile);
-      tma_load_2d(smem_u32(c_hi), th, jn.I0 * NB, jn.J * NB, smem_u32(&cfull));
-      tma_load_2d(smem_u32(c_lo), tl, jn.I0 * NB, jn.J * NB, smem_u32(&cfull));
-      c_issued = j;
-    };
-    if (leader && myjobs > 0) load_c(0);
+    const int quarter = warp & 3;                // TMEM lanes 32 quarter .. + 31
+    const int cbase = ((warp - 2) >> 2) * 32;    // this warp's 32 columns of the tile
+    const int r = quarter * 32 + lane;           // row of the 128-row tile
+    // this warp's quarter of the C tile, [column][row] for hi then lo
+    float *cs = reinterpret_cast<float *>(base + kOz2Stages * kOz2Stage + (warp - 2) * 8192);
     for (int j = 0; j < myjobs; ++j) {
       const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk,
                                 (int)blockIdx.x + j * (int)gridDim.x);
       const BlkInfo bi = args.blk[jb.b];
       const long long slot0 = bi.soff + jb.I0, slotJ = bi.soff + jb.J;
+      const int row0 = jb.I0 * NB + quarter * 32;   // first row of the warp's quarter
+      const int grow = row0 + lane;
+      const int col0 = jb.J * NB + cbase;
+      // C quarter -> shared memory by cp.async before the products are ready:
+      // 16-byte copies of 4 rows, 8 per column, rows past the matrix
+      // zero-filled, columns past it skipped
+      __syncwarp();   // every lane has finished reading the previous job's quarter
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int arr = t >> 3, c = ((t & 7) << 2) | (lane >> 3), part = lane & 7;
+        const int rr = row0 + part * 4;
+        const int valid = col0 + c < bi.a ? max(0, min(4, bi.a - rr)) : 0;
+        const float *src = (arr ? args.lo : args.hi) + bi.base;
+        const float *g = valid ? src + (long long)(col0 + c) * bi.lda + rr : src;
+        cp_async16_oz(cs + arr * 1024 + c * 32 + part * 4, g, valid * 4);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
       const int er = (r < NB || jb.has_i1) ? args.dexp[slot0 * NB + r] : 0;
-      int ok = 1;
+      const int ec = args.dexp[slotJ * NB + cbase + lane];   // lane u: column cbase + u
+      int ok = 0;
       if (lane == 0) ok = mbar_wait(smem_u32(&tfull), j & 1) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
-      // the six accumulators -> sum_q 2^(-8q) D_q as a float-float pair
-      float sh[32], sl[32];
-      if (ok) {
-        tc_fence_after();
-#pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-          float D[kOzQ][8];
-#pragma unroll
-          for (int q = 0; q < kOzQ; ++q)
-            tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) +
-                         (uint32_t)(q * kTcN + cbase + ch * 8),
-                     D[q]);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            float h = D[0][u], l = 0.0f;
-#pragma unroll
-            for (int q = 1; q < kOzQ; ++q) {
-              float t = ldexpf(D[q][u], -8 * q);   // exact
-              two_sum(h, t);
-              l = __fadd_rn(l, t);
-            }
-            two_sum(h, l);
-            sh[ch * 8 + u] = h;
-            sl[ch * 8 + u] = l;
-          }
-        }
-        tc_fence_before();
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty))
-                     : "memory");
-        if (lane == 0 && !mbar_wait(smem_u32(&cfull), j & 1)) s_epi_fail = 1;
-      } else if (lane == 0) {
-        s_epi_fail = 1;
-      }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (s_epi_fail) {   // the same verdict in all eight warps
-        if (leader) atomicExch(&s_fail, 3);
+      if (!ok) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        atomicExch(&s_fail, 3);
         break;
       }
-      const int grow = jb.I0 * NB + r;
+      tc_fence_after();
+      // the six accumulators -> sum_q 2^(-8q) D_q as a float-float pair
+      float sh[32], sl[32];
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) {
+        float D[kOzQ][4];
+#pragma unroll
+        for (int q = 0; q < kOzQ; ++q)
+          tmem_ld4(tmem + ((uint32_t)(quarter * 32) << 16) +
+                       (uint32_t)(q * kTcN + cbase + c4 * 4),
+                   D[q]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float Dq[kOzQ];
+#pragma unroll
+          for (int q = 0; q < kOzQ; ++q) Dq[q] = D[q][u];
+          oz_combine(Dq, sh[c4 * 4 + u], sl[c4 * 4 + u]);
+        }
+      }
+      tc_fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty))
+                   : "memory");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncwarp();   // the other lanes' copies are visible
+      // C - P on the lower triangle of the matrix (rows and columns past it,
+      // and entries above the diagonal, keep their values)
+      const long long g0 = bi.base + (long long)col0 * bi.lda + grow;
 #pragma unroll
       for (int u = 0; u < 32; ++u) {
-        const int c = cbase + u, gcol = jb.J * NB + c;
-        // entries above the diagonal keep their value (the tile goes back
-        // whole); rows and columns past the matrix are clipped by the store
-        if (gcol > grow) continue;
-        const int sc = er + args.dexp[slotJ * NB + c] - 18;
+        const int sc = er + __shfl_sync(0xffffffffu, ec, u) - 18;
+        if (!(grow < bi.a && col0 + u <= grow)) continue;
+        const float chv = cs[u * 32 + lane], clv = cs[1024 + u * 32 + lane];
         const float ph = ldexpf(sh[u], sc), pl = ldexpf(sl[u], sc);
         // (ch + cl) - (ph + pl): two-sum of the high parts, low parts added
-        const int e = c * kTcM + r;
-        const float chv = c_hi[e], clv = c_lo[e];
         const float tt = __fsub_rn(chv, ph);
         const float bv = __fsub_rn(tt, chv);
         const float err = __fadd_rn(__fsub_rn(chv, __fsub_rn(tt, bv)), __fsub_rn(-ph, bv));
         const float el = __fadd_rn(err, __fsub_rn(clv, pl));
         const float hh = __fadd_rn(tt, el);
-        c_hi[e] = hh;
-        c_lo[e] = __fsub_rn(el, __fsub_rn(hh, tt));
+        args.hi[g0 + (long long)u * bi.lda] = hh;
+        args.lo[g0 + (long long)u * bi.lda] = __fsub_rn(el, __fsub_rn(hh, tt));
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (leader) {
-        tma_store_2d(tmh0 + jb.b, jb.I0 * NB, jb.J * NB, smem_u32(c_hi));
-        tma_store_2d(tml0 + jb.b, jb.I0 * NB, jb.J * NB, smem_u32(c_lo));
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        // the next tile may overwrite shared memory once the store has read it
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-        if (j + 1 < myjobs) load_c(j + 1);
-      }
-    }
-    if (leader) {
-      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-      if (*vfail && c_issued >= 0)   // a C tile load still in flight lands before exit
-        mbar_wait(smem_u32(&cfull), c_issued & 1);
     }
   }
   __syncwarp();
@@ -1197,7 +1188,7 @@ cudaError_t launch_update_oz(ahlp_problem *p, int k, cudaStream_t s) {
   if (jobs <= 0) return cudaSuccess;
   OzArgs a{p->dstage, p->dexp, p->tc_joff + (size_t)k * (p->h_blk.size() + 1), p->blk,
            reinterpret_cast<const CUtensorMap *>(p->oz_tmap), (int)p->h_blk.size(), k,
-           p->status};
+           p->status, p->aug32, p->aug_lo};
   if (p->ff_update == 3) {   // persistent pipeline: one CTA per SM
     const int grid = (int)std::min<long long>(jobs, p->num_sms);
     count_launch(), pchol_update_oz2_kernel<<<grid, kOz2Threads, kOz2Smem, s>>>(a, (int)jobs);

@@ -123,15 +123,21 @@ def test_persistent_update_matches_per_tile_update(P):
     lp = random_block_lp(11, N=N, m_sizes=m, n_sizes=n, nnz_per_col=5, n0=4, w_density=0.2,
                          l=[4] * (N - 1), mg=2, global_nnz=4)
     A, x, z, *_ = _point(lp, 6, 0.5)
-    probs = {u: P.arrowhead_lp_create(lp, _fp32(P, u)) for u in (1, 2, 3)}
+    probs = {u: P.arrowhead_lp_create(lp, _fp32(P, u)) for u in (2, 3)}
+    probs[0] = P.arrowhead_lp_create(lp)   # FP64 factors
     for prob in probs.values():
         P.kkt_factor(prob, x, z, 0.0, 0.0)
     for i in range(N):
         F2 = kkt_block_factor_dense(probs[2], i)
         F3 = kkt_block_factor_dense(probs[3], i)
         assert np.array_equal(F2, F3), i
-        Fc = kkt_block_factor_dense(probs[1], i)
-        assert np.abs(F3 - Fc).max() <= 2e-5 * np.abs(Fc).max(), i
+        # FP32-level accuracy against the FP64 factor, relative to the block's
+        # scale (hi + lo carries 22 of x's 24 bits and lo*lo is dropped, so
+        # the split product's error exceeds the FP32 pipe's by up to ~20x;
+        # the Schur corner carries the cancellation of C - G' M^-1 G)
+        F64 = kkt_block_factor_dense(probs[0], i)
+        e3 = np.abs(F3 - F64).max()
+        assert e3 <= 2e-5 * np.abs(F64).max(), (i, e3)
     S_ref = oschur.schur_reduced(lp, x, z)
     S = P.kkt_schur_dense(probs[3])
     assert np.abs(S - S_ref).max() <= 1e-4 * np.abs(S_ref).max()
