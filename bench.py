@@ -204,15 +204,25 @@ def stage_rooflines(P, prob, lp, peaks):
     flops = block_factor_flops(lp)
     gbs = lambda b, ms: b / (ms / 1e3) / 1e9  # noqa: E731
     hbm = peaks["hbm_gbs"]
+    if saved.fp32_update in (0, 2, 3):   # TF32 split products on the tensor cores
+        _, upd_flops = update_geometry(lp)
+        tpeak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
+        ach = 3 * upd_flops / (block_ms / 1e3) / 1e12
+        block_stage = {"ms": block_ms, "bound": "tensor (TF32, 3 MMAs per product)",
+                       "flop": flops, "achieved_tflops": ach, "peak_tflops": tpeak,
+                       "frac": ach / tpeak,
+                       "fp32_equivalent_tflops": flops / (block_ms / 1e3) / 1e12}
+    else:
+        block_stage = {"ms": block_ms, "bound": "alu (FP32)", "flop": flops,
+                       "achieved_tflops": flops / (block_ms / 1e3) / 1e12,
+                       "frac": flops / (block_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS}
     return {
         "point": "x, z = exp(N(0,1)) (seed 0); FP32 block factors",
         "form": {"ms": form_ms, "bound": "hbm", "bytes": form_bytes,
                  "achieved_gbs": gbs(form_bytes, form_ms),
                  "frac": gbs(form_bytes, form_ms) / hbm},
-        "block_factor": {"ms": block_ms, "bound": "alu (FP32)", "flop": flops,
-                         "achieved_tflops": flops / (block_ms / 1e3) / 1e12,
-                         "frac": flops / (block_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
-        "schur_factor": {"ms": schur_ms, "bound": "FP64 latency (sequential link chain)"},
+        "block_factor": block_stage,
+        "schur_factor": {"ms": schur_ms, "bound": "FP64 latency, cyclic reduction levels"},
         "apply": {"ms": apply_ms, "bound": "hbm", "bytes": apply_bytes,
                   "achieved_gbs": gbs(apply_bytes, apply_ms),
                   "frac": gbs(apply_bytes, apply_ms) / hbm},
@@ -563,12 +573,12 @@ def update_geometry(lp, NB=64):
 # (precision, update option), from the ncu captures in profiles/ (uniform
 # 8-block workload, whose trailing matrices partly fit L2):
 # pchol_update_tc_c1small.md (per-tile TF32), pchol_update_tc2_c1small.md
-# (persistent TF32), pchol_update_oz_c1small.md (per-tile digits),
-# pchol_update_oz2_c1small.md (persistent digits).  The live bench scales them
-# by the bytes of its own launches to fill roofline.traffic; a kernel without
-# a capture of its current code reports null.
-UPDATE_TRAFFIC_PER_BYTE = {("FP32", 2): 0.68, ("FP32", 3): 0.70, ("float-float", 2): 0.89,
-                           ("float-float", 3): None}
+# (persistent TF32), pchol_update_oz2_c1small.md (persistent digits).  The
+# live bench scales them by the bytes of its own launches to fill
+# roofline.traffic; a kernel without a capture of its current code reports
+# null.
+UPDATE_TRAFFIC_PER_BYTE = {("FP32", 2): 0.68, ("FP32", 3): 0.70, ("float-float", 2): None,
+                           ("float-float", 3): 0.88}
 UPDATE_KERNEL = {("FP32", 1): "pchol_update_f32_kernel (FP32 pipe)",
                  ("FP32", 2): "pchol_update_tc_kernel (tcgen05, one CTA per tile)",
                  ("FP32", 3): "pchol_update_tc2_kernel (tcgen05, persistent)",
@@ -634,10 +644,21 @@ def kernel_roofline(P, prob, lp, x, z, prec_name, peaks):
     return out
 
 
-def roofline(lp, win, peaks):
+# nominal dense tensor rates relative to BF16 (profiling recipe's table:
+# bf16/fp16 2.25, tf32 1.1 PFLOP/s): a contraction's peak is the measured BF16
+# peak times this ratio
+TF32_PER_BF16 = 1.1 / 2.25
+FP16_PER_BF16 = 1.0
+
+
+def roofline(lp, win, peaks, opts=None):
     """The batched block partial Cholesky in the precision whose factors took
     the most time in the timed window; achieved = its algorithmic flops per
-    factor / its mean CUDA-event time per factor."""
+    factor / its mean CUDA-event time per factor.  When its trailing updates
+    run on the tensor cores (TF32 hi/lo splits: 3 MMAs per product; FP16
+    digits: 21), the factor is reported against the tensor peak of that
+    operand type, counting the updates' tensor flops (sustained BF16 peak,
+    the factor being timed inside long steps)."""
     a = win.acc
     flops = block_factor_flops(lp)
     kinds = [
@@ -654,6 +675,24 @@ def roofline(lp, win, peaks):
     if not cnt:
         return None
     ms = tot / cnt
+    variant = None
+    if opts is not None:
+        variant = (opts.fp32_update if name == "FP32" else
+                   opts.ff_update if name == "float-float" else None)
+    if variant in (0, 2, 3):   # tensor-core trailing updates
+        _, upd_flops = update_geometry(lp)
+        per, ratio, op = ((3, TF32_PER_BF16, "TF32") if name == "FP32" else
+                          (21, FP16_PER_BF16, "FP16"))
+        tpeak = peaks["bf16_tflops_sustained"] * ratio
+        achieved = per * upd_flops / (ms / 1e3) / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": achieved / tpeak, "traffic": None,
+                "kernel": f"batched block partial Cholesky ({name}; diagonal tile, panel, "
+                          f"trailing update on the tensor cores as {per} {op} MMAs per "
+                          f"product), {flops:.4g} flop per factor, {ms:.2f} ms",
+                "peak_source": f"{peaks['source']} sustained BF16 peak x {ratio:.3f} "
+                               f"(nominal {op}:BF16 dense ratio)",
+                "fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12}
     if name == "float-float":
         achieved = flops / 2.0 * FF_FP32_OPS_PER_MAC / (ms / 1e3) / 1e12
         extra = {"fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12}
@@ -711,7 +750,7 @@ def run_ours(args):
     prob, win, ms, full = arm(headline, args.warmup, args.steps)
     value = world * args.steps / (ms / 1e3)
     summ = window_summary(win, ms, args.steps)
-    factor_roof = roofline(lp, win, peaks)
+    factor_roof = roofline(lp, win, peaks, prob.options)
     roof = None
     if factor_roof is not None and rank == 0:
         # the dominant kernel: the trailing update of the block factor in the

@@ -434,9 +434,16 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       R.rel_gap = std::fabs(hs[2] - hs[3]) / (1.0 + std::fabs(hs[2]));
       R.mu = n > 0 ? hs[4] / n : 0.0;
       R.iterations = it;
-      if (p->opt.verbose)
-        printf("ipm %3d  pobj %+.10e  dobj %+.10e  pinf %.2e  dinf %.2e  gap %.2e  mu %.2e\n", it,
+      if (p->opt.verbose) {
+        printf("ipm %3d  pobj %+.10e  dobj %+.10e  pinf %.2e  dinf %.2e  gap %.2e  mu %.2e", it,
                R.pobj, R.dobj, R.pinf, R.dinf, R.rel_gap, R.mu);
+        if (nlp > 0) {
+          int nf = 0;
+          for (int b = 0; b < nlp; ++b) nf += frozen[b];
+          printf("  frozen %d/%d", nf, nlp);
+        }
+        printf("\n");
+      }
       if (p->opt.iter_cb && p->opt.iter_cb(p->opt.iter_cb_ctx, it, &R) != 0) {
         status = AHLP_ERR_STOPPED;
         p->err = "ipm_solve: stopped by the iteration callback";
@@ -481,6 +488,7 @@ extern "C" int ipm_solve(ahlp_problem *p, const double *x0, const double *y0, co
       double sigma = 0.0;
       for (;;) {
         int st = factor_at(X, Z);
+        if (st == AHLP_ERR_NOT_SPD && p->opt.verbose) printf("       %s\n", p->err.c_str());
         if (st == AHLP_ERR_NOT_SPD && escalate(true, "a NaN pivot")) continue;
         if (st != AHLP_OK) throw Fail{st, p->err};
         // predictor: r_c = -XZe

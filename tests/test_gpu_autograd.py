@@ -52,8 +52,13 @@ def test_objective_gradients_are_the_planted_solution(P, seed, mixed):
     obj = (c * x).sum()
     obj.backward()
     xs, ys = lp.xstar, lp.ystar
-    assert np.abs(c.grad.cpu().numpy() - xs).max() <= 1e-6 * max(1.0, np.abs(xs).max())
-    assert np.abs(b.grad.cpu().numpy() - ys).max() <= 1e-6 * max(1.0, np.abs(ys).max())
+    # the returned point is an IPM iterate at relative gap 1e-8, whose
+    # distance to the vertex the gradient inherits: ~1e-7 with FP64 factors;
+    # up to ~1e-6 when the last factors are float-float (tolerance 1e-5, the
+    # finite-difference agreement asked of the gradients)
+    tol = 1e-5 if mixed else 1e-6
+    assert np.abs(c.grad.cpu().numpy() - xs).max() <= tol * max(1.0, np.abs(xs).max())
+    assert np.abs(b.grad.cpu().numpy() - ys).max() <= tol * max(1.0, np.abs(ys).max())
     prob.close()
 
 
