@@ -583,9 +583,10 @@ __device__ __forceinline__ void two_sum(float &a, float &b) {   // (a, b) <- fl(
 __device__ __forceinline__ void oz_combine(const float (&D)[kOzQ], float &h, float &l) {
   h = D[0];
   l = 0.0f;
+  const float pw[kOzQ] = {1.0f, 0x1p-8f, 0x1p-16f, 0x1p-24f, 0x1p-32f, 0x1p-40f};
 #pragma unroll
   for (int q = 1; q < kOzQ; ++q) {
-    float t = ldexpf(D[q], -8 * q);   // exact
+    float t = __fmul_rn(D[q], pw[q]);   // exact: an integer times a power of two
     two_sum(h, t);
     l = __fadd_rn(l, t);
   }
@@ -789,11 +790,12 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_oz_kernel(const OzArg
 //           accumulators, once both units have landed and the epilogue has
 //           read job j - 1 out of tensor memory;
 //   warps 2-9  epilogue: two warps per TMEM lane quarter, each owning a
-//           32-row x 32-column quarter of the output tile.  A warp loads its
-//           part of C (hi, lo; coalesced, one column per instruction) into
-//           registers before the job's products are ready, takes the
-//           accumulators out of tensor memory as float-float values (freeing
-//           it for the next job's MMAs), and writes C - P back directly.
+//           32-row x 32-column quarter of the output tile.  A warp requests
+//           its quarter of C (hi, lo) by cp.async into its own shared memory
+//           before the job's products are ready, then, four columns at a
+//           time, reads the six accumulators, turns them into a float-float
+//           value and writes C - P back with plain stores; tensor memory is
+//           released to the next job's MMAs after the last four columns.
 // Warps of the epilogue never wait for each other.  The D_q are exact
 // integers whatever the order of their products, so the factor equals the
 // one-CTA-per-job kernel's bit for bit.  Every wait is bounded as above.
@@ -980,8 +982,14 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
       }
       tc_fence_after();
       // the six accumulators -> sum_q 2^(-8q) D_q as a float-float pair
-      float sh[32], sl[32];
-#pragma unroll
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncwarp();   // the other lanes' copies are visible
+      // four columns at a time: accumulators -> float-float value -> C - P on
+      // the lower triangle of the matrix (rows and columns past it, and
+      // entries above the diagonal, keep their values); the loop stays rolled
+      // so that the epilogue's code stays short
+      const long long g0 = bi.base + (long long)col0 * bi.lda + grow;
+#pragma unroll 1
       for (int c4 = 0; c4 < 8; ++c4) {
         float D[kOzQ][4];
 #pragma unroll
@@ -991,36 +999,29 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
                    D[q]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float Dq[kOzQ];
+        for (int v = 0; v < 4; ++v) {
+          const int u = c4 * 4 + v;
+          float Dq[kOzQ], shv, slv;
 #pragma unroll
-          for (int q = 0; q < kOzQ; ++q) Dq[q] = D[q][u];
-          oz_combine(Dq, sh[c4 * 4 + u], sl[c4 * 4 + u]);
+          for (int q = 0; q < kOzQ; ++q) Dq[q] = D[q][v];
+          oz_combine(Dq, shv, slv);
+          const int sc = er + __shfl_sync(0xffffffffu, ec, u) - 18;
+          if (!(grow < bi.a && col0 + u <= grow)) continue;
+          const float chv = cs[u * 32 + lane], clv = cs[1024 + u * 32 + lane];
+          const float ph = ldexpf(shv, sc), pl = ldexpf(slv, sc);
+          const float tt = __fsub_rn(chv, ph);
+          const float bv = __fsub_rn(tt, chv);
+          const float err = __fadd_rn(__fsub_rn(chv, __fsub_rn(tt, bv)), __fsub_rn(-ph, bv));
+          const float el = __fadd_rn(err, __fsub_rn(clv, pl));
+          const float hh = __fadd_rn(tt, el);
+          args.hi[g0 + (long long)u * bi.lda] = hh;
+          args.lo[g0 + (long long)u * bi.lda] = __fsub_rn(el, __fsub_rn(hh, tt));
         }
       }
+      // all six accumulators read: the next job's MMAs may overwrite them
       tc_fence_before();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty))
                    : "memory");
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      __syncwarp();   // the other lanes' copies are visible
-      // C - P on the lower triangle of the matrix (rows and columns past it,
-      // and entries above the diagonal, keep their values)
-      const long long g0 = bi.base + (long long)col0 * bi.lda + grow;
-#pragma unroll
-      for (int u = 0; u < 32; ++u) {
-        const int sc = er + __shfl_sync(0xffffffffu, ec, u) - 18;
-        if (!(grow < bi.a && col0 + u <= grow)) continue;
-        const float chv = cs[u * 32 + lane], clv = cs[1024 + u * 32 + lane];
-        const float ph = ldexpf(sh[u], sc), pl = ldexpf(sl[u], sc);
-        // (ch + cl) - (ph + pl): two-sum of the high parts, low parts added
-        const float tt = __fsub_rn(chv, ph);
-        const float bv = __fsub_rn(tt, chv);
-        const float err = __fadd_rn(__fsub_rn(chv, __fsub_rn(tt, bv)), __fsub_rn(-ph, bv));
-        const float el = __fadd_rn(err, __fsub_rn(clv, pl));
-        const float hh = __fadd_rn(tt, el);
-        args.hi[g0 + (long long)u * bi.lda] = hh;
-        args.lo[g0 + (long long)u * bi.lda] = __fsub_rn(el, __fsub_rn(hh, tt));
-      }
     }
   }
   __syncwarp();

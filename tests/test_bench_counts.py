@@ -45,3 +45,32 @@ def test_block_factor_flops_is_the_partial_cholesky_count(seed):
         np.testing.assert_allclose(np.tril(L[:m, :m]), np.linalg.cholesky(M[:m, :m]), rtol=1e-12)
         total += f
     assert bench.block_factor_flops(lp) == total
+
+
+def test_block_factor_roofline_uses_the_update_operand_peak():
+    """With the trailing updates on the tensor cores the block factor is
+    reported against the tensor peak of the updates' operand type (TF32 for
+    FP32 factors: 3 split MMAs per product; FP16 digits for float-float: 21),
+    and with the FP32-pipe updates against the FP32 pipe."""
+    from types import SimpleNamespace
+    lp = random_block_lp(3, N=3, m_sizes=[70, 130, 90], n_sizes=[100, 190, 140], nnz_per_col=3,
+                         n0=2, w_density=0.5, l=[2, 3], mg=1, global_nnz=2)
+    peaks = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0,
+             "source": "test"}
+    _, upd = bench.update_geometry(lp)
+    for name, key, per, ratio in (("FP32", "fp32", 3, bench.TF32_PER_BF16),
+                                  ("float-float", "ff", 21, bench.FP16_PER_BF16)):
+        acc = {"factors_fp32": 0, "ms_block_fp32": 0.0, "factors_ff": 0, "ms_block_ff": 0.0,
+               "factors_fp64": 0, "ms_block_fp64": 0.0}
+        acc[f"factors_{key}"] = 2
+        acc[f"ms_block_{key}"] = 4.0   # 2 ms per factor
+        win = SimpleNamespace(acc=acc)
+        for variant in (0, 2, 3):
+            opts = SimpleNamespace(fp32_update=variant, ff_update=variant)
+            r = bench.roofline(lp, win, peaks, opts)
+            assert r["bound"] == "tensor" and name in r["kernel"]
+            assert r["achieved"] == pytest.approx(per * upd / 2e-3 / 1e12)
+            assert r["peak"] == pytest.approx(1700.0 * ratio)
+            assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+        r = bench.roofline(lp, win, peaks, SimpleNamespace(fp32_update=1, ff_update=1))
+        assert r["bound"] == "alu"
