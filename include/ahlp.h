@@ -210,16 +210,14 @@ typedef struct {
                            trailing updates) for kkt_factor_kernel_times (0) */
   ahlp_iter_cb iter_cb; /* progress callback of ipm_solve, or NULL (NULL)        */
   void   *iter_cb_ctx;  /* passed to iter_cb (NULL)                              */
-  int32_t pivot_mode;   /* pivots of the block factors M_i and of the link
-                           chain's cyclic reduction that fail the pivot_tol
-                           test (cancellation or NaN): 0 = clamp to pivot_tol
-                           times their starting diagonal; 1 = drop: replace by
-                           a huge value, so the row is left out of the factor
-                           (its solution entry ~0, its column ~0) and the
-                           Krylov refinement, which solves the exact Newton
-                           system, sees it unpreconditioned.  The border's
-                           pivots (and those of schur_chain = 1) are always
-                           clamped (0)                                        */
+  int32_t pivot_mode;   /* pivots of the block factors M_i that fail the
+                           pivot_tol test (cancellation or NaN): 0 = clamp to
+                           pivot_tol times their starting diagonal; 1 = drop:
+                           replace by a huge value, so the row is left out of
+                           the factor (its solution entry ~0, its column ~0)
+                           and the Krylov refinement, which solves the exact
+                           Newton system, sees it unpreconditioned.  The Schur
+                           complement's pivots are always clamped (0)        */
 } ahlp_options;
 
 typedef struct ahlp_result_s {

@@ -47,7 +47,6 @@ struct BArgs {
   double *Et;                          // [B][nl]: E' in, Z out
   const double *Td_diag0;
   double tol;
-  double drop;                         // > 0: failing pivots dropped (pivot_fix)
   int *status;
   int B, nl;
 };
@@ -107,16 +106,15 @@ __global__ void __launch_bounds__(kBcrThreads) bcr_factor_kernel(BArgs A) {
         double piv = T[c + c * lj];
         const double orig = A.Td_diag0[A.link_off[j] + c];
         const double lim = A.tol * orig, floor_v = lim > 0.0 ? lim : 1.0;
-        const double repl = A.drop > 0.0 ? A.drop * fmax(orig, 1.0) : floor_v;
         if (!(piv == piv)) {
           if (lane == 0 && atomicAdd(&A.status[0], 1) == 0) {
             A.status[2] = -1 - j;
             A.status[3] = c;
           }
-          piv = repl;
+          piv = floor_v;
         } else if (!(piv > lim) || !(piv > 0.0)) {
           if (lane == 0) atomicAdd(&A.status[1], 1);
-          piv = repl;
+          piv = floor_v;
         }
         const double inv = rsqrt(piv);
         __syncwarp();
@@ -138,7 +136,7 @@ __global__ void __launch_bounds__(kBcrThreads) bcr_factor_kernel(BArgs A) {
     for (int c = 0; c < lj; ++c) {
       if (tid == 0) {
         double piv = T[c + c * lj];
-        pivot_fix(piv, A.Td_diag0[A.link_off[j] + c], A.tol, A.status, -1 - j, c, A.drop);
+        pivot_fix(piv, A.Td_diag0[A.link_off[j] + c], A.tol, A.status, -1 - j, c);
         const double lcc = sqrt(piv);
         T[c + c * lj] = lcc;
         Tinv[c] = 1.0 / lcc;
@@ -358,7 +356,6 @@ BArgs bargs(ahlp_problem *p) {
   A.Et = p->Et;
   A.Td_diag0 = p->Td_diag0;
   A.tol = p->fac_pivot_tol;
-  A.drop = p->opt.pivot_mode == 1 ? kDropFP64 : 0.0;
   A.status = p->status;
   A.B = p->B;
   A.nl = p->nl;
