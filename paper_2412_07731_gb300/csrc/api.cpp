@@ -1082,9 +1082,9 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     p->nfg0 = (long long)fg0i.size();
     p->Bld = (int)round_up(std::max(p->B, 1), 8);
     p->h_bx = BlkInfo{0, 0, 0, p->Bld, p->B, n0, (p->B + NB - 1) / NB, (n0 + NB - 1) / NB,
-                      kTagBorderX, 0, 0};
+                      kTagBorderX, 0, 0, 0};
     p->h_bp = BlkInfo{(long long)n0 * p->Bld + n0, n0, n0, p->Bld, mg, mg, (mg + NB - 1) / NB,
-                      (mg + NB - 1) / NB, kTagBorderG, 0, 0};
+                      (mg + NB - 1) / NB, kTagBorderG, 0, 0, 0};
     // ---- device memory ----------------------------------------------------------
     ck(cudaGetDevice(&p->device), "cudaGetDevice");
     p->b = dupload(p, bgl);

@@ -95,13 +95,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
       : "memory");
 }
 
-// TF32 rounding (round to nearest, ties away) as a 32-bit pattern
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t u;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-  return __uint_as_float(u);
-}
-
 // Shared-memory matrix descriptor of a K-major operand without swizzling:
 // 8-row x 16-byte core matrices, LBO = byte distance between core matrices
 // adjacent in K, SBO = byte distance between adjacent 8-row groups.
