@@ -169,9 +169,7 @@ def stage_rooflines(P, prob, lp, peaks):
                 sum_j 2 (7/3) l_j^3 + 2 (N-1) l^2 B + B^3 / 3, are reported as
                 an FP64 rate;
       apply  -- HBM: the FP32 block factors read twice (forward and backward
-                wavefront solves);
-      refine_spmv -- HBM: one Newton-matrix product with its residual and norms
-                (kkt_residual_noalloc), 2 nnz(A) x 12 bytes of A and A'."""
+                wavefront solves)."""
     import numpy as np
     import torch
     from paper_2412_07731_gb300 import _lib as L
@@ -197,33 +195,6 @@ def stage_rooflines(P, prob, lp, peaks):
             sol.append(P.kkt_stage_times(prob)["last_solve_ms"])
     finally:
         P.set_options(prob, saved)
-    # one Newton-matrix product (the refinement's SpMV pair) at this point
-    spmv = None
-    try:
-        from paper_2412_07731_gb300._lib import kkt_residual_noalloc
-        n, m = prob.n, prob.m
-        d = [torch.tensor(rng.standard_normal(k), **f64) for k in (n, m, n, n, m, n)]
-        out = torch.zeros(1, **f64)
-        stream = torch.cuda.current_stream()
-        kkt_residual_noalloc(prob, *d, out)   # first call: symbol lookup
-        ts = []
-        for _ in range(5):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            kkt_residual_noalloc(prob, *d, out)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        nnz = sum(int(a.nnz) for a in _blocks_A(lp))
-        sp_bytes = 2 * nnz * 12
-        sp_ms = statistics.median(ts[1:])
-        spmv = {"ms": sp_ms, "bound": "hbm", "bytes": sp_bytes,
-                "achieved_gbs": sp_bytes / (sp_ms / 1e3) / 1e9,
-                "frac": sp_bytes / (sp_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                "note": "kkt_residual_noalloc: J d - r with A and A' products, norms"}
-    except Exception as exc:   # reported, never fatal to the bench line
-        spmv = {"error": str(exc)[:200]}
     med = lambda v: statistics.median(v[1:])  # noqa: E731
     form_ms = med([f["form_ms"] for f in fac])
     block_ms = med([f["block_factor_ms"] for f in fac])
@@ -255,18 +226,11 @@ def stage_rooflines(P, prob, lp, peaks):
         "block_factor": block_stage,
         "schur_factor": dict({"ms": schur_ms, "bound": "FP64 latency, cyclic reduction levels"},
                              **schur_rate(lp, schur_ms)),
-        "refine_spmv": spmv,
         "apply": {"ms": apply_ms, "bound": "hbm", "bytes": apply_bytes,
                   "achieved_gbs": gbs(apply_bytes, apply_ms),
                   "frac": gbs(apply_bytes, apply_ms) / hbm},
         "peaks": {"hbm_gbs": hbm, "fp32_tflops": FP32_PEAK_TFLOPS},
     }
-
-
-def _blocks_A(lp):
-    """The A_i of every LP of a workload (one LP or a batch)."""
-    for q in _blocks(lp):
-        yield from q.A
 
 
 def schur_rate(lp, ms):
