@@ -266,7 +266,8 @@ def random_block_lp(seed: int, N: int, m_sizes, n_sizes, nnz_per_col: int, n0: i
     N(0,1) entries (w_density = 1 gives dense columns).  l: local link rows per
     adjacent pair (int or array of N-1); each link row has link_nnz[0] entries in
     the left block and link_nnz[1] in the right one.  mg global rows with
-    global_nnz entries per block.  plant: "half_zero", "nondegenerate" or None.
+    global_nnz entries per block.  plant: "half_zero", "nondegenerate" (small
+    instances: dense basis check), "basis_blocks" (large instances) or None.
     """
     rng = np.random.default_rng(seed)
     m_sizes = np.asarray(m_sizes, dtype=np.int64)
@@ -317,6 +318,8 @@ def random_block_lp(seed: int, N: int, m_sizes, n_sizes, nnz_per_col: int, n0: i
         plant_half_zero(lp, rng)
     elif plant == "nondegenerate":
         plant_nondegenerate(lp, rng)
+    elif plant == "basis_blocks":
+        plant_basis_blocks(lp, rng)
     elif plant is None:
         pass
     else:
@@ -352,6 +355,62 @@ def plant_nondegenerate(lp: BlockLP, rng: np.random.Generator):
     lp.basis = B
 
 
+def plant_basis_blocks(lp: BlockLP, rng: np.random.Generator):
+    """Nondegenerate plant for large block LPs, with a basis built block by block.
+
+    Basic columns: per block i, the m_i columns that a maximum bipartite
+    matching of A_i's rows to its randomly permuted columns assigns (so
+    A_i[:, B_i] is structurally nonsingular); per local link row and per
+    global row, one further column of that row's own support that is not
+    basic yet (a random nonbasic column of the blocks it touches if its
+    support is used up); the linking variables x_0 stay nonbasic.  So |B| =
+    m, A_B has a perfect row-to-column matching, and x*_B, z*_N ~ U(0.1, 1),
+    y* ~ N(0, 1) is the unique, strictly complementary optimum whenever A_B
+    is numerically nonsingular (tests check it by a sparse LU with a
+    condition estimate).
+    """
+    from scipy.sparse.csgraph import maximum_bipartite_matching
+    N = lp.N
+    xo = lp.x_offsets()
+    n, m = lp.n_total, lp.m_total
+    basic = np.zeros(n, dtype=bool)
+    for i in range(N):
+        mi, ni = lp.A[i].shape
+        perm = rng.permutation(ni)
+        Ap = sp.csr_matrix(sp.csc_matrix(lp.A[i])[:, perm])
+        match = maximum_bipartite_matching(Ap, perm_type="column")   # row -> column
+        if np.any(match < 0):
+            raise RuntimeError(f"block {i}: A_i has no full row matching")
+        basic[xo[i] + perm[match]] = True
+
+    def one_more(cands, blocks):
+        cands = [c for c in cands if not basic[c]]
+        if not cands:
+            cands = [c for b in blocks for c in range(xo[b], xo[b + 1]) if not basic[c]]
+        basic[cands[rng.integers(len(cands))]] = True
+
+    for j in range(N - 1):
+        FL, FR = sp.csr_matrix(lp.FL[j]), sp.csr_matrix(lp.FR[j])
+        for r in range(int(lp.l[j])):
+            cands = [xo[j] + int(c) for c in FL[r].indices] + \
+                    [xo[j + 1] + int(c) for c in FR[r].indices]
+            one_more(cands, (j, j + 1))
+    for g in range(lp.mg):
+        cands = []
+        for i in range(N):
+            Fg = sp.csr_matrix(lp.Fg[i])
+            cands += [xo[i] + int(c) for c in Fg[g].indices]
+        one_more(cands, tuple(range(N)))
+    assert int(basic.sum()) == m, (int(basic.sum()), m)
+    x = np.zeros(n)
+    z = rng.uniform(0.1, 1.0, n)
+    x[basic] = rng.uniform(0.1, 1.0, m)
+    z[basic] = 0.0
+    y = rng.standard_normal(m)
+    _set_rhs_from_plant(lp, x, y, z)
+    lp.basis = np.flatnonzero(basic)
+
+
 def _assemble_for_rank(lp: BlockLP) -> sp.csc_matrix:
     """Column-by-column image of the unit vectors (basis drawing only)."""
     n = lp.n_total
@@ -381,19 +440,22 @@ def config1(seed: int = 1, N: int = 64) -> BlockLP:
 
 
 def config2(seed: int = 2, N: int = 512, nondegenerate: bool = False) -> BlockLP:
-    """Uneven blocks: m_i ~ U{500..4000}, n_i = floor(1.5 m_i), n0=100 at 5%, l=16."""
+    """Uneven blocks: m_i ~ U{500..4000}, n_i = floor(1.5 m_i), n0=100 at 5%, l=16.
+    nondegenerate: a unique optimal basis built block by block (plant_basis_blocks)
+    instead of the half-zero complementary split."""
     rng = np.random.default_rng(seed + 1000)
     m = rng.integers(500, 4001, size=N)
     n = (3 * m) // 2
     return random_block_lp(seed, N=N, m_sizes=m, n_sizes=n, nnz_per_col=8, n0=100,
                            w_density=0.05, l=16, link_nnz=(5, 5), mg=0,
-                           plant="nondegenerate" if nondegenerate else "half_zero",
+                           plant="basis_blocks" if nondegenerate else "half_zero",
                            name=f"C2 N={N} uneven 500..4000 n0=100 l=16")
 
 
 def config4(seed: int = 4, N: int = 128):
-    """16 independent LPs of the uneven shape with N=128 (seeds seed..seed+15)."""
-    return [config2(seed + k, N=N) for k in range(16)]
+    """16 independent LPs of the uneven shape with N=128 (seeds seed..seed+15),
+    each with a nondegenerate planted optimum (unique optimal basis)."""
+    return [config2(seed + k, N=N, nondegenerate=True) for k in range(16)]
 
 
 def config3(seed: int = 3, days: int = 365, nodes: int = 30, hours: int = 24,
