@@ -504,11 +504,23 @@ __device__ __forceinline__ void ff_renorm(float &sh, float &sl) {
   sh = h;
 }
 
-// hi + lo -> FP64 copy of the float-float factor, used by the solves
+// hi + lo -> FP64 copy of the float-float factor, used by the solves; four
+// entries per thread and step (16-byte loads of each word, two 16-byte
+// stores; the buffers are cudaMalloc-aligned), the last n % 4 one by one
 __global__ void ff_expand_kernel(const float *__restrict__ hi, const float *__restrict__ lo,
                                  double *__restrict__ out, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
+  const long long n4 = n / 4;
+  const float4 *h4 = reinterpret_cast<const float4 *>(hi);
+  const float4 *l4 = reinterpret_cast<const float4 *>(lo);
+  double2 *o2 = reinterpret_cast<double2 *>(out);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const float4 h = __ldcs(h4 + i), l = __ldcs(l4 + i);
+    __stcs(o2 + 2 * i, make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y));
+    __stcs(o2 + 2 * i + 1, make_double2((double)h.z + (double)l.z, (double)h.w + (double)l.w));
+  }
+  for (long long i = 4 * n4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += stride)
     out[i] = (double)hi[i] + (double)lo[i];
 }
 
