@@ -17,6 +17,9 @@ Modules
            App. A Schur block structure and the Observation-1 nnz bound
   vertex   brute-force vertex enumeration for tiny LPs
   adjoint  transposed Newton solve for implicit differentiation
+  general  the full LP statement of Sec. 3.2 (inequality rows, bounds of every
+           kind) reduced to the standard form by textbook transformations,
+           solved by ipm and mapped back
 
 Every function is pinned by a test in tests/test_oracle_*.py against something
 other than itself (brute force, planted optima, library routines, closed forms).
