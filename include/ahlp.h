@@ -161,7 +161,8 @@ typedef struct {
                            it x100 (up to 1e-8) when a direction's residual
                            stays above 1e-6 or a NaN appears, once the block
                            factors are FP64                                      */
-  int32_t verbose;      /* 0: silent                                              */
+  int32_t verbose;      /* 0: silent; 1: one line per IPM iteration; 2: also the
+                           Krylov residual estimate of every refinement step */
   int32_t max_correctors; /* multiple centrality correctors per iteration, each
                            one more solve with the same factor, tried while the
                            step length stays below 0.9 (4; 0..8); see

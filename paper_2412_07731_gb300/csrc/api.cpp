@@ -1614,6 +1614,9 @@ int solve_impl(ahlp_problem *p, const double *rd, const double *rp, const double
       g[j + 1] = -sn[j] * g[j];
       g[j] = cs[j] * g[j];
       ++j;
+      if (p->opt.verbose >= 2)
+        printf("         krylov step %d  residual estimate %.3e\n", steps + j,
+               std::fabs(g[j]) / (rn > 0 ? rn : 1.0));
       if (!(std::fabs(g[j]) > tol * rn) || !(hn > 1e-300 * en)) break;
     }
     // y = R^-1 g, d += Z y
