@@ -219,6 +219,13 @@ typedef struct {
                            and the Krylov refinement, which solves the exact
                            Newton system, sees it unpreconditioned.  The Schur
                            complement's pivots are always clamped (0)        */
+  int32_t tile_sparse;  /* 1: the tensor-core trailing updates skip the tile
+                           jobs whose product is structurally zero (a tile-level
+                           symbolic factorisation of each block's augmented
+                           matrix, from its formation pattern); the factor is
+                           bitwise the same, banded blocks cost less.  0: every
+                           tile pair of the trailing triangle.  Read when a
+                           handle first factors on the tensor cores (1)       */
 } ahlp_options;
 
 typedef struct ahlp_result_s {

@@ -55,7 +55,8 @@ class Options(C.Structure):
                 ("fp32_update", C.c_int32), ("ff_update", C.c_int32),
                 ("schur_chain", C.c_int32), ("profile_kernels", C.c_int32),
                 ("iter_cb", C.c_void_p),
-                ("iter_cb_ctx", C.c_void_p), ("pivot_mode", C.c_int32)]
+                ("iter_cb_ctx", C.c_void_p), ("pivot_mode", C.c_int32),
+                ("tile_sparse", C.c_int32)]
 
 
 class Result(C.Structure):

@@ -249,6 +249,13 @@ struct ahlp_problem {
   bool oz_ready = false;
   void *oz_tmap = nullptr;           // [2N] CUtensorMap: each block's hi, then lo matrix
   int ff_update = 0;                 // trailing update of float-float factors: 1 FP32 pipe, 2 tensor cores
+  // per block, T x T: lower tile (I, J) of the formed augmented matrix has entries
+  std::vector<std::vector<unsigned char>> tile_nz;
+  // tile-sparse update jobs (option tile_sparse): per step, the kept jobs of the
+  // dense enumeration as {block, I0, J, has_i1}; nullptr = the dense triangle
+  int4 *tc_jtab = nullptr;
+  std::vector<long long> tc_jtab_off;
+  long long tc_jobs_dense = 0, tc_jobs_kept = 0;
   int fp32_update = 0;               // trailing update of FP32 factors: 1 SIMT, 2 tensor
                                      // cores (one CTA per job), 3 tensor cores (persistent
                                      // warp-specialised pipeline)

@@ -170,6 +170,7 @@ struct Con {
 };
 
 struct Pattern {
+  std::vector<unsigned char> nz;     // T x T (row I, column J <= I): the tile has entries
   std::vector<FormTile> tiles;
   std::vector<long long> tile_ent;   // entry begin per tile (absolute)
   std::vector<int> ent_pos;
@@ -281,11 +282,13 @@ void build_block_pattern(int blk, const Csc &A, const Csc &W, const std::vector<
   }
   // tiles in id order (J-major lower), entries grouped by key
   size_t c = 0;
+  P.nz.assign((size_t)T * T, 0);
   for (int Jt = 0; Jt < T; ++Jt)
     for (int It = Jt; It < T; ++It) {
       const long long id = tile_id(It, Jt);
       P.tiles.push_back({blk, It, Jt, 0});
       P.tile_ent.push_back((long long)P.ent_pos.size());
+      if (c < cons.size() && cons[c].key / (NB * NB) == id) P.nz[(size_t)It * T + Jt] = 1;
       while (c < cons.size() && cons[c].key / (NB * NB) == id) {
         const long long key = cons[c].key;
         const int within = (int)(key % (NB * NB));
@@ -335,6 +338,7 @@ void ahlp_default_options(ahlp_options *o) {
   o->iter_cb = nullptr;
   o->iter_cb_ctx = nullptr;
   o->pivot_mode = 0;
+  o->tile_sparse = 1;
 }
 
 const char *ahlp_status_string(int s) {
@@ -396,7 +400,7 @@ static int check_options(const ahlp_options &o, std::string &err) {
       (o.correctors_by_cost != 0 && o.correctors_by_cost != 1) || o.fp32_update < 0 ||
       o.fp32_update > 3 || o.ff_update < 0 || o.ff_update > 3 || o.schur_chain < 0 ||
       o.schur_chain > 1 || o.profile_kernels < 0 || o.profile_kernels > 1 ||
-      o.pivot_mode < 0 || o.pivot_mode > 1) {
+      o.pivot_mode < 0 || o.pivot_mode > 1 || o.tile_sparse < 0 || o.tile_sparse > 1) {
     err = "invalid option value";
     return AHLP_ERR_INVALID_ARG;
   }
@@ -980,6 +984,7 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     // thread count.  A failure reports the first failing block, as a
     // sequential pass would.
     std::vector<Pattern> part(N);
+    p->tile_nz.assign(N, {});
     std::vector<int> pcode(N, 0);
     std::vector<std::string> pmsg(N);
     auto one_block = [&](int i) {
@@ -1022,6 +1027,7 @@ int arrowhead_lp_create(const ahlp_desc *descs, int32_t batch, const ahlp_option
     std::vector<long long> tb(N + 1, 0), eb(N + 1, 0), cb(N + 1, 0);
     for (int i = 0; i < N; ++i) {
       tb[i + 1] = tb[i] + (long long)part[i].tiles.size();
+      p->tile_nz[i] = std::move(part[i].nz);
       eb[i + 1] = eb[i] + (long long)part[i].ent_pos.size();
       cb[i + 1] = cb[i] + (long long)part[i].con_idx.size();
     }

@@ -32,6 +32,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdio>
 
 #include "ahlp_internal.h"
 
@@ -168,7 +169,16 @@ struct Job {
 };
 
 __device__ __forceinline__ Job decode_job(const int *joff, int nblk, int k, const BlkInfo *blk,
-                                          int q) {
+                                          int q, const int4 *jt) {
+  if (jt) {   // tile-sparse: the kept jobs of this step, in the dense order
+    const int4 v = jt[q];
+    Job j;
+    j.b = v.x;
+    j.I0 = v.y;
+    j.J = v.z;
+    j.has_i1 = v.w != 0;
+    return j;
+  }
   int lo = 0, hi = nblk;   // joff[lo] <= q < joff[hi]
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -195,6 +205,7 @@ struct TcArgs {
   const CUtensorMap *tmap; // [nblk] each block's FP32 augmented matrix
   int nblk, k;
   int *status;             // status[4] := 1 when a bounded wait ran out
+  const int4 *jt;          // this step's tile-sparse job table, or nullptr
 };
 
 __global__ void __launch_bounds__(kTcThreads) pchol_update_tc_kernel(const TcArgs args) {
@@ -211,7 +222,7 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_tc_kernel(const TcArg
   float *b_lo = reinterpret_cast<float *>(base + 2 * kSmemA + kSmemB);
 
   // ---- which block and tiles ------------------------------------------------
-  const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk, blockIdx.x);
+  const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk, blockIdx.x, args.jt);
   const int b = jb.b, I0 = jb.I0, J = jb.J;
   const bool has_i1 = jb.has_i1;
   const BlkInfo bi = args.blk[b];
@@ -394,7 +405,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) pchol_update_tc2_kernel(const 
           break;
         }
         const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk,
-                                  (int)blockIdx.x + j * (int)gridDim.x);
+                                (int)blockIdx.x + j * (int)gridDim.x, args.jt);
         const BlkInfo bi = args.blk[jb.b];
         const float *st0 = args.stage + (bi.soff + jb.I0) * 8192LL;
         const float *stJ = args.stage + (bi.soff + jb.J) * 8192LL;
@@ -476,7 +487,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) pchol_update_tc2_kernel(const 
         break;
       }
       const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk,
-                                (int)blockIdx.x + j * (int)gridDim.x);
+                                (int)blockIdx.x + j * (int)gridDim.x, args.jt);
       const int grow = jb.I0 * NB + r;
 #pragma unroll
       for (int h = 0; h < 2; ++h)
@@ -595,6 +606,7 @@ struct OzArgs {
   int nblk, k;
   int *status;
   float *hi, *lo;          // the augmented matrices' words (persistent kernel)
+  const int4 *jt;          // this step's tile-sparse job table, or nullptr
 };
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, int x, int y,
@@ -625,7 +637,7 @@ __global__ void __launch_bounds__(kTcThreads) pchol_update_oz_kernel(const OzArg
   float *c_hi = reinterpret_cast<float *>(base + kOzQ * kOzPlaneA + kOzQ * kOzPlaneB);
   float *c_lo = c_hi + kTcM * kTcN;
 
-  const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk, blockIdx.x);
+  const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk, blockIdx.x, args.jt);
   const int b = jb.b, I0 = jb.I0, J = jb.J;
   const bool has_i1 = jb.has_i1;
   const BlkInfo bi = args.blk[b];
@@ -868,7 +880,7 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
         }
         if (h == 0) {   // next job: its C tile towards L2 ahead of the epilogue's loads
           jb = decode_job(args.joff, args.nblk, args.k, args.blk,
-                          (int)blockIdx.x + j * (int)gridDim.x);
+                                (int)blockIdx.x + j * (int)gridDim.x, args.jt);
           const CUtensorMap *th = args.tmap + jb.b, *tl = args.tmap + args.nblk + jb.b;
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(th) : "memory");
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tl) : "memory");
@@ -943,7 +955,7 @@ __global__ void __launch_bounds__(kOz2Threads, 1) pchol_update_oz2_kernel(const 
     float *cs = reinterpret_cast<float *>(base + kOz2Stages * kOz2Stage + (warp - 2) * 8192);
     for (int j = 0; j < myjobs; ++j) {
       const Job jb = decode_job(args.joff, args.nblk, args.k, args.blk,
-                                (int)blockIdx.x + j * (int)gridDim.x);
+                                (int)blockIdx.x + j * (int)gridDim.x, args.jt);
       const BlkInfo bi = args.blk[jb.b];
       const long long slot0 = bi.soff + jb.I0, slotJ = bi.soff + jb.J;
       const int row0 = jb.I0 * NB + quarter * 32;   // first row of the warp's quarter
@@ -1059,8 +1071,74 @@ void jobs_setup(ahlp_problem *p) {
     }
     joff[(size_t)k * (N + 1) + N] = (int)acc;
     p->tc_jobs[k] = acc;
+    p->tc_jobs_dense += acc;
   }
   p->tc_joff = static_cast<int *>(dupload_bytes(p, joff.data(), joff.size() * sizeof(int)));
+  p->tc_jobs_kept = p->tc_jobs_dense;
+  if (!p->opt.tile_sparse || (int)p->tile_nz.size() != N) return;
+  // Tile-sparse jobs.  A tile-level symbolic factorisation of each block's
+  // augmented matrix: tile (I, J) of L is nonzero if the formed matrix has
+  // entries there or if some pivot step k < J has nonzero tiles (I, k) and
+  // (J, k) (right-looking fill).  The update of step k adds L_Ik L_Jk' to the
+  // tile pair's rows and column J; a job whose two row tiles are both zero in
+  // column k, or whose column tile J is, adds exact zeros and is left out.
+  // The kept jobs stay in the dense enumeration's order (block, row pair,
+  // column), so the CTAs that run them and the factor are the same.
+  std::vector<std::vector<unsigned char>> L(N);
+  for (int b = 0; b < N; ++b) {
+    const BlkInfo &bi = p->h_blk[b];
+    const int T = bi.T;
+    L[b] = p->tile_nz[b];
+    if ((int)L[b].size() != T * T) {   // no pattern: every tile counts as nonzero
+      L[b].assign((size_t)T * T, 1);
+      continue;
+    }
+    bool dense = true;
+    for (int I = 0; I < T && dense; ++I)
+      for (int J = 0; J <= I; ++J)
+        if (!L[b][(size_t)I * T + J]) {
+          dense = false;
+          break;
+        }
+    if (dense) continue;
+    std::vector<int> rows;
+    for (int k = 0; k < bi.Tp; ++k) {
+      rows.clear();
+      for (int I = k + 1; I < T; ++I)
+        if (L[b][(size_t)I * T + k]) rows.push_back(I);
+      for (size_t x = 0; x < rows.size(); ++x)
+        for (size_t y = 0; y <= x; ++y) L[b][(size_t)rows[x] * T + rows[y]] = 1;
+    }
+  }
+  std::vector<int4> tab;
+  p->tc_jtab_off.assign(maxTp + 1, 0);
+  long long kept = 0;
+  for (int k = 0; k < maxTp; ++k) {
+    p->tc_jtab_off[k] = (long long)tab.size();
+    for (int b = 0; b < N; ++b) {
+      const BlkInfo &bi = p->h_blk[b];
+      if (k >= bi.Tp) continue;
+      const int T = bi.T, t = T - k - 1;
+      const unsigned char *Lb = L[b].data();
+      for (int R = 0; 2 * R < t; ++R) {
+        const int I0 = k + 1 + 2 * R;
+        const bool has_i1 = 2 * R + 1 < t;
+        if (!Lb[(size_t)I0 * T + k] && !(has_i1 && Lb[(size_t)(I0 + 1) * T + k])) continue;
+        const int jend = k + std::min(2 * R + 2, t);
+        for (int J = k + 1; J <= jend; ++J)
+          if (Lb[(size_t)J * T + k]) tab.push_back(make_int4(b, I0, J, has_i1 ? 1 : 0));
+      }
+    }
+    p->tc_jobs[k] = (long long)tab.size() - p->tc_jtab_off[k];
+    kept += p->tc_jobs[k];
+  }
+  p->tc_jtab_off[maxTp] = (long long)tab.size();
+  p->tc_jobs_kept = kept;
+  if (p->opt.verbose)
+    printf("       tile-sparse trailing updates: %lld of %lld tile jobs kept\n", kept,
+           p->tc_jobs_dense);
+  if (!tab.empty())
+    p->tc_jtab = static_cast<int4 *>(dupload_bytes(p, tab.data(), tab.size() * sizeof(int4)));
 }
 
 }  // namespace
@@ -1118,7 +1196,7 @@ cudaError_t launch_update_tc(ahlp_problem *p, int k, cudaStream_t s) {
   if (jobs <= 0) return cudaSuccess;
   TcArgs a{p->pstage, p->tc_joff + (size_t)k * (p->h_blk.size() + 1), p->blk,
            reinterpret_cast<const CUtensorMap *>(p->tc_tmap), (int)p->h_blk.size(), k,
-           p->status};
+           p->status, p->tc_jtab ? p->tc_jtab + p->tc_jtab_off[k] : nullptr};
   if (p->fp32_update == 3) {   // persistent pipeline: one CTA per SM
     const int grid = (int)std::min<long long>(jobs, p->num_sms);
     count_launch(), pchol_update_tc2_kernel<<<grid, kTc2Threads, kTc2Smem, s>>>(a, (int)jobs);
@@ -1182,7 +1260,8 @@ cudaError_t launch_update_oz(ahlp_problem *p, int k, cudaStream_t s) {
   if (jobs <= 0) return cudaSuccess;
   OzArgs a{p->dstage, p->dexp, p->tc_joff + (size_t)k * (p->h_blk.size() + 1), p->blk,
            reinterpret_cast<const CUtensorMap *>(p->oz_tmap), (int)p->h_blk.size(), k,
-           p->status, p->aug32, p->aug_lo};
+           p->status, p->aug32, p->aug_lo,
+           p->tc_jtab ? p->tc_jtab + p->tc_jtab_off[k] : nullptr};
   if (p->ff_update == 3) {   // persistent pipeline: one CTA per SM
     const int grid = (int)std::min<long long>(jobs, p->num_sms);
     count_launch(), pchol_update_oz2_kernel<<<grid, kOz2Threads, kOz2Smem, s>>>(a, (int)jobs);
