@@ -1137,7 +1137,9 @@ void jobs_setup(ahlp_problem *p) {
   if (p->opt.verbose)
     printf("       tile-sparse trailing updates: %lld of %lld tile jobs kept\n", kept,
            p->tc_jobs_dense);
-  if (!tab.empty())
+  // Nothing left out (every block tile-dense): the kernels keep decoding the
+  // dense enumeration and no table is uploaded.
+  if (kept < p->tc_jobs_dense && !tab.empty())
     p->tc_jtab = static_cast<int4 *>(dupload_bytes(p, tab.data(), tab.size() * sizeof(int4)));
 }
 
