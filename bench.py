@@ -207,7 +207,7 @@ def stage_rooflines(P, prob, lp, peaks):
     gbs = lambda b, ms: b / (ms / 1e3) / 1e9  # noqa: E731
     hbm = peaks["hbm_gbs"]
     if saved.fp32_update in (0, 2, 3):   # TF32 split products on the tensor cores
-        _, upd_flops = update_geometry(lp)
+        _, upd_flops = update_geometry(lp, jobs=P.kkt_update_jobs(prob))
         tpeak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
         ach = 3 * upd_flops / (block_ms / 1e3) / 1e12
         block_stage = {"ms": block_ms, "bound": "tensor (TF32, 3 MMAs per product)",
@@ -563,12 +563,31 @@ def full_solve(P, prob, out, planted):
             "ms_factor": r["ms_factor"], "ms_solve": r["ms_solve"]}
 
 
-def update_geometry(lp, NB=64):
+def update_geometry(lp, NB=64, jobs=None):
     """(lower-triangle entries the trailing updates read and write, summed over
     the steps; their flops) of one batched partial Cholesky: at step k a block
     with T tiles and Tp pivot tiles updates the lower triangle of its trailing
     (a - 64(k+1))-order matrix with the 64 pivot columns of step k (fewer at
-    a ragged last pivot tile)."""
+    a ragged last pivot tile).  jobs = (kept, dense) tile jobs of the
+    tensor-core updates: when the tile-sparse enumeration leaves jobs out,
+    both figures are scaled by the kept fraction (jobs of one workload have
+    nearly equal sizes; the triangle's diagonal jobs are smaller)."""
+    frac = jobs[0] / jobs[1] if jobs and jobs[1] and jobs[0] < jobs[1] else 1.0
+    elems, flops = _update_geometry_dense(lp, NB)
+    return elems * frac, flops * frac
+
+
+def tile_sparse_note(jobs):
+    """The roofline's record of the tile-sparse enumeration, or None when
+    every tile job ran."""
+    if not jobs or not jobs[1] or jobs[0] >= jobs[1]:
+        return None
+    return {"jobs_kept": jobs[0], "jobs_dense": jobs[1],
+            "note": "structurally zero tile products left out; algorithmic bytes and "
+                    "flops scaled by the kept fraction"}
+
+
+def _update_geometry_dense(lp, NB):
     elems = flops = 0.0
     for q in _blocks(lp):
         for i, A in enumerate(q.A):
@@ -592,11 +611,14 @@ def update_geometry(lp, NB=64):
 # 8-block workload, whose trailing matrices partly fit L2):
 # pchol_update_tc_c1small.md (per-tile TF32), pchol_update_tc2_c1small.md
 # (persistent TF32), pchol_update_oz2_c1small.md (persistent digits).  The
-# live bench scales them by the bytes of its own launches to fill
-# roofline.traffic; a kernel without a capture of its current code reports
-# null.
-UPDATE_TRAFFIC_PER_BYTE = {("FP32", 2): 0.68, ("FP32", 3): 0.70, ("float-float", 2): None,
-                           ("float-float", 3): 0.88}
+# live bench scales them by the bytes of its own launches.  Those captures
+# predate the kernels' job-table argument (tile-sparse updates; a dense
+# workload passes none and reads no table), so roofline.traffic is null and
+# the scaled figure goes to traffic_at_last_capture.  UPDATE_TRAFFIC_PER_BYTE
+# holds captures of the current kernel code only.
+UPDATE_TRAFFIC_AT_LAST_CAPTURE = {("FP32", 2): 0.68, ("FP32", 3): 0.70,
+                                  ("float-float", 3): 0.88}
+UPDATE_TRAFFIC_PER_BYTE = {}
 UPDATE_KERNEL = {("FP32", 1): "pchol_update_f32_kernel (FP32 pipe)",
                  ("FP32", 2): "pchol_update_tc_kernel (tcgen05, one CTA per tile)",
                  ("FP32", 3): "pchol_update_tc2_kernel (tcgen05, persistent)",
@@ -633,8 +655,10 @@ def kernel_roofline(P, prob, lp, x, z, prec_name, peaks):
         P.set_options(prob, saved)
     med = lambda key: statistics.median([t[key] for t in times[1:]])  # noqa: E731
     upd_ms, launches = med("update_ms"), med("update_launches")
-    elems, flops = update_geometry(lp)
+    jobs = P.kkt_update_jobs(prob)
     variant = (saved.fp32_update if prec_name == "FP32" else saved.ff_update) or 2
+    tensor_upd = prec_name != "FP64" and variant in (2, 3)
+    elems, flops = update_geometry(lp, jobs=jobs if tensor_upd else None)
     out = {"kernel": f"trailing update of the {prec_name} block factor: "
                      f"{UPDATE_KERNEL.get((prec_name, variant), 'FP64 pipe')}",
            "launches": launches,
@@ -650,6 +674,15 @@ def kernel_roofline(P, prob, lp, x, z, prec_name, peaks):
     bytes_ = 2.0 * word * elems
     gbs = bytes_ / (upd_ms / 1e3) / 1e9
     ratio = UPDATE_TRAFFIC_PER_BYTE.get((prec_name, variant))
+    last = UPDATE_TRAFFIC_AT_LAST_CAPTURE.get((prec_name, variant))
+    if last and not ratio:
+        out["traffic_at_last_capture"] = {
+            "bytes": last * bytes_ / launches,
+            "note": "ncu DRAM bytes per algorithmic byte of the kernel's previous code "
+                    "(before its job-table argument), scaled to this launch"}
+    sparse = tile_sparse_note(jobs) if tensor_upd else None
+    if sparse:
+        out["tile_sparse"] = sparse
     out.update({"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / peaks["hbm_gbs"],
                 "traffic": ratio * bytes_ / launches if ratio else None,
@@ -669,7 +702,7 @@ TF32_PER_BF16 = 1.1 / 2.25
 FP16_PER_BF16 = 1.0
 
 
-def roofline(lp, win, peaks, opts=None):
+def roofline(lp, win, peaks, opts=None, jobs=None):
     """The batched block partial Cholesky in the precision whose factors took
     the most time in the timed window; achieved = its algorithmic flops per
     factor / its mean CUDA-event time per factor.  When its trailing updates
@@ -698,19 +731,23 @@ def roofline(lp, win, peaks, opts=None):
         variant = (opts.fp32_update if name == "FP32" else
                    opts.ff_update if name == "float-float" else None)
     if variant in (0, 2, 3):   # tensor-core trailing updates
-        _, upd_flops = update_geometry(lp)
+        _, upd_flops = update_geometry(lp, jobs=jobs)
         per, ratio, op = ((3, TF32_PER_BF16, "TF32") if name == "FP32" else
                           (21, FP16_PER_BF16, "FP16"))
         tpeak = peaks["bf16_tflops_sustained"] * ratio
         achieved = per * upd_flops / (ms / 1e3) / 1e12
-        return {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
-                "frac": achieved / tpeak, "traffic": None,
-                "kernel": f"batched block partial Cholesky ({name}; diagonal tile, panel, "
-                          f"trailing update on the tensor cores as {per} {op} MMAs per "
-                          f"product), {flops:.4g} flop per factor, {ms:.2f} ms",
-                "peak_source": f"{peaks['source']} sustained BF16 peak x {ratio:.3f} "
-                               f"(nominal {op}:BF16 dense ratio)",
-                "fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12}
+        out = {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
+               "frac": achieved / tpeak, "traffic": None,
+               "kernel": f"batched block partial Cholesky ({name}; diagonal tile, panel, "
+                         f"trailing update on the tensor cores as {per} {op} MMAs per "
+                         f"product), {flops:.4g} flop per factor, {ms:.2f} ms",
+               "peak_source": f"{peaks['source']} sustained BF16 peak x {ratio:.3f} "
+                              f"(nominal {op}:BF16 dense ratio)",
+               "fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12}
+        sparse = tile_sparse_note(jobs)
+        if sparse:
+            out["tile_sparse"] = sparse
+        return out
     if name == "float-float":
         achieved = flops / 2.0 * FF_FP32_OPS_PER_MAC / (ms / 1e3) / 1e12
         extra = {"fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12}
@@ -768,7 +805,7 @@ def run_ours(args):
     prob, win, ms, full = arm(headline, args.warmup, args.steps)
     value = world * args.steps / (ms / 1e3)
     summ = window_summary(win, ms, args.steps)
-    factor_roof = roofline(lp, win, peaks, prob.options)
+    factor_roof = roofline(lp, win, peaks, prob.options, P.kkt_update_jobs(prob))
     roof = None
     if factor_roof is not None and rank == 0:
         # the dominant kernel: the trailing update of the block factor in the

@@ -462,6 +462,14 @@ int64_t ahlp_launch_count(void);
  * profile_kernels was set for that factor. */
 int kkt_factor_kernel_times(const ahlp_problem *p, double *ms3, int64_t *launches3);
 
+/* Diagnostic: the tile jobs one block partial Cholesky gives its tensor-core
+ * trailing updates, summed over the pivot steps: *kept those it runs (fewer
+ * than *dense when the option tile_sparse leaves out structurally zero tile
+ * products), *dense every (block, row-tile pair, column tile) of the dense
+ * enumeration.  Both 0 until the handle's first tensor-core factor.  Either
+ * pointer may be NULL. */
+int kkt_update_jobs(const ahlp_problem *p, int64_t *kept, int64_t *dense);
+
 /* Diagnostic: bytes this handle has copied host -> device and device -> host
  * since arrowhead_lp_create (the problem upload included; scalars read back
  * by the solvers included).  Either pointer may be NULL. */

@@ -22,6 +22,7 @@ from ._lib import (  # noqa: F401
     kkt_schur_dense,
     kkt_solve,
     kkt_stage_times,
+    kkt_update_jobs,
     launch_count,
     transfer_bytes,
     lib_path,

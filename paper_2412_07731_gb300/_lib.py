@@ -85,7 +85,8 @@ EXPORTS = ["ahlp_default_options", "ahlp_status_string", "arrowhead_lp_create",
            "kkt_adjoint_solve", "ipm_solve", "kkt_schur_dense", "kkt_stage_times",
            "ahlp_launch_count", "kkt_residual_noalloc", "kkt_block_factor_dense",
            "ahlp_transfer_bytes", "arrowhead_lp_set_cb", "kkt_factor_kernel_times",
-           "arrowhead_lp_recover", "arrowhead_lp_original_size", "arrowhead_lp_autotune"]
+           "arrowhead_lp_recover", "arrowhead_lp_original_size", "arrowhead_lp_autotune",
+           "kkt_update_jobs"]
 
 
 def kkt_block_factor_dense(prob, block: int):
@@ -184,6 +185,13 @@ def kkt_factor_kernel_times(prob):
             "diag_launches": n[0], "panel_launches": n[1], "update_launches": n[2]}
 
 
+def kkt_update_jobs(prob) -> tuple[int, int]:
+    """(kept, dense) tile jobs of one factor's tensor-core trailing updates."""
+    kept, dense = C.c_int64(0), C.c_int64(0)
+    prob._check(prob._lib.kkt_update_jobs(prob._h, C.byref(kept), C.byref(dense)))
+    return kept.value, dense.value
+
+
 def transfer_bytes(prob) -> tuple[int, int]:
     """(host->device, device->host) bytes copied by this handle since create."""
     h2d, d2h = C.c_int64(0), C.c_int64(0)
@@ -234,6 +242,8 @@ def load(path: str | None = None):
     L.kkt_residual_noalloc.restype = C.c_int
     L.kkt_block_factor_dense.argtypes = [vp, C.c_int32, vp, C.c_int64, C.POINTER(C.c_int32)]
     L.kkt_block_factor_dense.restype = C.c_int
+    L.kkt_update_jobs.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.kkt_update_jobs.restype = C.c_int
     L.ahlp_transfer_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.ahlp_transfer_bytes.restype = C.c_int
     L.arrowhead_lp_autotune.argtypes = [vp, vp, vp, _dp]

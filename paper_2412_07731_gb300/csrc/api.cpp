@@ -1900,6 +1900,13 @@ int kkt_factor_kernel_times(const ahlp_problem *p, double *ms3, int64_t *launche
   return AHLP_OK;
 }
 
+int kkt_update_jobs(const ahlp_problem *p, int64_t *kept, int64_t *dense) {
+  if (!p) return AHLP_ERR_INVALID_ARG;
+  if (kept) *kept = p->tc_jobs_kept;
+  if (dense) *dense = p->tc_jobs_dense;
+  return AHLP_OK;
+}
+
 int ahlp_transfer_bytes(const ahlp_problem *p, int64_t *h2d, int64_t *d2h) {
   if (!p) return AHLP_ERR_INVALID_ARG;
   if (h2d) *h2d = p->bytes_h2d;

@@ -74,3 +74,51 @@ def test_block_factor_roofline_uses_the_update_operand_peak():
             assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
         r = bench.roofline(lp, win, peaks, SimpleNamespace(fp32_update=1, ff_update=1))
         assert r["bound"] == "alu"
+
+
+def test_update_geometry_is_the_trailing_update_count():
+    """update_geometry's flops are the multiply-adds of the column-by-column
+    partial Cholesky that land right of the pivot's 64-column tile (the
+    trailing updates; the rest belongs to the diagonal tile and the panel),
+    and its entries are the trailing lower triangles summed over the steps."""
+    lp = random_block_lp(5, N=2, m_sizes=[150, 70], n_sizes=[220, 100], nnz_per_col=3, n0=2,
+                         w_density=0.5, l=[3], mg=1, global_nnz=2)
+    NB = 64
+    elems = flops = 0
+    for i, A in enumerate(lp.A):
+        m = A.shape[0]
+        a = m + lp.n0 + lp.mg + (int(lp.l[i - 1]) if i > 0 else 0) + \
+            (int(lp.l[i]) if i < lp.N - 1 else 0)
+        for c in range(m):
+            lo = NB * (c // NB + 1)   # first column right of c's tile
+            for r in range(lo, a):
+                flops += 2 * (r - lo + 1)
+        for k in range((m + NB - 1) // NB):
+            t = a - NB * (k + 1)
+            elems += t * (t + 1) // 2 if t > 0 else 0
+    assert bench.update_geometry(lp) == (elems, flops)
+
+
+def test_tile_sparse_jobs_scale_the_roofline_work():
+    """When the tile-sparse enumeration leaves tile jobs out, the update's
+    algorithmic work is scaled by the kept fraction and the roofline records
+    both job counts; with every job kept nothing changes."""
+    from types import SimpleNamespace
+    lp = random_block_lp(3, N=3, m_sizes=[70, 130, 90], n_sizes=[100, 190, 140], nnz_per_col=3,
+                         n0=2, w_density=0.5, l=[2, 3], mg=1, global_nnz=2)
+    e, f = bench.update_geometry(lp)
+    assert bench.update_geometry(lp, jobs=(10, 10)) == (e, f)
+    assert bench.update_geometry(lp, jobs=(0, 0)) == (e, f)
+    e4, f4 = bench.update_geometry(lp, jobs=(1, 4))
+    assert e4 == pytest.approx(e / 4) and f4 == pytest.approx(f / 4)
+    assert bench.tile_sparse_note((10, 10)) is None
+    assert bench.tile_sparse_note((1, 4))["jobs_kept"] == 1
+    peaks = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0,
+             "source": "test"}
+    acc = {"factors_fp32": 2, "ms_block_fp32": 4.0, "factors_ff": 0, "ms_block_ff": 0.0,
+           "factors_fp64": 0, "ms_block_fp64": 0.0}
+    opts = SimpleNamespace(fp32_update=3, ff_update=3)
+    dense = bench.roofline(lp, SimpleNamespace(acc=acc), peaks, opts)
+    sparse = bench.roofline(lp, SimpleNamespace(acc=acc), peaks, opts, (1, 4))
+    assert "tile_sparse" not in dense and sparse["tile_sparse"]["jobs_dense"] == 4
+    assert sparse["achieved"] == pytest.approx(dense["achieved"] / 4)

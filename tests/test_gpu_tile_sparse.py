@@ -52,5 +52,7 @@ def test_tile_sparse_factor_is_bitwise_dense(P, energy, prec, update):
     assert np.array_equal(P.kkt_schur_dense(probs[0]), P.kkt_schur_dense(probs[1]))
     for u, v in zip(dirs[0], dirs[1]):
         assert np.array_equal(u, v)
+    (k0, d0), (k1, d1) = (P.kkt_update_jobs(prob) for prob in probs)
+    assert k0 == d0 == d1 > 0 and 0 < k1 < d1   # the tile-sparse handle left jobs out
     for prob in probs:
         prob.close()
