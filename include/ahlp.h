@@ -470,6 +470,35 @@ int kkt_factor_kernel_times(const ahlp_problem *p, double *ms3, int64_t *launche
  * pointer may be NULL. */
 int kkt_update_jobs(const ahlp_problem *p, int64_t *kept, int64_t *dense);
 
+/*
+ * ahlp_tile_sparse_jobs -- host only (no handle, no device): the tile jobs of
+ * the tensor-core trailing updates that the option tile_sparse keeps, for
+ * nblk blocks of the batched partial Cholesky (the block factorisation and
+ * Schur-contribution steps of Alg. 2, on 64 x 64 tiles).  Step k of a block
+ * with T tiles and Tp pivot tiles updates its trailing tiles I, J > k with
+ * L_Ik L_Jk'; a job is (block, first row tile I0, column tile J, 1 if row
+ * tile I0 + 1 belongs to it), rows I0 = k+1, k+3, ... in pairs, columns J =
+ * k+1 .. min(I0+1, T-1).  A tile-level symbolic factorisation (right-looking
+ * fill) of each block's pattern leaves out the jobs whose column tile J, or
+ * both row tiles, are zero in pivot column k.
+ *
+ *   T, Tp      nblk tile counts (1 <= T[b] <= 32768, 0 <= Tp[b] <= T[b]).
+ *   nz         per block a T[b] x T[b] row-major byte matrix, nonzero where
+ *              the formed matrix has an entry in tile (I, J) (lower triangle
+ *              read), blocks concatenated; NULL: every tile nonzero.
+ *   jobs       out, 4 int32 per kept job, ordered by step, block, row pair,
+ *              column (the dense enumeration's order); may be NULL.
+ *   step_off   out, max(Tp) + 1 offsets: the jobs of step k are
+ *              [step_off[k], step_off[k+1]); may be NULL.
+ *   cap        capacity of jobs in jobs.
+ *   njobs      out, the jobs kept; ndense (may be NULL) the dense count.
+ * Returns AHLP_ERR_INVALID_ARG for bad sizes, a NULL njobs, or cap < *njobs
+ * with jobs given (then *njobs is set and nothing is written to jobs).
+ */
+int ahlp_tile_sparse_jobs(int32_t nblk, const int32_t *T, const int32_t *Tp, const uint8_t *nz,
+                          int32_t *jobs, int64_t *step_off, int64_t cap, int64_t *njobs,
+                          int64_t *ndense);
+
 /* Diagnostic: bytes this handle has copied host -> device and device -> host
  * since arrowhead_lp_create (the problem upload included; scalars read back
  * by the solvers included).  Either pointer may be NULL. */

@@ -23,6 +23,7 @@ from ._lib import (  # noqa: F401
     kkt_solve,
     kkt_stage_times,
     kkt_update_jobs,
+    tile_sparse_jobs,
     launch_count,
     transfer_bytes,
     lib_path,

@@ -86,7 +86,7 @@ EXPORTS = ["ahlp_default_options", "ahlp_status_string", "arrowhead_lp_create",
            "ahlp_launch_count", "kkt_residual_noalloc", "kkt_block_factor_dense",
            "ahlp_transfer_bytes", "arrowhead_lp_set_cb", "kkt_factor_kernel_times",
            "arrowhead_lp_recover", "arrowhead_lp_original_size", "arrowhead_lp_autotune",
-           "kkt_update_jobs"]
+           "kkt_update_jobs", "ahlp_tile_sparse_jobs"]
 
 
 def kkt_block_factor_dense(prob, block: int):
@@ -192,6 +192,36 @@ def kkt_update_jobs(prob) -> tuple[int, int]:
     return kept.value, dense.value
 
 
+def tile_sparse_jobs(T, Tp, nz=None):
+    """The tile-sparse job table (host only, no device): T, Tp per block and
+    nz (list of per-block T x T tile patterns, or None for dense blocks).
+    Returns (jobs as an int32 array of (block, I0, J, has_i1) rows, step
+    offsets, dense job count)."""
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    Tp = np.ascontiguousarray(Tp, dtype=np.int32)
+    nblk = len(T)
+    pat = None
+    if nz is not None:
+        pat = np.ascontiguousarray(np.concatenate(
+            [np.asarray(z, dtype=np.uint8).reshape(-1) for z in nz]) if nblk else
+            np.zeros(0, np.uint8))
+    lib = load()
+    kept, dense = C.c_int64(0), C.c_int64(0)
+    maxtp = int(Tp.max()) if nblk else 0
+    off = np.zeros(maxtp + 1, dtype=np.int64)
+    ptr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+    st = lib.ahlp_tile_sparse_jobs(nblk, ptr(T), ptr(Tp), ptr(pat), None, ptr(off), 0,
+                                   C.byref(kept), C.byref(dense))
+    if st != AHLP_OK:
+        raise AHLPError(st, "ahlp_tile_sparse_jobs: invalid sizes")
+    jobs = np.zeros((kept.value, 4), dtype=np.int32)
+    st = lib.ahlp_tile_sparse_jobs(nblk, ptr(T), ptr(Tp), ptr(pat), ptr(jobs), ptr(off),
+                                   kept.value, C.byref(kept), C.byref(dense))
+    if st != AHLP_OK:
+        raise AHLPError(st, "ahlp_tile_sparse_jobs failed")
+    return jobs, off, dense.value
+
+
 def transfer_bytes(prob) -> tuple[int, int]:
     """(host->device, device->host) bytes copied by this handle since create."""
     h2d, d2h = C.c_int64(0), C.c_int64(0)
@@ -242,6 +272,9 @@ def load(path: str | None = None):
     L.kkt_residual_noalloc.restype = C.c_int
     L.kkt_block_factor_dense.argtypes = [vp, C.c_int32, vp, C.c_int64, C.POINTER(C.c_int32)]
     L.kkt_block_factor_dense.restype = C.c_int
+    L.ahlp_tile_sparse_jobs.argtypes = [C.c_int32, vp, vp, vp, vp, vp, C.c_int64,
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.ahlp_tile_sparse_jobs.restype = C.c_int
     L.kkt_update_jobs.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.kkt_update_jobs.restype = C.c_int
     L.ahlp_transfer_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]

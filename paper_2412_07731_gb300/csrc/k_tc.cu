@@ -33,6 +33,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <new>
 
 #include "ahlp_internal.h"
 
@@ -1055,6 +1056,67 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// Tile-sparse jobs of the tensor-core trailing updates (host only).  A
+// tile-level symbolic factorisation of each block's augmented matrix: tile
+// (I, J) of L is nonzero if the formed matrix has entries there or if some
+// pivot step k < J has nonzero tiles (I, k) and (J, k) (right-looking fill).
+// The update of step k adds L_Ik L_Jk' to the tile pair's rows and column J;
+// a job whose two row tiles are both zero in column k, or whose column tile J
+// is, adds exact zeros and is left out.  The kept jobs stay in the dense
+// enumeration's order (step, block, row pair, column), so the CTAs that run
+// them and the factor are the same.  nz[b]: block b's T[b] x T[b] row-major
+// tile pattern (lower triangle read), or nullptr for a dense block.  Fills
+// tab and off (maxTp + 1 step offsets into tab); returns the jobs kept.
+long long tile_sparse_jobs(int nblk, const int *T, const int *Tp,
+                           const unsigned char *const *nz, int maxTp, std::vector<int4> &tab,
+                           std::vector<long long> &off) {
+  std::vector<std::vector<unsigned char>> L(nblk);
+  for (int b = 0; b < nblk; ++b) {
+    const int Tb = T[b];
+    if (!nz[b]) {
+      L[b].assign((size_t)Tb * Tb, 1);
+      continue;
+    }
+    L[b].assign(nz[b], nz[b] + (size_t)Tb * Tb);
+    bool dense = true;
+    for (int I = 0; I < Tb && dense; ++I)
+      for (int J = 0; J <= I; ++J)
+        if (!L[b][(size_t)I * Tb + J]) {
+          dense = false;
+          break;
+        }
+    if (dense) continue;
+    std::vector<int> rows;
+    for (int k = 0; k < Tp[b]; ++k) {
+      rows.clear();
+      for (int I = k + 1; I < Tb; ++I)
+        if (L[b][(size_t)I * Tb + k]) rows.push_back(I);
+      for (size_t x = 0; x < rows.size(); ++x)
+        for (size_t y = 0; y <= x; ++y) L[b][(size_t)rows[x] * Tb + rows[y]] = 1;
+    }
+  }
+  tab.clear();
+  off.assign((size_t)maxTp + 1, 0);
+  for (int k = 0; k < maxTp; ++k) {
+    off[k] = (long long)tab.size();
+    for (int b = 0; b < nblk; ++b) {
+      if (k >= Tp[b]) continue;
+      const int Tb = T[b], t = Tb - k - 1;
+      const unsigned char *Lb = L[b].data();
+      for (int R = 0; 2 * R < t; ++R) {
+        const int I0 = k + 1 + 2 * R;
+        const bool has_i1 = 2 * R + 1 < t;
+        if (!Lb[(size_t)I0 * Tb + k] && !(has_i1 && Lb[(size_t)(I0 + 1) * Tb + k])) continue;
+        const int jend = k + std::min(2 * R + 2, t);
+        for (int J = k + 1; J <= jend; ++J)
+          if (Lb[(size_t)J * Tb + k]) tab.push_back(make_int4(b, I0, J, has_i1 ? 1 : 0));
+      }
+    }
+  }
+  off[maxTp] = (long long)tab.size();
+  return (long long)tab.size();
+}
+
 // job offsets per step, over the blocks (shared by both tensor-core updates)
 void jobs_setup(ahlp_problem *p) {
   if (p->tc_joff) return;
@@ -1076,63 +1138,18 @@ void jobs_setup(ahlp_problem *p) {
   p->tc_joff = static_cast<int *>(dupload_bytes(p, joff.data(), joff.size() * sizeof(int)));
   p->tc_jobs_kept = p->tc_jobs_dense;
   if (!p->opt.tile_sparse || (int)p->tile_nz.size() != N) return;
-  // Tile-sparse jobs.  A tile-level symbolic factorisation of each block's
-  // augmented matrix: tile (I, J) of L is nonzero if the formed matrix has
-  // entries there or if some pivot step k < J has nonzero tiles (I, k) and
-  // (J, k) (right-looking fill).  The update of step k adds L_Ik L_Jk' to the
-  // tile pair's rows and column J; a job whose two row tiles are both zero in
-  // column k, or whose column tile J is, adds exact zeros and is left out.
-  // The kept jobs stay in the dense enumeration's order (block, row pair,
-  // column), so the CTAs that run them and the factor are the same.
-  std::vector<std::vector<unsigned char>> L(N);
+  std::vector<int> T(N), Tp(N);
+  std::vector<const unsigned char *> nz(N);
   for (int b = 0; b < N; ++b) {
-    const BlkInfo &bi = p->h_blk[b];
-    const int T = bi.T;
-    L[b] = p->tile_nz[b];
-    if ((int)L[b].size() != T * T) {   // no pattern: every tile counts as nonzero
-      L[b].assign((size_t)T * T, 1);
-      continue;
-    }
-    bool dense = true;
-    for (int I = 0; I < T && dense; ++I)
-      for (int J = 0; J <= I; ++J)
-        if (!L[b][(size_t)I * T + J]) {
-          dense = false;
-          break;
-        }
-    if (dense) continue;
-    std::vector<int> rows;
-    for (int k = 0; k < bi.Tp; ++k) {
-      rows.clear();
-      for (int I = k + 1; I < T; ++I)
-        if (L[b][(size_t)I * T + k]) rows.push_back(I);
-      for (size_t x = 0; x < rows.size(); ++x)
-        for (size_t y = 0; y <= x; ++y) L[b][(size_t)rows[x] * T + rows[y]] = 1;
-    }
+    T[b] = p->h_blk[b].T;
+    Tp[b] = p->h_blk[b].Tp;
+    // no pattern: every tile counts as nonzero
+    nz[b] = p->tile_nz[b].size() == (size_t)T[b] * T[b] ? p->tile_nz[b].data() : nullptr;
   }
   std::vector<int4> tab;
-  p->tc_jtab_off.assign(maxTp + 1, 0);
-  long long kept = 0;
-  for (int k = 0; k < maxTp; ++k) {
-    p->tc_jtab_off[k] = (long long)tab.size();
-    for (int b = 0; b < N; ++b) {
-      const BlkInfo &bi = p->h_blk[b];
-      if (k >= bi.Tp) continue;
-      const int T = bi.T, t = T - k - 1;
-      const unsigned char *Lb = L[b].data();
-      for (int R = 0; 2 * R < t; ++R) {
-        const int I0 = k + 1 + 2 * R;
-        const bool has_i1 = 2 * R + 1 < t;
-        if (!Lb[(size_t)I0 * T + k] && !(has_i1 && Lb[(size_t)(I0 + 1) * T + k])) continue;
-        const int jend = k + std::min(2 * R + 2, t);
-        for (int J = k + 1; J <= jend; ++J)
-          if (Lb[(size_t)J * T + k]) tab.push_back(make_int4(b, I0, J, has_i1 ? 1 : 0));
-      }
-    }
-    p->tc_jobs[k] = (long long)tab.size() - p->tc_jtab_off[k];
-    kept += p->tc_jobs[k];
-  }
-  p->tc_jtab_off[maxTp] = (long long)tab.size();
+  const long long kept =
+      tile_sparse_jobs(N, T.data(), Tp.data(), nz.data(), maxTp, tab, p->tc_jtab_off);
+  for (int k = 0; k < maxTp; ++k) p->tc_jobs[k] = p->tc_jtab_off[k + 1] - p->tc_jtab_off[k];
   p->tc_jobs_kept = kept;
   if (p->opt.verbose)
     printf("       tile-sparse trailing updates: %lld of %lld tile jobs kept\n", kept,
@@ -1274,3 +1291,44 @@ cudaError_t launch_update_oz(ahlp_problem *p, int k, cudaStream_t s) {
 }
 
 }  // namespace ahlp
+
+extern "C" int ahlp_tile_sparse_jobs(int32_t nblk, const int32_t *T, const int32_t *Tp,
+                                     const uint8_t *nz, int32_t *jobs, int64_t *step_off,
+                                     int64_t cap, int64_t *njobs, int64_t *ndense) {
+  using namespace ahlp;
+  if (nblk < 0 || (nblk > 0 && (!T || !Tp)) || !njobs) return AHLP_ERR_INVALID_ARG;
+  int maxTp = 0;
+  long long dense = 0;
+  std::vector<const unsigned char *> pat(nblk, nullptr);
+  size_t at = 0;
+  for (int b = 0; b < nblk; ++b) {
+    if (T[b] < 1 || T[b] > 32768 || Tp[b] < 0 || Tp[b] > T[b]) return AHLP_ERR_INVALID_ARG;
+    maxTp = std::max(maxTp, (int)Tp[b]);
+    for (int k = 0; k < Tp[b]; ++k) dense += tc_jobs_of(T[b] - k - 1);
+    if (nz) pat[b] = nz + at;
+    at += (size_t)T[b] * T[b];
+  }
+  std::vector<int> Ti(T, T + nblk), Tpi(Tp, Tp + nblk);
+  std::vector<int4> tab;
+  std::vector<long long> off;
+  long long kept = 0;
+  try {
+    kept = tile_sparse_jobs(nblk, Ti.data(), Tpi.data(), pat.data(), maxTp, tab, off);
+  } catch (const std::bad_alloc &) {
+    return AHLP_ERR_OOM;
+  }
+  *njobs = kept;
+  if (ndense) *ndense = dense;
+  if (step_off)
+    for (int k = 0; k <= maxTp; ++k) step_off[k] = off[k];
+  if (jobs) {
+    if (cap < kept) return AHLP_ERR_INVALID_ARG;
+    for (long long j = 0; j < kept; ++j) {
+      jobs[4 * j + 0] = tab[j].x;
+      jobs[4 * j + 1] = tab[j].y;
+      jobs[4 * j + 2] = tab[j].z;
+      jobs[4 * j + 3] = tab[j].w;
+    }
+  }
+  return AHLP_OK;
+}
