@@ -300,6 +300,23 @@ _COUNTERS = ("ms_factor", "ms_solve", "refine_steps", "factors_fp32", "factors_f
              "factors_fp64", "ms_block_fp32", "ms_block_ff", "ms_block_fp64", "correctors")
 
 
+def max_over_ranks(dist, x, device=None):
+    """The maximum of the float x over the ranks of the process group (x
+    itself without one): the job's time is its slowest rank's."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, iterations, ms):
+    """Whole-job IPM iterations/s of `world` replicas that each ran
+    `iterations` iterations, the slowest in `ms` milliseconds."""
+    return world * iterations / (ms / 1e3)
+
+
 class IterWindow:
     """Times exactly `steps` IPM iterations after `warmup` completed ones,
     across as many solves as it takes.  The library calls back at the start
@@ -381,12 +398,7 @@ class IterWindow:
         finally:
             L.set_options(prob, saved)
         self.clocks = self.sampler.stop()
-        ms = self.e0.elapsed_time(self.e1)
-        if self.dist:
-            t = self.torch.tensor([ms], device=out[0].device)
-            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(self.dist, self.e0.elapsed_time(self.e1), out[0].device)
 
 
 # ---------------------------------------------------------------------------
@@ -803,7 +815,7 @@ def run_ours(args):
         return prob, win, ms, full
 
     prob, win, ms, full = arm(headline, args.warmup, args.steps)
-    value = world * args.steps / (ms / 1e3)
+    value = replica_value(world, args.steps, ms)
     summ = window_summary(win, ms, args.steps)
     factor_roof = roofline(lp, win, peaks, prob.options, P.kkt_update_jobs(prob))
     roof = None
@@ -825,7 +837,7 @@ def run_ours(args):
         ow = min(args.warmup, 2)
         oprob, owin, oms, ofull = arm(other, ow, osteps)
         other_line = dict({"precision": "FP64" if other == P.PREC_FP64 else "mixed",
-                           "value": world * osteps / (oms / 1e3), "unit": "IPM iters/s",
+                           "value": replica_value(world, osteps, oms), "unit": "IPM iters/s",
                            "steps": osteps, "warmup": ow, "clocks": owin.clocks,
                            "solve": ofull}, **window_summary(owin, oms, osteps))
         oprob.close()
@@ -877,12 +889,8 @@ def run_ours(args):
         h2d, d2h = P.transfer_bytes(q)
         q.close()
         torch.cuda.synchronize(dev)
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * r["iterations"] / el, "unit": "IPM iters/s",
+        el = max_over_ranks(dist, time.perf_counter() - t0, dev)
+        e2e = {"value": replica_value(world, r["iterations"], el * 1e3), "unit": "IPM iters/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "step": f"create from the host LP (upload + symbolic analysis) + one complete "
                        f"solve ({r['iterations']} iterations) + x, y, z to pinned host memory "
