@@ -122,3 +122,48 @@ def test_tile_sparse_jobs_scale_the_roofline_work():
     sparse = bench.roofline(lp, SimpleNamespace(acc=acc), peaks, opts, (1, 4))
     assert "tile_sparse" not in dense and sparse["tile_sparse"]["jobs_dense"] == 4
     assert sparse["achieved"] == pytest.approx(dense["achieved"] / 4)
+
+
+def test_kernel_roofline_from_recorded_kernel_times():
+    """The headline roofline of the trailing-update kernel, from the kernel
+    times a factor records (stand-in handle): algorithmic bytes over the
+    update's time against the copy bandwidth, no traffic figure for kernel
+    code without a capture, and the kept fraction applied when the
+    tile-sparse enumeration left jobs out."""
+    from types import SimpleNamespace
+    import paper_2412_07731_gb300 as P
+    lp = random_block_lp(3, N=3, m_sizes=[70, 130, 90], n_sizes=[100, 190, 140], nnz_per_col=3,
+                         n0=2, w_density=0.5, l=[2, 3], mg=1, global_nnz=2)
+    peaks = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0,
+             "source": "test"}
+
+    class Handle:
+        def __init__(self, jobs):
+            self.jobs = jobs
+            self.PREC_MIXED, self.PREC_FP64 = P.PREC_MIXED, P.PREC_FP64
+
+        def set_options(self, prob, o):
+            prob.options = o
+
+        def kkt_factor(self, prob, x, z):
+            pass
+
+        def kkt_factor_kernel_times(self, prob):
+            return {"update_ms": 2.0, "update_launches": 10, "diag_ms": 0.1, "panel_ms": 0.2}
+
+        def kkt_update_jobs(self, prob):
+            return self.jobs
+
+    elems, _ = bench.update_geometry(lp)
+    for prec, word, key in (("FP32", 4, ("FP32", 3)), ("float-float", 8, ("float-float", 3))):
+        prob = SimpleNamespace(options=P.default_options(fp32_update=3, ff_update=3))
+        r = bench.kernel_roofline(Handle((40, 40)), prob, lp, None, None, prec, peaks)
+        gbs = 2 * word * elems / 2e-3 / 1e9
+        assert r["bound"] == "hbm" and r["achieved"] == pytest.approx(gbs)
+        assert r["frac"] == pytest.approx(gbs / 6800.0)
+        assert r["traffic"] is None and "tile_sparse" not in r
+        last = bench.UPDATE_TRAFFIC_AT_LAST_CAPTURE[key]
+        assert r["traffic_at_last_capture"]["bytes"] == pytest.approx(
+            last * 2 * word * elems / 10)
+        s = bench.kernel_roofline(Handle((10, 40)), prob, lp, None, None, prec, peaks)
+        assert s["achieved"] == pytest.approx(gbs / 4) and s["tile_sparse"]["jobs_kept"] == 10
