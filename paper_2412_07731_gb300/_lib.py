@@ -143,7 +143,8 @@ def set_cb(prob, c=None, b=None):
 def autotune(prob, x=None, z=None):
     """Choose the faster trailing-update kernels (FP32 and float-float block
     factors) for this handle at (x, z) (default x = z = 1); the choice goes
-    into the handle's options.  Returns the four block-factor times (ms)."""
+    into the handle's options.  Returns the six candidates' block-factor times
+    (ms) and the chosen fp32_update and ff_update."""
     keep = _Keep()
     prob._stream_for(x, z)
     ms = (C.c_double * 6)()
