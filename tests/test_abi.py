@@ -171,3 +171,47 @@ def test_validation_reports_the_first_failing_block():
     for _ in range(5):
         st, msg = _create_status(lp)
         assert st == -1 and "block 3" in msg and "non-finite" in msg, msg
+
+
+def _general_status(mutate):
+    from instances import general_block_lp
+    lp = general_block_lp(3, N=3, m=12, n=18)
+    mutate(lp)
+    return _create_status(lp)
+
+
+def test_full_statement_validation():
+    """The full statement is checked and reduced on the host before any device
+    work: inconsistent bounds and inequality rows are rejected by name, and a
+    valid LP in the full statement gets as far as the device (no GPU here)."""
+    torch = pytest.importorskip("torch")
+
+    def lo_above_hi(lp):
+        lp.lb[1] = lp.lb[1].copy()
+        lp.ub[1] = lp.ub[1].copy()
+        lp.lb[1][2], lp.ub[1][2] = 1.0, 0.5
+
+    def nan_bound(lp):
+        lp.ub0 = lp.ub0.copy()
+        lp.ub0[0] = np.nan
+
+    def row_lo_above_hi(lp):
+        lp.dlo[0] = lp.dlo[0].copy()
+        lp.dhi[0] = lp.dhi[0].copy()
+        lp.dlo[0][1], lp.dhi[0][1] = 2.0, -2.0
+
+    def infinite_lower_row(lp):
+        lp.gglo = np.full_like(lp.gglo, np.inf)
+
+    def nan_in_D(lp):
+        lp.D[2] = lp.D[2].copy()
+        lp.D[2].data[0] = np.nan
+
+    for mutate, words in ((lo_above_hi, "bounds"), (nan_bound, "bounds"),
+                          (row_lo_above_hi, "bounds"), (infinite_lower_row, "bounds"),
+                          (nan_in_D, "NaN")):
+        st, msg = _general_status(mutate)
+        assert st == -1 and words in msg, (mutate.__name__, st, msg)
+    if not torch.cuda.is_available():
+        st, msg = _general_status(lambda lp: None)
+        assert st == -8, msg
