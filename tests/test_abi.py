@@ -215,3 +215,14 @@ def test_full_statement_validation():
     if not torch.cuda.is_available():
         st, msg = _general_status(lambda lp: None)
         assert st == -8, msg
+
+
+@pytest.mark.parametrize("bad", [dict(tile_sparse=2), dict(tile_sparse=-1), dict(pivot_mode=2),
+                                 dict(fp32_update=4), dict(ff_update=-1), dict(schur_chain=2),
+                                 dict(max_correctors=9), dict(eta=1.0), dict(tol=0.0),
+                                 dict(fp32_cond_max=0.5), dict(profile_kernels=3),
+                                 dict(correctors_by_cost=2)])
+def test_option_ranges_are_checked(bad):
+    L = _lib()
+    st, msg = _create_status(_small_lp(), options=L.default_options(**bad))
+    assert st == -1 and "option" in msg, (bad, st, msg)
